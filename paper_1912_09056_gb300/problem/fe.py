@@ -1,0 +1,128 @@
+"""Trilinear hex8 linear-elasticity assembly on structured bricks (input generation).
+
+The paper's systems come from a finite element discretisation of each solid body
+(Sec. 2.2: nodal displacement DOFs, first-order Lagrange elements).  This module
+produces the stiffness block K of those systems for the synthetic workloads:
+isotropic linear elasticity, 2x2x2 Gauss quadrature, assembled into a node-blocked
+(3x3) sparse matrix.  It holds none of the multigrid method's arithmetic.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Local node order of the hex8 element in natural coordinates.
+HEX8_XI = np.array(
+    [[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+     [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], dtype=np.float64)
+
+_G = 1.0 / np.sqrt(3.0)
+GAUSS_2x2x2 = np.array([[a, b, c] for c in (-_G, _G) for b in (-_G, _G) for a in (-_G, _G)])
+
+
+def hex8_dN_dxi(p: np.ndarray) -> np.ndarray:
+    """Derivatives of the 8 trilinear shape functions at natural point p -> (8, 3)."""
+    t = 1.0 + HEX8_XI * p[None, :]                      # (8,3) factors (1 + xi_a xi)
+    d = np.empty((8, 3))
+    d[:, 0] = 0.125 * HEX8_XI[:, 0] * t[:, 1] * t[:, 2]
+    d[:, 1] = 0.125 * HEX8_XI[:, 1] * t[:, 0] * t[:, 2]
+    d[:, 2] = 0.125 * HEX8_XI[:, 2] * t[:, 0] * t[:, 1]
+    return d
+
+
+def elasticity_matrix(E: float, nu: float) -> np.ndarray:
+    """Isotropic Hooke matrix, Voigt order (xx, yy, zz, xy, yz, zx), engineering shear."""
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    C = np.zeros((6, 6))
+    C[:3, :3] = lam
+    C[0, 0] = C[1, 1] = C[2, 2] = lam + 2.0 * mu
+    C[3, 3] = C[4, 4] = C[5, 5] = mu
+    return C
+
+
+def hex8_stiffness(X: np.ndarray, E: np.ndarray, nu: float) -> np.ndarray:
+    """Element stiffness matrices for elements with nodal coordinates X (ne, 8, 3).
+
+    E is the per-element Young's modulus (ne,), nu the Poisson ratio of the body.
+    Returns (ne, 24, 24) with DOF order (node, component).
+    """
+    ne = X.shape[0]
+    C1 = elasticity_matrix(1.0, nu)
+    Ke = np.zeros((ne, 24, 24))
+    B = np.zeros((ne, 6, 24))
+    for p in GAUSS_2x2x2:
+        dNdxi = hex8_dN_dxi(p)                           # (8,3)
+        J = np.einsum("na,enb->eab", dNdxi, X)           # J_ab = d x_b / d xi_a
+        detJ = np.linalg.det(J)
+        if np.any(detJ <= 0):
+            raise ValueError("inverted hex8 element")
+        Jinv = np.linalg.inv(J)
+        dNdx = np.einsum("eab,nb->ena", Jinv, dNdxi)     # (ne,8,3)
+        B[:] = 0.0
+        B[:, 0, 0::3] = dNdx[:, :, 0]
+        B[:, 1, 1::3] = dNdx[:, :, 1]
+        B[:, 2, 2::3] = dNdx[:, :, 2]
+        B[:, 3, 0::3] = dNdx[:, :, 1]
+        B[:, 3, 1::3] = dNdx[:, :, 0]
+        B[:, 4, 1::3] = dNdx[:, :, 2]
+        B[:, 4, 2::3] = dNdx[:, :, 1]
+        B[:, 5, 0::3] = dNdx[:, :, 2]
+        B[:, 5, 2::3] = dNdx[:, :, 0]
+        CB = np.einsum("ij,ejb->eib", C1, B)
+        Ke += np.matmul(B.transpose(0, 2, 1), CB) * (detJ * E)[:, None, None]
+    return Ke
+
+
+def brick_mesh(nx: int, ny: int, nz: int, lo, hi):
+    """Structured brick [lo, hi] with nx*ny*nz hex8 elements.
+
+    Returns (coords (nn,3), conn (ne,8), ijk (nn,3)).  Node id = i + (nx+1)(j + (ny+1)k).
+    """
+    xs = np.linspace(lo[0], hi[0], nx + 1)
+    ys = np.linspace(lo[1], hi[1], ny + 1)
+    zs = np.linspace(lo[2], hi[2], nz + 1)
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    i = i.ravel(); j = j.ravel(); k = k.ravel()
+    coords = np.stack([xs[i], ys[j], zs[k]], axis=1)
+    ijk = np.stack([i, j, k], axis=1)
+    ek, ej, ei = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ei = ei.ravel(); ej = ej.ravel(); ek = ek.ravel()
+
+    def nid(a, b, c):
+        return a + (nx + 1) * (b + (ny + 1) * c)
+    conn = np.stack([nid(ei, ej, ek), nid(ei + 1, ej, ek), nid(ei + 1, ej + 1, ek), nid(ei, ej + 1, ek),
+                     nid(ei, ej, ek + 1), nid(ei + 1, ej, ek + 1), nid(ei + 1, ej + 1, ek + 1),
+                     nid(ei, ej + 1, ek + 1)], axis=1).astype(np.int64)
+    return coords, conn, ijk
+
+
+def block_pattern(conn: np.ndarray, n_nodes: int):
+    """Node-graph CSR (sorted columns, diagonal included) of the elements' couplings."""
+    ne = conn.shape[0]
+    r = np.repeat(conn, 8, axis=1).ravel()
+    c = np.tile(conn, (1, 8)).ravel()
+    keys = np.unique(r * n_nodes + c)
+    rows = keys // n_nodes
+    cols = keys % n_nodes
+    rowptr = np.zeros(n_nodes + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    del ne
+    return rowptr, cols, keys
+
+
+def assemble_bsr(coords, conn, E_elem, nu, n_nodes, chunk=65536):
+    """Assemble K as node-blocked CSR: (rowptr, col, val (nnzb,3,3))."""
+    rowptr, cols, keys = block_pattern(conn, n_nodes)
+    val = np.zeros((keys.size, 3, 3))
+    for s in range(0, conn.shape[0], chunk):
+        cc = conn[s:s + chunk]
+        Ke = hex8_stiffness(coords[cc], E_elem[s:s + chunk], nu)
+        blk = Ke.reshape(-1, 8, 3, 8, 3).transpose(0, 1, 3, 2, 4)      # (ne,8,8,3,3)
+        r = np.repeat(cc, 8, axis=1).ravel()
+        c = np.tile(cc, (1, 8)).ravel()
+        pos = np.searchsorted(keys, r * n_nodes + c)
+        flat = blk.reshape(-1, 9)
+        for q in range(9):
+            val.reshape(-1, 9)[:, q] += np.bincount(pos, weights=flat[:, q], minlength=keys.size)
+    return rowptr, cols, val

@@ -1,0 +1,267 @@
+"""Pins of the AMG oracle against closed forms, invariants, special cases and brute force."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle.aggregate import (ROOT, aggregate_nodes, aggregation_graph, fmix32, lagmult_aggregation,
+                              mis2_roots, priorities)
+from oracle.amg import Options, d_rows, setup
+from oracle.krylov import fgmres
+from oracle.saddle import block_diag3, build_saddle, pattern
+from oracle.smoother import atilde_diag, cheap_simple_sweep
+from oracle.transfer import galerkin, lambda_max, smoothed_prolongator, tentative_lagmult, tentative_prolongator
+
+
+def _bfs_dist(G, src, cutoff=3):
+    dist = {src: 0}
+    frontier = [src]
+    for d in range(1, cutoff + 1):
+        nxt = []
+        for i in frontier:
+            for j in G.indices[G.indptr[i]:G.indptr[i + 1]]:
+                if j not in dist:
+                    dist[j] = d
+                    nxt.append(j)
+        frontier = nxt
+    return dist
+
+
+def _random_graph(n, deg, seed):
+    rng = np.random.default_rng(seed)
+    r = rng.integers(0, n, size=n * deg)
+    c = rng.integers(0, n, size=n * deg)
+    keep = r != c
+    A = sp.csr_matrix((np.ones(keep.sum()), (r[keep], c[keep])), shape=(n, n))
+    A = ((A + A.T) > 0).astype(float).tocsr()
+    A.sort_indices()
+    return A
+
+
+def test_fmix32_is_a_bijection_sample():
+    x = np.arange(1 << 20, dtype=np.uint64)
+    h = fmix32(x)
+    assert np.unique(h).size == x.size
+    assert int(fmix32(np.array([0]))[0]) == 0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 7])
+def test_mis2_equals_sequential_greedy(seed):
+    """Brute force: the parallel rule picks exactly the greedy MIS-2 in decreasing priority order."""
+    for gseed in range(3):
+        G = _random_graph(60, 2, gseed)
+        state, _ = mis2_roots(G, seed)
+        key = priorities(G.shape[0], seed)
+        chosen = []
+        for i in np.argsort(-key.astype(np.float64), kind="stable"):
+            i = int(i)
+            d = _bfs_dist(G, i, 2)
+            if not any(r in d for r in chosen):
+                chosen.append(i)
+        assert sorted(chosen) == sorted(np.nonzero(state == ROOT)[0].tolist())
+
+
+def test_aggregation_invariants(cfg0):
+    S = build_saddle(cfg0)
+    G = aggregation_graph(S.K.pat, cfg0.body_id)
+    # no inter-body edge survives
+    rows = np.repeat(np.arange(G.shape[0]), np.diff(G.indptr))
+    assert np.all(cfg0.body_id[rows] == cfg0.body_id[G.indices])
+    assert np.all(rows != G.indices)
+    agg, roots = aggregate_nodes(G, 0x5EED)
+    assert agg.min() == 0 and agg.max() == roots.size - 1
+    assert np.all(agg[roots] == np.arange(roots.size))
+    # roots pairwise at distance >= 3, every node within distance 2 of a root
+    rootset = set(roots.tolist())
+    covered = set()
+    for r in roots:
+        d = _bfs_dist(G, int(r), 2)
+        assert not (set(d) - {int(r)}) & rootset
+        covered |= set(d)
+    assert covered == set(range(G.shape[0]))
+    # aggregates never cross the interface; phase-2 members are root neighbours
+    for a, r in enumerate(roots):
+        members = np.nonzero(agg == a)[0]
+        assert np.all(cfg0.body_id[members] == cfg0.body_id[r])
+        nb = set(G.indices[G.indptr[r]:G.indptr[r + 1]].tolist())
+        assert nb <= set(members.tolist())
+
+
+def test_lagmult_aggregation_follows_displacement_aggregates(cfg0):
+    """Algorithm 1: multiplier aggregates are the slave aggregates' images, numbered in DOF order."""
+    h = setup(cfg0, Options(levels_max=3, coarse_max_rows=0))
+    L0 = h.levels[0]
+    agg, lagg = L0.agg, L0.lagg
+    s_agg = agg[cfg0.slave_node]
+    # same displacement aggregate <=> same multiplier aggregate
+    for j in range(cfg0.n_s):
+        for k in range(cfg0.n_s):
+            assert (s_agg[j] == s_agg[k]) == (lagg[j] == lagg[k])
+    # one multiplier aggregate per slave-side displacement aggregate touching the interface
+    assert L0.n_lagg == np.unique(s_agg).size
+    # numbering: first appearance when scanning slave DOFs in increasing order
+    order = []
+    for j in np.argsort(cfg0.slave_node):
+        if s_agg[j] not in order:
+            order.append(s_agg[j])
+    for j in range(cfg0.n_s):
+        assert lagg[j] == order.index(s_agg[j])
+    # non-diagonal D: a multiplier coupled to two aggregates keeps its first one
+    lg, d, cnt = lagmult_aggregation(np.array([0, 1, 1]), [(0, [0, 3]), (3, [0]), (6, [3, 6])], 3)
+    assert lg == {0: 0, 1: 0, 2: 1} and d == {0: 0, 1: 1} and cnt == 2
+
+
+def test_tentative_prolongator_reproduces_nullspace(cfg0):
+    S = build_saddle(cfg0)
+    G = aggregation_graph(S.K.pat, cfg0.body_id)
+    agg, roots = aggregate_nodes(G, 3)
+    Ph, Bc = tentative_prolongator(agg, roots.size, cfg0.nullspace, 3)
+    assert np.abs(Ph.val @ Bc - cfg0.nullspace).max() <= 1e-13 * np.abs(cfg0.nullspace).max()
+    PtP = (Ph.val.T @ Ph.val).toarray()
+    assert np.abs(PtP - np.eye(PtP.shape[0])).max() <= 1e-13
+    for a in range(roots.size):
+        R = Bc[6 * a:6 * a + 6]
+        assert np.all(np.diag(R) > 0) and np.abs(np.tril(R, -1)).max() == 0.0
+
+
+def _free_floating_brick():
+    from paper_1912_09056_gb300.problem import rigid_body_modes
+    from paper_1912_09056_gb300.problem.fe import assemble_bsr, brick_mesh
+    from oracle.saddle import BlockMat, bsr_to_scalar
+    X, conn, _ = brick_mesh(5, 4, 4, (0, 0, 0), (1.0, 0.8, 0.9))
+    rng = np.random.default_rng(5)
+    X = X + rng.uniform(-0.02, 0.02, X.shape)
+    rp, col, val = assemble_bsr(X, conn, np.exp(rng.normal(0, 0.3, conn.shape[0])), 0.3, X.shape[0])
+    n = X.shape[0]
+    K = BlockMat(bsr_to_scalar(rp, col, val, n, n), pattern(np.repeat(np.arange(n), np.diff(rp)), col, (n, n)), 3, 3)
+    return K, rigid_body_modes(X)
+
+
+@pytest.mark.parametrize("smoothed", [False, True])
+def test_galerkin_keeps_rigid_modes_of_a_floating_body(smoothed):
+    """K B = 0 and P-hat B_c = B imply K_c B_c = 0, for PA and for SA transfers."""
+    K, B = _free_floating_brick()
+    assert np.abs(K.val @ B).max() <= 1e-12 * abs(K.val).max()
+    G = aggregation_graph(K.pat, np.zeros(K.pat.shape[0], dtype=np.int64))
+    agg, roots = aggregate_nodes(G, 11)
+    Ph, Bc = tentative_prolongator(agg, roots.size, B, 3)
+    P = smoothed_prolongator(K, Ph, (4 / 3) / lambda_max(K.val)) if smoothed else Ph
+    Z = np.zeros((0, 3, 3))
+    from oracle.saddle import BlockMat
+    E1 = BlockMat(sp.csr_matrix((K.val.shape[0], 0)), sp.csr_matrix((K.pat.shape[0], 0)), 3, 3)
+    E2 = BlockMat(sp.csr_matrix((0, K.val.shape[0])), sp.csr_matrix((0, K.pat.shape[0])), 3, 3)
+    Pl = BlockMat(sp.csr_matrix((0, 0)), sp.csr_matrix((0, 0)), 3, 3)
+    Kc, _, _, _ = galerkin(K, E1, E2, Z, P, Pl, np.zeros(0, dtype=np.int64), 0)
+    assert np.abs(Kc.val @ Bc).max() <= 1e-11 * abs(Kc.val).max()
+    if smoothed:
+        assert np.abs(P.val @ Bc - B).max() <= 1e-11 * np.abs(B).max()
+
+
+def test_galerkin_patterns_match_dense_boolean_products(cfg0):
+    h = setup(cfg0, Options(levels_max=3, coarse_max_rows=0, transfer=1))
+    L0, L1 = h.levels[0], h.levels[1]
+
+    def dpat(M):
+        return (M.pat.toarray() > 0).astype(int)
+    P = dpat(L0.P); K = dpat(L0.K); B1 = dpat(L0.B1); B2 = dpat(L0.B2); Pl = dpat(L0.Pl)
+    assert np.array_equal(dpat(L1.K), ((P.T @ K @ P) > 0).astype(int))
+    assert np.array_equal(dpat(L1.B1), ((P.T @ B1 @ Pl) > 0).astype(int))
+    assert np.array_equal(dpat(L1.B2), ((Pl.T @ B2 @ P) > 0).astype(int))
+    # values agree with the dense triple product of the full block transfers
+    A0 = L0.A().toarray()
+    Pf = sla.block_diag(L0.P.val.toarray(), L0.Pl.val.toarray())
+    assert np.abs(Pf.T @ A0 @ Pf - L1.A().toarray()).max() <= 1e-12 * np.abs(A0).max()
+
+
+def test_lambda_max_bounds():
+    """Generalised Rayleigh quotient: below lambda_max(D^-1 K), and close to it after 20 steps."""
+    K, _ = _free_floating_brick()
+    Kd = K.val.toarray()
+    d = np.diag(Kd)
+    ev = sla.eigh(Kd, np.diag(d), eigvals_only=True)
+    est = lambda_max(K.val)
+    assert est <= ev[-1] * (1 + 1e-12)
+    assert est >= 0.9 * ev[-1]
+
+
+def test_simple_with_exact_schur_satisfies_constraints(cfg0):
+    """Eq. ch6_errormatsimple_special: exact S_hat and alpha = 1 zero the constraint residual."""
+    S = build_saddle(cfg0)
+    K, B1, B2 = S.K.val, S.B1.val, S.B2.val
+    Zf = block_diag3(S.Z)
+    at_inv = 1.0 / atilde_diag(K, False)
+    Sh = (Zf + B2 @ sp.diags(at_inv) @ B1).toarray()
+    rng = np.random.default_rng(0)
+    u = rng.normal(size=K.shape[0]); lam = rng.normal(size=Zf.shape[0])
+    f = rng.normal(size=K.shape[0]); g = rng.normal(size=Zf.shape[0])
+    u2, lam2 = cheap_simple_sweep(K, B1, B2, Zf, u, lam, f, g, 1.0 / K.diagonal(), 0.5, 2, at_inv,
+                                  lambda r: np.linalg.solve(Sh, r), 1.0)
+    res = g - B2 @ u2 + Zf @ lam2
+    assert np.abs(res).max() <= 1e-12 * np.abs(g).max()
+    # with damping alpha < 1 the residual is only scaled by (1 - alpha)
+    u3, lam3 = cheap_simple_sweep(K, B1, B2, Zf, u, lam, f, g, 1.0 / K.diagonal(), 0.5, 2, at_inv,
+                                  lambda r: np.linalg.solve(Sh, r), 0.8)
+    uh = u
+    for _ in range(2):
+        uh = uh + 0.5 * (f - K @ uh - B1 @ lam) / K.diagonal()
+    r_half = g - B2 @ uh + Zf @ lam
+    assert np.abs((g - B2 @ u3 + Zf @ lam3) - 0.2 * r_half).max() <= 1e-12 * np.abs(r_half).max()
+
+
+def test_two_level_coarse_correction_is_a_projection(cfg0):
+    """Without smoothing, E = I - P A_c^{-1} R A satisfies E^2 = E (Galerkin coarse operator)."""
+    h = setup(cfg0, Options(levels_max=2, coarse_max_rows=0, smoother_sweeps=0, transfer=1))
+    A = h.A0()
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=A.shape[0])
+
+    def E(x):
+        return x - h.vcycle(A @ x)
+    e1 = E(v)
+    assert np.abs(E(e1) - e1).max() <= 1e-9 * np.abs(e1).max()
+    assert np.abs(e1).max() > 1e-3 * np.abs(v).max()
+
+
+def test_vcycle_is_linear(cfg0):
+    h = setup(cfg0, Options(levels_max=3, coarse_max_rows=0))
+    rng = np.random.default_rng(2)
+    x, y = rng.normal(size=(2, cfg0.n))
+    lhs = h.vcycle(2.0 * x - 3.0 * y)
+    rhs = 2.0 * h.vcycle(x) - 3.0 * h.vcycle(y)
+    assert np.abs(lhs - rhs).max() <= 1e-10 * np.abs(rhs).max()
+
+
+def test_fgmres_special_cases():
+    rng = np.random.default_rng(4)
+    n = 40
+    A = sp.csr_matrix(rng.normal(size=(n, n)) + n * np.eye(n))
+    b = rng.normal(size=n)
+    xe = np.linalg.solve(A.toarray(), b)
+    # exact preconditioner: one iteration
+    Ainv = np.linalg.inv(A.toarray())
+    x, it, _ = fgmres(A, b, lambda v: Ainv @ v, tol=1e-12)
+    assert it == 1 and np.abs(x - xe).max() <= 1e-12 * np.abs(xe).max()
+    # identity preconditioner: converges within n steps, monotone residual history
+    x, it, hist = fgmres(A, b, lambda v: v, tol=1e-12, restart=n)
+    assert it <= n and np.all(np.diff(hist) <= 1e-15)
+    assert np.linalg.norm(b - A @ x) <= 1e-11 * np.linalg.norm(b)
+    # restarted run still reaches the tolerance
+    x, it, hist = fgmres(A, b, lambda v: v, tol=1e-10, restart=5)
+    assert np.linalg.norm(b - A @ x) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_amg_fgmres_solves_tiny_contact_problem(cfg0):
+    """Config 0: 3-level PA-AMG + CheapSIMPLE inside FGMRES against a dense LU solve."""
+    h = setup(cfg0, Options(levels_max=3, coarse_max_rows=0))
+    assert h.n_levels == 3
+    A = h.A0()
+    b = cfg0.rhs
+    x, it, hist = fgmres(A, b, h.vcycle, tol=1e-8)
+    xd = sla.lu_solve(sla.lu_factor(A.toarray()), b)
+    assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+    assert np.linalg.norm(x - xd) <= 1e-5 * np.linalg.norm(xd)
+    assert it < 60
+    # contact pressure is compressive: lambda_n = lambda . n > 0 on active nodes
+    lam = x[cfg0.n_u:].reshape(-1, 3)
+    ln = np.einsum("ji,ji->j", lam, cfg0.triad[:, 0])
+    assert ln.mean() > 0
