@@ -1,0 +1,203 @@
+/*
+ * amgc -- fully coupled block algebraic multigrid for mortar-contact saddle-point systems
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The linear system is the linearised frictionless contact system of Sec. 2.3
+ * (Eq. ch6_finalsaddlepointsystem, compact form Eq. ch6_finalsaddlepointsystem_comprehensive):
+ *
+ *        [ K   B1 ] [ u      ]   [ f ]
+ *        [ B2  -Z ] [ lambda ] = [ g ]
+ *
+ * K: stiffness block in 3x3 nodal blocks; B1 = C1^T carries D^T (slave rows) and -M^T
+ * (master rows); B2 = C2 carries the linearised weighted gap n^T(D u_s - M u_m) for active
+ * slave nodes; -Z carries the frictionless tangential rows (active) or the identity (inactive).
+ * Multipliers are Cartesian, three per slave interface node.
+ *
+ * The preconditioner is the paper's method: segregated aggregation with multiplier aggregates
+ * derived from the slave displacement aggregates through D (Sec. 4, Algorithm 1), plain or
+ * smoothed aggregation transfers (Sec. 3.1.2, Eq. ProlongatorSmoothing, Eq.
+ * ch6_segregatedtransfers), Galerkin coarse operators, CheapSIMPLE level smoothing (Algorithm 4,
+ * Sec. 5.2) in a V-cycle (Fig. mgalgorithm) with a direct coarsest solve, inside flexible GMRES
+ * (Sec. 3; stopping rule Eq. ch7_linearstoppingcriterion).
+ *
+ * Conventions for every call:
+ *  - Return value: AMGC_OK (0) or a negative AMGC_E* code; amgc_strerror() names it and
+ *    amgc_last_error() gives the detail of the last failure in the calling thread.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).  Every call
+ *    orders its device work on that stream; calls that return host-visible results
+ *    (sizes, iteration counts) synchronise that stream before returning.
+ *  - Index arrays are int32, floating-point arrays are IEEE double unless stated.
+ *  - Input pointers to amgc_setup may be host or device memory (unified addressing decides);
+ *    they are copied and may be freed after the call.  Vector arguments of the apply calls are
+ *    DEVICE pointers unless the call says otherwise.
+ *  - The hierarchy is owned by the library until amgc_destroy().  A failed amgc_setup leaves
+ *    *out == NULL and frees everything it allocated.
+ */
+#ifndef AMGC_H
+#define AMGC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  AMGC_OK = 0,
+  AMGC_EINVAL = -1,          /* malformed argument or input structure                         */
+  AMGC_ESINGULAR = -2,       /* singular nodal block, rank-deficient aggregate or coarse pivot  */
+  AMGC_NOT_CONVERGED = -3,   /* FGMRES reached maxit without meeting the tolerance              */
+  AMGC_BREAKDOWN = -4,       /* non-finite value or Arnoldi breakdown                           */
+  AMGC_TIMEOUT = -5,         /* a bounded device wait expired                                   */
+  AMGC_ECUDA = -6,           /* CUDA runtime error                                              */
+  AMGC_ENOMEM = -7           /* device allocation failed                                        */
+};
+
+/* Block-sparse row matrix: n_brow x n_bcol blocks of br x bc, row-major blocks,
+ * rowptr[n_brow+1], col[nnzb] sorted ascending within each row, val[nnzb*br*bc]. */
+typedef struct {
+  int32_t n_brow, n_bcol, br, bc;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+} amgc_bsr;
+
+/* Scalar CSR matrix n_row x n_col (used for the mortar matrix M, slave x master). */
+typedef struct {
+  int32_t n_row, n_col;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+} amgc_csr;
+
+typedef struct {
+  int32_t levels_max;        /* maximum number of levels (>= 1)                               */
+  int32_t coarse_max_rows;   /* stop coarsening once the saddle system has fewer rows           */
+  int32_t transfer;          /* 0 = plain aggregation (PA), 1 = smoothed aggregation for u (SA) */
+  int32_t smoother_sweeps;   /* CheapSIMPLE sweeps, pre and post (>= 0)                        */
+  int32_t jacobi_sweeps;     /* damped-Jacobi sweeps in the predictor (>= 1)                   */
+  int32_t simplec;           /* 0: A~ = diag(K);  1: A~ = absolute row sums (SIMPLEC)          */
+  int32_t precision;         /* 64 = FP64 V-cycle (32 reserved for the FP32 cycle)             */
+  int32_t fgmres_restart;    /* Krylov subspace size m (1..256)                               */
+  int32_t fgmres_maxit;      /* total FGMRES iterations allowed                                */
+  uint32_t seed;             /* MIS-2 priority seed                                           */
+  double sa_omega;           /* SA damping numerator: omega = sa_omega / lambda_max(D^-1 K)    */
+  double jacobi_omega;       /* <= 0: (4/3) / lambda_max(D^-1 K) per level                     */
+  double simple_alpha;       /* SIMPLE damping alpha of the multiplier correction              */
+  double tol;                /* relative residual tolerance ||r_k|| / ||r_0||                  */
+} amgc_options;
+
+typedef struct {
+  int32_t n_levels;
+  int32_t rows[16];          /* saddle rows per level                                          */
+  int32_t disp_nodes[16];    /* displacement (super)nodes per level                            */
+  int32_t lm_nodes[16];      /* multiplier nodes per level                                     */
+  int32_t dofs_per_node[16]; /* 3 on level 0, 6 below                                          */
+  int64_t nnz[16];           /* scalar nonzeros of the level's saddle matrix                   */
+  double operator_complexity;
+  double lambda_max[16];     /* estimate of lambda_max(D_K^-1 K) per level                     */
+  double setup_ms;           /* wall time of the last amgc_setup                               */
+  int32_t last_iters;        /* FGMRES iterations of the last solve                            */
+  double last_relres;        /* true relative residual at the end of the last solve           */
+} amgc_stats_t;
+
+/* Fills the defaults: levels_max 10, coarse_max_rows 5000, SA, 1 sweep, 1 Jacobi sweep,
+ * SIMPLE (diag K), FP64, restart 50, maxit 1000, seed 0x5EED, sa_omega 4/3, jacobi_omega
+ * automatic, alpha 0.8, tol 1e-8 (Sec. 6.2 settings, Eq. ch7_linearstoppingcriterion). */
+void amgc_default_options(amgc_options* opts);
+
+/* Builds the hierarchy (Sec. 4: segregated aggregation with Algorithm 1, transfers of
+ * Sec. 3.1.2 / Eq. ch6_segregatedtransfers, Galerkin products, CheapSIMPLE data, coarsest
+ * dense factorisation).
+ *   K           n x n nodal 3x3 BSR, Dirichlet nodes already eliminated; every row must hold
+ *               its diagonal block.
+ *   D_diag      n_s diagonal entries of the dual-mortar D (slave node j <-> multiplier node j).
+ *   M           n_s x n_m scalar CSR mortar matrix (slave rows, master columns).
+ *   slave_node  n_s   K block row of slave interface node j.
+ *   master_node n_m   K block row of master interface node l.
+ *   triad       n_s x 3 x 3, rows (n, tau_xi, tau_eta) of each slave node, orthonormal.
+ *   active      n_s   1 = active (normal gap row + tangential rows), 0 = inactive (lambda = 0).
+ *   body_id     n     body of each K block row; couplings between bodies are dropped during
+ *               aggregation (Sec. 4.2).
+ *   nullspace   3n x 6 row-major rigid-body modes (t_x, t_y, t_z, r_x, r_y, r_z).
+ * Errors: AMGC_EINVAL (sizes, indices out of range, missing diagonal block, nothing to
+ * aggregate), AMGC_ESINGULAR (rank-deficient aggregate, singular Schur block or coarse pivot),
+ * AMGC_ENOMEM, AMGC_ECUDA.  On error *out is NULL and nothing stays allocated. */
+int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M,
+               const int32_t* slave_node, const int32_t* master_node,
+               const double* triad, const uint8_t* active, const int32_t* body_id,
+               const double* nullspace, const amgc_options* opts, void* stream,
+               struct amgc_hierarchy** out);
+
+/* z = V-cycle(r) with zero initial guess (Fig. mgalgorithm).  r, z: device vectors of
+ * length rows[0] = 3n + 3 n_s, ordered [u; lambda].  r and z must not overlap. */
+int amgc_vcycle(struct amgc_hierarchy* h, const double* r, double* z, void* stream);
+
+/* y = A x with the fine-level saddle operator [K B1; B2 -Z]; device vectors of length rows[0]. */
+int amgc_apply(struct amgc_hierarchy* h, const double* x, double* y, void* stream);
+
+/* Solves A x = rhs by right-preconditioned flexible GMRES with one V-cycle per iteration,
+ * x_0 = 0, stopped when ||b - A x_k|| / ||b|| < tol (Eq. ch7_linearstoppingcriterion).
+ * rhs, x: device vectors of length rows[0]; iters / relres may be NULL.  Returns
+ * AMGC_NOT_CONVERGED (x holds the last iterate) or AMGC_BREAKDOWN on failure. */
+int amgc_solve(struct amgc_hierarchy* h, const double* rhs, double* x, int32_t* iters,
+               double* relres, void* stream);
+
+/* Same as amgc_solve but rhs and x are HOST arrays: the call copies rhs to the device,
+ * solves, and copies x back (synchronous with respect to the host). */
+int amgc_solve_host(struct amgc_hierarchy* h, const double* rhs_host, double* x_host,
+                    int32_t* iters, double* relres, void* stream);
+
+int amgc_stats(const struct amgc_hierarchy* h, amgc_stats_t* out);
+
+/* Copies one internal array of level `level` to the host buffer dst (capacity `bytes`).
+ * what: see AMGC_EXPORT_*.  Returns the number of bytes the array holds (>= 0) or an error;
+ * with dst == NULL only the size is returned.  Used by the parity tests. */
+enum {
+  AMGC_EXPORT_AGG = 1,        /* int32[disp_nodes]   displacement aggregate of each node       */
+  AMGC_EXPORT_LAGG = 2,       /* int32[lm_nodes]     multiplier aggregate of each node         */
+  AMGC_EXPORT_P_ROWPTR = 3,   /* int32  prolongator (u) BSR of this level -> next             */
+  AMGC_EXPORT_P_COL = 4,
+  AMGC_EXPORT_P_VAL = 5,      /* double bu x 6 blocks                                          */
+  AMGC_EXPORT_K_ROWPTR = 6,   /* K block of this level                                         */
+  AMGC_EXPORT_K_COL = 7,
+  AMGC_EXPORT_K_VAL = 8,
+  AMGC_EXPORT_B1_ROWPTR = 9,
+  AMGC_EXPORT_B1_COL = 10,
+  AMGC_EXPORT_B1_VAL = 11,
+  AMGC_EXPORT_B2_ROWPTR = 12,
+  AMGC_EXPORT_B2_COL = 13,
+  AMGC_EXPORT_B2_VAL = 14,
+  AMGC_EXPORT_Z = 15,         /* double[lm_nodes*9]                                            */
+  AMGC_EXPORT_SINV = 16,      /* double[lm_nodes*9]  inverted nodal blocks of S_hat            */
+  AMGC_EXPORT_NULLSPACE = 17, /* double[dofs*6]                                                */
+  AMGC_EXPORT_PL_W = 18,      /* double[lm_nodes]    multiplier tentative-transfer weights     */
+  AMGC_EXPORT_ATINV = 19,     /* double[dofs]        A~^-1                                     */
+  AMGC_EXPORT_OMEGA = 20,     /* double[2]           (lambda_max, omega_J)                     */
+  AMGC_EXPORT_COARSE_INV = 21 /* double[rows*rows]   inverse of the coarsest saddle matrix     */
+};
+int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what, void* dst,
+                    int64_t bytes);
+
+/* Diagnostic timing of the dominant kernel family: the fine-level K-block applies (residual,
+ * Jacobi predictor and saddle apply, one launch each).  With enable != 0 every such launch is
+ * bracketed by CUDA events recorded on the launching stream; amgc_profile_read synchronises
+ * that stream and returns the accumulated device time (ms), the number of launches and the
+ * algorithmic bytes those launches move (matrix values and indices once, every vector once).
+ * Enabling resets the counters.  Not for production runs: each launch adds two event records. */
+int amgc_profile(struct amgc_hierarchy* h, int32_t enable);
+int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes);
+
+void amgc_destroy(struct amgc_hierarchy* h);
+const char* amgc_strerror(int code);
+const char* amgc_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the calling process so far. */
+int64_t amgc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMGC_H */

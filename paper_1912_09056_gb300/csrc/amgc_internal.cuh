@@ -1,0 +1,193 @@
+// Internal data structures and device helpers of the amgc library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/amgc.h"
+
+namespace amgc {
+
+// ------------------------------------------------------------------ error handling
+void set_error(const std::string& msg);
+
+#define AMGC_CUDA_TRY(expr)                                                             \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      ::amgc::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));            \
+      return e_ == cudaErrorMemoryAllocation ? AMGC_ENOMEM : AMGC_ECUDA;                \
+    }                                                                                   \
+  } while (0)
+
+#define AMGC_TRY(expr)            \
+  do {                            \
+    int s_ = (expr);              \
+    if (s_ != AMGC_OK) return s_; \
+  } while (0)
+
+// Every kernel launch of the library goes through AMGC_LAUNCH, which counts it.
+extern std::atomic<long long> g_launches;
+#define AMGC_LAUNCH(...) (::amgc::g_launches.fetch_add(1, std::memory_order_relaxed), __VA_ARGS__)
+
+// Device status bits written by kernels that detect bad input or a singular block.
+enum : int {
+  ST_BAD_INDEX = 1,
+  ST_NO_DIAG = 2,
+  ST_SINGULAR = 4,
+  ST_RANK = 8,
+  ST_ROW_TOO_DENSE = 16,
+  ST_NONFINITE = 32,
+};
+
+// ------------------------------------------------------------------ device memory
+// Owning device buffer (cudaMalloc/cudaFree); the hierarchy keeps these alive.
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  int alloc(size_t count) {
+    release();
+    n = count;
+    if (count == 0) return AMGC_OK;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      n = 0;
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return AMGC_ENOMEM;
+    }
+    return AMGC_OK;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+// Block-sparse row matrix on the device (row-major br x bc blocks).
+struct DBsr {
+  int nbr = 0, nbc = 0, br = 0, bc = 0;
+  int64_t nnzb = 0;
+  DBuf<int> rowptr, col;
+  DBuf<double> val;
+};
+
+// One level of the hierarchy.
+struct Level {
+  int nn = 0;     // displacement (super)nodes
+  int bu = 3;     // DOFs per displacement node
+  int nl = 0;     // multiplier nodes (3 DOFs each)
+  int nu() const { return nn * bu; }
+  int rows() const { return nn * bu + 3 * nl; }
+
+  DBsr K, B1, B2;          // saddle blocks
+  DBuf<double> Z;          // nl*9
+  DBuf<int> body;          // nn
+  DBuf<double> B;          // nullspace nu*6
+  DBuf<double> Bl;         // multiplier nullspace per node (nl)
+  DBuf<int> lm_dnode;      // nl: displacement node coupled through D
+
+  // transfer to the next level
+  DBuf<int> agg;           // nn
+  int n_agg = 0;
+  DBuf<int> lagg;          // nl
+  int n_lagg = 0;
+  DBsr P, R;               // u prolongator (bu x 6) and restriction (6 x bu)
+  DBuf<double> pl_w;       // nl weights of P-hat^lambda
+  DBuf<int> rl_ptr, rl_idx;  // coarse multiplier node -> sorted member list
+
+  // CheapSIMPLE data
+  double lam_max = 0.0, omega_j = 0.0;
+  DBuf<double> kdiag, dinv, atinv;  // nu: pointwise diagonal of K, its inverse, A~^-1
+  DBuf<double> Sinv;         // nl*9
+  DBuf<int> b1_rows;         // displacement nodes with B1 entries
+  int n_b1_rows = 0;
+
+  // coarsest level
+  DBuf<double> Ainv;         // rows*rows (row-major)
+
+  // work vectors [u; lambda]
+  DBuf<double> x, b, r, t;
+  DBuf<double> dlam;         // nl*3
+};
+
+}  // namespace amgc
+
+struct amgc_hierarchy {
+  std::vector<amgc::Level> L;
+  amgc_options opts{};
+  amgc_stats_t stats{};
+  cudaStream_t stream = nullptr;
+  amgc::DBuf<int> status;          // device status word
+  amgc::DBuf<double> scratch;      // reductions
+  // FGMRES workspace
+  int m_alloc = 0;
+  amgc::DBuf<double> V, Zs, H, givens, gvec, y, wk, xk, rk;
+  amgc::DBuf<double> partial;      // per-block partial dot products
+  double* h_pinned = nullptr;      // pinned host scalars
+  // event timing of the fine-level K applies (amgc_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_pending = 0;
+  double prof_ms = 0.0, prof_bytes = 0.0;
+  int64_t prof_launches = 0;
+};
+
+namespace amgc {
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ host-side kernel drivers
+// scan.cu
+int exclusive_scan(const int* in, int* out, int n, cudaStream_t s, int* total_host);
+// assembly / setup (setup.cu)
+int build_fine_level(amgc_hierarchy* h, const amgc_bsr* K, const double* D, const amgc_csr* M,
+                     const int* slave_node, const int* master_node, const double* triad,
+                     const uint8_t* active, const int* body_id, const double* nullspace);
+int coarsen_level(amgc_hierarchy* h, int l);
+int smoother_setup(amgc_hierarchy* h, int l);
+int coarse_setup(amgc_hierarchy* h, int l);
+int check_status(amgc_hierarchy* h, const char* where);
+// kernel timing (api.cu)
+int prof_begin(amgc_hierarchy* h);
+int prof_end(amgc_hierarchy* h, double bytes);
+int prof_flush(amgc_hierarchy* h);
+// sparse kernels (sparse.cu)
+int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
+int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out);
+int dot(amgc_hierarchy* h, int64_t n, const double* a, const double* b, const double* wgt, double* out_dev);
+// V-cycle (vcycle.cu)
+int vcycle(amgc_hierarchy* h, int l, const double* b, double* x);
+int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y);
+// FGMRES (krylov.cu)
+int fgmres(amgc_hierarchy* h, const double* rhs, double* x, int* iters, double* relres);
+
+}  // namespace amgc

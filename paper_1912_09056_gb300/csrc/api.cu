@@ -1,0 +1,313 @@
+// C-ABI entry points of the amgc library (declared in include/amgc.h).
+#include "amgc_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+namespace amgc {
+
+static thread_local std::string g_last_error;
+std::atomic<long long> g_launches{0};
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// Largest coarsest system solved with the dense explicit inverse.
+constexpr int kMaxDenseRows = 16384;
+
+static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, const amgc_csr* M,
+                 const int32_t* slave_node, const int32_t* master_node, const double* triad,
+                 const uint8_t* active, const int32_t* body_id, const double* nullspace) {
+  const auto t0 = std::chrono::steady_clock::now();
+  AMGC_TRY(h->status.alloc(1));
+  AMGC_CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
+  AMGC_TRY(h->partial.alloc(4096));
+  AMGC_CUDA_TRY(cudaMallocHost(&h->h_pinned, 64 * sizeof(double)));
+  h->L.reserve(16);
+  h->L.emplace_back();
+  AMGC_TRY(build_fine_level(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace));
+  const amgc_options& o = h->opts;
+  while ((int)h->L.size() < std::min(o.levels_max, 16) && h->L.back().rows() >= o.coarse_max_rows) {
+    const int l = (int)h->L.size() - 1;
+    AMGC_TRY(smoother_setup(h, l));
+    AMGC_TRY(coarsen_level(h, l));
+    if (h->L[l + 1].nn >= h->L[l].nn) {   // no reduction: keep the finer level as the coarsest
+      h->L.pop_back();
+      break;
+    }
+  }
+  const int lc = (int)h->L.size() - 1;
+  if (h->L[lc].rows() > kMaxDenseRows) {
+    set_error("coarsest level has " + std::to_string(h->L[lc].rows()) +
+              " rows; raise levels_max or lower coarse_max_rows (dense limit " + std::to_string(kMaxDenseRows) + ")");
+    return AMGC_EINVAL;
+  }
+  AMGC_TRY(coarse_setup(h, lc));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  // statistics
+  amgc_stats_t& st = h->stats;
+  std::memset(&st, 0, sizeof(st));
+  st.n_levels = (int)h->L.size();
+  double nnz0 = 0.0, nnz_all = 0.0;
+  for (int l = 0; l < st.n_levels; ++l) {
+    const Level& L = h->L[l];
+    st.rows[l] = L.rows();
+    st.disp_nodes[l] = L.nn;
+    st.lm_nodes[l] = L.nl;
+    st.dofs_per_node[l] = L.bu;
+    st.nnz[l] = L.K.nnzb * L.bu * L.bu + L.B1.nnzb * L.bu * 3 + L.B2.nnzb * 3 * L.bu + (int64_t)L.nl * 9;
+    st.lambda_max[l] = L.lam_max;
+    if (l == 0) nnz0 = (double)st.nnz[l];
+    nnz_all += (double)st.nnz[l];
+  }
+  st.operator_complexity = nnz0 > 0 ? nnz_all / nnz0 : 0.0;
+  st.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return AMGC_OK;
+}
+
+constexpr int kProfPairs = 1024;
+
+int prof_flush(amgc_hierarchy* h) {
+  if (h->prof_pending == 0) return AMGC_OK;
+  AMGC_CUDA_TRY(cudaEventSynchronize(h->prof_ev[2 * h->prof_pending - 1]));
+  for (int i = 0; i < h->prof_pending; ++i) {
+    float ms = 0.f;
+    AMGC_CUDA_TRY(cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+    h->prof_ms += ms;
+  }
+  h->prof_pending = 0;
+  return AMGC_OK;
+}
+
+int prof_begin(amgc_hierarchy* h) {
+  if (!h->prof) return AMGC_OK;
+  if (h->prof_ev.empty()) {
+    h->prof_ev.resize(2 * kProfPairs);
+    for (auto& e : h->prof_ev) AMGC_CUDA_TRY(cudaEventCreate(&e));
+  }
+  if (h->prof_pending == kProfPairs) AMGC_TRY(prof_flush(h));
+  AMGC_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_pending], h->stream));
+  return AMGC_OK;
+}
+
+int prof_end(amgc_hierarchy* h, double bytes) {
+  if (!h->prof) return AMGC_OK;
+  AMGC_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_pending + 1], h->stream));
+  h->prof_pending++;
+  h->prof_launches++;
+  h->prof_bytes += bytes;
+  return AMGC_OK;
+}
+
+}  // namespace amgc
+
+using namespace amgc;
+
+extern "C" {
+
+void amgc_default_options(amgc_options* o) {
+  if (!o) return;
+  o->levels_max = 10;
+  o->coarse_max_rows = 5000;
+  o->transfer = 1;
+  o->smoother_sweeps = 1;
+  o->jacobi_sweeps = 1;
+  o->simplec = 0;
+  o->precision = 64;
+  o->fgmres_restart = 50;
+  o->fgmres_maxit = 1000;
+  o->seed = 0x5EED;
+  o->sa_omega = 4.0 / 3.0;
+  o->jacobi_omega = 0.0;
+  o->simple_alpha = 0.8;
+  o->tol = 1e-8;
+}
+
+int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const int32_t* slave_node,
+               const int32_t* master_node, const double* triad, const uint8_t* active, const int32_t* body_id,
+               const double* nullspace, const amgc_options* opts, void* stream, struct amgc_hierarchy** out) {
+  if (!out) {
+    set_error("amgc_setup: out is NULL");
+    return AMGC_EINVAL;
+  }
+  *out = nullptr;
+  if (!K || !M || !opts || !K->rowptr || !K->col || !K->val || !body_id || !nullspace || !M->rowptr ||
+      K->br != 3 || K->bc != 3 || K->n_brow != K->n_bcol || K->n_brow <= 0 || M->n_row < 0 || M->n_col < 0 ||
+      (M->n_row > 0 && (!D_diag || !slave_node || !triad || !active)) || (M->n_col > 0 && !master_node) ||
+      opts->levels_max < 1 || opts->smoother_sweeps < 0 || opts->jacobi_sweeps < 1 || opts->fgmres_restart < 1 ||
+      opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 || !(opts->tol > 0.0) || opts->precision != 64) {
+    set_error("amgc_setup: invalid argument");
+    return AMGC_EINVAL;
+  }
+  amgc_hierarchy* h = new (std::nothrow) amgc_hierarchy();
+  if (!h) return AMGC_ENOMEM;
+  h->opts = *opts;
+  h->stream = (cudaStream_t)stream;
+  int st = build(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace);
+  if (st != AMGC_OK) {
+    cudaStreamSynchronize(h->stream);
+    amgc_destroy(h);
+    return st;
+  }
+  *out = h;
+  return AMGC_OK;
+}
+
+int amgc_vcycle(struct amgc_hierarchy* h, const double* r, double* z, void* stream) {
+  if (!h || !r || !z || r == z) {
+    set_error("amgc_vcycle: invalid argument");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  return vcycle(h, 0, r, z);
+}
+
+int amgc_apply(struct amgc_hierarchy* h, const double* x, double* y, void* stream) {
+  if (!h || !x || !y || x == y) {
+    set_error("amgc_apply: invalid argument");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  return saddle_apply(h, 0, x, y);
+}
+
+int amgc_solve(struct amgc_hierarchy* h, const double* rhs, double* x, int32_t* iters, double* relres, void* stream) {
+  if (!h || !rhs || !x || rhs == x) {
+    set_error("amgc_solve: invalid argument");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  int it = 0;
+  double rr = 0.0;
+  int st = fgmres(h, rhs, x, &it, &rr);
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return st;
+}
+
+int amgc_solve_host(struct amgc_hierarchy* h, const double* rhs_host, double* x_host, int32_t* iters, double* relres,
+                    void* stream) {
+  if (!h || !rhs_host || !x_host) {
+    set_error("amgc_solve_host: invalid argument");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  const size_t n = (size_t)h->L[0].rows();
+  DBuf<double> b, x;
+  AMGC_TRY(b.alloc(n));
+  AMGC_TRY(x.alloc(n));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(b.p, rhs_host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  int it = 0;
+  double rr = 0.0;
+  int st = fgmres(h, b.p, x.p, &it, &rr);
+  if (st == AMGC_OK || st == AMGC_NOT_CONVERGED)
+    AMGC_CUDA_TRY(cudaMemcpyAsync(x_host, x.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return st;
+}
+
+int amgc_stats(const struct amgc_hierarchy* h, amgc_stats_t* out) {
+  if (!h || !out) {
+    set_error("amgc_stats: invalid argument");
+    return AMGC_EINVAL;
+  }
+  *out = h->stats;
+  return AMGC_OK;
+}
+
+int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what, void* dst, int64_t bytes) {
+  if (!h || level < 0 || level >= (int)h->L.size()) {
+    set_error("amgc_export: invalid level");
+    return AMGC_EINVAL;
+  }
+  const Level& L = h->L[level];
+  const void* src = nullptr;
+  int64_t nb = 0;
+  double scal[2] = {L.lam_max, L.omega_j};
+  switch (what) {
+    case AMGC_EXPORT_AGG: src = L.agg.p; nb = L.agg.p ? (int64_t)L.nn * 4 : 0; break;
+    case AMGC_EXPORT_LAGG: src = L.lagg.p; nb = L.lagg.p ? (int64_t)L.nl * 4 : 0; break;
+    case AMGC_EXPORT_P_ROWPTR: src = L.P.rowptr.p; nb = L.P.rowptr.p ? (int64_t)(L.P.nbr + 1) * 4 : 0; break;
+    case AMGC_EXPORT_P_COL: src = L.P.col.p; nb = L.P.nnzb * 4; break;
+    case AMGC_EXPORT_P_VAL: src = L.P.val.p; nb = L.P.nnzb * L.P.br * L.P.bc * 8; break;
+    case AMGC_EXPORT_K_ROWPTR: src = L.K.rowptr.p; nb = (int64_t)(L.K.nbr + 1) * 4; break;
+    case AMGC_EXPORT_K_COL: src = L.K.col.p; nb = L.K.nnzb * 4; break;
+    case AMGC_EXPORT_K_VAL: src = L.K.val.p; nb = L.K.nnzb * L.K.br * L.K.bc * 8; break;
+    case AMGC_EXPORT_B1_ROWPTR: src = L.B1.rowptr.p; nb = (int64_t)(L.B1.nbr + 1) * 4; break;
+    case AMGC_EXPORT_B1_COL: src = L.B1.col.p; nb = L.B1.nnzb * 4; break;
+    case AMGC_EXPORT_B1_VAL: src = L.B1.val.p; nb = L.B1.nnzb * L.B1.br * L.B1.bc * 8; break;
+    case AMGC_EXPORT_B2_ROWPTR: src = L.B2.rowptr.p; nb = (int64_t)(L.B2.nbr + 1) * 4; break;
+    case AMGC_EXPORT_B2_COL: src = L.B2.col.p; nb = L.B2.nnzb * 4; break;
+    case AMGC_EXPORT_B2_VAL: src = L.B2.val.p; nb = L.B2.nnzb * L.B2.br * L.B2.bc * 8; break;
+    case AMGC_EXPORT_Z: src = L.Z.p; nb = (int64_t)L.nl * 9 * 8; break;
+    case AMGC_EXPORT_SINV: src = L.Sinv.p; nb = L.Sinv.p ? (int64_t)L.nl * 9 * 8 : 0; break;
+    case AMGC_EXPORT_NULLSPACE: src = L.B.p; nb = (int64_t)L.nu() * 6 * 8; break;
+    case AMGC_EXPORT_PL_W: src = L.pl_w.p; nb = L.pl_w.p ? (int64_t)L.nl * 8 : 0; break;
+    case AMGC_EXPORT_ATINV: src = L.atinv.p; nb = L.atinv.p ? (int64_t)L.nu() * 8 : 0; break;
+    case AMGC_EXPORT_OMEGA: src = scal; nb = 16; break;
+    case AMGC_EXPORT_COARSE_INV: src = L.Ainv.p; nb = L.Ainv.p ? (int64_t)L.rows() * L.rows() * 8 : 0; break;
+    default: set_error("amgc_export: unknown array"); return AMGC_EINVAL;
+  }
+  if (!dst || nb == 0) return nb;
+  if (bytes < nb) {
+    set_error("amgc_export: destination too small");
+    return AMGC_EINVAL;
+  }
+  AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  AMGC_CUDA_TRY(cudaMemcpy(dst, src, nb, cudaMemcpyDefault));
+  return nb;
+}
+
+int amgc_profile(struct amgc_hierarchy* h, int32_t enable) {
+  if (!h) {
+    set_error("amgc_profile: invalid argument");
+    return AMGC_EINVAL;
+  }
+  AMGC_TRY(prof_flush(h));
+  h->prof = enable != 0;
+  h->prof_ms = 0.0;
+  h->prof_bytes = 0.0;
+  h->prof_launches = 0;
+  return AMGC_OK;
+}
+
+int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes) {
+  if (!h) {
+    set_error("amgc_profile_read: invalid argument");
+    return AMGC_EINVAL;
+  }
+  AMGC_TRY(prof_flush(h));
+  if (total_ms) *total_ms = h->prof_ms;
+  if (launches) *launches = h->prof_launches;
+  if (bytes) *bytes = h->prof_bytes;
+  return AMGC_OK;
+}
+
+void amgc_destroy(struct amgc_hierarchy* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& e : h->prof_ev) cudaEventDestroy(e);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  delete h;
+}
+
+const char* amgc_strerror(int code) {
+  switch (code) {
+    case AMGC_OK: return "ok";
+    case AMGC_EINVAL: return "invalid argument or input structure";
+    case AMGC_ESINGULAR: return "singular block, rank-deficient aggregate or coarse pivot";
+    case AMGC_NOT_CONVERGED: return "FGMRES did not converge";
+    case AMGC_BREAKDOWN: return "non-finite value or Krylov breakdown";
+    case AMGC_TIMEOUT: return "bounded device wait expired";
+    case AMGC_ECUDA: return "CUDA runtime error";
+    case AMGC_ENOMEM: return "device allocation failed";
+    default: return "unknown error";
+  }
+}
+
+const char* amgc_last_error(void) { return g_last_error.c_str(); }
+
+int64_t amgc_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

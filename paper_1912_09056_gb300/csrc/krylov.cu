@@ -1,0 +1,253 @@
+// Right-preconditioned flexible GMRES(m) with one V-cycle per iteration (Sec. 3), stopped on
+// ||r_k|| / ||r_0|| < tol for the full residual [r_u; r_lambda] (Eq. ch7_linearstoppingcriterion).
+// Arnoldi: classical Gram-Schmidt with one re-orthogonalisation pass (CGS2), so each pass is a
+// single streaming multi-dot plus a single streaming update over the basis.  Hessenberg
+// columns, Givens rotations and the residual estimate live on the device; the host reads one
+// scalar per iteration to decide whether to stop.
+#include "amgc_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace amgc {
+
+constexpr int kMdThreads = 256;
+constexpr int kMdBlocks = 304;   // 2 x 152 SMs
+constexpr int kMaxRestart = 256;
+
+// part[b * ldp + k] = sum over block b's rows of V[k][i] * w[i], k = 0..nk-1
+__global__ void __launch_bounds__(kMdThreads)
+k_multidot(int64_t n, int nk, const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ part,
+           int ldp) {
+  __shared__ double sh[kMdThreads / 32];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = blockIdx.x * chunk;
+  const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+  for (int k = 0; k < nk; ++k) {
+    const double* v = V + (int64_t)k * n;
+    double s = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kMdThreads) s = fma(v[i], w[i], s);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double t = threadIdx.x < kMdThreads / 32 ? sh[threadIdx.x] : 0.0;
+      t = warp_sum(t);
+      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * ldp + k] = t;
+    }
+    __syncthreads();
+  }
+}
+// out[k*ldo] (+)= sum_b part[b*ldp + k]  (fixed order: deterministic)
+__global__ void k_multidot_final(int nk, int nb, const double* __restrict__ part, int ldp, double* __restrict__ out,
+                                 int ldo, int accumulate, double* __restrict__ hk) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(int64_t)b * ldp + k];
+  if (hk) hk[k] = s;
+  out[(int64_t)k * ldo] = accumulate ? out[(int64_t)k * ldo] + s : s;
+}
+// w[i] -= sum_k V[k][i] h[k]
+__global__ void k_basis_update(int64_t n, int nk, const double* __restrict__ V, const double* __restrict__ h,
+                               double* __restrict__ w) {
+  __shared__ double hs[kMaxRestart + 1];
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = h[k];
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = w[i];
+  for (int k = 0; k < nk; ++k) s = fma(-V[(int64_t)k * n + i], hs[k], s);
+  w[i] = s;
+}
+// x[i] += sum_k Zs[k][i] y[k]
+__global__ void k_solution_update(int64_t n, int nk, const double* __restrict__ Zs, const double* __restrict__ y,
+                                  double* __restrict__ x) {
+  __shared__ double ys[kMaxRestart];
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) ys[k] = y[k];
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = x[i];
+  for (int k = 0; k < nk; ++k) s = fma(Zs[(int64_t)k * n + i], ys[k], s);
+  x[i] = s;
+}
+// v = w / sqrt(nrm2) (zero vector on breakdown); H[j+1][j] = sqrt(nrm2)
+__global__ void k_arnoldi_normalize(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ w,
+                                    double* __restrict__ v, double* __restrict__ hsub) {
+  const double nr = sqrt(*nrm2);
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0) *hsub = nr;
+  if (i < n) v[i] = nr > 0.0 ? w[i] / nr : 0.0;
+}
+// start of a cycle: v0 = r / beta, g = (beta, 0, ...)
+__global__ void k_cycle_start(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ r,
+                              double* __restrict__ v0, double* __restrict__ g, int m) {
+  const double beta = sqrt(*nrm2);
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v0[i] = r[i] / beta;
+  if (i <= m) g[i] = i == 0 ? beta : 0.0;
+}
+// Givens update of column j (single thread); scal[0] = |g_{j+1}| / beta0
+__global__ void k_givens(int j, int m, double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                         double* __restrict__ g, double beta0, double* __restrict__ scal) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * m + j], b = H[(i + 1) * m + j];
+    H[i * m + j] = cs[i] * a + sn[i] * b;
+    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = H[j * m + j], b = H[(j + 1) * m + j];
+  const double den = hypot(a, b);
+  const double c = den > 0.0 ? a / den : 1.0;
+  const double s = den > 0.0 ? b / den : 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  const double gj = g[j];
+  g[j + 1] = -s * gj;
+  g[j] = c * gj;
+  scal[0] = fabs(g[j + 1]) / beta0;
+  scal[1] = isfinite(den) && isfinite(g[j + 1]) ? 0.0 : 1.0;
+}
+// back substitution H(0:k,0:k) y = g(0:k) (single thread)
+__global__ void k_backsolve(int k, int m, const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int q = i + 1; q < k; ++q) s -= H[i * m + q] * y[q];
+    y[i] = s / H[i * m + i];
+  }
+}
+__global__ void k_sub(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i] - b[i];
+}
+__global__ void k_zero_vec(int64_t n, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = 0.0;
+}
+
+static int ensure_workspace(amgc_hierarchy* h, int64_t n, int m) {
+  if (h->m_alloc == m && h->V.n == (size_t)(m + 1) * n) return AMGC_OK;
+  AMGC_TRY(h->V.alloc((size_t)(m + 1) * n));
+  AMGC_TRY(h->Zs.alloc((size_t)m * n));
+  AMGC_TRY(h->H.alloc((size_t)(m + 1) * m));
+  AMGC_TRY(h->givens.alloc((size_t)2 * m));
+  AMGC_TRY(h->gvec.alloc(m + 1));
+  AMGC_TRY(h->y.alloc(m + 1));
+  AMGC_TRY(h->wk.alloc((size_t)kMdBlocks * (m + 1)));
+  AMGC_TRY(h->rk.alloc(n));
+  AMGC_TRY(h->xk.alloc(8));
+  h->m_alloc = m;
+  return AMGC_OK;
+}
+
+// h = V[0..nk)^T w into H column (stride m), optionally accumulating; hk receives the new values
+static int multidot(amgc_hierarchy* h, int64_t n, int nk, const double* V, const double* w, double* Hcol, int m,
+                    int accumulate, double* hk) {
+  cudaStream_t s = h->stream;
+  AMGC_LAUNCH(k_multidot<<<kMdBlocks, kMdThreads, 0, s>>>(n, nk, V, w, h->wk.p, nk));
+  AMGC_LAUNCH(k_multidot_final<<<div_up(nk, 128), 128, 0, s>>>(nk, kMdBlocks, h->wk.p, nk, Hcol, m, accumulate, hk));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+int fgmres(amgc_hierarchy* h, const double* rhs, double* x, int* iters_out, double* relres_out) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->L[0].rows();
+  const int m = std::max(1, std::min(h->opts.fgmres_restart, kMaxRestart));
+  const int maxit = std::max(1, h->opts.fgmres_maxit);
+  const double tol = h->opts.tol;
+  AMGC_TRY(ensure_workspace(h, n, m));
+  const int th = 256;
+  const int gn = div_up(n, th);
+  double* scal = h->xk.p;          // [0] residual estimate, [1] breakdown flag, [2] norm^2, [3] scratch
+  double* hk = h->y.p;             // reuse: projection coefficients of the current pass
+  DBuf<double> hbuf;
+  AMGC_TRY(hbuf.alloc(m + 1));
+  double* cs = h->givens.p;
+  double* sn = h->givens.p + m;
+  double* pin = h->h_pinned;
+
+  AMGC_LAUNCH(k_zero_vec<<<gn, th, 0, s>>>(n, x));
+  AMGC_TRY(dot(h, n, rhs, rhs, nullptr, scal + 2));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(pin, scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  const double beta0 = std::sqrt(pin[0]);
+  if (!std::isfinite(beta0)) {
+    set_error("fgmres: non-finite right-hand side");
+    return AMGC_BREAKDOWN;
+  }
+  if (beta0 == 0.0) {
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    return AMGC_OK;
+  }
+  AMGC_CUDA_TRY(cudaMemcpyAsync(h->rk.p, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int total = 0;
+  bool converged = false;
+  double relres = 1.0;
+  while (total < maxit && !converged) {
+    // ||r||^2 is in scal[2]
+    AMGC_LAUNCH(k_cycle_start<<<div_up(std::max<int64_t>(n, m + 1), th), th, 0, s>>>(n, scal + 2, h->rk.p, h->V.p, h->gvec.p, m));
+    AMGC_CUDA_TRY(cudaMemsetAsync(h->H.p, 0, (size_t)(m + 1) * m * sizeof(double), s));
+    int jd = 0;
+    for (int j = 0; j < m && total < maxit; ++j) {
+      double* vj = h->V.p + (int64_t)j * n;
+      double* zj = h->Zs.p + (int64_t)j * n;
+      double* w = h->V.p + (int64_t)(j + 1) * n;
+      AMGC_TRY(vcycle(h, 0, vj, zj));
+      AMGC_TRY(saddle_apply(h, 0, zj, w));
+      // CGS2
+      for (int pass = 0; pass < 2; ++pass) {
+        AMGC_TRY(multidot(h, n, j + 1, h->V.p, w, h->H.p + j, m, pass, hbuf.p));
+        AMGC_LAUNCH(k_basis_update<<<gn, th, 0, s>>>(n, j + 1, h->V.p, hbuf.p, w));
+        AMGC_CUDA_TRY(cudaGetLastError());
+      }
+      AMGC_TRY(dot(h, n, w, w, nullptr, scal + 2));
+      AMGC_LAUNCH(k_arnoldi_normalize<<<gn, th, 0, s>>>(n, scal + 2, w, w, h->H.p + (int64_t)(j + 1) * m + j));
+      AMGC_LAUNCH(k_givens<<<1, 32, 0, s>>>(j, m, h->H.p, cs, sn, h->gvec.p, beta0, scal));
+      AMGC_CUDA_TRY(cudaGetLastError());
+      AMGC_CUDA_TRY(cudaMemcpyAsync(pin, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+      ++total;
+      jd = j + 1;
+      relres = pin[0];
+      if (pin[1] != 0.0 || !std::isfinite(relres)) {
+        set_error("fgmres: non-finite Hessenberg entry");
+        return AMGC_BREAKDOWN;
+      }
+      if (relres < tol) {
+        converged = true;
+        break;
+      }
+    }
+    AMGC_LAUNCH(k_backsolve<<<1, 32, 0, s>>>(jd, m, h->H.p, h->gvec.p, hk));
+    AMGC_LAUNCH(k_solution_update<<<gn, th, 0, s>>>(n, jd, h->Zs.p, hk, x));
+    // true residual r = b - A x
+    AMGC_TRY(saddle_apply(h, 0, x, h->rk.p));
+    AMGC_LAUNCH(k_sub<<<gn, th, 0, s>>>(n, rhs, h->rk.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    AMGC_TRY(dot(h, n, h->rk.p, h->rk.p, nullptr, scal + 2));
+  }
+  AMGC_CUDA_TRY(cudaMemcpyAsync(pin, scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  const double true_rel = std::sqrt(pin[0]) / beta0;
+  if (iters_out) *iters_out = total;
+  if (relres_out) *relres_out = true_rel;
+  h->stats.last_iters = total;
+  h->stats.last_relres = true_rel;
+  if (!std::isfinite(true_rel)) {
+    set_error("fgmres: non-finite residual");
+    return AMGC_BREAKDOWN;
+  }
+  if (!converged) {
+    set_error("fgmres: iteration limit reached");
+    return AMGC_NOT_CONVERGED;
+  }
+  return AMGC_OK;
+}
+
+}  // namespace amgc

@@ -1,0 +1,1303 @@
+// Hierarchy setup kernels: fine-level assembly, MIS-2 aggregation, multiplier aggregation
+// (Algorithm 1), tentative transfers by per-aggregate QR, smoothed prolongator, block SpGEMM
+// Galerkin products, CheapSIMPLE data and the coarsest dense inverse.
+#include "amgc_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace amgc {
+
+// ======================================================================== small utilities
+__device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit); }
+
+__global__ void k_iota(int n, int* __restrict__ y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = i;
+}
+__global__ void k_fill_int(int64_t n, int v, int* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = v;
+}
+__global__ void k_fill_dbl(int64_t n, double v, double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = v;
+}
+
+// Sorts each segment [ptr[s], ptr[s+1]) of (key, payload) by key (insertion sort; segments are short).
+__global__ void k_sort_segments(int nseg, const int* __restrict__ ptr, int* __restrict__ key, int* __restrict__ pay) {
+  int sgi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sgi >= nseg) return;
+  int b = ptr[sgi], e = ptr[sgi + 1];
+  for (int i = b + 1; i < e; ++i) {
+    int k = key[i], p = pay ? pay[i] : 0;
+    int j = i - 1;
+    while (j >= b && key[j] > k) {
+      key[j + 1] = key[j];
+      if (pay) pay[j + 1] = pay[j];
+      --j;
+    }
+    key[j + 1] = k;
+    if (pay) pay[j + 1] = p;
+  }
+}
+
+// Counting sort of items 0..n-1 by bucket id: out ptr (nb+1) and idx (items sorted by bucket,
+// ascending item id inside a bucket).
+__global__ void k_count(int n, const int* __restrict__ bucket, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && bucket[i] >= 0) atomicAdd(cnt + bucket[i], 1);
+}
+__global__ void k_scatter(int n, const int* __restrict__ bucket, int* __restrict__ cursor, int* __restrict__ idx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && bucket[i] >= 0) idx[atomicAdd(cursor + bucket[i], 1)] = i;
+}
+__global__ void k_copy_int(int n, const int* __restrict__ a, int* __restrict__ b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+
+static int bucket_lists(int n, const int* bucket, int nb, DBuf<int>& ptr, DBuf<int>& idx, cudaStream_t s) {
+  AMGC_TRY(ptr.alloc(nb + 1));
+  DBuf<int> cur;
+  AMGC_TRY(cur.alloc(nb + 1));
+  AMGC_CUDA_TRY(cudaMemsetAsync(ptr.p, 0, (nb + 1) * sizeof(int), s));
+  if (n > 0) AMGC_LAUNCH(k_count<<<div_up(n, 256), 256, 0, s>>>(n, bucket, ptr.p));
+  int total = 0;
+  AMGC_TRY(exclusive_scan(ptr.p, ptr.p, nb + 1, s, &total));
+  AMGC_TRY(idx.alloc(std::max(total, 1)));
+  AMGC_LAUNCH(k_copy_int<<<div_up(nb + 1, 256), 256, 0, s>>>(nb + 1, ptr.p, cur.p));
+  if (n > 0) AMGC_LAUNCH(k_scatter<<<div_up(n, 256), 256, 0, s>>>(n, bucket, cur.p, idx.p));
+  if (nb > 0) AMGC_LAUNCH(k_sort_segments<<<div_up(nb, 128), 128, 0, s>>>(nb, ptr.p, idx.p, nullptr));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMGC_OK;
+}
+
+int check_status(amgc_hierarchy* h, const char* where) {
+  int st = 0;
+  AMGC_CUDA_TRY(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (st == 0) return AMGC_OK;
+  AMGC_CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
+  std::string m = std::string(where) + ":";
+  if (st & ST_BAD_INDEX) m += " index out of range or unsorted;";
+  if (st & ST_NO_DIAG) m += " missing diagonal block;";
+  if (st & ST_SINGULAR) m += " singular block or pivot;";
+  if (st & ST_RANK) m += " rank-deficient nullspace on an aggregate;";
+  if (st & ST_ROW_TOO_DENSE) m += " product row exceeds the hash capacity;";
+  if (st & ST_NONFINITE) m += " non-finite value;";
+  set_error(m);
+  if (st & (ST_SINGULAR | ST_RANK)) return AMGC_ESINGULAR;
+  return AMGC_EINVAL;
+}
+
+// ======================================================================== fine-level assembly
+__global__ void k_validate_bsr(int nbr, int nbc, const int* __restrict__ rp, const int* __restrict__ col,
+                               int require_diag, int* st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  int b = rp[i], e = rp[i + 1];
+  if (e < b) { set_status(st, ST_BAD_INDEX); return; }
+  bool diag = false;
+  for (int q = b; q < e; ++q) {
+    int c = col[q];
+    if (c < 0 || c >= nbc || (q > b && col[q - 1] >= c)) set_status(st, ST_BAD_INDEX);
+    if (c == i) diag = true;
+  }
+  if (require_diag && !diag) set_status(st, ST_NO_DIAG);
+}
+__global__ void k_validate_index(int n, const int* __restrict__ a, int hi, int* st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (a[i] < 0 || a[i] >= hi)) set_status(st, ST_BAD_INDEX);
+}
+__global__ void k_role(int n, const int* __restrict__ node, int* __restrict__ role, int* st) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  if (atomicCAS(role + node[j], -1, j) != -1) set_status(st, ST_BAD_INDEX);   // duplicate node
+}
+__global__ void k_role_clash(int n, const int* __restrict__ a, const int* __restrict__ b, int* st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && a[i] >= 0 && b[i] >= 0) set_status(st, ST_BAD_INDEX);
+}
+__global__ void k_b1_count(int nn, const int* __restrict__ sl_of, const int* __restrict__ ms_of,
+                           const int* __restrict__ mt_ptr, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  int c = 0;
+  if (sl_of[i] >= 0) c += 1;
+  if (ms_of[i] >= 0) c += mt_ptr[ms_of[i] + 1] - mt_ptr[ms_of[i]];
+  cnt[i] = c;
+}
+// B1 row i: slave node -> (j, D_j I3); master node l -> (j, -M_jl I3) for the sorted slaves j of column l.
+__global__ void k_b1_fill(int nn, const int* __restrict__ rp, const int* __restrict__ sl_of, const int* __restrict__ ms_of,
+                          const double* __restrict__ D, const int* __restrict__ mt_ptr, const int* __restrict__ mt_idx,
+                          const int* __restrict__ m_pos, const double* __restrict__ Mval, int* __restrict__ col,
+                          double* __restrict__ val) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  int q = rp[i];
+  auto put = [&](int j, double a) {
+    col[q] = j;
+    double* v = val + (int64_t)q * 9;
+    for (int t = 0; t < 9; ++t) v[t] = 0.0;
+    v[0] = v[4] = v[8] = a;
+    ++q;
+  };
+  if (sl_of[i] >= 0) put(sl_of[i], D[sl_of[i]]);
+  if (ms_of[i] >= 0) {
+    int l = ms_of[i];
+    for (int e = mt_ptr[l]; e < mt_ptr[l + 1]; ++e) put(mt_idx[e], -Mval[m_pos[e]]);
+  }
+}
+// M^T: per master column, the slave rows (mt_idx) and the positions in M's value array (m_pos)
+__global__ void k_mt_count(int ns, const int* __restrict__ mrp, const int* __restrict__ mcol, int nm,
+                           int* __restrict__ cnt, int* st) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ns) return;
+  for (int q = mrp[j]; q < mrp[j + 1]; ++q) {
+    int l = mcol[q];
+    if (l < 0 || l >= nm) { set_status(st, ST_BAD_INDEX); continue; }
+    atomicAdd(cnt + l, 1);
+  }
+}
+__global__ void k_mt_scatter(int ns, const int* __restrict__ mrp, const int* __restrict__ mcol, int nm,
+                             int* __restrict__ cur, int* __restrict__ mt_idx, int* __restrict__ m_pos) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ns) return;
+  for (int q = mrp[j]; q < mrp[j + 1]; ++q) {
+    int l = mcol[q];
+    if (l < 0 || l >= nm) continue;
+    int p = atomicAdd(cur + l, 1);
+    mt_idx[p] = j;
+    m_pos[p] = q;
+  }
+}
+__global__ void k_b2_count(int ns, const uint8_t* __restrict__ active, const int* __restrict__ mrp, int* __restrict__ cnt) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < ns) cnt[j] = active[j] ? 1 + (mrp[j + 1] - mrp[j]) : 0;
+}
+// B2 row j (active): n^T on the slave node (times D_j) and on the master nodes (times -M_jl),
+// sorted by node; Z block: active (0; -tau_xi; -tau_eta), inactive -I3.
+__global__ void k_b2_fill(int ns, const uint8_t* __restrict__ active, const int* __restrict__ rp,
+                          const int* __restrict__ slave_node, const int* __restrict__ master_node,
+                          const double* __restrict__ D, const int* __restrict__ mrp, const int* __restrict__ mcol,
+                          const double* __restrict__ mval, const double* __restrict__ triad, int* __restrict__ col,
+                          double* __restrict__ val, double* __restrict__ Z) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ns) return;
+  const double* T = triad + (int64_t)j * 9;
+  double* z = Z + (int64_t)j * 9;
+  if (!active[j]) {
+    for (int t = 0; t < 9; ++t) z[t] = 0.0;
+    z[0] = z[4] = z[8] = -1.0;
+    return;
+  }
+  z[0] = z[1] = z[2] = 0.0;
+  for (int t = 0; t < 3; ++t) {
+    z[3 + t] = -T[3 + t];
+    z[6 + t] = -T[6 + t];
+  }
+  int b = rp[j];
+  int q = b;
+  auto put = [&](int node, double a) {
+    // insertion into the sorted row
+    int p = q;
+    while (p > b && col[p - 1] > node) {
+      col[p] = col[p - 1];
+      for (int t = 0; t < 9; ++t) val[(int64_t)p * 9 + t] = val[(int64_t)(p - 1) * 9 + t];
+      --p;
+    }
+    col[p] = node;
+    double* v = val + (int64_t)p * 9;
+    v[0] = a * T[0];
+    v[1] = a * T[1];
+    v[2] = a * T[2];
+    for (int t = 3; t < 9; ++t) v[t] = 0.0;
+    ++q;
+  };
+  put(slave_node[j], D[j]);
+  for (int e = mrp[j]; e < mrp[j + 1]; ++e) put(master_node[mcol[e]], -mval[e]);
+}
+
+int build_fine_level(amgc_hierarchy* h, const amgc_bsr* K, const double* D, const amgc_csr* M,
+                     const int* slave_node, const int* master_node, const double* triad,
+                     const uint8_t* active, const int* body_id, const double* nullspace) {
+  cudaStream_t s = h->stream;
+  Level& L = h->L[0];
+  const int nn = K->n_brow, ns = M->n_row, nm = M->n_col;
+  L.nn = nn;
+  L.bu = 3;
+  L.nl = ns;
+  // --- K
+  int kn = 0;
+  AMGC_CUDA_TRY(cudaMemcpy(&kn, K->rowptr + nn, sizeof(int), cudaMemcpyDefault));
+  L.K.nbr = nn; L.K.nbc = nn; L.K.br = 3; L.K.bc = 3; L.K.nnzb = kn;
+  AMGC_TRY(L.K.rowptr.alloc(nn + 1));
+  AMGC_TRY(L.K.col.alloc(std::max(kn, 1)));
+  AMGC_TRY(L.K.val.alloc((size_t)std::max(kn, 1) * 9));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.K.rowptr.p, K->rowptr, (nn + 1) * sizeof(int), cudaMemcpyDefault, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.K.col.p, K->col, (size_t)kn * sizeof(int), cudaMemcpyDefault, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.K.val.p, K->val, (size_t)kn * 9 * sizeof(double), cudaMemcpyDefault, s));
+  AMGC_LAUNCH(k_validate_bsr<<<div_up(nn, 256), 256, 0, s>>>(nn, nn, L.K.rowptr.p, L.K.col.p, 1, h->status.p));
+  AMGC_TRY(check_status(h, "K"));
+  // --- per-node arrays
+  AMGC_TRY(L.body.alloc(nn));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.body.p, body_id, nn * sizeof(int), cudaMemcpyDefault, s));
+  AMGC_TRY(L.B.alloc((size_t)nn * 3 * 6));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.B.p, nullspace, (size_t)nn * 18 * sizeof(double), cudaMemcpyDefault, s));
+  // --- interface data
+  DBuf<double> dD, dMv, dT;
+  DBuf<int> dMrp, dMcol, dSl, dMs;
+  DBuf<uint8_t> dAct;
+  int mnnz = 0;
+  AMGC_CUDA_TRY(cudaMemcpy(&mnnz, M->rowptr + ns, sizeof(int), cudaMemcpyDefault));
+  AMGC_TRY(dD.alloc(std::max(ns, 1)));
+  AMGC_TRY(dMv.alloc(std::max(mnnz, 1)));
+  AMGC_TRY(dT.alloc((size_t)std::max(ns, 1) * 9));
+  AMGC_TRY(dMrp.alloc(ns + 1));
+  AMGC_TRY(dMcol.alloc(std::max(mnnz, 1)));
+  AMGC_TRY(dSl.alloc(std::max(ns, 1)));
+  AMGC_TRY(dMs.alloc(std::max(nm, 1)));
+  AMGC_TRY(dAct.alloc(std::max(ns, 1)));
+  if (ns > 0) {
+    AMGC_CUDA_TRY(cudaMemcpyAsync(dD.p, D, ns * sizeof(double), cudaMemcpyDefault, s));
+    AMGC_CUDA_TRY(cudaMemcpyAsync(dT.p, triad, (size_t)ns * 9 * sizeof(double), cudaMemcpyDefault, s));
+    AMGC_CUDA_TRY(cudaMemcpyAsync(dSl.p, slave_node, ns * sizeof(int), cudaMemcpyDefault, s));
+    AMGC_CUDA_TRY(cudaMemcpyAsync(dAct.p, active, ns, cudaMemcpyDefault, s));
+  }
+  AMGC_CUDA_TRY(cudaMemcpyAsync(dMrp.p, M->rowptr, (ns + 1) * sizeof(int), cudaMemcpyDefault, s));
+  if (mnnz > 0) {
+    AMGC_CUDA_TRY(cudaMemcpyAsync(dMv.p, M->val, (size_t)mnnz * sizeof(double), cudaMemcpyDefault, s));
+    AMGC_CUDA_TRY(cudaMemcpyAsync(dMcol.p, M->col, (size_t)mnnz * sizeof(int), cudaMemcpyDefault, s));
+  }
+  if (nm > 0) AMGC_CUDA_TRY(cudaMemcpyAsync(dMs.p, master_node, nm * sizeof(int), cudaMemcpyDefault, s));
+  if (ns > 0) AMGC_LAUNCH(k_validate_index<<<div_up(ns, 256), 256, 0, s>>>(ns, dSl.p, nn, h->status.p));
+  if (nm > 0) AMGC_LAUNCH(k_validate_index<<<div_up(nm, 256), 256, 0, s>>>(nm, dMs.p, nn, h->status.p));
+  AMGC_TRY(check_status(h, "interface node ids"));
+  // roles of the displacement nodes
+  DBuf<int> sl_of, ms_of;
+  AMGC_TRY(sl_of.alloc(nn));
+  AMGC_TRY(ms_of.alloc(nn));
+  AMGC_LAUNCH(k_fill_int<<<div_up(nn, 256), 256, 0, s>>>(nn, -1, sl_of.p));
+  AMGC_LAUNCH(k_fill_int<<<div_up(nn, 256), 256, 0, s>>>(nn, -1, ms_of.p));
+  if (ns > 0) AMGC_LAUNCH(k_role<<<div_up(ns, 256), 256, 0, s>>>(ns, dSl.p, sl_of.p, h->status.p));
+  if (nm > 0) AMGC_LAUNCH(k_role<<<div_up(nm, 256), 256, 0, s>>>(nm, dMs.p, ms_of.p, h->status.p));
+  AMGC_LAUNCH(k_role_clash<<<div_up(nn, 256), 256, 0, s>>>(nn, sl_of.p, ms_of.p, h->status.p));
+  // M^T
+  DBuf<int> mt_ptr, mt_cur, mt_idx, m_pos;
+  AMGC_TRY(mt_ptr.alloc(nm + 1));
+  AMGC_TRY(mt_cur.alloc(nm + 1));
+  AMGC_TRY(mt_idx.alloc(std::max(mnnz, 1)));
+  AMGC_TRY(m_pos.alloc(std::max(mnnz, 1)));
+  AMGC_CUDA_TRY(cudaMemsetAsync(mt_ptr.p, 0, (nm + 1) * sizeof(int), s));
+  if (ns > 0) AMGC_LAUNCH(k_mt_count<<<div_up(ns, 256), 256, 0, s>>>(ns, dMrp.p, dMcol.p, nm, mt_ptr.p, h->status.p));
+  AMGC_TRY(check_status(h, "mortar M"));
+  AMGC_TRY(exclusive_scan(mt_ptr.p, mt_ptr.p, nm + 1, s, nullptr));
+  AMGC_LAUNCH(k_copy_int<<<div_up(nm + 1, 256), 256, 0, s>>>(nm + 1, mt_ptr.p, mt_cur.p));
+  if (ns > 0) AMGC_LAUNCH(k_mt_scatter<<<div_up(ns, 256), 256, 0, s>>>(ns, dMrp.p, dMcol.p, nm, mt_cur.p, mt_idx.p, m_pos.p));
+  if (nm > 0) AMGC_LAUNCH(k_sort_segments<<<div_up(nm, 128), 128, 0, s>>>(nm, mt_ptr.p, mt_idx.p, m_pos.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  // --- B1 (nn x ns, 3x3)
+  L.B1.nbr = nn; L.B1.nbc = ns; L.B1.br = 3; L.B1.bc = 3;
+  AMGC_TRY(L.B1.rowptr.alloc(nn + 1));
+  AMGC_CUDA_TRY(cudaMemsetAsync(L.B1.rowptr.p, 0, (nn + 1) * sizeof(int), s));   // entry nn joins the scan
+  AMGC_LAUNCH(k_b1_count<<<div_up(nn, 256), 256, 0, s>>>(nn, sl_of.p, ms_of.p, mt_ptr.p, L.B1.rowptr.p));
+  int b1n = 0;
+  AMGC_TRY(exclusive_scan(L.B1.rowptr.p, L.B1.rowptr.p, nn + 1, s, &b1n));
+  L.B1.nnzb = b1n;
+  AMGC_TRY(L.B1.col.alloc(std::max(b1n, 1)));
+  AMGC_TRY(L.B1.val.alloc((size_t)std::max(b1n, 1) * 9));
+  AMGC_LAUNCH(k_b1_fill<<<div_up(nn, 256), 256, 0, s>>>(nn, L.B1.rowptr.p, sl_of.p, ms_of.p, dD.p, mt_ptr.p, mt_idx.p, m_pos.p,
+                                            dMv.p, L.B1.col.p, L.B1.val.p));
+  // --- B2 (ns x nn, 3x3) and Z
+  L.B2.nbr = ns; L.B2.nbc = nn; L.B2.br = 3; L.B2.bc = 3;
+  AMGC_TRY(L.B2.rowptr.alloc(ns + 1));
+  AMGC_CUDA_TRY(cudaMemsetAsync(L.B2.rowptr.p, 0, (ns + 1) * sizeof(int), s));   // entry ns joins the scan
+  if (ns > 0) AMGC_LAUNCH(k_b2_count<<<div_up(ns, 256), 256, 0, s>>>(ns, dAct.p, dMrp.p, L.B2.rowptr.p));
+  int b2n = 0;
+  AMGC_TRY(exclusive_scan(L.B2.rowptr.p, L.B2.rowptr.p, ns + 1, s, &b2n));
+  L.B2.nnzb = b2n;
+  AMGC_TRY(L.B2.col.alloc(std::max(b2n, 1)));
+  AMGC_TRY(L.B2.val.alloc((size_t)std::max(b2n, 1) * 9));
+  AMGC_TRY(L.Z.alloc((size_t)std::max(ns, 1) * 9));
+  if (ns > 0)
+    AMGC_LAUNCH(k_b2_fill<<<div_up(ns, 256), 256, 0, s>>>(ns, dAct.p, L.B2.rowptr.p, dSl.p, dMs.p, dD.p, dMrp.p, dMcol.p, dMv.p,
+                                              dT.p, L.B2.col.p, L.B2.val.p, L.Z.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(check_status(h, "interface assembly"));
+  // --- multiplier data
+  AMGC_TRY(L.Bl.alloc(std::max(ns, 1)));
+  AMGC_LAUNCH(k_fill_dbl<<<div_up(std::max(ns, 1), 256), 256, 0, s>>>(ns, 1.0, L.Bl.p));
+  AMGC_TRY(L.lm_dnode.alloc(std::max(ns, 1)));
+  if (ns > 0) AMGC_LAUNCH(k_copy_int<<<div_up(ns, 256), 256, 0, s>>>(ns, dSl.p, L.lm_dnode.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMGC_OK;
+}
+
+// ======================================================================== MIS-2 aggregation
+// Priority of node i: fmix32(i ^ seed) * 2^32 + i (MurmurHash3 finaliser, A. Appleby); the
+// stored value is priority + 1 for an undecided node and 0 otherwise.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+enum : int8_t { UND = 0, ROOT = 1, OUT = 2 };
+
+__global__ void k_mis_key(int n, const int8_t* __restrict__ state, uint32_t seed, unsigned long long* __restrict__ kv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long key = ((unsigned long long)fmix32((uint32_t)i ^ seed) << 32) | (unsigned long long)(uint32_t)i;
+  kv[i] = state[i] == UND ? key + 1ull : 0ull;
+}
+// out[i] = max(in[i], max over graph neighbours j of in[j]); the graph is K's pattern without
+// the diagonal and without couplings between different bodies.
+__global__ void k_mis_max(int n, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ body,
+                          const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long m = in[i];
+  const int bi = body[i];
+  for (int q = rp[i]; q < rp[i + 1]; ++q) {
+    int j = col[q];
+    if (j == i || body[j] != bi) continue;
+    unsigned long long v = in[j];
+    m = v > m ? v : m;
+  }
+  out[i] = m;
+}
+__global__ void k_mis_newroot(int n, const unsigned long long* __restrict__ kv, const unsigned long long* __restrict__ m2,
+                              int8_t* __restrict__ state, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int f = (state[i] == UND && kv[i] == m2[i]) ? 1 : 0;
+  flag[i] = f;
+}
+__global__ void k_mis_any(int n, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ body,
+                          const int* __restrict__ in, int* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = in[i];
+  const int bi = body[i];
+  for (int q = rp[i]; q < rp[i + 1] && !a; ++q) {
+    int j = col[q];
+    if (j == i || body[j] != bi) continue;
+    a |= in[j];
+  }
+  out[i] = a;
+}
+__global__ void k_mis_mark(int n, const int* __restrict__ newroot, const int* __restrict__ near2, int8_t* __restrict__ state,
+                           int* __restrict__ undecided) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int8_t st = state[i];
+  if (st == UND) {
+    if (newroot[i]) st = ROOT;
+    else if (near2[i]) st = OUT;
+    state[i] = st;
+  }
+  if (st == UND) atomicAdd(undecided, 1);
+}
+__global__ void k_root_flag(int n, const int8_t* __restrict__ state, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = state[i] == ROOT ? 1 : 0;
+}
+// phase 1/2: root -> own aggregate; neighbour of a root -> the root's aggregate
+__global__ void k_agg_phase2(int n, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ body,
+                             const int8_t* __restrict__ state, const int* __restrict__ rank, int* __restrict__ agg,
+                             int* __restrict__ roots) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (state[i] == ROOT) {
+    agg[i] = rank[i];
+    roots[rank[i]] = i;
+    return;
+  }
+  int a = -1;
+  const int bi = body[i];
+  for (int q = rp[i]; q < rp[i + 1]; ++q) {
+    int j = col[q];
+    if (j == i || body[j] != bi) continue;
+    if (state[j] == ROOT) { a = rank[j]; break; }
+  }
+  agg[i] = a;
+}
+// phase 3: unassigned node -> phase-2 aggregate with most shared edges, ties to the smallest id
+__global__ void k_agg_phase3(int n, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ body,
+                             const int* __restrict__ agg2, int* __restrict__ agg, int* st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (agg2[i] >= 0) { agg[i] = agg2[i]; return; }
+  const int bi = body[i];
+  int best = -1, best_cnt = 0;
+  const int b = rp[i], e = rp[i + 1];
+  for (int q = b; q < e; ++q) {
+    int j = col[q];
+    if (j == i || body[j] != bi) continue;
+    int a = agg2[j];
+    if (a < 0) continue;
+    int cnt = 0;
+    for (int r = b; r < e; ++r) {
+      int k = col[r];
+      if (k == i || body[k] != bi) continue;
+      cnt += agg2[k] == a;
+    }
+    if (cnt > best_cnt || (cnt == best_cnt && a < best)) { best = a; best_cnt = cnt; }
+  }
+  if (best < 0) set_status(st, ST_BAD_INDEX);
+  agg[i] = best;
+}
+
+static int mis2_aggregate(amgc_hierarchy* h, Level& L, DBuf<int>& roots, int* n_agg) {
+  cudaStream_t s = h->stream;
+  const int n = L.nn;
+  DBuf<int8_t> state;
+  DBuf<unsigned long long> kv, m1, m2;
+  DBuf<int> nr, a1, a2, cnt;
+  AMGC_TRY(state.alloc(n));
+  AMGC_TRY(kv.alloc(n));
+  AMGC_TRY(m1.alloc(n));
+  AMGC_TRY(m2.alloc(n));
+  AMGC_TRY(nr.alloc(n + 1));
+  AMGC_TRY(a1.alloc(n));
+  AMGC_TRY(a2.alloc(n));
+  AMGC_TRY(cnt.alloc(1));
+  AMGC_CUDA_TRY(cudaMemsetAsync(state.p, 0, n, s));
+  const int g = div_up(n, 256);
+  const int* rp = L.K.rowptr.p;
+  const int* col = L.K.col.p;
+  const int* body = L.body.p;
+  for (int round = 0; round < 10000; ++round) {
+    AMGC_LAUNCH(k_mis_key<<<g, 256, 0, s>>>(n, state.p, h->opts.seed, kv.p));
+    AMGC_LAUNCH(k_mis_max<<<g, 256, 0, s>>>(n, rp, col, body, kv.p, m1.p));
+    AMGC_LAUNCH(k_mis_max<<<g, 256, 0, s>>>(n, rp, col, body, m1.p, m2.p));
+    AMGC_LAUNCH(k_mis_newroot<<<g, 256, 0, s>>>(n, kv.p, m2.p, state.p, nr.p));
+    AMGC_LAUNCH(k_mis_any<<<g, 256, 0, s>>>(n, rp, col, body, nr.p, a1.p));
+    AMGC_LAUNCH(k_mis_any<<<g, 256, 0, s>>>(n, rp, col, body, a1.p, a2.p));
+    AMGC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int), s));
+    AMGC_LAUNCH(k_mis_mark<<<g, 256, 0, s>>>(n, nr.p, a2.p, state.p, cnt.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    int und = 0;
+    AMGC_CUDA_TRY(cudaMemcpyAsync(&und, cnt.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (und == 0) break;
+  }
+  // aggregate ids by ascending root id
+  AMGC_LAUNCH(k_root_flag<<<g, 256, 0, s>>>(n, state.p, nr.p));
+  int na = 0;
+  AMGC_TRY(exclusive_scan(nr.p, nr.p, n, s, &na));
+  if (na == 0) {
+    set_error("aggregation produced no aggregate");
+    return AMGC_EINVAL;
+  }
+  AMGC_TRY(roots.alloc(na));
+  AMGC_LAUNCH(k_agg_phase2<<<g, 256, 0, s>>>(n, rp, col, body, state.p, nr.p, a1.p, roots.p));
+  AMGC_TRY(L.agg.alloc(n));
+  AMGC_LAUNCH(k_agg_phase3<<<g, 256, 0, s>>>(n, rp, col, body, a1.p, L.agg.p, h->status.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(check_status(h, "aggregation"));
+  *n_agg = na;
+  return AMGC_OK;
+}
+
+// ======================================================================== multiplier aggregation (Algorithm 1)
+// Scanning the slave displacement DOFs in increasing order, the multiplier aggregate of a
+// displacement aggregate k is opened at the first slave DOF of k; since D couples each
+// multiplier node to exactly one displacement node, aggregate k's multiplier aggregate is
+// numbered by the rank of the smallest coupled displacement node of k.
+__global__ void k_lm_first(int nl, const int* __restrict__ lm_dnode, const int* __restrict__ agg, int* __restrict__ first) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  int d = lm_dnode[l];
+  atomicMin(first + agg[d], d);
+}
+__global__ void k_lm_mark(int nn, const int* __restrict__ agg, const int* __restrict__ first, int* __restrict__ mark) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nn) mark[i] = first[agg[i]] == i ? 1 : 0;
+}
+__global__ void k_lm_assign(int nl, const int* __restrict__ lm_dnode, const int* __restrict__ agg, const int* __restrict__ first,
+                            const int* __restrict__ rank, int* __restrict__ lagg, int* __restrict__ lm_dnode_c) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  int k = agg[lm_dnode[l]];
+  int L = rank[first[k]];
+  lagg[l] = L;
+  lm_dnode_c[L] = k;    // all members of L map to the same k
+}
+
+// ======================================================================== tentative prolongator by QR
+// One warp per aggregate: classical Gram-Schmidt with one re-orthogonalisation pass on the
+// aggregate's nullspace rows (member nodes ascending, DOF-minor); Q goes to P-hat's blocks,
+// R (positive diagonal) to the coarse nullspace.
+__global__ void k_tentative_qr(int n_agg, int bu, const int* __restrict__ mptr, const int* __restrict__ midx,
+                               const double* __restrict__ B, double* __restrict__ Pval, double* __restrict__ Bc, int* st) {
+  const int lane = threadIdx.x & 31;
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (a >= n_agg) return;
+  const int m0 = mptr[a], m1 = mptr[a + 1];
+  const int nrows = (m1 - m0) * bu;
+  auto addr = [&](int t, int c) -> int64_t {
+    int node = midx[m0 + t / bu];
+    return ((int64_t)node * bu + (t % bu)) * 6 + c;
+  };
+  for (int t = lane; t < nrows; t += 32)
+    for (int c = 0; c < 6; ++c) Pval[addr(t, c)] = B[addr(t, c)];
+  __syncwarp();
+  double R[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) R[i][j] = 0.0;
+  double rmax = 0.0;
+  for (int c = 0; c < 6; ++c) {
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int k = 0; k < c; ++k) {
+        double d = 0.0;
+        for (int t = lane; t < nrows; t += 32) d = fma(Pval[addr(t, k)], Pval[addr(t, c)], d);
+        d = warp_sum(d);
+        for (int t = lane; t < nrows; t += 32) Pval[addr(t, c)] -= d * Pval[addr(t, k)];
+        __syncwarp();
+        R[k][c] += d;
+      }
+    }
+    double nr = 0.0;
+    for (int t = lane; t < nrows; t += 32) {
+      double v = Pval[addr(t, c)];
+      nr = fma(v, v, nr);
+    }
+    nr = sqrt(warp_sum(nr));
+    R[c][c] = nr;
+    rmax = fmax(rmax, nr);
+    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    for (int t = lane; t < nrows; t += 32) Pval[addr(t, c)] *= inv;
+    __syncwarp();
+  }
+  double rmin = R[0][0];
+  for (int c = 1; c < 6; ++c) rmin = fmin(rmin, R[c][c]);
+  if (nrows < 6 || !(rmin > 1e-12 * rmax)) {
+    if (lane == 0) set_status(st, ST_RANK);
+  }
+  if (lane < 6) {
+    for (int j = 0; j < 6; ++j) Bc[((int64_t)a * 6 + lane) * 6 + j] = R[lane][j];
+  }
+}
+__global__ void k_tentative_pattern(int nn, const int* __restrict__ agg, int* __restrict__ rp, int* __restrict__ col) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nn) {
+    rp[i] = i;
+    col[i] = agg[i];
+  }
+  if (i == nn) rp[nn] = nn;
+}
+
+// multiplier tentative transfer: norms per aggregate (members ascending), weights per node
+__global__ void k_lm_norm(int nlc, const int* __restrict__ ptr, const int* __restrict__ idx, const double* __restrict__ Bl,
+                          double* __restrict__ norm) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= nlc) return;
+  double s = 0.0;
+  for (int e = ptr[L]; e < ptr[L + 1]; ++e) {
+    double v = Bl[idx[e]];
+    s += v * v;
+  }
+  norm[L] = sqrt(s);
+}
+__global__ void k_lm_weight(int nl, const int* __restrict__ lagg, const double* __restrict__ Bl, const double* __restrict__ norm,
+                            double* __restrict__ w) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < nl) w[l] = Bl[l] / norm[lagg[l]];
+}
+// P-hat^lambda as BSR (one block w_l I3 per row) and its transpose
+__global__ void k_pl_bsr(int nl, const int* __restrict__ lagg, const double* __restrict__ w, int* __restrict__ rp,
+                         int* __restrict__ col, double* __restrict__ val) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < nl) {
+    rp[l] = l;
+    col[l] = lagg[l];
+    double* v = val + (int64_t)l * 9;
+    for (int t = 0; t < 9; ++t) v[t] = 0.0;
+    v[0] = v[4] = v[8] = w[l];
+  }
+  if (l == nl) rp[nl] = nl;
+}
+__global__ void k_rl_bsr(int nlc, const int* __restrict__ ptr, const int* __restrict__ idx, const double* __restrict__ w,
+                         int* __restrict__ rp, int* __restrict__ col, double* __restrict__ val) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L < nlc) {
+    rp[L] = ptr[L];
+    for (int e = ptr[L]; e < ptr[L + 1]; ++e) {
+      int l = idx[e];
+      col[e] = l;
+      double* v = val + (int64_t)e * 9;
+      for (int t = 0; t < 9; ++t) v[t] = 0.0;
+      v[0] = v[4] = v[8] = w[l];
+    }
+  }
+  if (L == nlc) rp[nlc] = ptr[nlc];
+}
+// Z_c[L] = sum_{l in L} w_l^2 Z_l
+__global__ void k_zc(int nlc, const int* __restrict__ ptr, const int* __restrict__ idx, const double* __restrict__ w,
+                     const double* __restrict__ Z, double* __restrict__ Zc) {
+  int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= nlc) return;
+  double acc[9];
+  for (int t = 0; t < 9; ++t) acc[t] = 0.0;
+  for (int e = ptr[L]; e < ptr[L + 1]; ++e) {
+    int l = idx[e];
+    double w2 = w[l] * w[l];
+    for (int t = 0; t < 9; ++t) acc[t] += w2 * Z[(int64_t)l * 9 + t];
+  }
+  for (int t = 0; t < 9; ++t) Zc[(int64_t)L * 9 + t] = acc[t];
+}
+
+// ======================================================================== block SpGEMM C = A B
+// One warp per row of A with a shared-memory hash set of block columns (symbolic), then a
+// numeric pass that walks A's row in order and lets the lanes take B's entries: within one
+// A entry the lanes hit distinct C blocks, so no atomics are needed and the summation order
+// is fixed (deterministic results).
+constexpr int kHashCap = 1024;
+constexpr int kGemmWarps = 4;
+
+__device__ __forceinline__ int hash_insert(int* tab, int key) {
+  unsigned slot = ((unsigned)key * 2654435761u) & (kHashCap - 1);
+  for (int probe = 0; probe < kHashCap; ++probe) {
+    int prev = atomicCAS(tab + slot, -1, key);
+    if (prev == -1) return 1;
+    if (prev == key) return 0;
+    slot = (slot + 1) & (kHashCap - 1);
+  }
+  return -1;
+}
+
+// MODE 0: count unique columns per row into cnt; MODE 1: write sorted unique columns into ccol
+template <int MODE>
+__global__ void __launch_bounds__(kGemmWarps * 32)
+k_spgemm_symbolic(int nrow, const int* __restrict__ arp, const int* __restrict__ acol, const int* __restrict__ brp,
+                  const int* __restrict__ bcol, int* __restrict__ cnt, const int* __restrict__ crp,
+                  int* __restrict__ ccol, int* st) {
+  __shared__ int tab[kGemmWarps][kHashCap];
+  __shared__ int lst[kGemmWarps][kHashCap];
+  __shared__ int nlist[kGemmWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row = blockIdx.x * kGemmWarps + wid;
+  if (row >= nrow) return;
+  int* T = tab[wid];
+  for (int k = lane; k < kHashCap; k += 32) T[k] = -1;
+  __syncwarp();
+  int mine = 0;
+  bool overflow = false;
+  for (int e = arp[row]; e < arp[row + 1]; ++e) {
+    const int k = acol[e];
+    for (int t = brp[k] + lane; t < brp[k + 1]; t += 32) {
+      int r = hash_insert(T, bcol[t]);
+      if (r < 0) overflow = true;
+      else mine += r;
+    }
+  }
+  __syncwarp();
+  int total = mine;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+  if (__any_sync(0xffffffffu, overflow) || total > (kHashCap * 3) / 4) {
+    if (lane == 0) set_status(st, ST_ROW_TOO_DENSE);
+    if (MODE == 0 && lane == 0) cnt[row] = 0;
+    return;
+  }
+  if (MODE == 0) {
+    if (lane == 0) cnt[row] = total;
+    return;
+  }
+  // compact the keys, then rank them
+  int* Ls = lst[wid];
+  if (lane == 0) nlist[wid] = 0;
+  __syncwarp();
+  for (int base = 0; base < kHashCap; base += 32) {
+    int key = T[base + lane];
+    unsigned m = __ballot_sync(0xffffffffu, key >= 0);
+    int pos = nlist[wid] + __popc(m & ((1u << lane) - 1u));
+    if (key >= 0) Ls[pos] = key;
+    __syncwarp();
+    if (lane == 0) nlist[wid] += __popc(m);
+    __syncwarp();
+  }
+  const int nk = nlist[wid];
+  const int off = crp[row];
+  for (int q = lane; q < nk; q += 32) {
+    int key = Ls[q];
+    int rank = 0;
+    for (int r = 0; r < nk; ++r) rank += Ls[r] < key;
+    ccol[off + rank] = key;
+  }
+}
+
+template <int BR, int BK, int BC>
+__global__ void __launch_bounds__(kGemmWarps * 32)
+k_spgemm_numeric(int nrow, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
+                 const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
+                 const int* __restrict__ crp, const int* __restrict__ ccol, double* __restrict__ cval) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row = blockIdx.x * kGemmWarps + wid;
+  if (row >= nrow) return;
+  const int c0 = crp[row], c1 = crp[row + 1];
+  for (int64_t q = (int64_t)c0 * BR * BC + lane; q < (int64_t)c1 * BR * BC; q += 32) cval[q] = 0.0;
+  __syncwarp();
+  for (int e = arp[row]; e < arp[row + 1]; ++e) {
+    const int k = acol[e];
+    double a[BR * BK];
+#pragma unroll
+    for (int t = 0; t < BR * BK; ++t) a[t] = aval[(int64_t)e * BR * BK + t];
+    for (int t = brp[k] + lane; t < brp[k + 1]; t += 32) {
+      const int c = bcol[t];
+      int lo = c0, hi = c1 - 1;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (ccol[mid] < c) lo = mid + 1;
+        else hi = mid;
+      }
+      const double* b = bval + (int64_t)t * BK * BC;
+      double* cv = cval + (int64_t)lo * BR * BC;
+#pragma unroll
+      for (int i = 0; i < BR; ++i)
+#pragma unroll
+        for (int j = 0; j < BC; ++j) {
+          double s = cv[i * BC + j];
+#pragma unroll
+          for (int m = 0; m < BK; ++m) s = fma(a[i * BK + m], b[m * BC + j], s);
+          cv[i * BC + j] = s;
+        }
+    }
+    __syncwarp();
+  }
+}
+
+template <int BR, int BK, int BC>
+static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, cudaStream_t s) {
+  AMGC_LAUNCH(k_spgemm_numeric<BR, BK, BC><<<div_up(A.nbr, kGemmWarps), kGemmWarps * 32, 0, s>>>(
+      A.nbr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C) {
+  cudaStream_t s = h->stream;
+  if (A.bc != B.br || A.nbc != B.nbr) {
+    set_error("spgemm: shape mismatch");
+    return AMGC_EINVAL;
+  }
+  C.nbr = A.nbr;
+  C.nbc = B.nbc;
+  C.br = A.br;
+  C.bc = B.bc;
+  AMGC_TRY(C.rowptr.alloc(A.nbr + 1));
+  AMGC_CUDA_TRY(cudaMemsetAsync(C.rowptr.p, 0, (A.nbr + 1) * sizeof(int), s));
+  const int g = div_up(A.nbr, kGemmWarps);
+  if (A.nbr > 0)
+    AMGC_LAUNCH(k_spgemm_symbolic<0><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p, C.rowptr.p,
+                                                       nullptr, nullptr, h->status.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(check_status(h, "spgemm symbolic"));
+  int nnz = 0;
+  AMGC_TRY(exclusive_scan(C.rowptr.p, C.rowptr.p, A.nbr + 1, s, &nnz));
+  C.nnzb = nnz;
+  AMGC_TRY(C.col.alloc(std::max(nnz, 1)));
+  AMGC_TRY(C.val.alloc((size_t)std::max(nnz, 1) * C.br * C.bc));
+  if (A.nbr > 0)
+    AMGC_LAUNCH(k_spgemm_symbolic<1><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p, nullptr,
+                                                       C.rowptr.p, C.col.p, h->status.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  if (A.nbr == 0) return AMGC_OK;
+  const int br = A.br, bk = A.bc, bc = B.bc;
+#define AMGC_GEMM_CASE(R, K, C_)                                   \
+  if (br == R && bk == K && bc == C_) return spgemm_numeric<R, K, C_>(A, B, C, s);
+  AMGC_GEMM_CASE(3, 3, 6)
+  AMGC_GEMM_CASE(6, 3, 6)
+  AMGC_GEMM_CASE(3, 3, 3)
+  AMGC_GEMM_CASE(6, 3, 3)
+  AMGC_GEMM_CASE(6, 6, 6)
+  AMGC_GEMM_CASE(6, 6, 3)
+  AMGC_GEMM_CASE(3, 6, 6)
+#undef AMGC_GEMM_CASE
+  set_error("spgemm: unsupported block shape");
+  return AMGC_EINVAL;
+}
+
+// ======================================================================== BSR transpose
+__global__ void k_tr_count(int64_t nnzb, const int* __restrict__ col, int* __restrict__ cnt) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nnzb) atomicAdd(cnt + col[e], 1);
+}
+__global__ void k_tr_scatter(int nbr, const int* __restrict__ rp, const int* __restrict__ col, int* __restrict__ cur,
+                             int* __restrict__ trow, int* __restrict__ src) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    int p = atomicAdd(cur + col[e], 1);
+    trow[p] = i;
+    src[p] = e;
+  }
+}
+__global__ void k_tr_values(int64_t nnzb, int br, int bc, const int* __restrict__ src, const double* __restrict__ val,
+                            double* __restrict__ tval) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnzb) return;
+  const double* a = val + (int64_t)src[e] * br * bc;
+  double* t = tval + e * br * bc;
+  for (int i = 0; i < br; ++i)
+    for (int j = 0; j < bc; ++j) t[j * br + i] = a[i * bc + j];
+}
+
+static int bsr_transpose(amgc_hierarchy* h, const DBsr& A, DBsr& T) {
+  cudaStream_t s = h->stream;
+  T.nbr = A.nbc;
+  T.nbc = A.nbr;
+  T.br = A.bc;
+  T.bc = A.br;
+  T.nnzb = A.nnzb;
+  AMGC_TRY(T.rowptr.alloc(A.nbc + 1));
+  AMGC_TRY(T.col.alloc(std::max<int64_t>(A.nnzb, 1)));
+  AMGC_TRY(T.val.alloc((size_t)std::max<int64_t>(A.nnzb, 1) * A.br * A.bc));
+  DBuf<int> cur, src;
+  AMGC_TRY(cur.alloc(A.nbc + 1));
+  AMGC_TRY(src.alloc(std::max<int64_t>(A.nnzb, 1)));
+  AMGC_CUDA_TRY(cudaMemsetAsync(T.rowptr.p, 0, (A.nbc + 1) * sizeof(int), s));
+  if (A.nnzb > 0) AMGC_LAUNCH(k_tr_count<<<div_up(A.nnzb, 256), 256, 0, s>>>(A.nnzb, A.col.p, T.rowptr.p));
+  AMGC_TRY(exclusive_scan(T.rowptr.p, T.rowptr.p, A.nbc + 1, s, nullptr));
+  AMGC_LAUNCH(k_copy_int<<<div_up(A.nbc + 1, 256), 256, 0, s>>>(A.nbc + 1, T.rowptr.p, cur.p));
+  if (A.nbr > 0) AMGC_LAUNCH(k_tr_scatter<<<div_up(A.nbr, 256), 256, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, cur.p, T.col.p, src.p));
+  if (A.nbc > 0) AMGC_LAUNCH(k_sort_segments<<<div_up(A.nbc, 128), 128, 0, s>>>(A.nbc, T.rowptr.p, T.col.p, src.p));
+  if (A.nnzb > 0) AMGC_LAUNCH(k_tr_values<<<div_up(A.nnzb, 256), 256, 0, s>>>(A.nnzb, A.br, A.bc, src.p, A.val.p, T.val.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMGC_OK;
+}
+
+// ======================================================================== smoothed prolongator
+// P = P-hat - omega D^{-1} (K P-hat) on the pattern of K P-hat (K holds its diagonal blocks,
+// so that pattern contains P-hat's).
+template <int BU>
+__global__ void k_sa_values(int nn, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ agg,
+                            const double* __restrict__ phat, const double* __restrict__ dinv, double omega,
+                            double* __restrict__ val) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    double* v = val + (int64_t)e * BU * 6;
+    const bool own = col[e] == agg[i];
+    for (int r = 0; r < BU; ++r) {
+      const double d = omega * dinv[(int64_t)i * BU + r];
+      for (int c = 0; c < 6; ++c) {
+        double p = own ? phat[((int64_t)i * BU + r) * 6 + c] : 0.0;
+        v[r * 6 + c] = p - d * v[r * 6 + c];
+      }
+    }
+  }
+}
+
+// ======================================================================== smoother data
+template <int BU>
+__global__ void k_diag(int nn, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+                       int simplec, double* __restrict__ kdiag, double* __restrict__ dinv, double* __restrict__ atinv,
+                       int* st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  double dg[BU], as[BU];
+  for (int r = 0; r < BU; ++r) { dg[r] = 0.0; as[r] = 0.0; }
+  bool found = false;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const double* v = val + (int64_t)e * BU * BU;
+    if (col[e] == i) {
+      found = true;
+      for (int r = 0; r < BU; ++r) dg[r] = v[r * BU + r];
+    }
+    for (int r = 0; r < BU; ++r)
+      for (int c = 0; c < BU; ++c) as[r] += fabs(v[r * BU + c]);
+  }
+  if (!found) set_status(st, ST_NO_DIAG);
+  for (int r = 0; r < BU; ++r) {
+    if (!(dg[r] > 0.0) || !isfinite(dg[r])) set_status(st, ST_SINGULAR);
+    kdiag[(int64_t)i * BU + r] = dg[r];
+    dinv[(int64_t)i * BU + r] = 1.0 / dg[r];
+    atinv[(int64_t)i * BU + r] = 1.0 / (simplec ? as[r] : dg[r]);
+  }
+}
+// S_l = Z_l + sum_i B2[l,i] diag(atinv_i) B1[i,l]; Sinv_l = S_l^{-1}
+template <int BU>
+__global__ void k_schur(int nl, const int* __restrict__ rp2, const int* __restrict__ c2, const double* __restrict__ v2,
+                        const int* __restrict__ rp1, const int* __restrict__ c1, const double* __restrict__ v1,
+                        const double* __restrict__ atinv, const double* __restrict__ Z, double* __restrict__ Sinv, int* st) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  double S[9];
+  for (int t = 0; t < 9; ++t) S[t] = Z[(int64_t)l * 9 + t];
+  for (int e = rp2[l]; e < rp2[l + 1]; ++e) {
+    const int i = c2[e];
+    // find block (i, l) of B1
+    int lo = rp1[i], hi = rp1[i + 1] - 1, pos = -1;
+    while (lo <= hi) {
+      int mid = (lo + hi) >> 1;
+      int c = c1[mid];
+      if (c == l) { pos = mid; break; }
+      if (c < l) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    if (pos < 0) continue;
+    const double* b2 = v2 + (int64_t)e * 3 * BU;     // 3 x BU
+    const double* b1 = v1 + (int64_t)pos * BU * 3;   // BU x 3
+    for (int m = 0; m < BU; ++m) {
+      const double a = atinv[(int64_t)i * BU + m];
+      for (int r = 0; r < 3; ++r) {
+        const double x = b2[r * BU + m] * a;
+        for (int c = 0; c < 3; ++c) S[r * 3 + c] = fma(x, b1[m * 3 + c], S[r * 3 + c]);
+      }
+    }
+  }
+  // 3x3 inverse by cofactors
+  const double c00 = S[4] * S[8] - S[5] * S[7];
+  const double c01 = S[5] * S[6] - S[3] * S[8];
+  const double c02 = S[3] * S[7] - S[4] * S[6];
+  const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+  double nrm = 0.0;
+  for (int t = 0; t < 9; ++t) nrm = fmax(nrm, fabs(S[t]));
+  if (!(fabs(det) > 1e-14 * nrm * nrm * nrm) || !isfinite(det)) {
+    set_status(st, ST_SINGULAR);
+    return;
+  }
+  const double id = 1.0 / det;
+  double* o = Sinv + (int64_t)l * 9;
+  o[0] = c00 * id;
+  o[1] = (S[2] * S[7] - S[1] * S[8]) * id;
+  o[2] = (S[1] * S[5] - S[2] * S[4]) * id;
+  o[3] = c01 * id;
+  o[4] = (S[0] * S[8] - S[2] * S[6]) * id;
+  o[5] = (S[2] * S[3] - S[0] * S[5]) * id;
+  o[6] = c02 * id;
+  o[7] = (S[1] * S[6] - S[0] * S[7]) * id;
+  o[8] = (S[0] * S[4] - S[1] * S[3]) * id;
+}
+__global__ void k_nonempty(int n, const int* __restrict__ rp, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = rp[i + 1] > rp[i] ? 1 : 0;
+}
+__global__ void k_compact(int n, const int* __restrict__ flag_rp, const int* __restrict__ rank, int* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag_rp[i + 1] > flag_rp[i]) out[rank[i]] = i;
+}
+
+static int alloc_work(Level& L) {
+  const int n = L.rows();
+  AMGC_TRY(L.x.alloc(std::max(n, 1)));
+  AMGC_TRY(L.b.alloc(std::max(n, 1)));
+  AMGC_TRY(L.r.alloc(std::max(n, 1)));
+  AMGC_TRY(L.t.alloc(std::max(n, 1)));
+  AMGC_TRY(L.dlam.alloc(std::max(3 * L.nl, 1)));
+  return AMGC_OK;
+}
+
+int smoother_setup(amgc_hierarchy* h, int l) {
+  cudaStream_t s = h->stream;
+  Level& L = h->L[l];
+  const int nu = L.nu();
+  AMGC_TRY(L.kdiag.alloc(nu));
+  AMGC_TRY(L.dinv.alloc(nu));
+  AMGC_TRY(L.atinv.alloc(nu));
+  if (L.bu == 3)
+    AMGC_LAUNCH(k_diag<3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
+                                                L.dinv.p, L.atinv.p, h->status.p));
+  else
+    AMGC_LAUNCH(k_diag<6><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
+                                                L.dinv.p, L.atinv.p, h->status.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(check_status(h, "K diagonal"));
+  AMGC_TRY(L.Sinv.alloc((size_t)std::max(L.nl, 1) * 9));
+  if (L.nl > 0) {
+    if (L.bu == 3)
+      AMGC_LAUNCH(k_schur<3><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, L.B1.rowptr.p,
+                                                   L.B1.col.p, L.B1.val.p, L.atinv.p, L.Z.p, L.Sinv.p, h->status.p));
+    else
+      AMGC_LAUNCH(k_schur<6><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, L.B1.rowptr.p,
+                                                   L.B1.col.p, L.B1.val.p, L.atinv.p, L.Z.p, L.Sinv.p, h->status.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    AMGC_TRY(check_status(h, "Schur blocks"));
+  }
+  // rows of B1 with entries
+  DBuf<int> flag;
+  AMGC_TRY(flag.alloc(L.nn + 1));
+  AMGC_LAUNCH(k_nonempty<<<div_up(L.nn, 256), 256, 0, s>>>(L.nn, L.B1.rowptr.p, flag.p));
+  int cnt = 0;
+  AMGC_TRY(exclusive_scan(flag.p, flag.p, L.nn, s, &cnt));
+  L.n_b1_rows = cnt;
+  AMGC_TRY(L.b1_rows.alloc(std::max(cnt, 1)));
+  AMGC_LAUNCH(k_compact<<<div_up(L.nn, 256), 256, 0, s>>>(L.nn, L.B1.rowptr.p, flag.p, L.b1_rows.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  if (L.lam_max == 0.0) AMGC_TRY(lambda_max_estimate(h, L, &L.lam_max));
+  L.omega_j = h->opts.jacobi_omega > 0.0 ? h->opts.jacobi_omega : (4.0 / 3.0) / L.lam_max;
+  AMGC_TRY(alloc_work(L));
+  return AMGC_OK;
+}
+
+// ======================================================================== coarsening
+__global__ void k_gather_body(int n, const int* __restrict__ roots, const int* __restrict__ body, int* __restrict__ out) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n) out[a] = body[roots[a]];
+}
+
+int coarsen_level(amgc_hierarchy* h, int l) {
+  cudaStream_t s = h->stream;
+  Level& L = h->L[l];
+  // --- displacement aggregates
+  DBuf<int> roots;
+  int n_agg = 0;
+  AMGC_TRY(mis2_aggregate(h, L, roots, &n_agg));
+  L.n_agg = n_agg;
+  // --- multiplier aggregates (Algorithm 1)
+  DBuf<int> first, mark, lm_dnode_c;
+  AMGC_TRY(first.alloc(n_agg));
+  AMGC_TRY(mark.alloc(L.nn + 1));
+  AMGC_TRY(L.lagg.alloc(std::max(L.nl, 1)));
+  AMGC_TRY(lm_dnode_c.alloc(std::max(L.nl, 1)));
+  AMGC_LAUNCH(k_fill_int<<<div_up(n_agg, 256), 256, 0, s>>>(n_agg, 0x7fffffff, first.p));
+  if (L.nl > 0) AMGC_LAUNCH(k_lm_first<<<div_up(L.nl, 256), 256, 0, s>>>(L.nl, L.lm_dnode.p, L.agg.p, first.p));
+  AMGC_LAUNCH(k_lm_mark<<<div_up(L.nn, 256), 256, 0, s>>>(L.nn, L.agg.p, first.p, mark.p));
+  int n_lagg = 0;
+  AMGC_TRY(exclusive_scan(mark.p, mark.p, L.nn, s, &n_lagg));
+  if (L.nl > 0)
+    AMGC_LAUNCH(k_lm_assign<<<div_up(L.nl, 256), 256, 0, s>>>(L.nl, L.lm_dnode.p, L.agg.p, first.p, mark.p, L.lagg.p, lm_dnode_c.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  L.n_lagg = n_lagg;
+  // --- tentative displacement prolongator by QR
+  DBuf<int> mptr, midx;
+  AMGC_TRY(bucket_lists(L.nn, L.agg.p, n_agg, mptr, midx, s));
+  DBsr Phat;
+  Phat.nbr = L.nn; Phat.nbc = n_agg; Phat.br = L.bu; Phat.bc = 6; Phat.nnzb = L.nn;
+  AMGC_TRY(Phat.rowptr.alloc(L.nn + 1));
+  AMGC_TRY(Phat.col.alloc(L.nn));
+  AMGC_TRY(Phat.val.alloc((size_t)L.nn * L.bu * 6));
+  Level C;
+  C.nn = n_agg;
+  C.bu = 6;
+  C.nl = n_lagg;
+  AMGC_TRY(C.B.alloc((size_t)n_agg * 36));
+  AMGC_LAUNCH(k_tentative_pattern<<<div_up(L.nn + 1, 256), 256, 0, s>>>(L.nn, L.agg.p, Phat.rowptr.p, Phat.col.p));
+  AMGC_LAUNCH(k_tentative_qr<<<div_up((int64_t)n_agg * 32, 128), 128, 0, s>>>(n_agg, L.bu, mptr.p, midx.p, L.B.p, Phat.val.p, C.B.p,
+                                                                  h->status.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(check_status(h, "tentative prolongator"));
+  // --- multiplier tentative transfer
+  AMGC_TRY(bucket_lists(L.nl, L.lagg.p, n_lagg, L.rl_ptr, L.rl_idx, s));
+  AMGC_TRY(C.Bl.alloc(std::max(n_lagg, 1)));
+  AMGC_TRY(L.pl_w.alloc(std::max(L.nl, 1)));
+  DBsr Pl, Rl;
+  if (L.nl > 0) {
+    AMGC_LAUNCH(k_lm_norm<<<div_up(n_lagg, 128), 128, 0, s>>>(n_lagg, L.rl_ptr.p, L.rl_idx.p, L.Bl.p, C.Bl.p));
+    AMGC_LAUNCH(k_lm_weight<<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.lagg.p, L.Bl.p, C.Bl.p, L.pl_w.p));
+    Pl.nbr = L.nl; Pl.nbc = n_lagg; Pl.br = 3; Pl.bc = 3; Pl.nnzb = L.nl;
+    AMGC_TRY(Pl.rowptr.alloc(L.nl + 1));
+    AMGC_TRY(Pl.col.alloc(L.nl));
+    AMGC_TRY(Pl.val.alloc((size_t)L.nl * 9));
+    AMGC_LAUNCH(k_pl_bsr<<<div_up(L.nl + 1, 128), 128, 0, s>>>(L.nl, L.lagg.p, L.pl_w.p, Pl.rowptr.p, Pl.col.p, Pl.val.p));
+    Rl.nbr = n_lagg; Rl.nbc = L.nl; Rl.br = 3; Rl.bc = 3; Rl.nnzb = L.nl;
+    AMGC_TRY(Rl.rowptr.alloc(n_lagg + 1));
+    AMGC_TRY(Rl.col.alloc(L.nl));
+    AMGC_TRY(Rl.val.alloc((size_t)L.nl * 9));
+    AMGC_LAUNCH(k_rl_bsr<<<div_up(n_lagg + 1, 128), 128, 0, s>>>(n_lagg, L.rl_ptr.p, L.rl_idx.p, L.pl_w.p, Rl.rowptr.p, Rl.col.p,
+                                                      Rl.val.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  // --- lambda_max and smoothed prolongator
+  if (L.kdiag.p == nullptr) AMGC_TRY(smoother_setup(h, l));
+  if (h->opts.transfer == 1) {
+    AMGC_TRY(spgemm(h, L.K, Phat, L.P));
+    const double omega = h->opts.sa_omega / L.lam_max;
+    if (L.bu == 3)
+      AMGC_LAUNCH(k_sa_values<3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.P.rowptr.p, L.P.col.p, L.agg.p, Phat.val.p, L.dinv.p,
+                                                       omega, L.P.val.p));
+    else
+      AMGC_LAUNCH(k_sa_values<6><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.P.rowptr.p, L.P.col.p, L.agg.p, Phat.val.p, L.dinv.p,
+                                                       omega, L.P.val.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  } else {
+    L.P = std::move(Phat);
+  }
+  AMGC_TRY(bsr_transpose(h, L.P, L.R));
+  // --- Galerkin products
+  {
+    DBsr AP;
+    AMGC_TRY(spgemm(h, L.K, L.P, AP));
+    AMGC_TRY(spgemm(h, L.R, AP, C.K));
+  }
+  if (L.nl > 0) {
+    DBsr B1P, B2P;
+    AMGC_TRY(spgemm(h, L.B1, Pl, B1P));
+    AMGC_TRY(spgemm(h, L.R, B1P, C.B1));
+    AMGC_TRY(spgemm(h, L.B2, L.P, B2P));
+    AMGC_TRY(spgemm(h, Rl, B2P, C.B2));
+    AMGC_TRY(C.Z.alloc((size_t)n_lagg * 9));
+    AMGC_LAUNCH(k_zc<<<div_up(n_lagg, 128), 128, 0, s>>>(n_lagg, L.rl_ptr.p, L.rl_idx.p, L.pl_w.p, L.Z.p, C.Z.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  } else {
+    C.B1.nbr = n_agg; C.B1.nbc = 0; C.B1.br = 6; C.B1.bc = 3;
+    AMGC_TRY(C.B1.rowptr.alloc(n_agg + 1));
+    AMGC_CUDA_TRY(cudaMemsetAsync(C.B1.rowptr.p, 0, (n_agg + 1) * sizeof(int), s));
+    C.B2.nbr = 0; C.B2.nbc = n_agg; C.B2.br = 3; C.B2.bc = 6;
+    AMGC_TRY(C.B2.rowptr.alloc(1));
+    AMGC_CUDA_TRY(cudaMemsetAsync(C.B2.rowptr.p, 0, sizeof(int), s));
+  }
+  AMGC_TRY(check_status(h, "Galerkin products"));
+  // --- coarse per-node data
+  AMGC_TRY(C.body.alloc(n_agg));   // body of a coarse node = body of its root (filled below)
+  AMGC_TRY(C.lm_dnode.alloc(std::max(n_lagg, 1)));
+  if (n_lagg > 0) AMGC_LAUNCH(k_copy_int<<<div_up(n_lagg, 256), 256, 0, s>>>(n_lagg, lm_dnode_c.p, C.lm_dnode.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  h->L.push_back(std::move(C));
+  // (push_back may move the levels; re-fetch the references)
+  Level& Lf = h->L[l];
+  Level& Cn = h->L[l + 1];
+  AMGC_LAUNCH(k_gather_body<<<div_up(n_agg, 256), 256, 0, s>>>(n_agg, roots.p, Lf.body.p, Cn.body.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMGC_OK;
+}
+
+// ======================================================================== coarsest level: dense inverse
+template <int BR, int BC>
+__global__ void k_dense_put(int nbr, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+                            int row0, int col0, double sign, int n, double* __restrict__ A) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const double* v = val + (int64_t)e * BR * BC;
+    for (int r = 0; r < BR; ++r)
+      for (int c = 0; c < BC; ++c)
+        A[(int64_t)(row0 + i * BR + r) * n + col0 + col[e] * BC + c] = sign * v[r * BC + c];
+  }
+}
+__global__ void k_dense_z(int nl, const double* __restrict__ Z, int off, int n, double* __restrict__ A) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) A[(int64_t)(off + 3 * l + r) * n + off + 3 * l + c] = -Z[(int64_t)l * 9 + r * 3 + c];
+}
+// Gauss-Jordan step k, single block: pivot search (largest |A[i][k]|, i >= k, ties to the
+// smallest i), row swap, scaling of the pivot row, and the multiplier column f.
+__global__ void k_gj_pivot(int n, int k, double* __restrict__ A, int* __restrict__ piv, double* __restrict__ f, int* st) {
+  __shared__ double bv[1024];
+  __shared__ int bi[1024];
+  double best = -1.0;
+  int besti = n;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    double v = fabs(A[(int64_t)i * n + k]);
+    if (v > best || (v == best && i < besti)) { best = v; besti = i; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = besti;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      double v = bv[threadIdx.x + o];
+      int ii = bi[threadIdx.x + o];
+      if (v > bv[threadIdx.x] || (v == bv[threadIdx.x] && ii < bi[threadIdx.x])) {
+        bv[threadIdx.x] = v;
+        bi[threadIdx.x] = ii;
+      }
+    }
+    __syncthreads();
+  }
+  const int p = bi[0];
+  const double pmax = bv[0];
+  if (threadIdx.x == 0) piv[k] = p;
+  if (p != k && p < n) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double t = A[(int64_t)k * n + j];
+      A[(int64_t)k * n + j] = A[(int64_t)p * n + j];
+      A[(int64_t)p * n + j] = t;
+    }
+  }
+  __syncthreads();
+  double pv = A[(int64_t)k * n + k];
+  if (!(pmax > 0.0) || !isfinite(pv)) {
+    if (threadIdx.x == 0) set_status(st, ST_SINGULAR);
+    pv = 1.0;
+  }
+  __syncthreads();
+  // multiplier column (taken before the pivot row is scaled; column k is then cleared)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    f[i] = (i == k) ? 0.0 : A[(int64_t)i * n + k];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (i != k) A[(int64_t)i * n + k] = 0.0;
+  if (threadIdx.x == 0) A[(int64_t)k * n + k] = 1.0;
+  __syncthreads();
+  const double inv = 1.0 / pv;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) A[(int64_t)k * n + j] *= inv;
+}
+__global__ void k_gj_update(int n, int k, double* __restrict__ A, const double* __restrict__ f) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  if (i == k) return;
+  const double fi = f[i];
+  if (fi != 0.0) A[idx] -= fi * A[(int64_t)k * n + j];
+}
+// undo the row interchanges: swap columns k and piv[k] for k = n-1 .. 0 (one thread per row)
+__global__ void k_gj_unscramble(int n, const int* __restrict__ piv, double* __restrict__ A) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double* row = A + (int64_t)i * n;
+  for (int k = n - 1; k >= 0; --k) {
+    int p = piv[k];
+    if (p != k) {
+      double t = row[k];
+      row[k] = row[p];
+      row[p] = t;
+    }
+  }
+}
+
+int coarse_setup(amgc_hierarchy* h, int l) {
+  cudaStream_t s = h->stream;
+  Level& L = h->L[l];
+  const int n = L.rows();
+  const int nu = L.nu();
+  AMGC_TRY(L.Ainv.alloc((size_t)n * n));
+  AMGC_CUDA_TRY(cudaMemsetAsync(L.Ainv.p, 0, (size_t)n * n * sizeof(double), s));
+  if (L.bu == 3) {
+    AMGC_LAUNCH(k_dense_put<3, 3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, 0, 0, 1.0, n, L.Ainv.p));
+    if (L.nl > 0) {
+      AMGC_LAUNCH(k_dense_put<3, 3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.B1.rowptr.p, L.B1.col.p, L.B1.val.p, 0, nu, 1.0, n,
+                                                          L.Ainv.p));
+      AMGC_LAUNCH(k_dense_put<3, 3><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, nu, 0, 1.0, n,
+                                                          L.Ainv.p));
+    }
+  } else {
+    AMGC_LAUNCH(k_dense_put<6, 6><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, 0, 0, 1.0, n, L.Ainv.p));
+    if (L.nl > 0) {
+      AMGC_LAUNCH(k_dense_put<6, 3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.B1.rowptr.p, L.B1.col.p, L.B1.val.p, 0, nu, 1.0, n,
+                                                          L.Ainv.p));
+      AMGC_LAUNCH(k_dense_put<3, 6><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, nu, 0, 1.0, n,
+                                                          L.Ainv.p));
+    }
+  }
+  if (L.nl > 0) AMGC_LAUNCH(k_dense_z<<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.Z.p, nu, n, L.Ainv.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  DBuf<int> piv;
+  DBuf<double> f;
+  AMGC_TRY(piv.alloc(n));
+  AMGC_TRY(f.alloc(n));
+  const int64_t nn2 = (int64_t)n * n;
+  for (int k = 0; k < n; ++k) {
+    AMGC_LAUNCH(k_gj_pivot<<<1, 1024, 0, s>>>(n, k, L.Ainv.p, piv.p, f.p, h->status.p));
+    AMGC_LAUNCH(k_gj_update<<<div_up(nn2, 256), 256, 0, s>>>(n, k, L.Ainv.p, f.p));
+  }
+  AMGC_LAUNCH(k_gj_unscramble<<<div_up(n, 128), 128, 0, s>>>(n, piv.p, L.Ainv.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(check_status(h, "coarsest factorisation"));
+  AMGC_TRY(alloc_work(L));
+  return AMGC_OK;
+}
+
+}  // namespace amgc

@@ -112,12 +112,24 @@ def block_pattern(conn: np.ndarray, n_nodes: int):
 
 
 def assemble_bsr(coords, conn, E_elem, nu, n_nodes, chunk=65536):
-    """Assemble K as node-blocked CSR: (rowptr, col, val (nnzb,3,3))."""
+    """Assemble K as node-blocked CSR: (rowptr, col, val (nnzb,3,3)).
+
+    Elements that are translates of the body's last element (all but the jittered ones on a
+    structured brick) share its unit-modulus matrix, scaled by their own E.
+    """
     rowptr, cols, keys = block_pattern(conn, n_nodes)
     val = np.zeros((keys.size, 3, 3))
+    rel = coords[conn] - coords[conn[:, :1]]
+    h = np.abs(rel[-1]).max()
+    same = np.abs(rel - rel[-1][None]).max(axis=(1, 2)) <= 1e-12 * h
+    K_ref = hex8_stiffness(coords[conn[-1:]], np.ones(1), nu)[0]
     for s in range(0, conn.shape[0], chunk):
         cc = conn[s:s + chunk]
-        Ke = hex8_stiffness(coords[cc], E_elem[s:s + chunk], nu)
+        sm = same[s:s + chunk]
+        Ke = np.empty((cc.shape[0], 24, 24))
+        Ke[sm] = K_ref[None] * E_elem[s:s + chunk][sm][:, None, None]
+        if np.any(~sm):
+            Ke[~sm] = hex8_stiffness(coords[cc[~sm]], E_elem[s:s + chunk][~sm], nu)
         blk = Ke.reshape(-1, 8, 3, 8, 3).transpose(0, 1, 3, 2, 4)      # (ne,8,8,3,3)
         r = np.repeat(cc, 8, axis=1).ravel()
         c = np.tile(cc, (1, 8)).ravel()

@@ -57,7 +57,7 @@ def quad_map(X: np.ndarray, xi, eta):
     return x, J
 
 
-def quad_inverse_map(X: np.ndarray, pts: np.ndarray, iters: int = 30, tol: float = 1e-15):
+def quad_inverse_map(X: np.ndarray, pts: np.ndarray, iters: int = 30, tol: float = 1e-14):
     """Newton inverse of the bilinear map for points pts (n,2) -> (xi, eta)."""
     xi = np.zeros(pts.shape[0])
     eta = np.zeros(pts.shape[0])

@@ -1,0 +1,167 @@
+"""GPU parity: the CUDA library (through the C-ABI) against the FP64 oracle.
+
+Integer outputs (aggregates, multiplier aggregates, sparsity patterns) must agree bit for
+bit; FP64 values within 1e-10 relative; solves must reach the 1e-8 relative residual.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle.amg import Options, setup as oracle_setup  # noqa: E402
+from oracle.krylov import fgmres  # noqa: E402
+from paper_1912_09056_gb300 import amgc  # noqa: E402
+from paper_1912_09056_gb300.problem import two_block_problem, workload  # noqa: E402
+
+RTOL = 1e-10
+
+
+def rel(a, b):
+    d = np.abs(np.asarray(a) - np.asarray(b)).max() if np.size(a) else 0.0
+    s = np.abs(np.asarray(b)).max() if np.size(b) else 1.0
+    return d / (s if s > 0 else 1.0)
+
+
+def _pattern(M):
+    P = M.pat.tocsr()
+    P.sort_indices()
+    return P.indptr.astype(np.int32), P.indices.astype(np.int32)
+
+
+def _check_block(h, level, prefix, M, what):
+    rp, col = _pattern(M)
+    g_rp = h.export(level, f"{prefix}_rowptr")
+    g_col = h.export(level, f"{prefix}_col")
+    assert np.array_equal(g_rp, rp), f"{what}: row pointers differ on level {level}"
+    assert np.array_equal(g_col, col), f"{what}: block columns differ on level {level}"
+    blocks = M.blocks()
+    if blocks.size:
+        g_val = h.export(level, f"{prefix}_val").reshape(blocks.shape)
+        assert rel(g_val, blocks) <= RTOL, f"{what}: values differ on level {level}: {rel(g_val, blocks):.2e}"
+
+
+def compare_hierarchy(h, ref):
+    st = h.stats()
+    assert st["n_levels"] == ref.n_levels
+    for l, L in enumerate(ref.levels):
+        assert st["rows"][l] == L.rows and st["disp_nodes"][l] == L.nn and st["lm_nodes"][l] == L.nl
+        _check_block(h, l, "k", L.K, "K")
+        _check_block(h, l, "b1", L.B1, "B1")
+        _check_block(h, l, "b2", L.B2, "B2")
+        assert rel(h.export(l, "z").reshape(-1, 3, 3), L.Z) <= RTOL
+        if l < ref.n_levels - 1:
+            assert np.array_equal(h.export(l, "agg"), L.agg.astype(np.int32)), f"aggregates differ on level {l}"
+            assert np.array_equal(h.export(l, "lagg"), L.lagg.astype(np.int32)), f"LM aggregates differ on level {l}"
+            _check_block(h, l, "p", L.P, "P")
+            lam_max, omega = h.export(l, "omega")
+            assert abs(lam_max - L.lam_max) <= 1e-12 * L.lam_max
+            assert abs(omega - L.omega_j) <= 1e-12 * L.omega_j
+            assert rel(h.export(l, "atinv"), L.at_inv) <= RTOL
+            assert rel(h.export(l, "sinv").reshape(-1, 3, 3), L.S_inv) <= RTOL
+            w = np.asarray(L.Pl.val.sum(axis=1)).ravel()[0::3]
+            assert rel(h.export(l, "pl_w"), w) <= RTOL
+            Bn = h.export(l + 1, "nullspace").reshape(-1, 6)
+            assert rel(Bn, ref.levels[l + 1].B) <= RTOL
+        else:
+            Ad = L.A().toarray()
+            inv = h.export(l, "coarse_inv").reshape(Ad.shape)
+            ref_inv = np.linalg.inv(Ad)
+            # explicit inverse: agreement limited by cond(A_c) * eps
+            assert rel(inv, ref_inv) <= 1e-16 * np.linalg.cond(Ad) * 100
+
+
+def vcycle_and_apply(h, ref, n, seed=0):
+    rng = np.random.default_rng(seed)
+    r = rng.standard_normal(n)
+    rd = torch.from_numpy(r).cuda()
+    zd = torch.empty_like(rd)
+    h.vcycle(rd, zd)
+    yd = torch.empty_like(rd)
+    h.apply(rd, yd)
+    torch.cuda.synchronize()
+    z_ref = ref.vcycle(r)
+    y_ref = ref.A0() @ r
+    ez = np.linalg.norm(zd.cpu().numpy() - z_ref) / np.linalg.norm(z_ref)
+    ey = np.linalg.norm(yd.cpu().numpy() - y_ref) / np.linalg.norm(y_ref)
+    return ez, ey
+
+
+CASES = {
+    "tiny_PA_3lvl": (lambda: workload(0), dict(levels_max=3, coarse_max_rows=0, transfer=0)),
+    "tiny_SA_3lvl": (lambda: workload(0), dict(levels_max=3, coarse_max_rows=0, transfer=1)),
+    "small_tilted_partial_SA": (
+        lambda: two_block_problem(master_n=(13, 12, 11), slave_n=(10, 11, 9), E_slave=10.0, tilt_deg=5.0, seed=11,
+                                  active_fraction=0.6),
+        dict(levels_max=4, coarse_max_rows=200, transfer=1)),
+    "small_simplec_2sweeps": (
+        lambda: two_block_problem(master_n=(9, 9, 9), slave_n=(8, 8, 8), seed=5, active_fraction=0.5),
+        dict(levels_max=3, coarse_max_rows=0, transfer=1, simplec=1, smoother_sweeps=2, jacobi_sweeps=2)),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_hierarchy_vcycle_and_solve_match_oracle(case):
+    make, opts = CASES[case]
+    prob = make()
+    h = amgc.setup(prob, **opts)
+    ref = oracle_setup(prob, Options(**opts))
+    compare_hierarchy(h, ref)
+    ez, ey = vcycle_and_apply(h, ref, prob.n)
+    assert ey <= 1e-13, f"saddle apply differs: {ey:.2e}"
+    assert ez <= RTOL, f"V-cycle differs: {ez:.2e}"
+    b = torch.from_numpy(prob.rhs).cuda()
+    x = torch.zeros_like(b)
+    it, relres, _ = h.solve(b, x)
+    xr, it_ref, _ = fgmres(ref.A0(), prob.rhs, ref.vcycle, tol=1e-8)
+    A = ref.A0()
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(prob.rhs - A @ xg) <= 1e-8 * np.linalg.norm(prob.rhs)
+    assert abs(it - it_ref) <= 2, (it, it_ref)
+    assert np.linalg.norm(xg - xr) <= 1e-6 * np.linalg.norm(xr)
+    # host-buffer entry point gives the same solution
+    xh, it_h, rr_h, _ = h.solve_host(prob.rhs)
+    assert it_h == it and np.array_equal(xh, xg)
+    h.close()
+
+
+def test_setup_is_deterministic():
+    prob = two_block_problem(master_n=(10, 10, 10), slave_n=(9, 9, 9), seed=2, tilt_deg=3.0, active_fraction=0.7)
+    opts = dict(levels_max=3, coarse_max_rows=0, transfer=1)
+    h1 = amgc.setup(prob, **opts)
+    h2 = amgc.setup(prob, **opts)
+    for what in ("agg", "lagg", "p_col", "p_val", "sinv"):
+        assert np.array_equal(h1.export(0, what), h2.export(0, what)), what
+    for what in ("k_col", "k_val", "b1_val", "b2_val"):
+        assert np.array_equal(h1.export(1, what), h2.export(1, what)), what
+    h1.close()
+    h2.close()
+
+
+def test_rejects_bad_input():
+    prob = workload(0)
+    bad = workload(0)
+    bad.K_col = bad.K_col.copy()
+    bad.K_col[5] = prob.n_nodes + 7          # column out of range
+    with pytest.raises(amgc.AmgcError) as e:
+        amgc.setup(bad, levels_max=3, coarse_max_rows=0)
+    assert e.value.code == amgc.AMGC_EINVAL
+    bad = workload(0)
+    bad.slave_node = bad.slave_node.copy()
+    bad.slave_node[0] = bad.slave_node[1]    # duplicate slave node
+    with pytest.raises(amgc.AmgcError):
+        amgc.setup(bad, levels_max=3, coarse_max_rows=0)
+    # non-finite right-hand side -> breakdown, not a hang
+    h = amgc.setup(prob, levels_max=3, coarse_max_rows=0)
+    b = torch.from_numpy(prob.rhs).cuda()
+    b[3] = float("nan")
+    x = torch.zeros_like(b)
+    _, _, code = h.solve(b, x, check=False)
+    assert code == amgc.AMGC_BREAKDOWN
+    # iteration limit -> not converged
+    h2 = amgc.setup(prob, levels_max=3, coarse_max_rows=0, fgmres_maxit=2)
+    it, rr, code = h2.solve(torch.from_numpy(prob.rhs).cuda(), x, check=False)
+    assert code == amgc.AMGC_NOT_CONVERGED and it == 2 and rr > 1e-8
+    h.close()
+    h2.close()
