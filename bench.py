@@ -243,19 +243,59 @@ def main_gpu(args):
     torch.cuda.synchronize()
     solve_ms = ev[0].elapsed_time(ev[1]) / reps
     vcycle_ms = ev[2].elapsed_time(ev[3]) / nv
+    # ---- FP32 cycle (FP32 storage and arithmetic inside the V-cycle, FP64 FGMRES)
+    opts32 = amgc.default_options(precision=32, **OPTS)
+    h32 = amgc.setup(dprob, opts32)
+    x32 = torch.zeros_like(rhs_d)
+    h32.solve(rhs_d, x32)
+    torch.cuda.synchronize()
+    ev32 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev32[0].record()
+    for _ in range(reps):
+        it32, rr32, _ = h32.solve(rhs_d, x32)
+    ev32[1].record()
+    ev32[2].record()
+    for _ in range(nv):
+        h32.vcycle(r, z)
+    ev32[3].record()
+    torch.cuda.synchronize()
+    h32.profile(True)
+    h32.solve(rhs_d, x32)
+    kms32, kl32, kb32, _ = h32.profile_read()
+    h32.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        hh = amgc.setup(dprob, opts32)
+        hh.solve(rhs_d, x32)
+        hh.close()
+    torch.cuda.synchronize()
+    step32_ms = 1e3 * (time.perf_counter() - t0) / reps
+    fp32 = {"step_ms": round(step32_ms, 3), "solve_ms": round(ev32[0].elapsed_time(ev32[1]) / reps, 3),
+            "iters": it32, "relres": rr32, "vcycle_ms": round(ev32[2].elapsed_time(ev32[3]) / nv, 4),
+            "k_apply_us": round(1e3 * kms32 / kl32, 2) if kl32 else None,
+            "k_apply_gbs": round((kb32 / kl32) / (kms32 / kl32 * 1e-3) / 1e9, 1) if kl32 else None}
+    if kl32:
+        fp32["k_apply_hbm_frac"] = round(fp32["k_apply_gbs"] / float(
+            json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else fp32["k_apply_gbs"] / 6800.0, 4)
     # ---- dominant kernel: fine-level K apply, timed by events on its launching stream
     h.profile(True)
     for _ in range(reps):
         h.solve(rhs_d, x_d)
-    kms, kl, kbytes = h.profile_read()
+    kms, kl, kbytes, kflops = h.profile_read()
     h.profile(False)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = (kbytes / kl) / (kms / kl * 1e-3) / 1e9 if kl else 0.0
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # FP64 peak from the nominal GB300 figures: 1.25 TFLOP/s = 152 SMs x 2.07 GHz x 4 FLOP/clk/SM
+    fp64_peak = 152 * 2.07 * 4.0
+    t_launch = kms / kl * 1e-3 if kl else float("nan")
+    achieved_gbs = (kbytes / kl) / t_launch / 1e9 if kl else 0.0
+    achieved_gflops = (kflops / kl) / t_launch / 1e9 if kl else 0.0
     traffic = None
     try:
         prof = json.load(open(os.path.join(ROOT, "profiles", "k_apply_traffic.json")))
@@ -308,11 +348,16 @@ def main_gpu(args):
                        "parallelism": f"replicas x{world}"},
             "iters": iters[-1], "relres": relres[-1], "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
             "vcycle_ms": round(vcycle_ms, 4),
-            "roofline": {"bound": "hbm", "kernel": "fine-level K apply (k_rowop<3,3,3>)",
-                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+            "fp32_cycle": fp32,
+            "roofline": {"bound": "alu", "kernel": "fine-level K apply, FP64 (k_sell<3,3,*>)",
+                         "achieved": round(achieved_gflops, 1), "peak": round(fp64_peak, 1), "unit": "GFLOP/s",
+                         "frac": round(achieved_gflops / fp64_peak, 4),
+                         "peak_source": "FP64 FMA rate of the nominal GB300 figures (of nominal)",
                          "traffic": traffic, "launches": kl, "bytes_per_launch": round(kbytes / kl) if kl else None,
-                         "avg_launch_us": round(1e3 * kms / kl, 2) if kl else None},
+                         "flops_per_launch": round(kflops / kl) if kl else None,
+                         "avg_launch_us": round(1e6 * t_launch, 2) if kl else None,
+                         "hbm_achieved_gbs": round(achieved_gbs, 1), "hbm_peak_gbs": hbm_peak,
+                         "hbm_frac": round(achieved_gbs / hbm_peak, 4)},
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),

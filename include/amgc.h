@@ -78,7 +78,7 @@ typedef struct {
   int32_t smoother_sweeps;   /* CheapSIMPLE sweeps, pre and post (>= 0)                        */
   int32_t jacobi_sweeps;     /* damped-Jacobi sweeps in the predictor (>= 1)                   */
   int32_t simplec;           /* 0: A~ = diag(K);  1: A~ = absolute row sums (SIMPLEC)          */
-  int32_t precision;         /* 64 = FP64 V-cycle (32 reserved for the FP32 cycle)             */
+  int32_t precision;         /* 64: FP64 V-cycle; 32: FP32 storage and arithmetic in the cycle  */
   int32_t fgmres_restart;    /* Krylov subspace size m (1..256)                               */
   int32_t fgmres_maxit;      /* total FGMRES iterations allowed                                */
   uint32_t seed;             /* MIS-2 priority seed                                           */
@@ -131,7 +131,9 @@ int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M,
                struct amgc_hierarchy** out);
 
 /* z = V-cycle(r) with zero initial guess (Fig. mgalgorithm).  r, z: device vectors of
- * length rows[0] = 3n + 3 n_s, ordered [u; lambda].  r and z must not overlap. */
+ * length rows[0] = 3n + 3 n_s, ordered [u; lambda].  r and z must not overlap.  With
+ * precision 32 the cycle runs on FP32 copies of the level data (the inverted Schur blocks and
+ * the coarsest inverse stay FP64); r and z are still FP64. */
 int amgc_vcycle(struct amgc_hierarchy* h, const double* r, double* z, void* stream);
 
 /* y = A x with the fine-level saddle operator [K B1; B2 -Z]; device vectors of length rows[0]. */
@@ -183,11 +185,13 @@ int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what,
 /* Diagnostic timing of the dominant kernel family: the fine-level K-block applies (residual,
  * Jacobi predictor and saddle apply, one launch each).  With enable != 0 every such launch is
  * bracketed by CUDA events recorded on the launching stream; amgc_profile_read synchronises
- * that stream and returns the accumulated device time (ms), the number of launches and the
- * algorithmic bytes those launches move (matrix values and indices once, every vector once).
+ * that stream and returns the accumulated device time (ms), the number of launches, the
+ * algorithmic bytes those launches move (matrix values and indices once, every vector once) and
+ * their algorithmic floating-point operations (two per stored matrix value).
  * Enabling resets the counters.  Not for production runs: each launch adds two event records. */
 int amgc_profile(struct amgc_hierarchy* h, int32_t enable);
-int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes);
+int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes,
+                      double* flops);
 
 void amgc_destroy(struct amgc_hierarchy* h);
 const char* amgc_strerror(int code);

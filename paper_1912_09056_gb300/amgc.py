@@ -90,7 +90,8 @@ def load():
     lib.amgc_export.restype = C.c_int64
     lib.amgc_profile.argtypes = [vp, C.c_int32]
     lib.amgc_profile.restype = C.c_int
-    lib.amgc_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+    lib.amgc_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double)]
     lib.amgc_profile_read.restype = C.c_int
     lib.amgc_destroy.argtypes = [vp]
     lib.amgc_destroy.restype = None
@@ -199,8 +200,10 @@ class Hierarchy:
         ms = C.c_double(0.0)
         n = C.c_int64(0)
         b = C.c_double(0.0)
-        _check(self._lib.amgc_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(b)), "amgc_profile_read")
-        return ms.value, n.value, b.value
+        f = C.c_double(0.0)
+        _check(self._lib.amgc_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(b), C.byref(f)),
+               "amgc_profile_read")
+        return ms.value, n.value, b.value, f.value
 
     # ------------------------------------------------------------ device-vector calls
     def vcycle(self, r, z, stream=None):

@@ -88,6 +88,67 @@ struct DBsr {
   DBuf<double> val;
 };
 
+// SELL-32 copy of a BSR matrix for the thread-per-row apply: rows in slices of 32, each slice
+// padded to its longest row; slot t of slice s holds the t-th block of its 32 rows, the block
+// column at (off[s] + t) * 32 + lane and value k of the br x bc block at
+// ((off[s] + t) * br * bc + k) * 32 + lane.  Padding blocks point at column 0 with zero values.
+struct Sell {
+  int br = 0, bc = 0;
+  int nslice = 0;
+  int64_t slots = 0;
+  DBuf<int> off, len, col;
+  DBuf<double> val;
+};
+
+// FP32 mirrors of the cycle data of one level (values only; index arrays are shared).
+struct LevelF32 {
+  DBuf<float> K, B1, B2, P, R, Z, Ks, Ps, dinv, atinv, pl_w;
+  DBuf<float> x, b, r, t, dlam;
+};
+
+// Non-owning views of one level's cycle data in storage type T.
+template <class T>
+struct BsrV {
+  int nbr = 0, nbc = 0, br = 0, bc = 0;
+  int64_t nnzb = 0;
+  const int* rp = nullptr;
+  const int* col = nullptr;
+  const T* val = nullptr;
+};
+template <class T>
+struct SellV {
+  int br = 0, bc = 0, nslice = 0;
+  const int* off = nullptr;
+  const int* len = nullptr;
+  const int* col = nullptr;
+  const T* val = nullptr;
+};
+template <class T>
+struct LevelV {
+  int nn = 0, bu = 3, nl = 0;
+  int nu() const { return nn * bu; }
+  int rows() const { return nn * bu + 3 * nl; }
+  double omega_j = 0.0;
+  BsrV<T> K, B1, B2, P, R;
+  SellV<T> Ks, Ps;
+  const T* Z = nullptr;
+  const double* Sinv = nullptr;    // FP64 in both precisions
+  const T* dinv = nullptr;
+  const T* atinv = nullptr;
+  const T* pl_w = nullptr;
+  const int* lagg = nullptr;
+  const int* rl_ptr = nullptr;
+  const int* rl_idx = nullptr;
+  const int* b1_rows = nullptr;
+  int n_b1_rows = 0;
+  const double* Ainv = nullptr;    // coarsest level, FP64 in both precisions
+  T* x = nullptr;
+  T* b = nullptr;
+  T* r = nullptr;
+  T* t = nullptr;
+  T* dlam = nullptr;
+};
+
 // One level of the hierarchy.
 struct Level {
   int nn = 0;     // displacement (super)nodes
@@ -97,6 +158,7 @@ struct Level {
   int rows() const { return nn * bu + 3 * nl; }
 
   DBsr K, B1, B2;          // saddle blocks
+  Sell Ks, Ps;             // SELL-32 copies of K and P (finest level)
   DBuf<double> Z;          // nl*9
   DBuf<int> body;          // nn
   DBuf<double> B;          // nullspace nu*6
@@ -125,6 +187,8 @@ struct Level {
   // work vectors [u; lambda]
   DBuf<double> x, b, r, t;
   DBuf<double> dlam;         // nl*3
+
+  LevelF32 f;                // FP32 cycle data (precision 32)
 };
 
 }  // namespace amgc
@@ -140,12 +204,14 @@ struct amgc_hierarchy {
   int m_alloc = 0;
   amgc::DBuf<double> V, Zs, H, givens, gvec, y, wk, xk, rk;
   amgc::DBuf<double> partial;      // per-block partial dot products
+  std::vector<amgc::LevelV<double>> v64;   // cycle views, FP64
+  std::vector<amgc::LevelV<float>> v32;    // cycle views, FP32 (precision 32)
   double* h_pinned = nullptr;      // pinned host scalars
   // event timing of the fine-level K applies (amgc_profile)
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;
   int prof_pending = 0;
-  double prof_ms = 0.0, prof_bytes = 0.0;
+  double prof_ms = 0.0, prof_bytes = 0.0, prof_flops = 0.0;
   int64_t prof_launches = 0;
 };
 
@@ -174,18 +240,20 @@ int build_fine_level(amgc_hierarchy* h, const amgc_bsr* K, const double* D, cons
                      const uint8_t* active, const int* body_id, const double* nullspace);
 int coarsen_level(amgc_hierarchy* h, int l);
 int smoother_setup(amgc_hierarchy* h, int l);
+int build_sell(amgc_hierarchy* h, int l);
 int coarse_setup(amgc_hierarchy* h, int l);
 int check_status(amgc_hierarchy* h, const char* where);
 // kernel timing (api.cu)
 int prof_begin(amgc_hierarchy* h);
-int prof_end(amgc_hierarchy* h, double bytes);
+int prof_end(amgc_hierarchy* h, double bytes, double flops);
 int prof_flush(amgc_hierarchy* h);
-// sparse kernels (sparse.cu)
+// sparse kernels (cycle.cu)
 int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
 int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out);
 int dot(amgc_hierarchy* h, int64_t n, const double* a, const double* b, const double* wgt, double* out_dev);
-// V-cycle (vcycle.cu)
-int vcycle(amgc_hierarchy* h, int l, const double* b, double* x);
+// V-cycle (cycle.cu)
+int make_views(amgc_hierarchy* h);
+int precond_apply(amgc_hierarchy* h, const double* r, double* z);   // one V-cycle, FP64 in/out
 int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y);
 // FGMRES (krylov.cu)
 int fgmres(amgc_hierarchy* h, const double* rhs, double* x, int* iters, double* relres);

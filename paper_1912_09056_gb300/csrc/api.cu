@@ -25,6 +25,7 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
   h->L.reserve(16);
   h->L.emplace_back();
   AMGC_TRY(build_fine_level(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace));
+  AMGC_TRY(build_sell(h, 0));
   const amgc_options& o = h->opts;
   while ((int)h->L.size() < std::min(o.levels_max, 16) && h->L.back().rows() >= o.coarse_max_rows) {
     const int l = (int)h->L.size() - 1;
@@ -42,6 +43,8 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
     return AMGC_EINVAL;
   }
   AMGC_TRY(coarse_setup(h, lc));
+  if (lc > 0) AMGC_TRY(build_sell(h, 0));
+  AMGC_TRY(make_views(h));
   AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
   // statistics
   amgc_stats_t& st = h->stats;
@@ -89,12 +92,13 @@ int prof_begin(amgc_hierarchy* h) {
   return AMGC_OK;
 }
 
-int prof_end(amgc_hierarchy* h, double bytes) {
+int prof_end(amgc_hierarchy* h, double bytes, double flops) {
   if (!h->prof) return AMGC_OK;
   AMGC_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_pending + 1], h->stream));
   h->prof_pending++;
   h->prof_launches++;
   h->prof_bytes += bytes;
+  h->prof_flops += flops;
   return AMGC_OK;
 }
 
@@ -134,7 +138,7 @@ int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const
       K->br != 3 || K->bc != 3 || K->n_brow != K->n_bcol || K->n_brow <= 0 || M->n_row < 0 || M->n_col < 0 ||
       (M->n_row > 0 && (!D_diag || !slave_node || !triad || !active)) || (M->n_col > 0 && !master_node) ||
       opts->levels_max < 1 || opts->smoother_sweeps < 0 || opts->jacobi_sweeps < 1 || opts->fgmres_restart < 1 ||
-      opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 || !(opts->tol > 0.0) || opts->precision != 64) {
+      opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 || !(opts->tol > 0.0) || (opts->precision != 64 && opts->precision != 32)) {
     set_error("amgc_setup: invalid argument");
     return AMGC_EINVAL;
   }
@@ -158,7 +162,7 @@ int amgc_vcycle(struct amgc_hierarchy* h, const double* r, double* z, void* stre
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
-  return vcycle(h, 0, r, z);
+  return precond_apply(h, r, z);
 }
 
 int amgc_apply(struct amgc_hierarchy* h, const double* x, double* y, void* stream) {
@@ -268,11 +272,13 @@ int amgc_profile(struct amgc_hierarchy* h, int32_t enable) {
   h->prof = enable != 0;
   h->prof_ms = 0.0;
   h->prof_bytes = 0.0;
+  h->prof_flops = 0.0;
   h->prof_launches = 0;
   return AMGC_OK;
 }
 
-int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes) {
+int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes,
+                      double* flops) {
   if (!h) {
     set_error("amgc_profile_read: invalid argument");
     return AMGC_EINVAL;
@@ -281,6 +287,7 @@ int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launc
   if (total_ms) *total_ms = h->prof_ms;
   if (launches) *launches = h->prof_launches;
   if (bytes) *bytes = h->prof_bytes;
+  if (flops) *flops = h->prof_flops;
   return AMGC_OK;
 }
 

@@ -1,0 +1,667 @@
+// V-cycle (Fig. mgalgorithm) with CheapSIMPLE smoothing (Algorithm 4, Sec. 5.2), the fine-level
+// saddle apply, and the FP64 helpers of the setup (dot products, lambda_max power iteration).
+//
+// Every cycle kernel is templated on the storage and arithmetic type T: double for the FP64
+// cycle, float for the FP32 cycle (FP32 storage, arithmetic and accumulation).  In both, the
+// inverted nodal Schur blocks and the coarsest inverse stay FP64.
+//
+// GB300 retires FP64 fused multiply-adds at a small fraction of its FP32 rate, so a warp
+// FP64 instruction costs many SM cycles: every kernel issues one FMA per matrix value with
+// all lanes busy wherever the row structure allows, and keeps cross-lane reductions out of
+// the inner loops.  Two mappings:
+//  * SELL-32, one thread per block row (fine-level K and P: short rows, many rows);
+//  * one warp per block row, one lane per block, BR partial sums per lane reduced once at the
+//    end (restriction and coarse levels: long rows or few rows).
+#include "amgc_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace amgc {
+
+constexpr int kRowWarps = 8;   // warps per block of the warp-per-row kernels
+
+template <class T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+template <class T>
+__device__ __forceinline__ T ldcs(const T* p) { return __ldcs(p); }
+
+// MODE 0: y  = A1 x1 + A2 x2
+// MODE 1: y += A1 x1
+// MODE 2: y  = b - A1 x1 - A2 x2                        (residual)
+// MODE 3: y  = x0 + omega * dinv * (b - A1 x1 - A2 x2)    (damped Jacobi, out of place)
+template <int MODE, class T>
+__device__ __forceinline__ void store_row(T* __restrict__ y, const T* __restrict__ b, const T* __restrict__ x0,
+                                          const T* __restrict__ dinv, T omega, int64_t o, T s) {
+  if (MODE == 0) y[o] = s;
+  else if (MODE == 1) y[o] += s;
+  else if (MODE == 2) y[o] = b[o] - s;
+  else y[o] = x0[o] + omega * dinv[o] * (b[o] - s);
+}
+
+// lane-per-block accumulation of one block row: acc[r] += sum_c A[b][r][c] x[col[b]][c]
+template <int BR, int BC, class T>
+__device__ __forceinline__ void lane_blocks(int64_t b0, int64_t b1, const int* __restrict__ col,
+                                            const T* __restrict__ val, const T* __restrict__ x, int lane,
+                                            T (&acc)[BR]) {
+  for (int64_t b = b0 + lane; b < b1; b += 32) {
+    const T* xc = x + (int64_t)__ldg(col + b) * BC;
+    T xv[BC];
+#pragma unroll
+    for (int c = 0; c < BC; ++c) xv[c] = ldg(xc + c);
+    const T* v = val + b * (BR * BC);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int c = 0; c < BC; ++c) acc[r] = fma(ldg(v + r * BC + c), xv[c], acc[r]);
+  }
+}
+
+template <int BR, int BC1, int BC2, int MODE, class T>
+__global__ void __launch_bounds__(kRowWarps * 32)
+k_rowop(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const T* __restrict__ v1,
+        const T* __restrict__ x1, const int* __restrict__ rp2, const int* __restrict__ c2, const T* __restrict__ v2,
+        const T* __restrict__ x2, const T* __restrict__ b, const T* __restrict__ x0, const T* __restrict__ dinv,
+        T omega, T* __restrict__ y) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row = blockIdx.x * kRowWarps + wid;
+  if (row >= nbr) return;
+  T acc[BR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = T(0);
+  lane_blocks<BR, BC1, T>(rp1[row], rp1[row + 1], c1, v1, x1, lane, acc);
+  if (rp2 != nullptr) lane_blocks<BR, BC2, T>(rp2[row], rp2[row + 1], c2, v2, x2, lane, acc);
+  T out = T(0);
+#pragma unroll
+  for (int r = 0; r < BR; ++r) {
+    const T t = warp_sum(acc[r]);
+    if (lane == r) out = t;
+  }
+  if (lane < BR) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * BR + lane, out);
+}
+
+template <int BR, int BC1, int BC2, int MODE, class T>
+static int launch_rowop(const BsrV<T>& A1, const T* x1, const BsrV<T>* A2, const T* x2, const T* b, const T* x0,
+                        const T* dinv, double omega, T* y, cudaStream_t s) {
+  if (A1.nbr == 0) return AMGC_OK;
+  AMGC_LAUNCH(k_rowop<BR, BC1, BC2, MODE, T><<<div_up(A1.nbr, kRowWarps), kRowWarps * 32, 0, s>>>(
+      A1.nbr, A1.rp, A1.col, A1.val, x1, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr, A2 ? A2->val : nullptr, x2,
+      b, x0, dinv, (T)omega, y));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+template <int MODE, class T>
+static int rowop(const BsrV<T>& A1, const T* x1, const BsrV<T>* A2, const T* x2, const T* b, const T* x0,
+                 const T* dinv, double omega, T* y, cudaStream_t s) {
+  const int br = A1.br, bc1 = A1.bc, bc2 = A2 ? A2->bc : 3;
+#define AMGC_ROWOP_CASE(R, C1, C2) \
+  if (br == R && bc1 == C1 && bc2 == C2) return launch_rowop<R, C1, C2, MODE, T>(A1, x1, A2, x2, b, x0, dinv, omega, y, s);
+  AMGC_ROWOP_CASE(3, 3, 3)
+  AMGC_ROWOP_CASE(6, 6, 3)
+  AMGC_ROWOP_CASE(3, 6, 3)
+  AMGC_ROWOP_CASE(6, 3, 3)
+#undef AMGC_ROWOP_CASE
+  set_error("rowop: unsupported block shape");
+  return AMGC_EINVAL;
+}
+
+static BsrV<double> view_of(const DBsr& A) {
+  BsrV<double> v;
+  v.nbr = A.nbr; v.nbc = A.nbc; v.br = A.br; v.bc = A.bc; v.nnzb = A.nnzb;
+  v.rp = A.rowptr.p; v.col = A.col.p; v.val = A.val.p;
+  return v;
+}
+
+int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s) {
+  (void)alpha;
+  (void)beta;
+  const BsrV<double> v = view_of(A);
+  return rowop<0, double>(v, x, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, y, s);
+}
+
+// ------------------------------------------------------------------ SELL-32 thread-per-row apply
+// One thread per block row: value k of a block is one coalesced warp load, one FMA each, and
+// no cross-lane reduction.  Matrix data is streamed (evict-first) so the vectors stay cached.
+// An optional second matrix A2 (the B1 block, few rows) is added from its BSR rows.
+template <int BR, int BC, int MODE, class T>
+__global__ void __launch_bounds__(256)
+k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, const int* __restrict__ scol,
+       const T* __restrict__ sval, const T* __restrict__ x, const int* __restrict__ rp2, const int* __restrict__ c2,
+       const T* __restrict__ v2, const T* __restrict__ x2, const T* __restrict__ b, const T* __restrict__ x0,
+       const T* __restrict__ dinv, T omega, T* __restrict__ y) {
+  constexpr int BS = BR * BC;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  const int lane = row & 31, sl = row >> 5;
+  const int64_t o = soff[sl];
+  const int L = slen[sl];
+  const int* cp = scol + o * 32 + lane;
+  const T* vp = sval + o * (BS * 32) + lane;
+  T acc[BR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = T(0);
+#pragma unroll 3
+  for (int t = 0; t < L; ++t) {
+    const T* xc = x + (int64_t)__ldcs(cp + t * 32) * BC;
+    T xv[BC];
+#pragma unroll
+    for (int c = 0; c < BC; ++c) xv[c] = ldg(xc + c);
+    const T* v = vp + (int64_t)t * (BS * 32);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int c = 0; c < BC; ++c) acc[r] = fma(ldcs(v + (r * BC + c) * 32), xv[c], acc[r]);
+  }
+  if (rp2 != nullptr) {
+    for (int e = rp2[row]; e < rp2[row + 1]; ++e) {
+      const T* blk = v2 + (int64_t)e * BR * 3;
+      const T* d = x2 + 3 * (int64_t)c2[e];
+      const T d0 = d[0], d1 = d[1], d2 = d[2];
+#pragma unroll
+      for (int r = 0; r < BR; ++r) acc[r] = fma(blk[3 * r], d0, fma(blk[3 * r + 1], d1, fma(blk[3 * r + 2], d2, acc[r])));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < BR; ++r) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * BR + r, acc[r]);
+}
+
+template <int MODE, class T>
+static int sell_apply(const SellV<T>& S, int nbr, const BsrV<T>* A2, const T* x, const T* x2, const T* b, const T* x0,
+                      const T* dinv, double omega, T* y, cudaStream_t s) {
+  const int g = div_up(nbr, 256);
+  const int* rp2 = A2 ? A2->rp : nullptr;
+  const int* c2 = A2 ? A2->col : nullptr;
+  const T* v2 = A2 ? A2->val : nullptr;
+  if (S.br == 3 && S.bc == 3)
+    AMGC_LAUNCH(k_sell<3, 3, MODE, T><<<g, 256, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2, b, x0,
+                                                        dinv, (T)omega, y));
+  else if (S.br == 3 && S.bc == 6)
+    AMGC_LAUNCH(k_sell<3, 6, MODE, T><<<g, 256, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2, b, x0,
+                                                        dinv, (T)omega, y));
+  else {
+    set_error("sell_apply: unsupported block shape");
+    return AMGC_EINVAL;
+  }
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+// ------------------------------------------------------------------ multiplier-node kernels
+// One warp per multiplier node.
+// MODE 0: out_l = g_l - (B2 u)_l + Z_l lam_l                       (residual)
+// MODE 1: d = -Sinv_l (g_l - (B2 u)_l + Z_l lam_l); lam_l += alpha d; out_l = d  (corrector)
+// MODE 2: out_l = (B2 u)_l - Z_l lam_l                             (saddle apply)
+template <int BU, int MODE, class T>
+__global__ void __launch_bounds__(128)
+k_lm(int nl, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+     const T* __restrict__ u, const T* __restrict__ Z, const T* __restrict__ g, T* __restrict__ lam,
+     const double* __restrict__ Sinv, double alpha, T* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (l >= nl) return;
+  T acc[3] = {T(0), T(0), T(0)};
+  lane_blocks<3, BU, T>(rp[l], rp[l + 1], col, val, u, lane, acc);
+  const T bu0 = warp_sum(acc[0]), bu1 = warp_sum(acc[1]), bu2 = warp_sum(acc[2]);
+  if (lane != 0) return;
+  const T* z = Z + (int64_t)l * 9;
+  const T l0 = lam[3 * l], l1 = lam[3 * l + 1], l2 = lam[3 * l + 2];
+  const T zl0 = z[0] * l0 + z[1] * l1 + z[2] * l2;
+  const T zl1 = z[3] * l0 + z[4] * l1 + z[5] * l2;
+  const T zl2 = z[6] * l0 + z[7] * l1 + z[8] * l2;
+  if (MODE == 2) {
+    out[3 * l] = bu0 - zl0;
+    out[3 * l + 1] = bu1 - zl1;
+    out[3 * l + 2] = bu2 - zl2;
+    return;
+  }
+  const T r0 = g[3 * l] - bu0 + zl0, r1 = g[3 * l + 1] - bu1 + zl1, r2 = g[3 * l + 2] - bu2 + zl2;
+  if (MODE == 0) {
+    out[3 * l] = r0;
+    out[3 * l + 1] = r1;
+    out[3 * l + 2] = r2;
+    return;
+  }
+  const double* S = Sinv + (int64_t)l * 9;   // FP64 Schur-block inverse
+  const double d0 = -(S[0] * r0 + S[1] * r1 + S[2] * r2);
+  const double d1 = -(S[3] * r0 + S[4] * r1 + S[5] * r2);
+  const double d2 = -(S[6] * r0 + S[7] * r1 + S[8] * r2);
+  lam[3 * l] = (T)(l0 + alpha * d0);
+  lam[3 * l + 1] = (T)(l1 + alpha * d1);
+  lam[3 * l + 2] = (T)(l2 + alpha * d2);
+  out[3 * l] = (T)d0;
+  out[3 * l + 1] = (T)d1;
+  out[3 * l + 2] = (T)d2;
+}
+
+template <int MODE, class T>
+static int lm_op(const LevelV<T>& L, const T* u, const T* g, T* lam, double alpha, T* out, cudaStream_t s) {
+  if (L.nl == 0) return AMGC_OK;
+  const int th = 128;
+  const int gl = div_up((int64_t)L.nl * 32, th);
+  if (L.bu == 3)
+    AMGC_LAUNCH(k_lm<3, MODE, T><<<gl, th, 0, s>>>(L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam, L.Sinv, alpha, out));
+  else
+    AMGC_LAUNCH(k_lm<6, MODE, T><<<gl, th, 0, s>>>(L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam, L.Sinv, alpha, out));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+template <class T>
+__global__ void k_copy(int64_t n, const T* __restrict__ a, T* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a[i];
+}
+template <class Ta, class Tb>
+__global__ void k_convert(int64_t n, const Ta* __restrict__ a, Tb* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (Tb)a[i];
+}
+template <class T>
+__global__ void k_zero(int64_t n, T* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = T(0);
+}
+template <class T>
+__global__ void k_jacobi_zero(int64_t n, const T* __restrict__ f, const T* __restrict__ dinv, T omega, T* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = omega * dinv[i] * f[i];
+}
+// u_i -= alpha atinv_i (B1 dlam)_i over the rows of B1 with entries, one warp per row
+template <int BU, class T>
+__global__ void __launch_bounds__(128)
+k_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp, const int* __restrict__ col,
+            const T* __restrict__ val, const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha,
+            T* __restrict__ u) {
+  const int lane = threadIdx.x & 31;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (t >= nrows) return;
+  const int i = rows[t];
+  T acc[BU];
+#pragma unroll
+  for (int r = 0; r < BU; ++r) acc[r] = T(0);
+  lane_blocks<BU, 3, T>(rp[i], rp[i + 1], col, val, dlam, lane, acc);
+  T out = T(0);
+#pragma unroll
+  for (int r = 0; r < BU; ++r) {
+    const T v = warp_sum(acc[r]);
+    if (lane == r) out = v;
+  }
+  if (lane < BU) u[(int64_t)i * BU + lane] -= alpha * atinv[(int64_t)i * BU + lane] * out;
+}
+// multiplier restriction / prolongation through P-hat^lambda (weights w_l, aggregate lagg_l)
+template <class T>
+__global__ void k_restrict_lm(int nlc, const int* __restrict__ ptr, const int* __restrict__ idx, const T* __restrict__ w,
+                              const T* __restrict__ r, T* __restrict__ out) {
+  const int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= nlc) return;
+  T s0 = 0, s1 = 0, s2 = 0;
+  for (int e = ptr[L]; e < ptr[L + 1]; ++e) {
+    const int l = idx[e];
+    const T wl = w[l];
+    s0 += wl * r[3 * l];
+    s1 += wl * r[3 * l + 1];
+    s2 += wl * r[3 * l + 2];
+  }
+  out[3 * L] = s0;
+  out[3 * L + 1] = s1;
+  out[3 * L + 2] = s2;
+}
+template <class T>
+__global__ void k_prolong_lm(int nl, const int* __restrict__ lagg, const T* __restrict__ w, const T* __restrict__ c,
+                             T* __restrict__ lam) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const int L = lagg[l];
+  const T wl = w[l];
+  lam[3 * l] += wl * c[3 * L];
+  lam[3 * l + 1] += wl * c[3 * L + 1];
+  lam[3 * l + 2] += wl * c[3 * L + 2];
+}
+// coarsest solve: y = A^{-1} x with the FP64 inverse (row-major), one warp per row
+template <class T>
+__global__ void k_gemv(int n, const double* __restrict__ A, const T* __restrict__ x, T* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  const double* a = A + (int64_t)row * n;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s = fma(a[j], (double)x[j], s);
+  s = warp_sum(s);
+  if (lane == 0) y[row] = (T)s;
+}
+
+// ------------------------------------------------------------------ level operations
+// Algorithmic bytes of one fine-level K-apply launch: K and B1 values and indices once, x and
+// lambda once, the output once, plus `extra_vecs` further length-nu vectors.
+template <class T>
+static double k_apply_bytes(const LevelV<T>& L, int extra_vecs) {
+  const double s = sizeof(T);
+  double b = (double)L.K.nnzb * (L.bu * L.bu * s + 4.0) + 4.0 * (L.nn + 1);
+  b += (double)L.B1.nnzb * (L.bu * 3 * s + 4.0) + (L.nl ? 4.0 * (L.nn + 1) + 3.0 * L.nl * s : 0.0);
+  b += (2.0 + extra_vecs) * L.nu() * s;
+  return b;
+}
+
+// K apply of level l (MODE of k_rowop), timed when the level is the finest one.
+template <int MODE, class T>
+static int k_apply(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* x1, const T* lam, const T* b, const T* x0,
+                   T* y) {
+  const bool t = l == 0;
+  if (t) AMGC_TRY(prof_begin(h));
+  const BsrV<T>* B1 = L.nl ? &L.B1 : nullptr;
+  if (L.Ks.nslice > 0)
+    AMGC_TRY((sell_apply<MODE, T>(L.Ks, L.nn, B1, x1, lam, b, x0, L.dinv, L.omega_j, y, h->stream)));
+  else
+    AMGC_TRY((rowop<MODE, T>(L.K, x1, B1, lam, b, x0, L.dinv, L.omega_j, y, h->stream)));
+  if (t)
+    AMGC_TRY(prof_end(h, k_apply_bytes(L, MODE == 3 ? 3 : (MODE == 2 ? 1 : 0)),
+                      2.0 * ((double)L.K.nnzb * L.bu * L.bu + (double)L.B1.nnzb * L.bu * 3)));
+  return AMGC_OK;
+}
+
+template <class T>
+static int smooth(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, T* x, bool zero_guess) {
+  cudaStream_t s = h->stream;
+  const int nu = L.nu();
+  const T* f = b;
+  const T* g = b + nu;
+  T* u = x;
+  T* lam = x + nu;
+  T* t = L.t;   // u_half
+  const int th = 256;
+  for (int j = 0; j < h->opts.jacobi_sweeps; ++j) {
+    T* src = (j % 2 == 0) ? u : t;
+    T* dst = (j % 2 == 0) ? t : u;
+    if (zero_guess && j == 0) {
+      AMGC_LAUNCH(k_zero<T><<<div_up(3 * (int64_t)L.nl, th), th, 0, s>>>(3 * (int64_t)L.nl, lam));
+      AMGC_LAUNCH(k_jacobi_zero<T><<<div_up(nu, th), th, 0, s>>>(nu, f, L.dinv, (T)L.omega_j, dst));
+      AMGC_CUDA_TRY(cudaGetLastError());
+    } else {
+      AMGC_TRY((k_apply<3, T>(h, L, l, src, lam, f, src, dst)));
+    }
+  }
+  T* uh = (h->opts.jacobi_sweeps % 2 == 1) ? t : u;
+  // corrector on the multipliers: dlam = -S^-1 (g - B2 uh + Z lam), lam += alpha dlam
+  AMGC_TRY((lm_op<1, T>(L, uh, g, lam, h->opts.simple_alpha, L.dlam, s)));
+  // u = uh - alpha A~^-1 B1 dlam
+  if (uh != u) {
+    AMGC_LAUNCH(k_copy<T><<<div_up(nu, th), th, 0, s>>>(nu, uh, u));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  if (L.n_b1_rows > 0) {
+    const int gb = div_up((int64_t)L.n_b1_rows * 32, 128);
+    if (L.bu == 3)
+      AMGC_LAUNCH(k_b1_update<3, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
+                                                       L.atinv, (T)h->opts.simple_alpha, u));
+    else
+      AMGC_LAUNCH(k_b1_update<6, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
+                                                       L.atinv, (T)h->opts.simple_alpha, u));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  return AMGC_OK;
+}
+
+template <class T>
+static int residual(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, const T* x, T* r) {
+  const int nu = L.nu();
+  AMGC_TRY((k_apply<2, T>(h, L, l, x, x + nu, b, nullptr, r)));
+  AMGC_TRY((lm_op<0, T>(L, x, b + nu, const_cast<T*>(x + nu), 0.0, r + nu, h->stream)));
+  return AMGC_OK;
+}
+
+template <class T>
+static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T* b, T* x) {
+  const LevelV<T>& L = V[l];
+  cudaStream_t s = h->stream;
+  const int th = 256;
+  if (l == (int)V.size() - 1) {
+    const int n = L.rows();
+    AMGC_LAUNCH(k_gemv<T><<<div_up((int64_t)n * 32, th), th, 0, s>>>(n, L.Ainv, b, x));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    return AMGC_OK;
+  }
+  const int nu = L.nu();
+  const LevelV<T>& C = V[l + 1];
+  const int sweeps = h->opts.smoother_sweeps;
+  if (sweeps == 0) {
+    AMGC_LAUNCH(k_zero<T><<<div_up(L.rows(), th), th, 0, s>>>(L.rows(), x));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  for (int k = 0; k < sweeps; ++k) AMGC_TRY(smooth<T>(h, L, l, b, x, k == 0));
+  AMGC_TRY(residual<T>(h, L, l, b, x, L.r));
+  // restrict: C.b = [R r_u ; R^lambda r_lambda]
+  AMGC_TRY((rowop<0, T>(L.R, L.r, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, C.b, s)));
+  if (C.nl > 0) {
+    AMGC_LAUNCH(k_restrict_lm<T><<<div_up(C.nl, 128), 128, 0, s>>>(C.nl, L.rl_ptr, L.rl_idx, L.pl_w, L.r + nu,
+                                                                   C.b + C.nu()));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  AMGC_TRY(vcycle_t<T>(h, V, l + 1, C.b, C.x));
+  // prolongate and add
+  if (L.Ps.nslice > 0)
+    AMGC_TRY((sell_apply<1, T>(L.Ps, L.nn, nullptr, C.x, nullptr, nullptr, nullptr, nullptr, 0.0, x, s)));
+  else
+    AMGC_TRY((rowop<1, T>(L.P, C.x, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, x, s)));
+  if (L.nl > 0) {
+    AMGC_LAUNCH(k_prolong_lm<T><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.lagg, L.pl_w, C.x + C.nu(), x + nu));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  for (int k = 0; k < sweeps; ++k) AMGC_TRY(smooth<T>(h, L, l, b, x, false));
+  return AMGC_OK;
+}
+
+int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y) {
+  const LevelV<double>& L = h->v64[l];
+  const int nu = L.nu();
+  AMGC_TRY((k_apply<0, double>(h, L, l, x, x + nu, nullptr, nullptr, y)));
+  AMGC_TRY((lm_op<2, double>(L, x, nullptr, const_cast<double*>(x + nu), 0.0, y + nu, h->stream)));
+  return AMGC_OK;
+}
+
+// One V-cycle with FP64 input and output; the FP32 cycle converts at entry and exit.
+int precond_apply(amgc_hierarchy* h, const double* r, double* z) {
+  if (h->opts.precision == 32) {
+    LevelV<float>& L0 = h->v32[0];
+    const int64_t n = L0.rows();
+    const int th = 256;
+    float* bf = h->L[0].f.b.p;
+    float* xf = h->L[0].f.x.p;
+    AMGC_LAUNCH((k_convert<double, float><<<div_up(n, th), th, 0, h->stream>>>(n, r, bf)));
+    AMGC_TRY(vcycle_t<float>(h, h->v32, 0, bf, xf));
+    AMGC_LAUNCH((k_convert<float, double><<<div_up(n, th), th, 0, h->stream>>>(n, xf, z)));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    return AMGC_OK;
+  }
+  return vcycle_t<double>(h, h->v64, 0, r, z);
+}
+
+// ------------------------------------------------------------------ views and FP32 mirrors
+static int to_f32(amgc_hierarchy* h, const double* src, size_t n, DBuf<float>& dst) {
+  AMGC_TRY(dst.alloc(std::max<size_t>(n, 1)));
+  if (n == 0) return AMGC_OK;
+  AMGC_LAUNCH((k_convert<double, float><<<div_up((int64_t)n, 256), 256, 0, h->stream>>>((int64_t)n, src, dst.p)));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+template <class T>
+static BsrV<T> bview(const DBsr& A, const T* val) {
+  BsrV<T> v;
+  v.nbr = A.nbr; v.nbc = A.nbc; v.br = A.br; v.bc = A.bc; v.nnzb = A.nnzb;
+  v.rp = A.rowptr.p; v.col = A.col.p; v.val = val;
+  return v;
+}
+template <class T>
+static SellV<T> sview(const Sell& S, const T* val) {
+  SellV<T> v;
+  v.br = S.br; v.bc = S.bc; v.nslice = S.nslice;
+  v.off = S.off.p; v.len = S.len.p; v.col = S.col.p; v.val = val;
+  return v;
+}
+
+template <class T>
+static LevelV<T> common_view(const Level& L) {
+  LevelV<T> v;
+  v.nn = L.nn; v.bu = L.bu; v.nl = L.nl; v.omega_j = L.omega_j;
+  v.Sinv = L.Sinv.p; v.lagg = L.lagg.p; v.rl_ptr = L.rl_ptr.p; v.rl_idx = L.rl_idx.p;
+  v.b1_rows = L.b1_rows.p; v.n_b1_rows = L.n_b1_rows; v.Ainv = L.Ainv.p;
+  return v;
+}
+
+int make_views(amgc_hierarchy* h) {
+  h->v64.clear();
+  h->v32.clear();
+  const int nlev = (int)h->L.size();
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = h->L[l];
+    LevelV<double> v = common_view<double>(L);
+    v.K = bview<double>(L.K, L.K.val.p);
+    v.B1 = bview<double>(L.B1, L.B1.val.p);
+    v.B2 = bview<double>(L.B2, L.B2.val.p);
+    v.P = bview<double>(L.P, L.P.val.p);
+    v.R = bview<double>(L.R, L.R.val.p);
+    v.Ks = sview<double>(L.Ks, L.Ks.val.p);
+    v.Ps = sview<double>(L.Ps, L.Ps.val.p);
+    v.Z = L.Z.p; v.dinv = L.dinv.p; v.atinv = L.atinv.p; v.pl_w = L.pl_w.p;
+    v.x = L.x.p; v.b = L.b.p; v.r = L.r.p; v.t = L.t.p; v.dlam = L.dlam.p;
+    h->v64.push_back(v);
+  }
+  if (h->opts.precision != 32) return AMGC_OK;
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = h->L[l];
+    LevelF32& F = L.f;
+    const bool last = l == nlev - 1;
+    AMGC_TRY(to_f32(h, L.K.val.p, (size_t)L.K.nnzb * L.bu * L.bu, F.K));
+    AMGC_TRY(to_f32(h, L.B1.val.p, (size_t)L.B1.nnzb * L.bu * 3, F.B1));
+    AMGC_TRY(to_f32(h, L.B2.val.p, (size_t)L.B2.nnzb * 3 * L.bu, F.B2));
+    AMGC_TRY(to_f32(h, L.Z.p, (size_t)L.nl * 9, F.Z));
+    if (!last) {
+      AMGC_TRY(to_f32(h, L.P.val.p, (size_t)L.P.nnzb * L.P.br * L.P.bc, F.P));
+      AMGC_TRY(to_f32(h, L.R.val.p, (size_t)L.R.nnzb * L.R.br * L.R.bc, F.R));
+      AMGC_TRY(to_f32(h, L.dinv.p, (size_t)L.nu(), F.dinv));
+      AMGC_TRY(to_f32(h, L.atinv.p, (size_t)L.nu(), F.atinv));
+      AMGC_TRY(to_f32(h, L.pl_w.p, (size_t)L.nl, F.pl_w));
+    }
+    if (L.Ks.nslice > 0) AMGC_TRY(to_f32(h, L.Ks.val.p, (size_t)L.Ks.slots * 32 * 9, F.Ks));
+    if (L.Ps.nslice > 0) AMGC_TRY(to_f32(h, L.Ps.val.p, (size_t)L.Ps.slots * 32 * 18, F.Ps));
+    const size_t n = std::max(L.rows(), 1);
+    AMGC_TRY(F.x.alloc(n));
+    AMGC_TRY(F.b.alloc(n));
+    AMGC_TRY(F.r.alloc(n));
+    AMGC_TRY(F.t.alloc(n));
+    AMGC_TRY(F.dlam.alloc(std::max(3 * L.nl, 1)));
+    LevelV<float> v = common_view<float>(L);
+    v.K = bview<float>(L.K, F.K.p);
+    v.B1 = bview<float>(L.B1, F.B1.p);
+    v.B2 = bview<float>(L.B2, F.B2.p);
+    v.P = bview<float>(L.P, F.P.p);
+    v.R = bview<float>(L.R, F.R.p);
+    v.Ks = sview<float>(L.Ks, F.Ks.p);
+    v.Ps = sview<float>(L.Ps, F.Ps.p);
+    v.Z = F.Z.p; v.dinv = F.dinv.p; v.atinv = F.atinv.p; v.pl_w = F.pl_w.p;
+    v.x = F.x.p; v.b = F.b.p; v.r = F.r.p; v.t = F.t.p; v.dlam = F.dlam.p;
+    h->v32.push_back(v);
+  }
+  AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return AMGC_OK;
+}
+
+// ------------------------------------------------------------------ dot products, lambda_max
+__global__ void k_scale_dinv(int64_t n, const double* __restrict__ dinv, double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] *= dinv[i];
+}
+__global__ void k_fill(int64_t n, double v, double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = v;
+}
+// Deterministic two-stage dot products: stage 1 writes one partial per block.
+constexpr int kDotThreads = 256;
+constexpr int kDotBlocks = 1024;
+__global__ void k_dot_partial(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                              const double* __restrict__ wgt, double* __restrict__ part) {
+  __shared__ double sh[kDotThreads / 32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kDotThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kDotThreads)
+    s = fma(a[i] * (wgt ? wgt[i] : 1.0), b[i], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kDotThreads / 32 ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+__global__ void k_dot_final(int nparts, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (int)(blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) *out = v;
+  }
+}
+// y = src / sqrt(*nrm2)
+__global__ void k_normalize(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ src,
+                            double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = src[i] / sqrt(*nrm2);
+}
+
+int dot(amgc_hierarchy* h, int64_t n, const double* a, const double* b, const double* wgt, double* out_dev) {
+  cudaStream_t s = h->stream;
+  int blocks = (int)std::min<int64_t>(kDotBlocks, std::max<int64_t>(1, div_up(n, kDotThreads)));
+  AMGC_LAUNCH(k_dot_partial<<<blocks, kDotThreads, 0, s>>>(n, a, b, wgt, h->partial.p));
+  AMGC_LAUNCH(k_dot_final<<<1, 1024, 0, s>>>(blocks, h->partial.p, out_dev));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+// lambda_max(D^{-1} K): 20 power steps from the normalised ones vector, then the generalised
+// Rayleigh quotient (x^T K x)/(x^T D x) with D the pointwise diagonal of K (kdiag).
+int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out) {
+  cudaStream_t s = h->stream;
+  const int64_t n = L.nu();
+  const int th = 256;
+  DBuf<double> xv, yv, sc;
+  AMGC_TRY(xv.alloc(n));
+  AMGC_TRY(yv.alloc(n));
+  AMGC_TRY(sc.alloc(4));
+  AMGC_LAUNCH(k_fill<<<div_up(n, th), th, 0, s>>>(n, 1.0 / sqrt((double)n), xv.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  // y = K x on the SELL copy when the level has one, else on the BSR rows
+  auto spmv = [&](const double* xin, double* yout) -> int {
+    if (L.Ks.nslice > 0) {
+      const SellV<double> sv = sview<double>(L.Ks, L.Ks.val.p);
+      return sell_apply<0, double>(sv, L.nn, nullptr, xin, nullptr, nullptr, nullptr, nullptr, 0.0, yout, s);
+    }
+    return bsr_spmv(L.K, xin, yout, 1.0, 0.0, s);
+  };
+  for (int it = 0; it < 20; ++it) {
+    AMGC_TRY(spmv(xv.p, yv.p));
+    AMGC_LAUNCH(k_scale_dinv<<<div_up(n, th), th, 0, s>>>(n, L.dinv.p, yv.p));
+    AMGC_TRY(dot(h, n, yv.p, yv.p, nullptr, sc.p));
+    AMGC_LAUNCH(k_normalize<<<div_up(n, th), th, 0, s>>>(n, sc.p, yv.p, xv.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  AMGC_TRY(spmv(xv.p, yv.p));
+  AMGC_TRY(dot(h, n, xv.p, yv.p, nullptr, sc.p));             // x^T K x
+  AMGC_TRY(dot(h, n, xv.p, xv.p, L.kdiag.p, sc.p + 1));       // x^T D x
+  double hs[2] = {0.0, 0.0};
+  AMGC_CUDA_TRY(cudaMemcpyAsync(hs, sc.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (!(hs[1] > 0.0) || !std::isfinite(hs[0] / hs[1])) {
+    set_error("lambda_max: non-positive or non-finite Rayleigh quotient");
+    return AMGC_ESINGULAR;
+  }
+  *out = hs[0] / hs[1];
+  return AMGC_OK;
+}
+
+}  // namespace amgc

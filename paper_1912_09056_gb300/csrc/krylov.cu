@@ -12,41 +12,44 @@
 namespace amgc {
 
 constexpr int kMdThreads = 256;
-constexpr int kMdBlocks = 304;   // 2 x 152 SMs
+constexpr int kMdBlocks = 608;   // 4 x 152 SMs
 constexpr int kMaxRestart = 256;
 
-// part[b * ldp + k] = sum over block b's rows of V[k][i] * w[i], k = 0..nk-1
+// part[b * ldp + k] = sum over block b's row chunk of V[k][i] * w[i], k = 0..nk-1.
+// Warp q of the block takes the basis vectors k = q, q + 8, ...; lanes stream the chunk.
 __global__ void __launch_bounds__(kMdThreads)
 k_multidot(int64_t n, int nk, const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ part,
            int ldp) {
-  __shared__ double sh[kMdThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = blockIdx.x * chunk;
   const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
-  for (int k = 0; k < nk; ++k) {
+  for (int k = wid; k < nk; k += kMdThreads / 32) {
     const double* v = V + (int64_t)k * n;
-    double s = 0.0;
-    for (int64_t i = b0 + threadIdx.x; i < b1; i += kMdThreads) s = fma(v[i], w[i], s);
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double t = threadIdx.x < kMdThreads / 32 ? sh[threadIdx.x] : 0.0;
-      t = warp_sum(t);
-      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * ldp + k] = t;
+    double s0 = 0.0, s1 = 0.0;
+    int64_t i = b0 + lane;
+    for (; i + 32 < b1; i += 64) {
+      s0 = fma(v[i], w[i], s0);
+      s1 = fma(v[i + 32], w[i + 32], s1);
     }
-    __syncthreads();
+    if (i < b1) s0 = fma(v[i], w[i], s0);
+    const double t = warp_sum(s0 + s1);
+    if (lane == 0) part[(int64_t)blockIdx.x * ldp + k] = t;
   }
 }
-// out[k*ldo] (+)= sum_b part[b*ldp + k]  (fixed order: deterministic)
+// out[k*ldo] (+)= sum_b part[b*ldp + k], one warp per k (fixed order: deterministic)
 __global__ void k_multidot_final(int nk, int nb, const double* __restrict__ part, int ldp, double* __restrict__ out,
                                  int ldo, int accumulate, double* __restrict__ hk) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (k >= nk) return;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[(int64_t)b * ldp + k];
-  if (hk) hk[k] = s;
-  out[(int64_t)k * ldo] = accumulate ? out[(int64_t)k * ldo] + s : s;
+  for (int b = lane; b < nb; b += 32) s += part[(int64_t)b * ldp + k];
+  s = warp_sum(s);
+  if (lane == 0) {
+    if (hk) hk[k] = s;
+    out[(int64_t)k * ldo] = accumulate ? out[(int64_t)k * ldo] + s : s;
+  }
 }
 // w[i] -= sum_k V[k][i] h[k]
 __global__ void k_basis_update(int64_t n, int nk, const double* __restrict__ V, const double* __restrict__ h,
@@ -149,7 +152,8 @@ static int multidot(amgc_hierarchy* h, int64_t n, int nk, const double* V, const
                     int accumulate, double* hk) {
   cudaStream_t s = h->stream;
   AMGC_LAUNCH(k_multidot<<<kMdBlocks, kMdThreads, 0, s>>>(n, nk, V, w, h->wk.p, nk));
-  AMGC_LAUNCH(k_multidot_final<<<div_up(nk, 128), 128, 0, s>>>(nk, kMdBlocks, h->wk.p, nk, Hcol, m, accumulate, hk));
+  AMGC_LAUNCH(k_multidot_final<<<div_up((int64_t)nk * 32, 128), 128, 0, s>>>(nk, kMdBlocks, h->wk.p, nk, Hcol, m,
+                                                                            accumulate, hk));
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
@@ -198,7 +202,7 @@ int fgmres(amgc_hierarchy* h, const double* rhs, double* x, int* iters_out, doub
       double* vj = h->V.p + (int64_t)j * n;
       double* zj = h->Zs.p + (int64_t)j * n;
       double* w = h->V.p + (int64_t)(j + 1) * n;
-      AMGC_TRY(vcycle(h, 0, vj, zj));
+      AMGC_TRY(precond_apply(h, vj, zj));
       AMGC_TRY(saddle_apply(h, 0, zj, w));
       // CGS2
       for (int pass = 0; pass < 2; ++pass) {

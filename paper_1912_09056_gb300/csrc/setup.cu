@@ -43,6 +43,49 @@ __global__ void k_sort_segments(int nseg, const int* __restrict__ ptr, int* __re
   }
 }
 
+// Same, one warp per segment: each element's rank is the number of smaller keys (keys are
+// distinct within a segment); segments longer than the shared buffer fall back to one thread.
+constexpr int kSortCap = 1024;
+constexpr int kSortWarps = 4;
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_sort_segments_warp(int nseg, const int* __restrict__ ptr, int* __restrict__ key, int* __restrict__ pay) {
+  __shared__ int sk[kSortWarps][kSortCap];
+  __shared__ int sp[kSortWarps][kSortCap];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int sgi = blockIdx.x * kSortWarps + wid;
+  if (sgi >= nseg) return;
+  const int b = ptr[sgi], e = ptr[sgi + 1], n = e - b;
+  if (n <= 1) return;
+  if (n > kSortCap) {
+    if (lane == 0) {
+      for (int i = b + 1; i < e; ++i) {
+        int k = key[i], p = pay ? pay[i] : 0;
+        int j = i - 1;
+        while (j >= b && key[j] > k) {
+          key[j + 1] = key[j];
+          if (pay) pay[j + 1] = pay[j];
+          --j;
+        }
+        key[j + 1] = k;
+        if (pay) pay[j + 1] = p;
+      }
+    }
+    return;
+  }
+  for (int i = lane; i < n; i += 32) {
+    sk[wid][i] = key[b + i];
+    if (pay) sp[wid][i] = pay[b + i];
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    const int k = sk[wid][i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) r += sk[wid][j] < k;
+    key[b + r] = k;
+    if (pay) pay[b + r] = sp[wid][i];
+  }
+}
+
 // Counting sort of items 0..n-1 by bucket id: out ptr (nb+1) and idx (items sorted by bucket,
 // ascending item id inside a bucket).
 __global__ void k_count(int n, const int* __restrict__ bucket, int* __restrict__ cnt) {
@@ -69,7 +112,7 @@ static int bucket_lists(int n, const int* bucket, int nb, DBuf<int>& ptr, DBuf<i
   AMGC_TRY(idx.alloc(std::max(total, 1)));
   AMGC_LAUNCH(k_copy_int<<<div_up(nb + 1, 256), 256, 0, s>>>(nb + 1, ptr.p, cur.p));
   if (n > 0) AMGC_LAUNCH(k_scatter<<<div_up(n, 256), 256, 0, s>>>(n, bucket, cur.p, idx.p));
-  if (nb > 0) AMGC_LAUNCH(k_sort_segments<<<div_up(nb, 128), 128, 0, s>>>(nb, ptr.p, idx.p, nullptr));
+  if (nb > 0) AMGC_LAUNCH(k_sort_segments_warp<<<div_up(nb, kSortWarps), kSortWarps * 32, 0, s>>>(nb, ptr.p, idx.p, nullptr));
   AMGC_CUDA_TRY(cudaGetLastError());
   AMGC_CUDA_TRY(cudaStreamSynchronize(s));
   return AMGC_OK;
@@ -297,7 +340,7 @@ int build_fine_level(amgc_hierarchy* h, const amgc_bsr* K, const double* D, cons
   AMGC_TRY(exclusive_scan(mt_ptr.p, mt_ptr.p, nm + 1, s, nullptr));
   AMGC_LAUNCH(k_copy_int<<<div_up(nm + 1, 256), 256, 0, s>>>(nm + 1, mt_ptr.p, mt_cur.p));
   if (ns > 0) AMGC_LAUNCH(k_mt_scatter<<<div_up(ns, 256), 256, 0, s>>>(ns, dMrp.p, dMcol.p, nm, mt_cur.p, mt_idx.p, m_pos.p));
-  if (nm > 0) AMGC_LAUNCH(k_sort_segments<<<div_up(nm, 128), 128, 0, s>>>(nm, mt_ptr.p, mt_idx.p, m_pos.p));
+  if (nm > 0) AMGC_LAUNCH(k_sort_segments_warp<<<div_up(nm, kSortWarps), kSortWarps * 32, 0, s>>>(nm, mt_ptr.p, mt_idx.p, m_pos.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   // --- B1 (nn x ns, 3x3)
   L.B1.nbr = nn; L.B1.nbc = ns; L.B1.br = 3; L.B1.bc = 3;
@@ -739,38 +782,49 @@ __global__ void __launch_bounds__(kGemmWarps * 32)
 k_spgemm_numeric(int nrow, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
                  const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
                  const int* __restrict__ crp, const int* __restrict__ ccol, double* __restrict__ cval) {
+  constexpr int NQ = BR * BC;   // output elements per block product
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int row = blockIdx.x * kGemmWarps + wid;
   if (row >= nrow) return;
   const int c0 = crp[row], c1 = crp[row + 1];
-  for (int64_t q = (int64_t)c0 * BR * BC + lane; q < (int64_t)c1 * BR * BC; q += 32) cval[q] = 0.0;
+  for (int64_t q = (int64_t)c0 * NQ + lane; q < (int64_t)c1 * NQ; q += 32) cval[q] = 0.0;
   __syncwarp();
   for (int e = arp[row]; e < arp[row + 1]; ++e) {
     const int k = acol[e];
-    double a[BR * BK];
-#pragma unroll
-    for (int t = 0; t < BR * BK; ++t) a[t] = aval[(int64_t)e * BR * BK + t];
-    for (int t = brp[k] + lane; t < brp[k + 1]; t += 32) {
-      const int c = bcol[t];
-      int lo = c0, hi = c1 - 1;
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (ccol[mid] < c) lo = mid + 1;
-        else hi = mid;
-      }
-      const double* b = bval + (int64_t)t * BK * BC;
-      double* cv = cval + (int64_t)lo * BR * BC;
-#pragma unroll
-      for (int i = 0; i < BR; ++i)
-#pragma unroll
-        for (int j = 0; j < BC; ++j) {
-          double s = cv[i * BC + j];
-#pragma unroll
-          for (int m = 0; m < BK; ++m) s = fma(a[i * BK + m], b[m * BC + j], s);
-          cv[i * BC + j] = s;
+    const double* ae = aval + (int64_t)e * BR * BK;
+    const int t0 = brp[k], t1 = brp[k + 1];
+    for (int tc = t0; tc < t1; tc += 32) {
+      // position in C's row of the block column of B entry tc + lane
+      int pos = 0;
+      if (tc + lane < t1) {
+        const int c = bcol[tc + lane];
+        int lo = c0, hi = c1 - 1;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (ccol[mid] < c) lo = mid + 1;
+          else hi = mid;
         }
+        pos = lo;
+      }
+      const int nt = min(32, t1 - tc);
+      // work items (B entry t, output element qe); distinct items touch distinct C values
+      for (int wb = 0; wb < nt * NQ; wb += 32) {
+        const int w = wb + lane;
+        const int t = w / NQ;
+        const int p = __shfl_sync(0xffffffffu, pos, t < nt ? t : 0);
+        if (w < nt * NQ) {
+          const int qe = w - t * NQ;
+          const int i = qe / BC, j = qe - i * BC;
+          const double* bb = bval + (int64_t)(tc + t) * BK * BC + j;
+          const double* ai = ae + i * BK;
+          double sacc = cval[(int64_t)p * NQ + qe];
+#pragma unroll
+          for (int m = 0; m < BK; ++m) sacc = fma(__ldg(ai + m), __ldg(bb + m * BC), sacc);
+          cval[(int64_t)p * NQ + qe] = sacc;
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
@@ -868,7 +922,7 @@ static int bsr_transpose(amgc_hierarchy* h, const DBsr& A, DBsr& T) {
   AMGC_TRY(exclusive_scan(T.rowptr.p, T.rowptr.p, A.nbc + 1, s, nullptr));
   AMGC_LAUNCH(k_copy_int<<<div_up(A.nbc + 1, 256), 256, 0, s>>>(A.nbc + 1, T.rowptr.p, cur.p));
   if (A.nbr > 0) AMGC_LAUNCH(k_tr_scatter<<<div_up(A.nbr, 256), 256, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, cur.p, T.col.p, src.p));
-  if (A.nbc > 0) AMGC_LAUNCH(k_sort_segments<<<div_up(A.nbc, 128), 128, 0, s>>>(A.nbc, T.rowptr.p, T.col.p, src.p));
+  if (A.nbc > 0) AMGC_LAUNCH(k_sort_segments_warp<<<div_up(A.nbc, kSortWarps), kSortWarps * 32, 0, s>>>(A.nbc, T.rowptr.p, T.col.p, src.p));
   if (A.nnzb > 0) AMGC_LAUNCH(k_tr_values<<<div_up(A.nnzb, 256), 256, 0, s>>>(A.nnzb, A.br, A.bc, src.p, A.val.p, T.val.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   AMGC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1036,6 +1090,71 @@ int smoother_setup(amgc_hierarchy* h, int l) {
   if (L.lam_max == 0.0) AMGC_TRY(lambda_max_estimate(h, L, &L.lam_max));
   L.omega_j = h->opts.jacobi_omega > 0.0 ? h->opts.jacobi_omega : (4.0 / 3.0) / L.lam_max;
   AMGC_TRY(alloc_work(L));
+  return AMGC_OK;
+}
+
+// ======================================================================== SELL-32 copy of K
+__global__ void k_sell_len(int nbr, int nslice, const int* __restrict__ rp, int* __restrict__ len) {
+  int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= nslice) return;
+  int m = 0;
+  for (int r = sl * 32; r < sl * 32 + 32 && r < nbr; ++r) m = max(m, rp[r + 1] - rp[r]);
+  len[sl] = m;
+}
+__global__ void k_sell_fill(int nbr, int nslice, int bs, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ val, const int* __restrict__ off, const int* __restrict__ len,
+                            int* __restrict__ scol, double* __restrict__ sval) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nslice * 32) return;
+  const int lane = row & 31, sl = row >> 5;
+  const int64_t o = off[sl];
+  const int L = len[sl];
+  const int b0 = row < nbr ? rp[row] : 0;
+  const int nb = row < nbr ? rp[row + 1] - b0 : 0;
+  for (int t = 0; t < L; ++t) {
+    const int64_t ci = (o + t) * 32 + lane;
+    const int64_t vi = (o + t) * bs * 32 + lane;
+    if (t < nb) {
+      scol[ci] = col[b0 + t];
+      const double* v = val + (int64_t)(b0 + t) * bs;
+      for (int k = 0; k < bs; ++k) sval[vi + 32 * k] = v[k];
+    } else {
+      scol[ci] = 0;
+      for (int k = 0; k < bs; ++k) sval[vi + 32 * k] = 0.0;
+    }
+  }
+}
+
+static int build_sell_of(amgc_hierarchy* h, const DBsr& A, Sell& S) {
+  cudaStream_t s = h->stream;
+  const int ns = div_up(A.nbr, 32);
+  const int bs = A.br * A.bc;
+  S.br = A.br;
+  S.bc = A.bc;
+  AMGC_TRY(S.len.alloc(ns));
+  AMGC_TRY(S.off.alloc(ns + 1));
+  AMGC_LAUNCH(k_sell_len<<<div_up(ns, 128), 128, 0, s>>>(A.nbr, ns, A.rowptr.p, S.len.p));
+  AMGC_CUDA_TRY(cudaMemsetAsync(S.off.p, 0, (ns + 1) * sizeof(int), s));
+  AMGC_LAUNCH(k_copy_int<<<div_up(ns, 256), 256, 0, s>>>(ns, S.len.p, S.off.p));
+  int slots = 0;
+  AMGC_TRY(exclusive_scan(S.off.p, S.off.p, ns + 1, s, &slots));
+  S.slots = slots;
+  AMGC_TRY(S.col.alloc((size_t)std::max(slots, 1) * 32));
+  AMGC_TRY(S.val.alloc((size_t)std::max(slots, 1) * bs * 32));
+  AMGC_LAUNCH(k_sell_fill<<<div_up((int64_t)ns * 32, 256), 256, 0, s>>>(A.nbr, ns, bs, A.rowptr.p, A.col.p, A.val.p,
+                                                                      S.off.p, S.len.p, S.col.p, S.val.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  S.nslice = ns;
+  return AMGC_OK;
+}
+
+// SELL copies of the finest level's K (3x3) and, once it exists, P (3x6) for the
+// thread-per-row applies; each copy is built once.
+int build_sell(amgc_hierarchy* h, int l) {
+  Level& L = h->L[l];
+  if (L.bu != 3) return AMGC_OK;
+  if (L.Ks.nslice == 0) AMGC_TRY(build_sell_of(h, L.K, L.Ks));
+  if (L.P.nbr > 0 && L.Ps.nslice == 0) AMGC_TRY(build_sell_of(h, L.P, L.Ps));
   return AMGC_OK;
 }
 

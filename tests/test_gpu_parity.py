@@ -165,3 +165,34 @@ def test_rejects_bad_input():
     assert code == amgc.AMGC_NOT_CONVERGED and it == 2 and rr > 1e-8
     h.close()
     h2.close()
+
+
+# FP32 cycle: FP32 storage, arithmetic and accumulation inside the V-cycle, FP64 Schur-block
+# inverses, coarsest inverse and FGMRES.  One cycle's relative deviation from the FP64 oracle
+# is bounded by a few thousand FP32 roundings (2^-24 ~ 6e-8) through at most ~330-term sums
+# on three levels: 1e-4 leaves an order of magnitude of margin.  The solve itself is FP64 and
+# must reach the same 1e-8 relative residual.
+FP32_CYCLE_RTOL = 1e-4
+
+
+@pytest.mark.parametrize("case", ["tiny_SA_3lvl", "small_tilted_partial_SA", "small_simplec_2sweeps"])
+def test_fp32_cycle_matches_oracle_and_solves(case):
+    make, opts = CASES[case]
+    prob = make()
+    h64 = amgc.setup(prob, **opts)
+    h32 = amgc.setup(prob, precision=32, **opts)
+    ref = oracle_setup(prob, Options(**opts))
+    ez, ey = vcycle_and_apply(h32, ref, prob.n, seed=3)
+    assert ey <= 1e-13, "the operator apply stays FP64"
+    assert ez <= FP32_CYCLE_RTOL, f"FP32 V-cycle differs: {ez:.2e}"
+    assert ez > 1e-12, "FP32 cycle unexpectedly bit-identical to FP64"
+    b = torch.from_numpy(prob.rhs).cuda()
+    x64 = torch.zeros_like(b)
+    x32 = torch.zeros_like(b)
+    it64, rr64, _ = h64.solve(b, x64)
+    it32, rr32, _ = h32.solve(b, x32)
+    A = ref.A0()
+    assert np.linalg.norm(prob.rhs - A @ x32.cpu().numpy()) <= 1e-8 * np.linalg.norm(prob.rhs)
+    assert it32 <= it64 + 3, (it32, it64)
+    h64.close()
+    h32.close()
