@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--iters", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--reps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -259,7 +260,7 @@ def main_gpu(args):
         h32.vcycle(r, z)
     ev32[3].record()
     torch.cuda.synchronize()
-    h32.profile(True)
+    h32.profile(2)                      # the FP32 cycle's fine-level K applies only
     h32.solve(rhs_d, x32)
     kms32, kl32, kb32, _ = h32.profile_read()
     h32.close()
@@ -279,8 +280,36 @@ def main_gpu(args):
         fp32["k_apply_hbm_frac"] = round(fp32["k_apply_gbs"] / float(
             json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else fp32["k_apply_gbs"] / 6800.0, 4)
+    # ---- adjoint on the ~1M-row workload with a lognormal modulus field
+    adj_info = None
+    if not args.no_adjoint:
+        from paper_1912_09056_gb300.adjoint import ElementTables, contact_gradients
+        p4 = workload(4, keep_full=True)
+        tab = ElementTables(p4)
+        h4 = amgc.setup(p4, amgc.default_options(**OPTS))
+        b4 = torch.from_numpy(p4.rhs).to(dev)
+        x4 = torch.zeros_like(b4)
+        it4, rr4, _ = h4.solve(b4, x4)
+        contact_gradients(p4, h4, x4, tab, adj_tol=1e-10)          # builds the transposed data once
+        torch.cuda.synchronize()
+        ea = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ea[0].record()
+        for _ in range(reps):
+            h4.solve(b4, x4)
+        ea[1].record()
+        ea[2].record()
+        for _ in range(reps):
+            J4, gE4, gt4, _, ita = contact_gradients(p4, h4, x4, tab, adj_tol=1e-10)
+        ea[3].record()
+        torch.cuda.synchronize()
+        adj_info = {"workload": "adjoint_58^3_50^3", "rows": p4.n, "forward_ms": round(ea[0].elapsed_time(ea[1]) / reps, 3),
+                    "forward_iters": it4, "adjoint_ms": round(ea[2].elapsed_time(ea[3]) / reps, 3),
+                    "adjoint_iters": ita, "adjoint_tol": 1e-10, "n_elements": tab.ne,
+                    "step": "transposed FGMRES with the transposed hierarchy + element gradient kernel"}
+        h4.close()
+        del tab, p4
     # ---- dominant kernel: fine-level K apply, timed by events on its launching stream
-    h.profile(True)
+    h.profile(1)
     for _ in range(reps):
         h.solve(rhs_d, x_d)
     kms, kl, kbytes, kflops = h.profile_read()
@@ -349,6 +378,7 @@ def main_gpu(args):
             "iters": iters[-1], "relres": relres[-1], "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
             "vcycle_ms": round(vcycle_ms, 4),
             "fp32_cycle": fp32,
+            "adjoint": adj_info,
             "roofline": {"bound": "alu", "kernel": "fine-level K apply, FP64 (k_sell<3,3,*>)",
                          "achieved": round(achieved_gflops, 1), "peak": round(fp64_peak, 1), "unit": "GFLOP/s",
                          "frac": round(achieved_gflops / fp64_peak, 4),

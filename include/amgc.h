@@ -151,6 +151,44 @@ int amgc_solve(struct amgc_hierarchy* h, const double* rhs, double* x, int32_t* 
 int amgc_solve_host(struct amgc_hierarchy* h, const double* rhs_host, double* x_host,
                     int32_t* iters, double* relres, void* stream);
 
+/* Adjoint calls (transposed system).  The first one builds, once, the transposed data of every
+ * level (B1^T, B2^T, blockwise transposes of Z and of the Schur-block inverses, the transposed
+ * coarsest inverse).  They need jacobi_sweeps == 1 (AMGC_EINVAL otherwise) and run in FP64.
+ *
+ * amgc_apply_transposed:  y = A^T x.
+ * amgc_vcycle_transposed: z = M^T r, M the V-cycle of amgc_vcycle.  Since K is symmetric, M^T
+ *   is the V-cycle on A^T with each CheapSIMPLE sweep transposed (multiplier update
+ *   w = -alpha S^-T (e_lambda - B1^T A~^-1 e_u) first, then u += omega D^-1 (e_u - B2^T w)),
+ *   unchanged transfers and the transposed coarsest inverse, so <M x, y> = <x, M^T y>.
+ * amgc_solve_transposed:  FGMRES on A^T x = rhs preconditioned by M^T, stopped at
+ *   ||r_k|| / ||r_0|| < tol (tol <= 0: the setup tolerance).  Device vectors, as amgc_solve. */
+int amgc_apply_transposed(struct amgc_hierarchy* h, const double* x, double* y, void* stream);
+int amgc_vcycle_transposed(struct amgc_hierarchy* h, const double* r, double* z, void* stream);
+int amgc_solve_transposed(struct amgc_hierarchy* h, const double* rhs, double* x, double tol, int32_t* iters,
+                          double* relres, void* stream);
+
+/* Outer-product scatter of the adjoint: for x = A^{-1} b and adj = A^{-T} (dJ/dx),
+ * dJ/dK = -adj_u (x) x_u on every stored 3x3 block of the fine K (same order as the K given to
+ * amgc_setup), dJ/dB1 = -adj_u (x) lambda on B1's blocks, dJ/dB2 = -adj_lambda (x) u on B2's
+ * blocks, and dJ/db = adj.  gK: nnzb(K)*9 doubles; gB1, gB2: nnzb*9 doubles or NULL (block
+ * counts from amgc_export).  All device pointers; adj, x of length rows[0]. */
+int amgc_grad_scatter(struct amgc_hierarchy* h, const double* adj, const double* x, double* gK, double* gB1,
+                      double* gB2, void* stream);
+
+/* Element-level gradients for K = sum_e E_e Khat_e and the lifted right-hand side
+ * f = -K_fD u_D:
+ *   gE[e] = dJ/dE_e = -adj_e^T Khat_e u_e   (u_e: solution at free nodes, u_D at prescribed ones;
+ *                                            adj_e: adjoint at free nodes, 0 at prescribed ones)
+ *   gt[c] = dJ/dt_c for a uniform prescribed displacement t on the nodes flagged in lift_mask:
+ *           -sum_e E_e sum_{flagged nodes a of e} (Khat_e adj_e)_(a,c)   (gt may be NULL)
+ * conn: ne x 8 node ids (full numbering), shape: ne indices into Khat (n_shape x 24 x 24, unit
+ * modulus, DOF order node-major), node_free: full node -> free node (K block row) or -1,
+ * adj, x: length-rows[0] vectors, uD: n_all x 3 prescribed values, lift_mask: n_all bytes (or
+ * NULL), E: ne moduli.  All device pointers.  The reduction into gt is deterministic. */
+int amgc_grad_elements(int32_t ne, const int32_t* conn, const int32_t* shape, const double* Khat,
+                       const int32_t* node_free, const double* adj, const double* x, const double* uD,
+                       const uint8_t* lift_mask, const double* E, double* gE, double* gt, void* stream);
+
 int amgc_stats(const struct amgc_hierarchy* h, amgc_stats_t* out);
 
 /* Copies one internal array of level `level` to the host buffer dst (capacity `bytes`).
@@ -188,6 +226,7 @@ int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what,
  * that stream and returns the accumulated device time (ms), the number of launches, the
  * algorithmic bytes those launches move (matrix values and indices once, every vector once) and
  * their algorithmic floating-point operations (two per stored matrix value).
+ * enable is a mask: 1 times the FP64 applies, 2 the FP32 applies, 3 both, 0 stops timing.
  * Enabling resets the counters.  Not for production runs: each launch adds two event records. */
 int amgc_profile(struct amgc_hierarchy* h, int32_t enable);
 int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes,

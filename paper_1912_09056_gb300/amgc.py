@@ -93,6 +93,15 @@ def load():
     lib.amgc_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]
     lib.amgc_profile_read.restype = C.c_int
+    for name in ("amgc_vcycle_transposed", "amgc_apply_transposed"):
+        getattr(lib, name).argtypes = [vp, vp, vp, vp]
+        getattr(lib, name).restype = C.c_int
+    lib.amgc_solve_transposed.argtypes = [vp, vp, vp, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
+    lib.amgc_solve_transposed.restype = C.c_int
+    lib.amgc_grad_scatter.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.amgc_grad_scatter.restype = C.c_int
+    lib.amgc_grad_elements.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.amgc_grad_elements.restype = C.c_int
     lib.amgc_destroy.argtypes = [vp]
     lib.amgc_destroy.restype = None
     lib.amgc_strerror.argtypes = [C.c_int]
@@ -193,8 +202,10 @@ class Hierarchy:
                 raise AmgcError(int(r), "amgc_export")
         return out
 
-    def profile(self, enable: bool = True):
-        _check(self._lib.amgc_profile(self._h, int(enable)), "amgc_profile")
+    def profile(self, enable=True):
+        """enable: True/3 = FP64 and FP32 applies, 1 = FP64 only, 2 = FP32 only, False/0 = off."""
+        mask = 3 if enable is True else int(enable)
+        _check(self._lib.amgc_profile(self._h, mask), "amgc_profile")
 
     def profile_read(self):
         ms = C.c_double(0.0)
@@ -222,6 +233,30 @@ class Hierarchy:
             _check(code, "amgc_solve")
         return it.value, rr.value, code
 
+    def apply_transposed(self, x, y, stream=None):
+        _check(self._lib.amgc_apply_transposed(self._h, _ptr(x), _ptr(y), _stream_ptr(stream)),
+               "amgc_apply_transposed")
+        return y
+
+    def vcycle_transposed(self, r, z, stream=None):
+        _check(self._lib.amgc_vcycle_transposed(self._h, _ptr(r), _ptr(z), _stream_ptr(stream)),
+               "amgc_vcycle_transposed")
+        return z
+
+    def solve_transposed(self, rhs, x, tol: float = 0.0, stream=None, check: bool = True):
+        it = C.c_int32(0)
+        rr = C.c_double(0.0)
+        code = self._lib.amgc_solve_transposed(self._h, _ptr(rhs), _ptr(x), float(tol), C.byref(it), C.byref(rr),
+                                               _stream_ptr(stream))
+        if check:
+            _check(code, "amgc_solve_transposed")
+        return it.value, rr.value, code
+
+    def grad_scatter(self, adj, x, gK, gB1=None, gB2=None, stream=None):
+        _check(self._lib.amgc_grad_scatter(self._h, _ptr(adj), _ptr(x), _ptr(gK), _ptr(gB1), _ptr(gB2),
+                                           _stream_ptr(stream)), "amgc_grad_scatter")
+        return gK
+
     def solve_host(self, rhs: np.ndarray, stream=None, check: bool = True):
         rhs = np.ascontiguousarray(rhs, dtype=np.float64)
         x = np.empty_like(rhs)
@@ -232,6 +267,16 @@ class Hierarchy:
         if check:
             _check(code, "amgc_solve_host")
         return x, it.value, rr.value, code
+
+
+def grad_elements(conn, shape, Khat, node_free, adj, x, uD, E, gE, lift_mask=None, gt=None, stream=None):
+    """amgc_grad_elements on device tensors (see include/amgc.h)."""
+    lib = load()
+    ne = int(conn.shape[0])
+    _check(lib.amgc_grad_elements(ne, _ptr(conn), _ptr(shape), _ptr(Khat), _ptr(node_free), _ptr(adj), _ptr(x),
+                                  _ptr(uD), _ptr(lift_mask), _ptr(E), _ptr(gE), _ptr(gt), _stream_ptr(stream)),
+           "amgc_grad_elements")
+    return gE, gt
 
 
 def setup(prob, options: Optional[Options] = None, stream=None, **opt_kw) -> Hierarchy:

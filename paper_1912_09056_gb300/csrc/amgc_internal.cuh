@@ -142,6 +142,13 @@ struct LevelV {
   const int* b1_rows = nullptr;
   int n_b1_rows = 0;
   const double* Ainv = nullptr;    // coarsest level, FP64 in both precisions
+  // transposed cycle (FP64 only)
+  BsrV<T> B1T, B2T;
+  const T* ZT = nullptr;
+  const double* SinvT = nullptr;
+  const double* AinvT = nullptr;
+  const int* b2t_rows = nullptr;
+  int n_b2t_rows = 0;
   T* x = nullptr;
   T* b = nullptr;
   T* r = nullptr;
@@ -184,6 +191,14 @@ struct Level {
   // coarsest level
   DBuf<double> Ainv;         // rows*rows (row-major)
 
+  // transposed-cycle data (adjoint solves): B1^T, B2^T, blockwise transposed Z and S^-1,
+  // the transposed coarsest inverse, and the rows of B2^T with entries
+  DBsr B1T, B2T;
+  DBuf<double> ZT, SinvT, AinvT;
+  DBuf<int> b2t_rows;
+  int n_b2t_rows = 0;
+  bool has_transposed = false;
+
   // work vectors [u; lambda]
   DBuf<double> x, b, r, t;
   DBuf<double> dlam;         // nl*3
@@ -206,9 +221,10 @@ struct amgc_hierarchy {
   amgc::DBuf<double> partial;      // per-block partial dot products
   std::vector<amgc::LevelV<double>> v64;   // cycle views, FP64
   std::vector<amgc::LevelV<float>> v32;    // cycle views, FP32 (precision 32)
+  bool transposed = false;                 // FGMRES/cycle act on A^T (adjoint solve)
   double* h_pinned = nullptr;      // pinned host scalars
   // event timing of the fine-level K applies (amgc_profile)
-  bool prof = false;
+  int prof = 0;                    // mask: 1 FP64 applies, 2 FP32 applies
   std::vector<cudaEvent_t> prof_ev;
   int prof_pending = 0;
   double prof_ms = 0.0, prof_bytes = 0.0, prof_flops = 0.0;
@@ -243,9 +259,10 @@ int smoother_setup(amgc_hierarchy* h, int l);
 int build_sell(amgc_hierarchy* h, int l);
 int coarse_setup(amgc_hierarchy* h, int l);
 int check_status(amgc_hierarchy* h, const char* where);
+int transposed_setup(amgc_hierarchy* h);
 // kernel timing (api.cu)
-int prof_begin(amgc_hierarchy* h);
-int prof_end(amgc_hierarchy* h, double bytes, double flops);
+int prof_begin(amgc_hierarchy* h, int kind);
+int prof_end(amgc_hierarchy* h, int kind, double bytes, double flops);
 int prof_flush(amgc_hierarchy* h);
 // sparse kernels (cycle.cu)
 int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
@@ -256,6 +273,11 @@ int make_views(amgc_hierarchy* h);
 int precond_apply(amgc_hierarchy* h, const double* r, double* z);   // one V-cycle, FP64 in/out
 int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y);
 // FGMRES (krylov.cu)
-int fgmres(amgc_hierarchy* h, const double* rhs, double* x, int* iters, double* relres);
+int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol, int* iters, double* relres);
+// gradients (grad.cu)
+int grad_scatter(amgc_hierarchy* h, const double* adj, const double* x, double* gK, double* gB1, double* gB2);
+int grad_elements(int ne, const int* conn, const int* shape, const double* Khat, const int* node_free,
+                  const double* adj, const double* x, const double* uD, const uint8_t* lift_mask, const double* E,
+                  double* gE, double* gt, cudaStream_t s);
 
 }  // namespace amgc

@@ -81,8 +81,8 @@ int prof_flush(amgc_hierarchy* h) {
   return AMGC_OK;
 }
 
-int prof_begin(amgc_hierarchy* h) {
-  if (!h->prof) return AMGC_OK;
+int prof_begin(amgc_hierarchy* h, int kind) {
+  if (!(h->prof & kind)) return AMGC_OK;
   if (h->prof_ev.empty()) {
     h->prof_ev.resize(2 * kProfPairs);
     for (auto& e : h->prof_ev) AMGC_CUDA_TRY(cudaEventCreate(&e));
@@ -92,8 +92,8 @@ int prof_begin(amgc_hierarchy* h) {
   return AMGC_OK;
 }
 
-int prof_end(amgc_hierarchy* h, double bytes, double flops) {
-  if (!h->prof) return AMGC_OK;
+int prof_end(amgc_hierarchy* h, int kind, double bytes, double flops) {
+  if (!(h->prof & kind)) return AMGC_OK;
   AMGC_CUDA_TRY(cudaEventRecord(h->prof_ev[2 * h->prof_pending + 1], h->stream));
   h->prof_pending++;
   h->prof_launches++;
@@ -182,7 +182,7 @@ int amgc_solve(struct amgc_hierarchy* h, const double* rhs, double* x, int32_t* 
   h->stream = (cudaStream_t)stream;
   int it = 0;
   double rr = 0.0;
-  int st = fgmres(h, rhs, x, &it, &rr);
+  int st = fgmres(h, rhs, x, 0.0, &it, &rr);
   if (iters) *iters = it;
   if (relres) *relres = rr;
   return st;
@@ -202,13 +202,87 @@ int amgc_solve_host(struct amgc_hierarchy* h, const double* rhs_host, double* x_
   AMGC_CUDA_TRY(cudaMemcpyAsync(b.p, rhs_host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   int it = 0;
   double rr = 0.0;
-  int st = fgmres(h, b.p, x.p, &it, &rr);
+  int st = fgmres(h, b.p, x.p, 0.0, &it, &rr);
   if (st == AMGC_OK || st == AMGC_NOT_CONVERGED)
     AMGC_CUDA_TRY(cudaMemcpyAsync(x_host, x.p, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
   if (iters) *iters = it;
   if (relres) *relres = rr;
   return st;
+}
+
+static int enter_transposed(amgc_hierarchy* h, void* stream, const char* where) {
+  if (!h) {
+    set_error(std::string(where) + ": invalid argument");
+    return AMGC_EINVAL;
+  }
+  if (h->opts.jacobi_sweeps != 1) {
+    set_error(std::string(where) + ": the transposed cycle needs jacobi_sweeps == 1");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  if (!h->L[0].has_transposed) AMGC_TRY(transposed_setup(h));
+  h->transposed = true;
+  return AMGC_OK;
+}
+
+int amgc_apply_transposed(struct amgc_hierarchy* h, const double* x, double* y, void* stream) {
+  if (!x || !y || x == y) {
+    set_error("amgc_apply_transposed: invalid argument");
+    return AMGC_EINVAL;
+  }
+  AMGC_TRY(enter_transposed(h, stream, "amgc_apply_transposed"));
+  int st = saddle_apply(h, 0, x, y);
+  h->transposed = false;
+  return st;
+}
+
+int amgc_vcycle_transposed(struct amgc_hierarchy* h, const double* r, double* z, void* stream) {
+  if (!r || !z || r == z) {
+    set_error("amgc_vcycle_transposed: invalid argument");
+    return AMGC_EINVAL;
+  }
+  AMGC_TRY(enter_transposed(h, stream, "amgc_vcycle_transposed"));
+  int st = precond_apply(h, r, z);
+  h->transposed = false;
+  return st;
+}
+
+int amgc_solve_transposed(struct amgc_hierarchy* h, const double* rhs, double* x, double tol, int32_t* iters,
+                          double* relres, void* stream) {
+  if (!rhs || !x || rhs == x) {
+    set_error("amgc_solve_transposed: invalid argument");
+    return AMGC_EINVAL;
+  }
+  AMGC_TRY(enter_transposed(h, stream, "amgc_solve_transposed"));
+  int it = 0;
+  double rr = 0.0;
+  int st = fgmres(h, rhs, x, tol, &it, &rr);
+  h->transposed = false;
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return st;
+}
+
+int amgc_grad_scatter(struct amgc_hierarchy* h, const double* adj, const double* x, double* gK, double* gB1,
+                      double* gB2, void* stream) {
+  if (!h || !adj || !x || !gK) {
+    set_error("amgc_grad_scatter: invalid argument");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  return grad_scatter(h, adj, x, gK, gB1, gB2);
+}
+
+int amgc_grad_elements(int32_t ne, const int32_t* conn, const int32_t* shape, const double* Khat,
+                       const int32_t* node_free, const double* adj, const double* x, const double* uD,
+                       const uint8_t* lift_mask, const double* E, double* gE, double* gt, void* stream) {
+  if (ne < 0 || (ne > 0 && (!conn || !shape || !Khat || !node_free || !adj || !x || !uD || !gE)) ||
+      (gt && (!lift_mask || !E))) {
+    set_error("amgc_grad_elements: invalid argument");
+    return AMGC_EINVAL;
+  }
+  return grad_elements(ne, conn, shape, Khat, node_free, adj, x, uD, lift_mask, E, gE, gt, (cudaStream_t)stream);
 }
 
 int amgc_stats(const struct amgc_hierarchy* h, amgc_stats_t* out) {
@@ -269,7 +343,7 @@ int amgc_profile(struct amgc_hierarchy* h, int32_t enable) {
     return AMGC_EINVAL;
   }
   AMGC_TRY(prof_flush(h));
-  h->prof = enable != 0;
+  h->prof = enable & 3;
   h->prof_ms = 0.0;
   h->prof_bytes = 0.0;
   h->prof_flops = 0.0;

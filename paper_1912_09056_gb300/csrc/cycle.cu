@@ -120,65 +120,77 @@ int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double bet
   return rowop<0, double>(v, x, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, y, s);
 }
 
-// ------------------------------------------------------------------ SELL-32 thread-per-row apply
-// One thread per block row: value k of a block is one coalesced warp load, one FMA each, and
-// no cross-lane reduction.  Matrix data is streamed (evict-first) so the vectors stay cached.
-// An optional second matrix A2 (the B1 block, few rows) is added from its BSR rows.
+// ------------------------------------------------------------------ SELL-32 row apply
+// Two threads per block row: a warp covers 16 rows of a 32-row slice, lanes 0-15 take the even
+// slots and lanes 16-31 the odd slots (each half-warp load is 16 consecutive values), and one
+// shuffle adds the halves.  Value k of a block is one load and one FMA; matrix data is streamed
+// (evict-first) so the vectors stay cached.  An optional second matrix A2 (the B1 block, few
+// rows) is added from its BSR rows.
+constexpr int kSellThreads = 128;
+
 template <int BR, int BC, int MODE, class T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSellThreads)
 k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, const int* __restrict__ scol,
        const T* __restrict__ sval, const T* __restrict__ x, const int* __restrict__ rp2, const int* __restrict__ c2,
        const T* __restrict__ v2, const T* __restrict__ x2, const T* __restrict__ b, const T* __restrict__ x0,
        const T* __restrict__ dinv, T omega, T* __restrict__ y) {
   constexpr int BS = BR * BC;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nbr) return;
-  const int lane = row & 31, sl = row >> 5;
+  const int gt = blockIdx.x * kSellThreads + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int half = lane >> 4;                                  // slot parity handled by this lane
+  const int row = ((gt >> 5) << 4) + (lane & 15);              // 16 rows per warp
+  const bool live = row < nbr;
+  const int r = live ? row : nbr - 1;                          // dead lanes mirror a valid row
+  const int sl = r >> 5, ls = r & 31;
   const int64_t o = soff[sl];
   const int L = slen[sl];
-  const int* cp = scol + o * 32 + lane;
-  const T* vp = sval + o * (BS * 32) + lane;
+  const int* cp = scol + o * 32 + ls;
+  const T* vp = sval + o * (BS * 32) + ls;
   T acc[BR];
 #pragma unroll
-  for (int r = 0; r < BR; ++r) acc[r] = T(0);
-#pragma unroll 3
-  for (int t = 0; t < L; ++t) {
+  for (int q = 0; q < BR; ++q) acc[q] = T(0);
+#pragma unroll 2
+  for (int t = half; t < L; t += 2) {
     const T* xc = x + (int64_t)__ldcs(cp + t * 32) * BC;
     T xv[BC];
 #pragma unroll
     for (int c = 0; c < BC; ++c) xv[c] = ldg(xc + c);
     const T* v = vp + (int64_t)t * (BS * 32);
 #pragma unroll
-    for (int r = 0; r < BR; ++r)
+    for (int q = 0; q < BR; ++q)
 #pragma unroll
-      for (int c = 0; c < BC; ++c) acc[r] = fma(ldcs(v + (r * BC + c) * 32), xv[c], acc[r]);
+      for (int c = 0; c < BC; ++c) acc[q] = fma(ldcs(v + (q * BC + c) * 32), xv[c], acc[q]);
   }
+#pragma unroll
+  for (int q = 0; q < BR; ++q) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], 16);
+  if (half != 0 || !live) return;
   if (rp2 != nullptr) {
     for (int e = rp2[row]; e < rp2[row + 1]; ++e) {
       const T* blk = v2 + (int64_t)e * BR * 3;
       const T* d = x2 + 3 * (int64_t)c2[e];
       const T d0 = d[0], d1 = d[1], d2 = d[2];
 #pragma unroll
-      for (int r = 0; r < BR; ++r) acc[r] = fma(blk[3 * r], d0, fma(blk[3 * r + 1], d1, fma(blk[3 * r + 2], d2, acc[r])));
+      for (int q = 0; q < BR; ++q) acc[q] = fma(blk[3 * q], d0, fma(blk[3 * q + 1], d1, fma(blk[3 * q + 2], d2, acc[q])));
     }
   }
 #pragma unroll
-  for (int r = 0; r < BR; ++r) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * BR + r, acc[r]);
+  for (int q = 0; q < BR; ++q) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * BR + q, acc[q]);
 }
 
 template <int MODE, class T>
 static int sell_apply(const SellV<T>& S, int nbr, const BsrV<T>* A2, const T* x, const T* x2, const T* b, const T* x0,
                       const T* dinv, double omega, T* y, cudaStream_t s) {
-  const int g = div_up(nbr, 256);
+  const int g = div_up((int64_t)nbr * 2, kSellThreads);
   const int* rp2 = A2 ? A2->rp : nullptr;
   const int* c2 = A2 ? A2->col : nullptr;
   const T* v2 = A2 ? A2->val : nullptr;
+  if (nbr == 0) return AMGC_OK;
   if (S.br == 3 && S.bc == 3)
-    AMGC_LAUNCH(k_sell<3, 3, MODE, T><<<g, 256, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2, b, x0,
-                                                        dinv, (T)omega, y));
+    AMGC_LAUNCH(k_sell<3, 3, MODE, T><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
+                                                                 b, x0, dinv, (T)omega, y));
   else if (S.br == 3 && S.bc == 6)
-    AMGC_LAUNCH(k_sell<3, 6, MODE, T><<<g, 256, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2, b, x0,
-                                                        dinv, (T)omega, y));
+    AMGC_LAUNCH(k_sell<3, 6, MODE, T><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
+                                                                 b, x0, dinv, (T)omega, y));
   else {
     set_error("sell_apply: unsupported block shape");
     return AMGC_EINVAL;
@@ -235,14 +247,17 @@ k_lm(int nl, const int* __restrict__ rp, const int* __restrict__ col, const T* _
 }
 
 template <int MODE, class T>
-static int lm_op(const LevelV<T>& L, const T* u, const T* g, T* lam, double alpha, T* out, cudaStream_t s) {
+static int lm_op(const LevelV<T>& L, const T* u, const T* g, T* lam, double alpha, T* out, cudaStream_t s,
+                 bool transposed = false) {
   if (L.nl == 0) return AMGC_OK;
   const int th = 128;
   const int gl = div_up((int64_t)L.nl * 32, th);
+  const BsrV<T>& B = transposed ? L.B1T : L.B2;   // multiplier rows of A: B2; of A^T: B1^T
+  const T* Z = transposed ? L.ZT : L.Z;
   if (L.bu == 3)
-    AMGC_LAUNCH(k_lm<3, MODE, T><<<gl, th, 0, s>>>(L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam, L.Sinv, alpha, out));
+    AMGC_LAUNCH(k_lm<3, MODE, T><<<gl, th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g, lam, L.Sinv, alpha, out));
   else
-    AMGC_LAUNCH(k_lm<6, MODE, T><<<gl, th, 0, s>>>(L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam, L.Sinv, alpha, out));
+    AMGC_LAUNCH(k_lm<6, MODE, T><<<gl, th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g, lam, L.Sinv, alpha, out));
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
@@ -346,16 +361,19 @@ static double k_apply_bytes(const LevelV<T>& L, int extra_vecs) {
 // K apply of level l (MODE of k_rowop), timed when the level is the finest one.
 template <int MODE, class T>
 static int k_apply(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* x1, const T* lam, const T* b, const T* x0,
-                   T* y) {
+                   T* y, bool transposed = false) {
   const bool t = l == 0;
-  if (t) AMGC_TRY(prof_begin(h));
-  const BsrV<T>* B1 = L.nl ? &L.B1 : nullptr;
+  const int kind = sizeof(T) == 8 ? 1 : 2;
+  if (t) AMGC_TRY(prof_begin(h, kind));
+  // K is symmetric on every level (elasticity and Galerkin products), so A^T shares it;
+  // the multiplier coupling of the u rows is B1 for A and B2^T for A^T.
+  const BsrV<T>* B1 = L.nl ? (transposed ? &L.B2T : &L.B1) : nullptr;
   if (L.Ks.nslice > 0)
     AMGC_TRY((sell_apply<MODE, T>(L.Ks, L.nn, B1, x1, lam, b, x0, L.dinv, L.omega_j, y, h->stream)));
   else
     AMGC_TRY((rowop<MODE, T>(L.K, x1, B1, lam, b, x0, L.dinv, L.omega_j, y, h->stream)));
   if (t)
-    AMGC_TRY(prof_end(h, k_apply_bytes(L, MODE == 3 ? 3 : (MODE == 2 ? 1 : 0)),
+    AMGC_TRY(prof_end(h, kind, k_apply_bytes(L, MODE == 3 ? 3 : (MODE == 2 ? 1 : 0)),
                       2.0 * ((double)L.K.nnzb * L.bu * L.bu + (double)L.B1.nnzb * L.bu * 3)));
   return AMGC_OK;
 }
@@ -451,16 +469,140 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
   return AMGC_OK;
 }
 
+// ------------------------------------------------------------------ transposed cycle (adjoint)
+// The cycle operator is M = (I - Q A) [Q + P M_c R (I - A Q)] + Q for one sweep each side, Q the
+// CheapSIMPLE sweep operator; its transpose is the same V-cycle on A^T with the sweep Q^T, the
+// transfers R = P^T and P unchanged, and the transposed coarsest inverse.  From the residual
+// e = y - A^T x of a transposed sweep (one Jacobi predictor sweep):
+//   w   = -alpha S^-T (e_lambda - B1^T A~^-1 e_u),  lambda += w
+//   u  += omega D^-1 (e_u - B2^T w)
+// (the order of the multiplier and displacement updates is reversed with respect to Q).
+
+// w_l = -alpha S^-T_l (e_l - sum_i B1T[l,i] (atinv_i e_u,i)); lam_l += w_l; out_l = w_l
+template <int BU>
+__global__ void __launch_bounds__(128)
+k_lm_tsweep(int nl, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+            const double* __restrict__ eu, const double* __restrict__ atinv, const double* __restrict__ el,
+            const double* __restrict__ SinvT, double alpha, double* __restrict__ lam, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (l >= nl) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int64_t b = rp[l] + lane; b < rp[l + 1]; b += 32) {
+    const int64_t c0 = (int64_t)col[b] * BU;
+    const double* v = val + b * (3 * BU);
+#pragma unroll
+    for (int c = 0; c < BU; ++c) {
+      const double xv = atinv[c0 + c] * eu[c0 + c];
+      acc[0] = fma(v[c], xv, acc[0]);
+      acc[1] = fma(v[BU + c], xv, acc[1]);
+      acc[2] = fma(v[2 * BU + c], xv, acc[2]);
+    }
+  }
+  const double s0 = warp_sum(acc[0]), s1 = warp_sum(acc[1]), s2 = warp_sum(acc[2]);
+  if (lane != 0) return;
+  const double r0 = el[3 * l] - s0, r1 = el[3 * l + 1] - s1, r2 = el[3 * l + 2] - s2;
+  const double* S = SinvT + (int64_t)l * 9;
+  const double w0 = -alpha * (S[0] * r0 + S[1] * r1 + S[2] * r2);
+  const double w1 = -alpha * (S[3] * r0 + S[4] * r1 + S[5] * r2);
+  const double w2 = -alpha * (S[6] * r0 + S[7] * r1 + S[8] * r2);
+  lam[3 * l] += w0;
+  lam[3 * l + 1] += w1;
+  lam[3 * l + 2] += w2;
+  out[3 * l] = w0;
+  out[3 * l + 1] = w1;
+  out[3 * l + 2] = w2;
+}
+__global__ void k_axpy_dinv(int64_t n, const double* __restrict__ e, const double* __restrict__ dinv, double omega,
+                            double* __restrict__ u) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) u[i] += omega * dinv[i] * e[i];
+}
+
+template <class T>
+static int tsmooth(amgc_hierarchy* h, const LevelV<double>& L, int l, const double* y, double* x, bool zero_guess) {
+  cudaStream_t s = h->stream;
+  const int nu = L.nu();
+  const int th = 256;
+  double* e = L.r;
+  if (zero_guess) {
+    AMGC_LAUNCH(k_zero<double><<<div_up(L.rows(), th), th, 0, s>>>(L.rows(), x));
+    AMGC_LAUNCH(k_copy<double><<<div_up(L.rows(), th), th, 0, s>>>(L.rows(), y, e));
+  } else {
+    AMGC_TRY((k_apply<2, double>(h, L, l, x, x + nu, y, nullptr, e, true)));
+    AMGC_TRY((lm_op<0, double>(L, x, y + nu, x + nu, 0.0, e + nu, s, true)));
+  }
+  if (L.nl > 0) {
+    const int gl = div_up((int64_t)L.nl * 32, 128);
+    if (L.bu == 3)
+      AMGC_LAUNCH(k_lm_tsweep<3><<<gl, 128, 0, s>>>(L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
+                                                    h->opts.simple_alpha, x + nu, L.dlam));
+    else
+      AMGC_LAUNCH(k_lm_tsweep<6><<<gl, 128, 0, s>>>(L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
+                                                    h->opts.simple_alpha, x + nu, L.dlam));
+  }
+  AMGC_LAUNCH(k_axpy_dinv<<<div_up(nu, th), th, 0, s>>>(nu, e, L.dinv, L.omega_j, x));
+  if (L.n_b2t_rows > 0) {
+    const int gb = div_up((int64_t)L.n_b2t_rows * 32, 128);
+    if (L.bu == 3)
+      AMGC_LAUNCH(k_b1_update<3, double><<<gb, 128, 0, s>>>(L.n_b2t_rows, L.b2t_rows, L.B2T.rp, L.B2T.col, L.B2T.val,
+                                                            L.dlam, L.dinv, L.omega_j, x));
+    else
+      AMGC_LAUNCH(k_b1_update<6, double><<<gb, 128, 0, s>>>(L.n_b2t_rows, L.b2t_rows, L.B2T.rp, L.B2T.col, L.B2T.val,
+                                                            L.dlam, L.dinv, L.omega_j, x));
+  }
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+static int vcycle_transposed(amgc_hierarchy* h, int l, const double* y, double* x) {
+  std::vector<LevelV<double>>& V = h->v64;
+  const LevelV<double>& L = V[l];
+  cudaStream_t s = h->stream;
+  const int th = 256;
+  if (l == (int)V.size() - 1) {
+    const int n = L.rows();
+    AMGC_LAUNCH(k_gemv<double><<<div_up((int64_t)n * 32, th), th, 0, s>>>(n, L.AinvT, y, x));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    return AMGC_OK;
+  }
+  const int nu = L.nu();
+  const LevelV<double>& C = V[l + 1];
+  const int sweeps = h->opts.smoother_sweeps;
+  if (sweeps == 0) AMGC_LAUNCH(k_zero<double><<<div_up(L.rows(), th), th, 0, s>>>(L.rows(), x));
+  for (int k = 0; k < sweeps; ++k) AMGC_TRY(tsmooth<double>(h, L, l, y, x, k == 0));
+  // residual with A^T, then the same restriction as the forward cycle
+  AMGC_TRY((k_apply<2, double>(h, L, l, x, x + nu, y, nullptr, L.r, true)));
+  AMGC_TRY((lm_op<0, double>(L, x, y + nu, x + nu, 0.0, L.r + nu, s, true)));
+  AMGC_TRY((rowop<0, double>(L.R, L.r, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, C.b, s)));
+  if (C.nl > 0)
+    AMGC_LAUNCH(k_restrict_lm<double><<<div_up(C.nl, 128), 128, 0, s>>>(C.nl, L.rl_ptr, L.rl_idx, L.pl_w, L.r + nu,
+                                                                        C.b + C.nu()));
+  AMGC_TRY(vcycle_transposed(h, l + 1, C.b, C.x));
+  if (L.Ps.nslice > 0)
+    AMGC_TRY((sell_apply<1, double>(L.Ps, L.nn, nullptr, C.x, nullptr, nullptr, nullptr, nullptr, 0.0, x, s)));
+  else
+    AMGC_TRY((rowop<1, double>(L.P, C.x, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, x, s)));
+  if (L.nl > 0)
+    AMGC_LAUNCH(k_prolong_lm<double><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.lagg, L.pl_w, C.x + C.nu(), x + nu));
+  for (int k = 0; k < sweeps; ++k) AMGC_TRY(tsmooth<double>(h, L, l, y, x, false));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+// y = A x, or y = A^T x while the hierarchy is in transposed mode
 int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y) {
   const LevelV<double>& L = h->v64[l];
   const int nu = L.nu();
-  AMGC_TRY((k_apply<0, double>(h, L, l, x, x + nu, nullptr, nullptr, y)));
-  AMGC_TRY((lm_op<2, double>(L, x, nullptr, const_cast<double*>(x + nu), 0.0, y + nu, h->stream)));
+  const bool tr = h->transposed;
+  AMGC_TRY((k_apply<0, double>(h, L, l, x, x + nu, nullptr, nullptr, y, tr)));
+  AMGC_TRY((lm_op<2, double>(L, x, nullptr, const_cast<double*>(x + nu), 0.0, y + nu, h->stream, tr)));
   return AMGC_OK;
 }
 
 // One V-cycle with FP64 input and output; the FP32 cycle converts at entry and exit.
 int precond_apply(amgc_hierarchy* h, const double* r, double* z) {
+  if (h->transposed) return vcycle_transposed(h, 0, r, z);
   if (h->opts.precision == 32) {
     LevelV<float>& L0 = h->v32[0];
     const int64_t n = L0.rows();
@@ -525,6 +667,12 @@ int make_views(amgc_hierarchy* h) {
     v.Ps = sview<double>(L.Ps, L.Ps.val.p);
     v.Z = L.Z.p; v.dinv = L.dinv.p; v.atinv = L.atinv.p; v.pl_w = L.pl_w.p;
     v.x = L.x.p; v.b = L.b.p; v.r = L.r.p; v.t = L.t.p; v.dlam = L.dlam.p;
+    if (L.has_transposed) {
+      v.B1T = bview<double>(L.B1T, L.B1T.val.p);
+      v.B2T = bview<double>(L.B2T, L.B2T.val.p);
+      v.ZT = L.ZT.p; v.SinvT = L.SinvT.p; v.AinvT = L.AinvT.p;
+      v.b2t_rows = L.b2t_rows.p; v.n_b2t_rows = L.n_b2t_rows;
+    }
     h->v64.push_back(v);
   }
   if (h->opts.precision != 32) return AMGC_OK;

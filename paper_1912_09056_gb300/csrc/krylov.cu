@@ -158,12 +158,12 @@ static int multidot(amgc_hierarchy* h, int64_t n, int nk, const double* V, const
   return AMGC_OK;
 }
 
-int fgmres(amgc_hierarchy* h, const double* rhs, double* x, int* iters_out, double* relres_out) {
+int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol_in, int* iters_out, double* relres_out) {
   cudaStream_t s = h->stream;
   const int64_t n = h->L[0].rows();
   const int m = std::max(1, std::min(h->opts.fgmres_restart, kMaxRestart));
   const int maxit = std::max(1, h->opts.fgmres_maxit);
-  const double tol = h->opts.tol;
+  const double tol = tol_in > 0.0 ? tol_in : h->opts.tol;
   AMGC_TRY(ensure_workspace(h, n, m));
   const int th = 256;
   const int gn = div_up(n, th);

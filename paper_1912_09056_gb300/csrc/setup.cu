@@ -1281,6 +1281,54 @@ int coarsen_level(amgc_hierarchy* h, int l) {
   return AMGC_OK;
 }
 
+// ======================================================================== transposed-cycle data
+__global__ void k_transpose3(int n, const double* __restrict__ a, double* __restrict__ t) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) t[(int64_t)l * 9 + c * 3 + r] = a[(int64_t)l * 9 + r * 3 + c];
+}
+__global__ void k_transpose_dense(int n, const double* __restrict__ a, double* __restrict__ t) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  t[(int64_t)j * n + i] = a[idx];
+}
+
+// Builds, once, what the transposed V-cycle needs on every level.
+int transposed_setup(amgc_hierarchy* h) {
+  cudaStream_t s = h->stream;
+  const int nlev = (int)h->L.size();
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = h->L[l];
+    if (L.has_transposed) continue;
+    AMGC_TRY(bsr_transpose(h, L.B1, L.B1T));
+    AMGC_TRY(bsr_transpose(h, L.B2, L.B2T));
+    AMGC_TRY(L.ZT.alloc((size_t)std::max(L.nl, 1) * 9));
+    if (L.nl > 0) AMGC_LAUNCH(k_transpose3<<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.Z.p, L.ZT.p));
+    if (l < nlev - 1) {
+      AMGC_TRY(L.SinvT.alloc((size_t)std::max(L.nl, 1) * 9));
+      if (L.nl > 0) AMGC_LAUNCH(k_transpose3<<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.Sinv.p, L.SinvT.p));
+      DBuf<int> flag;
+      AMGC_TRY(flag.alloc(L.nn + 1));
+      AMGC_LAUNCH(k_nonempty<<<div_up(L.nn, 256), 256, 0, s>>>(L.nn, L.B2T.rowptr.p, flag.p));
+      int cnt = 0;
+      AMGC_TRY(exclusive_scan(flag.p, flag.p, L.nn, s, &cnt));
+      L.n_b2t_rows = cnt;
+      AMGC_TRY(L.b2t_rows.alloc(std::max(cnt, 1)));
+      AMGC_LAUNCH(k_compact<<<div_up(L.nn, 256), 256, 0, s>>>(L.nn, L.B2T.rowptr.p, flag.p, L.b2t_rows.p));
+    } else {
+      const int n = L.rows();
+      AMGC_TRY(L.AinvT.alloc((size_t)n * n));
+      AMGC_LAUNCH(k_transpose_dense<<<div_up((int64_t)n * n, 256), 256, 0, s>>>(n, L.Ainv.p, L.AinvT.p));
+    }
+    AMGC_CUDA_TRY(cudaGetLastError());
+    L.has_transposed = true;
+  }
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return make_views(h);
+}
+
 // ======================================================================== coarsest level: dense inverse
 template <int BR, int BC>
 __global__ void k_dense_put(int nbr, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,

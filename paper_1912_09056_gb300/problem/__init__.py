@@ -92,13 +92,15 @@ def two_block_problem(name: str = "two_block",
                       nu_master: float = 0.3, nu_slave: float = 0.3,
                       tilt_deg: float = 0.0, jitter: float = 0.2, seed: int = 0,
                       active_fraction: float = 1.0, top_disp=(0.0, 0.0, -0.01),
-                      log_E_sigma: float = 0.0, keep_full: bool = False) -> ContactProblem:
+                      log_E_sigma: float = 0.0, E_elem: Optional[np.ndarray] = None,
+                      keep_full: bool = False) -> ContactProblem:
     """Master brick below, slave brick on top, touching on the plane z = master top.
 
     Bottom face of the master is clamped, the slave's top face is moved by top_disp
     (all three components prescribed).  Interior slave-interface nodes are jittered
     in-plane by U(+-jitter*h), edge nodes only along their edge, corners not at all.
     The whole model is then rotated about the x-axis through the interface centre.
+    E_elem, if given, replaces the moduli of all elements (master elements first).
     """
     rng = np.random.default_rng(seed)
     mx, my, mz = master_n
@@ -150,6 +152,10 @@ def two_block_problem(name: str = "two_block",
     if log_E_sigma > 0:
         E_m *= np.exp(rng.normal(0.0, log_E_sigma, size=E_m.size))
         E_s *= np.exp(rng.normal(0.0, log_E_sigma, size=E_s.size))
+    if E_elem is not None:
+        E_elem = np.asarray(E_elem, dtype=np.float64)
+        E_m = E_elem[:conn_m.shape[0]].copy()
+        E_s = E_elem[conn_m.shape[0]:].copy()
     # rigid rotation about the x-axis through the interface centre
     R = rotation_x(tilt_deg)
     ctr = np.array([0.5 * (master_box[0][0] + master_box[1][0]),
@@ -199,6 +205,15 @@ def two_block_problem(name: str = "two_block",
     extra = dict(tilt_deg=tilt_deg, R=R, n_all_nodes=n_all, n_dofs_total=3 * n_all,
                  n_elements=conn_m.shape[0] + conn_s.shape[0])
     if keep_full:
+        from .fe import element_shapes
+        sh_m, Kh_m = element_shapes(coords[:nm_nodes], conn_m, nu_master)
+        sh_s, Kh_s = element_shapes(coords[nm_nodes:], conn_s, nu_slave)
+        node_free = newid.astype(np.int32)
+        top_mask = np.zeros(n_all, dtype=np.uint8)
+        top_mask[top] = 1
+        extra.update(elem_shape=np.concatenate([sh_m, sh_s + Kh_m.shape[0]]).astype(np.int32),
+                     Khat=np.concatenate([Kh_m, Kh_s]), node_free=node_free, top_mask=top_mask,
+                     top_disp=np.asarray(top_disp, dtype=np.float64))
         extra.update(full_rowptr=rowptr, full_col=col, full_val=val, full_coords=coords,
                      prescribed=presc, u_D=u_D, free=free, body_all=body,
                      conn=np.concatenate([conn_m, conn_s_g]), E_elem=np.concatenate([E_m, E_s]),

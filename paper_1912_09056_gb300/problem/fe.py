@@ -138,3 +138,22 @@ def assemble_bsr(coords, conn, E_elem, nu, n_nodes, chunk=65536):
         for q in range(9):
             val.reshape(-1, 9)[:, q] += np.bincount(pos, weights=flat[:, q], minlength=keys.size)
     return rowptr, cols, val
+
+
+def element_shapes(coords, conn, nu):
+    """Distinct unit-modulus element matrices of a brick: (shape id per element, Khat (ns,24,24)).
+
+    Elements that are translates of the last element share shape 0; every other element gets
+    its own shape (on the structured bricks these are the jittered interface elements).
+    """
+    rel = coords[conn] - coords[conn[:, :1]]
+    h = np.abs(rel[-1]).max()
+    same = np.abs(rel - rel[-1][None]).max(axis=(1, 2)) <= 1e-12 * h
+    others = np.nonzero(~same)[0]
+    shape = np.zeros(conn.shape[0], dtype=np.int32)
+    shape[others] = 1 + np.arange(others.size, dtype=np.int32)
+    Khat = np.empty((1 + others.size, 24, 24))
+    Khat[0] = hex8_stiffness(coords[conn[-1:]], np.ones(1), nu)[0]
+    if others.size:
+        Khat[1:] = hex8_stiffness(coords[conn[others]], np.ones(others.size), nu)
+    return shape, Khat
