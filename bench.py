@@ -376,6 +376,7 @@ def main_gpu(args):
                        "l2": "inputs larger than L2 (fine K block %.0f MB)" % (prob.K_val.nbytes / 1e6),
                        "parallelism": f"replicas x{world}"},
             "iters": iters[-1], "relres": relres[-1], "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
+            "setup_phase_ms": {k: round(v, 3) for k, v in st["setup_phase_ms"].items()},
             "vcycle_ms": round(vcycle_ms, 4),
             "fp32_cycle": fp32,
             "adjoint": adj_info,

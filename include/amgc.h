@@ -100,6 +100,11 @@ typedef struct {
   double setup_ms;           /* wall time of the last amgc_setup                               */
   int32_t last_iters;        /* FGMRES iterations of the last solve                            */
   double last_relres;        /* true relative residual at the end of the last solve           */
+  /* wall time of the setup phases, summed over levels (ms): 0 input copy and assembly,
+   * 1 aggregation (MIS-2), 2 multiplier aggregation, 3 tentative transfers (QR),
+   * 4 smoother data and lambda_max, 5 smoothed prolongator, 6 transpose, 7 Galerkin products,
+   * 8 coarsest inverse, 9 fine-level SELL copies and views */
+  double setup_phase_ms[10];
 } amgc_stats_t;
 
 /* Fills the defaults: levels_max 10, coarse_max_rows 5000, SA, 1 sweep, 1 Jacobi sweep,

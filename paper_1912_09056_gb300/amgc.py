@@ -50,10 +50,13 @@ class Stats(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("rows", C.c_int32 * 16), ("disp_nodes", C.c_int32 * 16),
                 ("lm_nodes", C.c_int32 * 16), ("dofs_per_node", C.c_int32 * 16), ("nnz", C.c_int64 * 16),
                 ("operator_complexity", C.c_double), ("lambda_max", C.c_double * 16), ("setup_ms", C.c_double),
-                ("last_iters", C.c_int32), ("last_relres", C.c_double)]
+                ("last_iters", C.c_int32), ("last_relres", C.c_double), ("setup_phase_ms", C.c_double * 10)]
 
 
 _lib = None
+
+SETUP_PHASES = ("input_assembly", "aggregation", "lm_aggregation", "tentative_qr", "smoother_lambda_max",
+                "smoothed_prolongator", "transpose", "galerkin", "coarsest_inverse", "sell_views")
 
 
 class AmgcError(RuntimeError):
@@ -188,7 +191,7 @@ class Hierarchy:
                     lm_nodes=list(st.lm_nodes[:n]), dofs_per_node=list(st.dofs_per_node[:n]),
                     nnz=list(st.nnz[:n]), operator_complexity=st.operator_complexity,
                     lambda_max=list(st.lambda_max[:n]), setup_ms=st.setup_ms, last_iters=st.last_iters,
-                    last_relres=st.last_relres)
+                    last_relres=st.last_relres, setup_phase_ms=dict(zip(SETUP_PHASES, st.setup_phase_ms)))
 
     def export(self, level: int, what: str) -> np.ndarray:
         code = EXPORT[what]

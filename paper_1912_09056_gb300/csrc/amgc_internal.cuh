@@ -260,6 +260,16 @@ int build_sell(amgc_hierarchy* h, int l);
 int coarse_setup(amgc_hierarchy* h, int l);
 int check_status(amgc_hierarchy* h, const char* where);
 int transposed_setup(amgc_hierarchy* h);
+// setup phase timer: synchronises the stream and adds the elapsed wall time to a phase
+struct PhaseTimer {
+  amgc_hierarchy* h;
+  int phase;
+  double t0;
+  PhaseTimer(amgc_hierarchy* hh, int ph);
+  ~PhaseTimer();
+};
+double now_ms();
+
 // kernel timing (api.cu)
 int prof_begin(amgc_hierarchy* h, int kind);
 int prof_end(amgc_hierarchy* h, int kind, double bytes, double flops);

@@ -18,18 +18,28 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
                  const int32_t* slave_node, const int32_t* master_node, const double* triad,
                  const uint8_t* active, const int32_t* body_id, const double* nullspace) {
   const auto t0 = std::chrono::steady_clock::now();
+  std::memset(&h->stats, 0, sizeof(h->stats));
   AMGC_TRY(h->status.alloc(1));
   AMGC_CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
   AMGC_TRY(h->partial.alloc(4096));
   AMGC_CUDA_TRY(cudaMallocHost(&h->h_pinned, 64 * sizeof(double)));
   h->L.reserve(16);
   h->L.emplace_back();
-  AMGC_TRY(build_fine_level(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace));
-  AMGC_TRY(build_sell(h, 0));
+  {
+    PhaseTimer pt(h, 0);
+    AMGC_TRY(build_fine_level(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace));
+  }
+  {
+    PhaseTimer pt(h, 9);
+    AMGC_TRY(build_sell(h, 0));
+  }
   const amgc_options& o = h->opts;
   while ((int)h->L.size() < std::min(o.levels_max, 16) && h->L.back().rows() >= o.coarse_max_rows) {
     const int l = (int)h->L.size() - 1;
-    AMGC_TRY(smoother_setup(h, l));
+    {
+      PhaseTimer pt(h, 4);
+      AMGC_TRY(smoother_setup(h, l));
+    }
     AMGC_TRY(coarsen_level(h, l));
     if (h->L[l + 1].nn >= h->L[l].nn) {   // no reduction: keep the finer level as the coarsest
       h->L.pop_back();
@@ -42,13 +52,18 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
               " rows; raise levels_max or lower coarse_max_rows (dense limit " + std::to_string(kMaxDenseRows) + ")");
     return AMGC_EINVAL;
   }
-  AMGC_TRY(coarse_setup(h, lc));
-  if (lc > 0) AMGC_TRY(build_sell(h, 0));
-  AMGC_TRY(make_views(h));
+  {
+    PhaseTimer pt(h, 8);
+    AMGC_TRY(coarse_setup(h, lc));
+  }
+  {
+    PhaseTimer pt(h, 9);
+    if (lc > 0) AMGC_TRY(build_sell(h, 0));
+    AMGC_TRY(make_views(h));
+  }
   AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
   // statistics
   amgc_stats_t& st = h->stats;
-  std::memset(&st, 0, sizeof(st));
   st.n_levels = (int)h->L.size();
   double nnz0 = 0.0, nnz_all = 0.0;
   for (int l = 0; l < st.n_levels; ++l) {
@@ -65,6 +80,18 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
   st.operator_complexity = nnz0 > 0 ? nnz_all / nnz0 : 0.0;
   st.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return AMGC_OK;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+PhaseTimer::PhaseTimer(amgc_hierarchy* hh, int ph) : h(hh), phase(ph) {
+  cudaStreamSynchronize(h->stream);
+  t0 = now_ms();
+}
+PhaseTimer::~PhaseTimer() {
+  cudaStreamSynchronize(h->stream);
+  h->stats.setup_phase_ms[phase] += now_ms() - t0;
 }
 
 constexpr int kProfPairs = 1024;

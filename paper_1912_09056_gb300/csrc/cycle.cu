@@ -121,24 +121,27 @@ int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double bet
 }
 
 // ------------------------------------------------------------------ SELL-32 row apply
-// Two threads per block row: a warp covers 16 rows of a 32-row slice, lanes 0-15 take the even
-// slots and lanes 16-31 the odd slots (each half-warp load is 16 consecutive values), and one
-// shuffle adds the halves.  Value k of a block is one load and one FMA; matrix data is streamed
-// (evict-first) so the vectors stay cached.  An optional second matrix A2 (the B1 block, few
-// rows) is added from its BSR rows.
+// TPR threads per block row (1 or 2).  With TPR = 2 a warp covers 16 rows of a 32-row slice,
+// lanes 0-15 take the even slots and lanes 16-31 the odd slots (each half-warp load is 16
+// consecutive values) and one shuffle adds the halves: twice the loads in flight for the
+// HBM-bound FP32 cycle.  The FP64 kernel is bound by the FP64 FMA rate and runs one thread
+// per row (no extra instructions).  Value k of a block is one load and one FMA; matrix data
+// is streamed (evict-first) so the vectors stay cached.  An optional second matrix A2 (the B1
+// block, few rows) is added from its BSR rows.
 constexpr int kSellThreads = 128;
 
-template <int BR, int BC, int MODE, class T>
+template <int BR, int BC, int MODE, class T, int TPR>
 __global__ void __launch_bounds__(kSellThreads)
 k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, const int* __restrict__ scol,
        const T* __restrict__ sval, const T* __restrict__ x, const int* __restrict__ rp2, const int* __restrict__ c2,
        const T* __restrict__ v2, const T* __restrict__ x2, const T* __restrict__ b, const T* __restrict__ x0,
        const T* __restrict__ dinv, T omega, T* __restrict__ y) {
   constexpr int BS = BR * BC;
+  constexpr int RPW = 32 / TPR;                                // rows per warp
   const int gt = blockIdx.x * kSellThreads + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const int half = lane >> 4;                                  // slot parity handled by this lane
-  const int row = ((gt >> 5) << 4) + (lane & 15);              // 16 rows per warp
+  const int part = lane / RPW;                                 // slot residue handled by this lane
+  const int row = (gt >> 5) * RPW + (lane % RPW);
   const bool live = row < nbr;
   const int r = live ? row : nbr - 1;                          // dead lanes mirror a valid row
   const int sl = r >> 5, ls = r & 31;
@@ -149,8 +152,8 @@ k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, cons
   T acc[BR];
 #pragma unroll
   for (int q = 0; q < BR; ++q) acc[q] = T(0);
-#pragma unroll 2
-  for (int t = half; t < L; t += 2) {
+#pragma unroll 3
+  for (int t = part; t < L; t += TPR) {
     const T* xc = x + (int64_t)__ldcs(cp + t * 32) * BC;
     T xv[BC];
 #pragma unroll
@@ -161,9 +164,11 @@ k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, cons
 #pragma unroll
       for (int c = 0; c < BC; ++c) acc[q] = fma(ldcs(v + (q * BC + c) * 32), xv[c], acc[q]);
   }
+  if (TPR == 2) {
 #pragma unroll
-  for (int q = 0; q < BR; ++q) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], 16);
-  if (half != 0 || !live) return;
+    for (int q = 0; q < BR; ++q) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], 16);
+  }
+  if (part != 0 || !live) return;
   if (rp2 != nullptr) {
     for (int e = rp2[row]; e < rp2[row + 1]; ++e) {
       const T* blk = v2 + (int64_t)e * BR * 3;
@@ -180,16 +185,17 @@ k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, cons
 template <int MODE, class T>
 static int sell_apply(const SellV<T>& S, int nbr, const BsrV<T>* A2, const T* x, const T* x2, const T* b, const T* x0,
                       const T* dinv, double omega, T* y, cudaStream_t s) {
-  const int g = div_up((int64_t)nbr * 2, kSellThreads);
+  constexpr int TPR = sizeof(T) == 8 ? 1 : 2;
+  const int g = div_up((int64_t)nbr * TPR, kSellThreads);
   const int* rp2 = A2 ? A2->rp : nullptr;
   const int* c2 = A2 ? A2->col : nullptr;
   const T* v2 = A2 ? A2->val : nullptr;
   if (nbr == 0) return AMGC_OK;
   if (S.br == 3 && S.bc == 3)
-    AMGC_LAUNCH(k_sell<3, 3, MODE, T><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
+    AMGC_LAUNCH(k_sell<3, 3, MODE, T, TPR><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
                                                                  b, x0, dinv, (T)omega, y));
   else if (S.br == 3 && S.bc == 6)
-    AMGC_LAUNCH(k_sell<3, 6, MODE, T><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
+    AMGC_LAUNCH(k_sell<3, 6, MODE, T, TPR><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
                                                                  b, x0, dinv, (T)omega, y));
   else {
     set_error("sell_apply: unsupported block shape");

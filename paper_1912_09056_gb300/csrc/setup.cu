@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 
 namespace amgc {
 
@@ -1170,9 +1171,13 @@ int coarsen_level(amgc_hierarchy* h, int l) {
   // --- displacement aggregates
   DBuf<int> roots;
   int n_agg = 0;
-  AMGC_TRY(mis2_aggregate(h, L, roots, &n_agg));
+  {
+    PhaseTimer pt(h, 1);
+    AMGC_TRY(mis2_aggregate(h, L, roots, &n_agg));
+  }
   L.n_agg = n_agg;
   // --- multiplier aggregates (Algorithm 1)
+  std::unique_ptr<PhaseTimer> ptm(new PhaseTimer(h, 2));
   DBuf<int> first, mark, lm_dnode_c;
   AMGC_TRY(first.alloc(n_agg));
   AMGC_TRY(mark.alloc(L.nn + 1));
@@ -1187,7 +1192,9 @@ int coarsen_level(amgc_hierarchy* h, int l) {
     AMGC_LAUNCH(k_lm_assign<<<div_up(L.nl, 256), 256, 0, s>>>(L.nl, L.lm_dnode.p, L.agg.p, first.p, mark.p, L.lagg.p, lm_dnode_c.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   L.n_lagg = n_lagg;
+  ptm.reset();
   // --- tentative displacement prolongator by QR
+  ptm.reset(new PhaseTimer(h, 3));
   DBuf<int> mptr, midx;
   AMGC_TRY(bucket_lists(L.nn, L.agg.p, n_agg, mptr, midx, s));
   DBsr Phat;
@@ -1226,7 +1233,9 @@ int coarsen_level(amgc_hierarchy* h, int l) {
                                                       Rl.val.p));
     AMGC_CUDA_TRY(cudaGetLastError());
   }
+  ptm.reset();
   // --- lambda_max and smoothed prolongator
+  ptm.reset(new PhaseTimer(h, 5));
   if (L.kdiag.p == nullptr) AMGC_TRY(smoother_setup(h, l));
   if (h->opts.transfer == 1) {
     AMGC_TRY(spgemm(h, L.K, Phat, L.P));
@@ -1241,8 +1250,13 @@ int coarsen_level(amgc_hierarchy* h, int l) {
   } else {
     L.P = std::move(Phat);
   }
-  AMGC_TRY(bsr_transpose(h, L.P, L.R));
+  ptm.reset();
+  {
+    PhaseTimer pt(h, 6);
+    AMGC_TRY(bsr_transpose(h, L.P, L.R));
+  }
   // --- Galerkin products
+  ptm.reset(new PhaseTimer(h, 7));
   {
     DBsr AP;
     AMGC_TRY(spgemm(h, L.K, L.P, AP));
@@ -1266,6 +1280,7 @@ int coarsen_level(amgc_hierarchy* h, int l) {
     AMGC_CUDA_TRY(cudaMemsetAsync(C.B2.rowptr.p, 0, sizeof(int), s));
   }
   AMGC_TRY(check_status(h, "Galerkin products"));
+  ptm.reset();
   // --- coarse per-node data
   AMGC_TRY(C.body.alloc(n_agg));   // body of a coarse node = body of its root (filled below)
   AMGC_TRY(C.lm_dnode.alloc(std::max(n_lagg, 1)));

@@ -163,7 +163,6 @@ def two_block_problem(name: str = "two_block",
     coords = (coords - ctr) @ R.T + ctr
     n_all = coords.shape[0]
     # stiffness of both bodies (no coupling between them)
-    from .fe import block_pattern  # noqa: F401  (kept for callers of the module)
     rp_m, col_m, val_m = assemble_bsr(coords[:nm_nodes], conn_m, E_m, nu_master, nm_nodes)
     rp_s, col_s, val_s = assemble_bsr(coords[nm_nodes:], conn_s, E_s, nu_slave, n_all - nm_nodes)
     rowptr = np.concatenate([rp_m, rp_s[1:] + rp_m[-1]])
@@ -186,6 +185,12 @@ def two_block_problem(name: str = "two_block",
     f = np.zeros((n_all, 3))
     np.add.at(f, rows_all[lift], -np.einsum("bij,bj->bi", val[lift], u_D[col[lift]]))
     f = f[free].ravel()
+    # lifting map of a uniform top displacement t given in the unrotated frame: f = L t
+    top_lift = np.zeros((n_all, 3, 3))
+    on_top = presc[col] & (col >= nm_nodes) & lift
+    blk = val[on_top] @ R                                     # K_fD (R e_c) per block
+    np.add.at(top_lift, rows_all[on_top], -blk)
+    top_lift = top_lift[free].reshape(-1, 3)
     kr = newid[rows_all[keep]]
     kc = newid[col[keep]]
     K_val = val[keep]
@@ -202,7 +207,7 @@ def two_block_problem(name: str = "two_block",
     t1 = R @ np.array([1.0, 0.0, 0.0])
     t2 = R @ np.array([0.0, 1.0, 0.0])
     triad = np.broadcast_to(np.stack([n_vec, t1, t2]), (ns, 3, 3)).copy()
-    extra = dict(tilt_deg=tilt_deg, R=R, n_all_nodes=n_all, n_dofs_total=3 * n_all,
+    extra = dict(tilt_deg=tilt_deg, R=R, n_all_nodes=n_all, n_dofs_total=3 * n_all, top_lift=top_lift,
                  n_elements=conn_m.shape[0] + conn_s.shape[0])
     if keep_full:
         from .fe import element_shapes
