@@ -135,6 +135,29 @@ int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M,
                const double* nullspace, const amgc_options* opts, void* stream,
                struct amgc_hierarchy** out);
 
+/* Batched problems: n_inst independent contact systems concatenated block-diagonally in the
+ * arrays of amgc_setup (instance q owns K block rows [node_ptr[q], node_ptr[q+1]) and slave /
+ * multiplier nodes [lm_ptr[q], lm_ptr[q+1]); no coupling between instances; body_id must
+ * separate the bodies of every instance).  One hierarchy serves all instances: MIS-2 keys use
+ * instance-local node indices, lambda_max and the dampings are computed per instance, the
+ * coarsest level is inverted per instance, and coarsening stops when the largest instance has
+ * fewer than coarse_max_rows rows (or at levels_max).  Every instance therefore gets the
+ * aggregates and transfers it would get alone.  node_ptr, lm_ptr: host arrays of n_inst + 1.
+ * Other arguments, ownership and errors as amgc_setup. */
+int amgc_setup_batched(const amgc_bsr* K, const double* D_diag, const amgc_csr* M,
+                       const int32_t* slave_node, const int32_t* master_node,
+                       const double* triad, const uint8_t* active, const int32_t* body_id,
+                       const double* nullspace, int32_t n_inst, const int32_t* node_ptr, const int32_t* lm_ptr,
+                       const amgc_options* opts, void* stream, struct amgc_hierarchy** out);
+
+/* Solves the n_inst x nrhs independent systems of a batched hierarchy by FGMRES in lockstep,
+ * one Krylov space, stopping test and iteration count per (instance, rhs) system.  rhs, x:
+ * device arrays of nrhs columns of length rows[0] (column-major).  iters, relres: host arrays of
+ * n_inst * nrhs entries, system q * nrhs + r (may be NULL).  Returns AMGC_NOT_CONVERGED when a
+ * system reached fgmres_maxit. */
+int amgc_solve_batched(struct amgc_hierarchy* h, int32_t nrhs, const double* rhs, double* x, int32_t* iters,
+                       double* relres, void* stream);
+
 /* z = V-cycle(r) with zero initial guess (Fig. mgalgorithm).  r, z: device vectors of
  * length rows[0] = 3n + 3 n_s, ordered [u; lambda].  r and z must not overlap.  With
  * precision 32 the cycle runs on FP32 copies of the level data (the inverted Schur blocks and
@@ -220,7 +243,8 @@ enum {
   AMGC_EXPORT_PL_W = 18,      /* double[lm_nodes]    multiplier tentative-transfer weights     */
   AMGC_EXPORT_ATINV = 19,     /* double[dofs]        A~^-1                                     */
   AMGC_EXPORT_OMEGA = 20,     /* double[2]           (lambda_max, omega_J)                     */
-  AMGC_EXPORT_COARSE_INV = 21 /* double[rows*rows]   inverse of the coarsest saddle matrix     */
+  AMGC_EXPORT_COARSE_INV = 21 /* double[rows*rows]   inverse of the coarsest saddle matrix
+                                 (batched: the instances' inverses one after the other)   */
 };
 int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what, void* dst,
                     int64_t bytes);

@@ -105,6 +105,11 @@ def load():
     lib.amgc_grad_scatter.restype = C.c_int
     lib.amgc_grad_elements.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.amgc_grad_elements.restype = C.c_int
+    lib.amgc_setup_batched.argtypes = [C.POINTER(Bsr), vp, C.POINTER(Csr), vp, vp, vp, vp, vp, vp, C.c_int32, vp, vp,
+                                       C.POINTER(Options), vp, C.POINTER(vp)]
+    lib.amgc_setup_batched.restype = C.c_int
+    lib.amgc_solve_batched.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp]
+    lib.amgc_solve_batched.restype = C.c_int
     lib.amgc_destroy.argtypes = [vp]
     lib.amgc_destroy.restype = None
     lib.amgc_strerror.argtypes = [C.c_int]
@@ -260,6 +265,17 @@ class Hierarchy:
                                            _stream_ptr(stream)), "amgc_grad_scatter")
         return gK
 
+    def solve_batched(self, rhs, x, n_sys: int, stream=None, check: bool = True):
+        """rhs, x: device tensors (nrhs, rows); returns (iters, relres) per system q * nrhs + r."""
+        nrhs = int(rhs.shape[0])
+        it = np.zeros(n_sys, dtype=np.int32)
+        rr = np.zeros(n_sys, dtype=np.float64)
+        code = self._lib.amgc_solve_batched(self._h, nrhs, _ptr(rhs), _ptr(x), it.ctypes.data, rr.ctypes.data,
+                                            _stream_ptr(stream))
+        if check:
+            _check(code, "amgc_solve_batched")
+        return it, rr, code
+
     def solve_host(self, rhs: np.ndarray, stream=None, check: bool = True):
         rhs = np.ascontiguousarray(rhs, dtype=np.float64)
         x = np.empty_like(rhs)
@@ -282,8 +298,12 @@ def grad_elements(conn, shape, Khat, node_free, adj, x, uD, E, gE, lift_mask=Non
     return gE, gt
 
 
-def setup(prob, options: Optional[Options] = None, stream=None, **opt_kw) -> Hierarchy:
-    """amgc_setup on a ContactProblem (host arrays; the library copies them to the device)."""
+def setup(prob, options: Optional[Options] = None, stream=None, node_ptr=None, lm_ptr=None, **opt_kw) -> Hierarchy:
+    """amgc_setup on a ContactProblem (host or device arrays; the library copies them).
+
+    With node_ptr / lm_ptr (host int32 arrays of n_inst + 1) the problem is a block-diagonal
+    batch and amgc_setup_batched is called.
+    """
     lib = load()
     o = options if options is not None else default_options(**opt_kw)
     keep = []
@@ -302,9 +322,20 @@ def setup(prob, options: Optional[Options] = None, stream=None, **opt_kw) -> Hie
     M = Csr(prob.n_s, int(prob.master_node.shape[0]), arr(prob.M_rowptr, np.int32), arr(prob.M_col, np.int32),
             arr(prob.M_val, np.float64))
     out = C.c_void_p(0)
-    code = lib.amgc_setup(C.byref(K), arr(prob.D, np.float64), C.byref(M), arr(prob.slave_node, np.int32),
-                          arr(prob.master_node, np.int32), arr(prob.triad, np.float64), arr(prob.active, np.uint8),
-                          arr(prob.body_id, np.int32), arr(prob.nullspace, np.float64), C.byref(o),
-                          _stream_ptr(stream), C.byref(out))
-    _check(code, "amgc_setup")
+    if node_ptr is None:
+        code = lib.amgc_setup(C.byref(K), arr(prob.D, np.float64), C.byref(M), arr(prob.slave_node, np.int32),
+                              arr(prob.master_node, np.int32), arr(prob.triad, np.float64),
+                              arr(prob.active, np.uint8), arr(prob.body_id, np.int32),
+                              arr(prob.nullspace, np.float64), C.byref(o), _stream_ptr(stream), C.byref(out))
+        _check(code, "amgc_setup")
+    else:
+        npt = np.ascontiguousarray(node_ptr, dtype=np.int32)
+        lpt = np.ascontiguousarray(lm_ptr, dtype=np.int32)
+        code = lib.amgc_setup_batched(C.byref(K), arr(prob.D, np.float64), C.byref(M),
+                                      arr(prob.slave_node, np.int32), arr(prob.master_node, np.int32),
+                                      arr(prob.triad, np.float64), arr(prob.active, np.uint8),
+                                      arr(prob.body_id, np.int32), arr(prob.nullspace, np.float64),
+                                      int(npt.size - 1), npt.ctypes.data, lpt.ctypes.data, C.byref(o),
+                                      _stream_ptr(stream), C.byref(out))
+        _check(code, "amgc_setup_batched")
     return Hierarchy(out.value, lib)

@@ -102,7 +102,7 @@ struct Sell {
 
 // FP32 mirrors of the cycle data of one level (values only; index arrays are shared).
 struct LevelF32 {
-  DBuf<float> K, B1, B2, P, R, Z, Ks, Ps, dinv, atinv, pl_w;
+  DBuf<float> K, B1, B2, P, R, Z, Ks, Ps, jdinv, atinv, pl_w;
   DBuf<float> x, b, r, t, dlam;
 };
 
@@ -142,6 +142,12 @@ struct LevelV {
   const int* b1_rows = nullptr;
   int n_b1_rows = 0;
   const double* Ainv = nullptr;    // coarsest level, FP64 in both precisions
+  // batched coarsest level (null when not batched)
+  const int* c_inst = nullptr;
+  const int* c_loc = nullptr;
+  const int* c_glob = nullptr;
+  const int* c_goff = nullptr;
+  const int64_t* c_doff = nullptr;
   // transposed cycle (FP64 only)
   BsrV<T> B1T, B2T;
   const T* ZT = nullptr;
@@ -184,12 +190,23 @@ struct Level {
   // CheapSIMPLE data
   double lam_max = 0.0, omega_j = 0.0;
   DBuf<double> kdiag, dinv, atinv;  // nu: pointwise diagonal of K, its inverse, A~^-1
+  DBuf<double> jdinv;               // nu: omega_J D^-1 (omega_J per instance when batched)
+  std::vector<double> inst_lam_max; // per instance (batched hierarchies)
+  DBuf<int> key_base;               // batched: first node of the node's instance (MIS-2 keys)
   DBuf<double> Sinv;         // nl*9
   DBuf<int> b1_rows;         // displacement nodes with B1 entries
   int n_b1_rows = 0;
 
   // coarsest level
-  DBuf<double> Ainv;         // rows*rows (row-major)
+  DBuf<double> Ainv;         // rows*rows (row-major); batched: one dense block per instance
+
+  // instances of a batched hierarchy: displacement nodes [nptr[i], nptr[i+1]) and multiplier
+  // nodes [lptr[i], lptr[i+1]) of every level belong to instance i
+  std::vector<int> nptr, lptr;
+  // batched coarsest level: row -> instance and local index, per-instance global row lists
+  // (u rows then multiplier rows), dense block offsets
+  DBuf<int> c_inst, c_loc, c_glob, c_goff;
+  DBuf<int64_t> c_doff;
 
   // transposed-cycle data (adjoint solves): B1^T, B2^T, blockwise transposed Z and S^-1,
   // the transposed coarsest inverse, and the rows of B2^T with entries
@@ -222,6 +239,10 @@ struct amgc_hierarchy {
   std::vector<amgc::LevelV<double>> v64;   // cycle views, FP64
   std::vector<amgc::LevelV<float>> v32;    // cycle views, FP32 (precision 32)
   bool transposed = false;                 // FGMRES/cycle act on A^T (adjoint solve)
+  int n_inst = 1;                          // instances of a batched hierarchy
+  // batched FGMRES workspace
+  amgc::DBuf<int> b_chunk_row0, b_chunk_row1, b_chunk_ptr, b_row_inst;
+  int b_nchunk = 0;
   double* h_pinned = nullptr;      // pinned host scalars
   // event timing of the fine-level K applies (amgc_profile)
   int prof = 0;                    // mask: 1 FP64 applies, 2 FP32 applies
@@ -277,6 +298,7 @@ int prof_flush(amgc_hierarchy* h);
 // sparse kernels (cycle.cu)
 int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
 int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out);
+int lambda_max_instances(amgc_hierarchy* h, Level& L, std::vector<double>& lam);
 int dot(amgc_hierarchy* h, int64_t n, const double* a, const double* b, const double* wgt, double* out_dev);
 // V-cycle (cycle.cu)
 int make_views(amgc_hierarchy* h);
@@ -284,6 +306,8 @@ int precond_apply(amgc_hierarchy* h, const double* r, double* z);   // one V-cyc
 int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y);
 // FGMRES (krylov.cu)
 int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol, int* iters, double* relres);
+// batched problems (batch.cu)
+int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, int* iters, double* relres);
 // gradients (grad.cu)
 int grad_scatter(amgc_hierarchy* h, const double* adj, const double* x, double* gK, double* gB1, double* gB2);
 int grad_elements(int ne, const int* conn, const int* shape, const double* Khat, const int* node_free,

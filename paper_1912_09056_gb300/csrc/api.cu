@@ -14,9 +14,19 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 // Largest coarsest system solved with the dense explicit inverse.
 constexpr int kMaxDenseRows = 16384;
 
+// rows of the largest instance of a level (the whole level when not batched)
+static int max_instance_rows(const amgc_hierarchy* h, const Level& L) {
+  if (h->n_inst <= 1) return L.rows();
+  int m = 0;
+  for (int q = 0; q < h->n_inst; ++q)
+    m = std::max(m, L.bu * (L.nptr[q + 1] - L.nptr[q]) + 3 * (L.lptr[q + 1] - L.lptr[q]));
+  return m;
+}
+
 static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, const amgc_csr* M,
                  const int32_t* slave_node, const int32_t* master_node, const double* triad,
-                 const uint8_t* active, const int32_t* body_id, const double* nullspace) {
+                 const uint8_t* active, const int32_t* body_id, const double* nullspace,
+                 const std::vector<int>& h_nptr, const std::vector<int>& h_lptr) {
   const auto t0 = std::chrono::steady_clock::now();
   std::memset(&h->stats, 0, sizeof(h->stats));
   AMGC_TRY(h->status.alloc(1));
@@ -25,6 +35,8 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
   AMGC_CUDA_TRY(cudaMallocHost(&h->h_pinned, 64 * sizeof(double)));
   h->L.reserve(16);
   h->L.emplace_back();
+  h->L[0].nptr = h_nptr;
+  h->L[0].lptr = h_lptr;
   {
     PhaseTimer pt(h, 0);
     AMGC_TRY(build_fine_level(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace));
@@ -34,7 +46,7 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
     AMGC_TRY(build_sell(h, 0));
   }
   const amgc_options& o = h->opts;
-  while ((int)h->L.size() < std::min(o.levels_max, 16) && h->L.back().rows() >= o.coarse_max_rows) {
+  while ((int)h->L.size() < std::min(o.levels_max, 16) && max_instance_rows(h, h->L.back()) >= o.coarse_max_rows) {
     const int l = (int)h->L.size() - 1;
     {
       PhaseTimer pt(h, 4);
@@ -47,7 +59,7 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
     }
   }
   const int lc = (int)h->L.size() - 1;
-  if (h->L[lc].rows() > kMaxDenseRows) {
+  if (max_instance_rows(h, h->L[lc]) > kMaxDenseRows) {
     set_error("coarsest level has " + std::to_string(h->L[lc].rows()) +
               " rows; raise levels_max or lower coarse_max_rows (dense limit " + std::to_string(kMaxDenseRows) + ")");
     return AMGC_EINVAL;
@@ -173,7 +185,9 @@ int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const
   if (!h) return AMGC_ENOMEM;
   h->opts = *opts;
   h->stream = (cudaStream_t)stream;
-  int st = build(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace);
+  h->n_inst = 1;
+  std::vector<int> np = {0, K->n_brow}, lp = {0, M->n_row};
+  int st = build(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace, np, lp);
   if (st != AMGC_OK) {
     cudaStreamSynchronize(h->stream);
     amgc_destroy(h);
@@ -181,6 +195,58 @@ int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const
   }
   *out = h;
   return AMGC_OK;
+}
+
+int amgc_setup_batched(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const int32_t* slave_node,
+                       const int32_t* master_node, const double* triad, const uint8_t* active, const int32_t* body_id,
+                       const double* nullspace, int32_t n_inst, const int32_t* node_ptr, const int32_t* lm_ptr,
+                       const amgc_options* opts, void* stream, struct amgc_hierarchy** out) {
+  if (!out || n_inst < 1 || !node_ptr || !lm_ptr || !K || !M || !opts) {
+    set_error("amgc_setup_batched: invalid argument");
+    if (out) *out = nullptr;
+    return AMGC_EINVAL;
+  }
+  *out = nullptr;
+  std::vector<int> np(node_ptr, node_ptr + n_inst + 1), lp(lm_ptr, lm_ptr + n_inst + 1);
+  bool ok = np[0] == 0 && lp[0] == 0 && np[n_inst] == K->n_brow && lp[n_inst] == M->n_row;
+  for (int q = 0; q < n_inst && ok; ++q) ok = np[q + 1] > np[q] && lp[q + 1] >= lp[q];
+  if (!ok) {
+    set_error("amgc_setup_batched: node_ptr / lm_ptr must be ascending and cover K and M");
+    return AMGC_EINVAL;
+  }
+  if (n_inst == 1)
+    return amgc_setup(K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace, opts, stream, out);
+  if (!K->rowptr || !K->col || !K->val || !body_id || !nullspace || !M->rowptr || K->br != 3 || K->bc != 3 ||
+      K->n_brow != K->n_bcol || (M->n_row > 0 && (!D_diag || !slave_node || !triad || !active)) ||
+      (M->n_col > 0 && !master_node) || opts->levels_max < 1 || opts->smoother_sweeps < 0 ||
+      opts->jacobi_sweeps < 1 || opts->fgmres_restart < 1 || opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 ||
+      !(opts->tol > 0.0) || (opts->precision != 64 && opts->precision != 32)) {
+    set_error("amgc_setup_batched: invalid argument");
+    return AMGC_EINVAL;
+  }
+  amgc_hierarchy* h = new (std::nothrow) amgc_hierarchy();
+  if (!h) return AMGC_ENOMEM;
+  h->opts = *opts;
+  h->stream = (cudaStream_t)stream;
+  h->n_inst = n_inst;
+  int st = build(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace, np, lp);
+  if (st != AMGC_OK) {
+    cudaStreamSynchronize(h->stream);
+    amgc_destroy(h);
+    return st;
+  }
+  *out = h;
+  return AMGC_OK;
+}
+
+int amgc_solve_batched(struct amgc_hierarchy* h, int32_t nrhs, const double* rhs, double* x, int32_t* iters,
+                       double* relres, void* stream) {
+  if (!h || nrhs < 1 || !rhs || !x || rhs == x) {
+    set_error("amgc_solve_batched: invalid argument");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  return fgmres_batched(h, nrhs, rhs, x, iters, relres);
 }
 
 int amgc_vcycle(struct amgc_hierarchy* h, const double* r, double* z, void* stream) {
@@ -245,6 +311,10 @@ static int enter_transposed(amgc_hierarchy* h, void* stream, const char* where) 
   }
   if (h->opts.jacobi_sweeps != 1) {
     set_error(std::string(where) + ": the transposed cycle needs jacobi_sweeps == 1");
+    return AMGC_EINVAL;
+  }
+  if (h->n_inst > 1) {
+    set_error(std::string(where) + ": not available for batched hierarchies");
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
@@ -351,7 +421,7 @@ int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what,
     case AMGC_EXPORT_PL_W: src = L.pl_w.p; nb = L.pl_w.p ? (int64_t)L.nl * 8 : 0; break;
     case AMGC_EXPORT_ATINV: src = L.atinv.p; nb = L.atinv.p ? (int64_t)L.nu() * 8 : 0; break;
     case AMGC_EXPORT_OMEGA: src = scal; nb = 16; break;
-    case AMGC_EXPORT_COARSE_INV: src = L.Ainv.p; nb = L.Ainv.p ? (int64_t)L.rows() * L.rows() * 8 : 0; break;
+    case AMGC_EXPORT_COARSE_INV: src = L.Ainv.p; nb = L.Ainv.p ? (int64_t)L.Ainv.n * 8 : 0; break;
     default: set_error("amgc_export: unknown array"); return AMGC_EINVAL;
   }
   if (!dst || nb == 0) return nb;

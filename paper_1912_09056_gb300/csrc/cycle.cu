@@ -352,6 +352,24 @@ __global__ void k_gemv(int n, const double* __restrict__ A, const T* __restrict_
   if (lane == 0) y[row] = (T)s;
 }
 
+// batched coarsest solve: y_g = sum_t A_q[loc(g)][t] x[glob_q(t)], q the instance of row g
+template <class T>
+__global__ void k_gemv_batched(int n, const int* __restrict__ inst, const int* __restrict__ loc,
+                               const int* __restrict__ glob, const int* __restrict__ goff,
+                               const int64_t* __restrict__ doff, const double* __restrict__ A,
+                               const T* __restrict__ x, T* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  const int q = inst[row];
+  const int g0 = goff[q], nq = goff[q + 1] - g0;
+  const double* a = A + doff[q] + (int64_t)loc[row] * nq;
+  double s = 0.0;
+  for (int j = lane; j < nq; j += 32) s = fma(a[j], (double)x[glob[g0 + j]], s);
+  s = warp_sum(s);
+  if (lane == 0) y[row] = (T)s;
+}
+
 // ------------------------------------------------------------------ level operations
 // Algorithmic bytes of one fine-level K-apply launch: K and B1 values and indices once, x and
 // lambda once, the output once, plus `extra_vecs` further length-nu vectors.
@@ -441,7 +459,11 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
   const int th = 256;
   if (l == (int)V.size() - 1) {
     const int n = L.rows();
-    AMGC_LAUNCH(k_gemv<T><<<div_up((int64_t)n * 32, th), th, 0, s>>>(n, L.Ainv, b, x));
+    if (L.c_inst)
+      AMGC_LAUNCH(k_gemv_batched<T><<<div_up((int64_t)n * 32, th), th, 0, s>>>(n, L.c_inst, L.c_loc, L.c_glob, L.c_goff,
+                                                                             L.c_doff, L.Ainv, b, x));
+    else
+      AMGC_LAUNCH(k_gemv<T><<<div_up((int64_t)n * 32, th), th, 0, s>>>(n, L.Ainv, b, x));
     AMGC_CUDA_TRY(cudaGetLastError());
     return AMGC_OK;
   }
@@ -651,9 +673,11 @@ static SellV<T> sview(const Sell& S, const T* val) {
 template <class T>
 static LevelV<T> common_view(const Level& L) {
   LevelV<T> v;
-  v.nn = L.nn; v.bu = L.bu; v.nl = L.nl; v.omega_j = L.omega_j;
+  // the Jacobi damping is folded into the dinv view (omega_J D^-1, per instance when batched)
+  v.nn = L.nn; v.bu = L.bu; v.nl = L.nl; v.omega_j = 1.0;
   v.Sinv = L.Sinv.p; v.lagg = L.lagg.p; v.rl_ptr = L.rl_ptr.p; v.rl_idx = L.rl_idx.p;
   v.b1_rows = L.b1_rows.p; v.n_b1_rows = L.n_b1_rows; v.Ainv = L.Ainv.p;
+  v.c_inst = L.c_inst.p; v.c_loc = L.c_loc.p; v.c_glob = L.c_glob.p; v.c_goff = L.c_goff.p; v.c_doff = L.c_doff.p;
   return v;
 }
 
@@ -671,7 +695,7 @@ int make_views(amgc_hierarchy* h) {
     v.R = bview<double>(L.R, L.R.val.p);
     v.Ks = sview<double>(L.Ks, L.Ks.val.p);
     v.Ps = sview<double>(L.Ps, L.Ps.val.p);
-    v.Z = L.Z.p; v.dinv = L.dinv.p; v.atinv = L.atinv.p; v.pl_w = L.pl_w.p;
+    v.Z = L.Z.p; v.dinv = L.jdinv.p; v.atinv = L.atinv.p; v.pl_w = L.pl_w.p;
     v.x = L.x.p; v.b = L.b.p; v.r = L.r.p; v.t = L.t.p; v.dlam = L.dlam.p;
     if (L.has_transposed) {
       v.B1T = bview<double>(L.B1T, L.B1T.val.p);
@@ -693,7 +717,7 @@ int make_views(amgc_hierarchy* h) {
     if (!last) {
       AMGC_TRY(to_f32(h, L.P.val.p, (size_t)L.P.nnzb * L.P.br * L.P.bc, F.P));
       AMGC_TRY(to_f32(h, L.R.val.p, (size_t)L.R.nnzb * L.R.br * L.R.bc, F.R));
-      AMGC_TRY(to_f32(h, L.dinv.p, (size_t)L.nu(), F.dinv));
+      AMGC_TRY(to_f32(h, L.jdinv.p, (size_t)L.nu(), F.jdinv));
       AMGC_TRY(to_f32(h, L.atinv.p, (size_t)L.nu(), F.atinv));
       AMGC_TRY(to_f32(h, L.pl_w.p, (size_t)L.nl, F.pl_w));
     }
@@ -713,7 +737,7 @@ int make_views(amgc_hierarchy* h) {
     v.R = bview<float>(L.R, F.R.p);
     v.Ks = sview<float>(L.Ks, F.Ks.p);
     v.Ps = sview<float>(L.Ps, F.Ps.p);
-    v.Z = F.Z.p; v.dinv = F.dinv.p; v.atinv = F.atinv.p; v.pl_w = F.pl_w.p;
+    v.Z = F.Z.p; v.dinv = F.jdinv.p; v.atinv = F.atinv.p; v.pl_w = F.pl_w.p;
     v.x = F.x.p; v.b = F.b.p; v.r = F.r.p; v.t = F.t.p; v.dlam = F.dlam.p;
     h->v32.push_back(v);
   }
@@ -774,6 +798,76 @@ int dot(amgc_hierarchy* h, int64_t n, const double* a, const double* b, const do
   AMGC_LAUNCH(k_dot_partial<<<blocks, kDotThreads, 0, s>>>(n, a, b, wgt, h->partial.p));
   AMGC_LAUNCH(k_dot_final<<<1, 1024, 0, s>>>(blocks, h->partial.p, out_dev));
   AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+// Per-instance dot products of a batched level: out[q] = sum over instance q's DOFs
+// [bu*nptr[q], bu*nptr[q+1]) of a*wgt*b, one block per instance (fixed order).
+__global__ void k_segdot(int ni, int bu, const int* __restrict__ nptr, const double* __restrict__ a,
+                         const double* __restrict__ b, const double* __restrict__ wgt, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int q = blockIdx.x;
+  if (q >= ni) return;
+  const int64_t i0 = (int64_t)bu * nptr[q], i1 = (int64_t)bu * nptr[q + 1];
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(a[i] * (wgt ? wgt[i] : 1.0), b[i], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (int)(blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[q] = v;
+  }
+}
+// y_i = src_i / sqrt(nrm2[inst(i)])
+__global__ void k_segnormalize(int ni, int bu, const int* __restrict__ nptr, const double* __restrict__ nrm2,
+                               const double* __restrict__ src, double* __restrict__ y) {
+  const int q = blockIdx.y;
+  const int64_t i0 = (int64_t)bu * nptr[q], i1 = (int64_t)bu * nptr[q + 1];
+  const double inv = 1.0 / sqrt(nrm2[q]);
+  for (int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < i1; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = src[i] * inv;
+}
+
+// The same power iteration per instance of a batched level: lam[q] for every instance.
+int lambda_max_instances(amgc_hierarchy* h, Level& L, std::vector<double>& lam) {
+  cudaStream_t s = h->stream;
+  const int ni = h->n_inst;
+  const int64_t n = L.nu();
+  const int th = 256;
+  DBuf<double> xv, yv, sc;
+  DBuf<int> dptr;
+  AMGC_TRY(xv.alloc(n));
+  AMGC_TRY(yv.alloc(n));
+  AMGC_TRY(sc.alloc(2 * ni));
+  AMGC_TRY(dptr.alloc(ni + 1));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(dptr.p, L.nptr.data(), (ni + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_LAUNCH(k_fill<<<div_up(n, th), th, 0, s>>>(n, 1.0, xv.p));
+  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, xv.p, xv.p, nullptr, sc.p));
+  const dim3 gs(64, ni);
+  AMGC_LAUNCH(k_segnormalize<<<gs, th, 0, s>>>(ni, L.bu, dptr.p, sc.p, xv.p, xv.p));
+  for (int it = 0; it < 20; ++it) {
+    AMGC_TRY(bsr_spmv(L.K, xv.p, yv.p, 1.0, 0.0, s));
+    AMGC_LAUNCH(k_scale_dinv<<<div_up(n, th), th, 0, s>>>(n, L.dinv.p, yv.p));
+    AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, yv.p, yv.p, nullptr, sc.p));
+    AMGC_LAUNCH(k_segnormalize<<<gs, th, 0, s>>>(ni, L.bu, dptr.p, sc.p, yv.p, xv.p));
+  }
+  AMGC_TRY(bsr_spmv(L.K, xv.p, yv.p, 1.0, 0.0, s));
+  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, xv.p, yv.p, nullptr, sc.p));
+  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, xv.p, xv.p, L.kdiag.p, sc.p + ni));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  std::vector<double> hs(2 * ni);
+  AMGC_CUDA_TRY(cudaMemcpyAsync(hs.data(), sc.p, 2 * ni * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  lam.resize(ni);
+  for (int q = 0; q < ni; ++q) {
+    lam[q] = hs[ni + q] > 0.0 ? hs[q] / hs[ni + q] : 0.0;
+    if (!(lam[q] > 0.0) || !std::isfinite(lam[q])) {
+      set_error("lambda_max: non-positive or non-finite Rayleigh quotient on an instance");
+      return AMGC_ESINGULAR;
+    }
+  }
   return AMGC_OK;
 }
 

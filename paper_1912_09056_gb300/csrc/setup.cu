@@ -394,10 +394,14 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
 }
 enum : int8_t { UND = 0, ROOT = 1, OUT = 2 };
 
-__global__ void k_mis_key(int n, const int8_t* __restrict__ state, uint32_t seed, unsigned long long* __restrict__ kv) {
+// key_base (batched hierarchies): first node of the node's instance, so that the hash uses the
+// instance-local index and every instance aggregates exactly as it would alone
+__global__ void k_mis_key(int n, const int8_t* __restrict__ state, uint32_t seed, const int* __restrict__ key_base,
+                          unsigned long long* __restrict__ kv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  unsigned long long key = ((unsigned long long)fmix32((uint32_t)i ^ seed) << 32) | (unsigned long long)(uint32_t)i;
+  const uint32_t li = (uint32_t)(key_base ? i - key_base[i] : i);
+  unsigned long long key = ((unsigned long long)fmix32(li ^ seed) << 32) | (unsigned long long)(uint32_t)i;
   kv[i] = state[i] == UND ? key + 1ull : 0ull;
 }
 // out[i] = max(in[i], max over graph neighbours j of in[j]); the graph is K's pattern without
@@ -518,7 +522,7 @@ static int mis2_aggregate(amgc_hierarchy* h, Level& L, DBuf<int>& roots, int* n_
   const int* col = L.K.col.p;
   const int* body = L.body.p;
   for (int round = 0; round < 10000; ++round) {
-    AMGC_LAUNCH(k_mis_key<<<g, 256, 0, s>>>(n, state.p, h->opts.seed, kv.p));
+    AMGC_LAUNCH(k_mis_key<<<g, 256, 0, s>>>(n, state.p, h->opts.seed, L.key_base.p, kv.p));
     AMGC_LAUNCH(k_mis_max<<<g, 256, 0, s>>>(n, rp, col, body, kv.p, m1.p));
     AMGC_LAUNCH(k_mis_max<<<g, 256, 0, s>>>(n, rp, col, body, m1.p, m2.p));
     AMGC_LAUNCH(k_mis_newroot<<<g, 256, 0, s>>>(n, kv.p, m2.p, state.p, nr.p));
@@ -936,14 +940,14 @@ static int bsr_transpose(amgc_hierarchy* h, const DBsr& A, DBsr& T) {
 template <int BU>
 __global__ void k_sa_values(int nn, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ agg,
                             const double* __restrict__ phat, const double* __restrict__ dinv, double omega,
-                            double* __restrict__ val) {
+                            const double* __restrict__ omega_dof, double* __restrict__ val) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nn) return;
   for (int e = rp[i]; e < rp[i + 1]; ++e) {
     double* v = val + (int64_t)e * BU * 6;
     const bool own = col[e] == agg[i];
     for (int r = 0; r < BU; ++r) {
-      const double d = omega * dinv[(int64_t)i * BU + r];
+      const double d = (omega_dof ? omega_dof[(int64_t)i * BU + r] : omega) * dinv[(int64_t)i * BU + r];
       for (int c = 0; c < 6; ++c) {
         double p = own ? phat[((int64_t)i * BU + r) * 6 + c] : 0.0;
         v[r * 6 + c] = p - d * v[r * 6 + c];
@@ -1042,6 +1046,30 @@ __global__ void k_compact(int n, const int* __restrict__ flag_rp, const int* __r
   if (i < n && flag_rp[i + 1] > flag_rp[i]) out[rank[i]] = i;
 }
 
+__global__ void k_scale_omega(int n, const double* __restrict__ dinv, double omega, const double* __restrict__ wdof,
+                              double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (wdof ? wdof[i] : omega) * dinv[i];
+}
+__global__ void k_key_base(int ni, const int* __restrict__ nptr, int* __restrict__ base) {
+  const int q = blockIdx.x;
+  if (q >= ni) return;
+  for (int i = nptr[q] + threadIdx.x; i < nptr[q + 1]; i += blockDim.x) base[i] = nptr[q];
+}
+// batched levels: first node of each node's instance (MIS-2 keys)
+static int build_key_base(amgc_hierarchy* h, Level& L) {
+  if (h->n_inst <= 1) return AMGC_OK;
+  cudaStream_t s = h->stream;
+  DBuf<int> dptr;
+  AMGC_TRY(dptr.alloc(h->n_inst + 1));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(dptr.p, L.nptr.data(), (h->n_inst + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_TRY(L.key_base.alloc(std::max(L.nn, 1)));
+  AMGC_LAUNCH(k_key_base<<<h->n_inst, 256, 0, s>>>(h->n_inst, dptr.p, L.key_base.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMGC_OK;
+}
+
 static int alloc_work(Level& L) {
   const int n = L.rows();
   AMGC_TRY(L.x.alloc(std::max(n, 1)));
@@ -1088,8 +1116,37 @@ int smoother_setup(amgc_hierarchy* h, int l) {
   AMGC_TRY(L.b1_rows.alloc(std::max(cnt, 1)));
   AMGC_LAUNCH(k_compact<<<div_up(L.nn, 256), 256, 0, s>>>(L.nn, L.B1.rowptr.p, flag.p, L.b1_rows.p));
   AMGC_CUDA_TRY(cudaGetLastError());
-  if (L.lam_max == 0.0) AMGC_TRY(lambda_max_estimate(h, L, &L.lam_max));
+  if (L.lam_max == 0.0) {
+    if (h->n_inst > 1) {
+      AMGC_TRY(lambda_max_instances(h, L, L.inst_lam_max));
+      L.lam_max = L.inst_lam_max[0];
+    } else {
+      AMGC_TRY(lambda_max_estimate(h, L, &L.lam_max));
+    }
+  }
   L.omega_j = h->opts.jacobi_omega > 0.0 ? h->opts.jacobi_omega : (4.0 / 3.0) / L.lam_max;
+  // omega_J D^-1 per DOF (omega_J per instance when batched)
+  {
+    std::vector<double> w;
+    const double* wp = nullptr;
+    if (h->n_inst > 1) {
+      w.resize(L.nu());
+      for (int q = 0; q < h->n_inst; ++q) {
+        const double om = h->opts.jacobi_omega > 0.0 ? h->opts.jacobi_omega : (4.0 / 3.0) / L.inst_lam_max[q];
+        for (int i = L.bu * L.nptr[q]; i < L.bu * L.nptr[q + 1]; ++i) w[i] = om;
+      }
+      wp = w.data();
+    }
+    AMGC_TRY(L.jdinv.alloc(nu));
+    DBuf<double> wd;
+    if (wp) {
+      AMGC_TRY(wd.alloc(nu));
+      AMGC_CUDA_TRY(cudaMemcpyAsync(wd.p, wp, nu * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    AMGC_LAUNCH(k_scale_omega<<<div_up(nu, 256), 256, 0, s>>>(nu, L.dinv.p, L.omega_j, wd.p, L.jdinv.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   AMGC_TRY(alloc_work(L));
   return AMGC_OK;
 }
@@ -1160,6 +1217,25 @@ int build_sell(amgc_hierarchy* h, int l) {
 }
 
 // ======================================================================== coarsening
+// coarse instance boundaries: aggregates are numbered by ascending root, so instance i owns the
+// aggregates whose root lies below its first node; multiplier aggregates follow the rank of
+// their first coupled displacement node
+__global__ void k_inst_bounds(int n_inst1, const int* __restrict__ nptr, const int* __restrict__ roots, int n_agg,
+                              const int* __restrict__ mark_rank, int nn, int n_lagg, int* __restrict__ nptr_c,
+                              int* __restrict__ lptr_c) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inst1) return;
+  const int b = nptr[i];
+  int lo = 0, hi = n_agg;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (roots[mid] < b) lo = mid + 1;
+    else hi = mid;
+  }
+  nptr_c[i] = lo;
+  lptr_c[i] = b < nn ? mark_rank[b] : n_lagg;
+}
+
 __global__ void k_gather_body(int n, const int* __restrict__ roots, const int* __restrict__ body, int* __restrict__ out) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a < n) out[a] = body[roots[a]];
@@ -1171,6 +1247,7 @@ int coarsen_level(amgc_hierarchy* h, int l) {
   // --- displacement aggregates
   DBuf<int> roots;
   int n_agg = 0;
+  AMGC_TRY(build_key_base(h, L));
   {
     PhaseTimer pt(h, 1);
     AMGC_TRY(mis2_aggregate(h, L, roots, &n_agg));
@@ -1192,6 +1269,23 @@ int coarsen_level(amgc_hierarchy* h, int l) {
     AMGC_LAUNCH(k_lm_assign<<<div_up(L.nl, 256), 256, 0, s>>>(L.nl, L.lm_dnode.p, L.agg.p, first.p, mark.p, L.lagg.p, lm_dnode_c.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   L.n_lagg = n_lagg;
+  std::vector<int> nptr_c, lptr_c;
+  if (h->n_inst > 1) {
+    const int ni1 = h->n_inst + 1;
+    DBuf<int> d_nptr, d_np, d_lp;
+    AMGC_TRY(d_nptr.alloc(ni1));
+    AMGC_TRY(d_np.alloc(ni1));
+    AMGC_TRY(d_lp.alloc(ni1));
+    AMGC_CUDA_TRY(cudaMemcpyAsync(d_nptr.p, L.nptr.data(), ni1 * sizeof(int), cudaMemcpyHostToDevice, s));
+    AMGC_LAUNCH(k_inst_bounds<<<div_up(ni1, 128), 128, 0, s>>>(ni1, d_nptr.p, roots.p, n_agg, mark.p, L.nn, n_lagg,
+                                                               d_np.p, d_lp.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    nptr_c.resize(ni1);
+    lptr_c.resize(ni1);
+    AMGC_CUDA_TRY(cudaMemcpyAsync(nptr_c.data(), d_np.p, ni1 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMGC_CUDA_TRY(cudaMemcpyAsync(lptr_c.data(), d_lp.p, ni1 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   ptm.reset();
   // --- tentative displacement prolongator by QR
   ptm.reset(new PhaseTimer(h, 3));
@@ -1206,6 +1300,8 @@ int coarsen_level(amgc_hierarchy* h, int l) {
   C.nn = n_agg;
   C.bu = 6;
   C.nl = n_lagg;
+  C.nptr = nptr_c;
+  C.lptr = lptr_c;
   AMGC_TRY(C.B.alloc((size_t)n_agg * 36));
   AMGC_LAUNCH(k_tentative_pattern<<<div_up(L.nn + 1, 256), 256, 0, s>>>(L.nn, L.agg.p, Phat.rowptr.p, Phat.col.p));
   AMGC_LAUNCH(k_tentative_qr<<<div_up((int64_t)n_agg * 32, 128), 128, 0, s>>>(n_agg, L.bu, mptr.p, midx.p, L.B.p, Phat.val.p, C.B.p,
@@ -1240,12 +1336,21 @@ int coarsen_level(amgc_hierarchy* h, int l) {
   if (h->opts.transfer == 1) {
     AMGC_TRY(spgemm(h, L.K, Phat, L.P));
     const double omega = h->opts.sa_omega / L.lam_max;
+    DBuf<double> wdof;   // per-DOF SA damping of a batched level (sa_omega / lambda_max of the instance)
+    if (h->n_inst > 1) {
+      std::vector<double> w(L.nu());
+      for (int q = 0; q < h->n_inst; ++q)
+        for (int i = L.bu * L.nptr[q]; i < L.bu * L.nptr[q + 1]; ++i) w[i] = h->opts.sa_omega / L.inst_lam_max[q];
+      AMGC_TRY(wdof.alloc(L.nu()));
+      AMGC_CUDA_TRY(cudaMemcpyAsync(wdof.p, w.data(), L.nu() * sizeof(double), cudaMemcpyHostToDevice, s));
+      AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     if (L.bu == 3)
       AMGC_LAUNCH(k_sa_values<3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.P.rowptr.p, L.P.col.p, L.agg.p, Phat.val.p, L.dinv.p,
-                                                       omega, L.P.val.p));
+                                                       omega, wdof.p, L.P.val.p));
     else
       AMGC_LAUNCH(k_sa_values<6><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.P.rowptr.p, L.P.col.p, L.agg.p, Phat.val.p, L.dinv.p,
-                                                       omega, L.P.val.p));
+                                                       omega, wdof.p, L.P.val.p));
     AMGC_CUDA_TRY(cudaGetLastError());
   } else {
     L.P = std::move(Phat);
@@ -1440,7 +1545,195 @@ __global__ void k_gj_unscramble(int n, const int* __restrict__ piv, double* __re
   }
 }
 
+// ---- batched coarsest level: one dense block per instance
+template <int BR, int BC>
+__global__ void k_dense_put_batched(int nbr, const int* __restrict__ rp, const int* __restrict__ col,
+                                    const double* __restrict__ val, int row0, int col0, const int* __restrict__ inst,
+                                    const int* __restrict__ loc, const int* __restrict__ goff,
+                                    const int64_t* __restrict__ doff, double* __restrict__ A) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const double* v = val + (int64_t)e * BR * BC;
+    for (int r = 0; r < BR; ++r) {
+      const int gr = row0 + i * BR + r;
+      const int q = inst[gr];
+      const int n = goff[q + 1] - goff[q];
+      for (int c = 0; c < BC; ++c) {
+        const int gc = col0 + col[e] * BC + c;
+        A[doff[q] + (int64_t)loc[gr] * n + loc[gc]] = v[r * BC + c];
+      }
+    }
+  }
+}
+__global__ void k_dense_z_batched(int nl, const double* __restrict__ Z, int off, const int* __restrict__ inst,
+                                  const int* __restrict__ loc, const int* __restrict__ goff,
+                                  const int64_t* __restrict__ doff, double* __restrict__ A) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  for (int r = 0; r < 3; ++r) {
+    const int gr = off + 3 * l + r;
+    const int q = inst[gr];
+    const int n = goff[q + 1] - goff[q];
+    for (int c = 0; c < 3; ++c) A[doff[q] + (int64_t)loc[gr] * n + loc[off + 3 * l + c]] = -Z[(int64_t)l * 9 + r * 3 + c];
+  }
+}
+// Gauss-Jordan inverse with partial pivoting of every instance block, one CTA per block; the
+// same elimination as the single-matrix path, with block barriers between the phases.
+constexpr int kGjThreads = 512;
+__global__ void __launch_bounds__(kGjThreads)
+k_gj_batched(int n_inst, const int* __restrict__ goff, const int64_t* __restrict__ doff, double* __restrict__ Aall,
+             double* __restrict__ fall, int* __restrict__ pivall, int* st) {
+  __shared__ double bv[kGjThreads];
+  __shared__ int bi[kGjThreads];
+  const int q = blockIdx.x;
+  if (q >= n_inst) return;
+  const int n = goff[q + 1] - goff[q];
+  double* A = Aall + doff[q];
+  double* f = fall + goff[q];
+  int* piv = pivall + goff[q];
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int besti = n;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      double v = fabs(A[(int64_t)i * n + k]);
+      if (v > best || (v == best && i < besti)) { best = v; besti = i; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = besti;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        double v = bv[threadIdx.x + o];
+        int ii = bi[threadIdx.x + o];
+        if (v > bv[threadIdx.x] || (v == bv[threadIdx.x] && ii < bi[threadIdx.x])) {
+          bv[threadIdx.x] = v;
+          bi[threadIdx.x] = ii;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = bi[0];
+    const double pmax = bv[0];
+    __syncthreads();
+    if (threadIdx.x == 0) piv[k] = p;
+    if (p != k && p < n) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double t = A[(int64_t)k * n + j];
+        A[(int64_t)k * n + j] = A[(int64_t)p * n + j];
+        A[(int64_t)p * n + j] = t;
+      }
+    }
+    __syncthreads();
+    double pv = A[(int64_t)k * n + k];
+    if (!(pmax > 0.0) || !isfinite(pv)) {
+      if (threadIdx.x == 0) set_status(st, ST_SINGULAR);
+      pv = 1.0;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == k) ? 0.0 : A[(int64_t)i * n + k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) A[(int64_t)i * n + k] = 0.0;
+    if (threadIdx.x == 0) A[(int64_t)k * n + k] = 1.0;
+    __syncthreads();
+    const double inv = 1.0 / pv;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) A[(int64_t)k * n + j] *= inv;
+    __syncthreads();
+    for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) {
+      const int i = (int)(idx / n), j = (int)(idx % n);
+      if (i != k && f[i] != 0.0) A[idx] -= f[i] * A[(int64_t)k * n + j];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double* row = A + (int64_t)i * n;
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = piv[k];
+      if (p != k) {
+        double t = row[k];
+        row[k] = row[p];
+        row[p] = t;
+      }
+    }
+  }
+}
+
+static int coarse_setup_batched(amgc_hierarchy* h, int l) {
+  cudaStream_t s = h->stream;
+  Level& L = h->L[l];
+  const int ni = h->n_inst;
+  const int rows = L.rows();
+  const int nu = L.nu();
+  std::vector<int> inst(rows), loc(rows), glob(rows), goff(ni + 1, 0);
+  std::vector<int64_t> doff(ni + 1, 0);
+  int g = 0;
+  for (int q = 0; q < ni; ++q) {
+    goff[q] = g;
+    int t = 0;
+    for (int r = L.bu * L.nptr[q]; r < L.bu * L.nptr[q + 1]; ++r, ++t, ++g) {
+      inst[r] = q; loc[r] = t; glob[g] = r;
+    }
+    for (int r = nu + 3 * L.lptr[q]; r < nu + 3 * L.lptr[q + 1]; ++r, ++t, ++g) {
+      inst[r] = q; loc[r] = t; glob[g] = r;
+    }
+    doff[q + 1] = doff[q] + (int64_t)t * t;
+  }
+  goff[ni] = g;
+  if (g != rows) {
+    set_error("batched coarsest level: instance ranges do not cover the level");
+    return AMGC_EINVAL;
+  }
+  AMGC_TRY(L.c_inst.alloc(rows));
+  AMGC_TRY(L.c_loc.alloc(rows));
+  AMGC_TRY(L.c_glob.alloc(rows));
+  AMGC_TRY(L.c_goff.alloc(ni + 1));
+  AMGC_TRY(L.c_doff.alloc(ni + 1));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.c_inst.p, inst.data(), rows * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.c_loc.p, loc.data(), rows * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.c_glob.p, glob.data(), rows * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.c_goff.p, goff.data(), (ni + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(L.c_doff.p, doff.data(), (ni + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  const int64_t tot = doff[ni];
+  AMGC_TRY(L.Ainv.alloc((size_t)std::max<int64_t>(tot, 1)));
+  AMGC_CUDA_TRY(cudaMemsetAsync(L.Ainv.p, 0, (size_t)tot * sizeof(double), s));
+  const int* ci = L.c_inst.p;
+  const int* cl = L.c_loc.p;
+  const int* cg = L.c_goff.p;
+  const int64_t* cd = L.c_doff.p;
+  if (L.bu == 3) {
+    AMGC_LAUNCH(k_dense_put_batched<3, 3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, 0,
+                                                                           0, ci, cl, cg, cd, L.Ainv.p));
+    if (L.nl > 0) {
+      AMGC_LAUNCH(k_dense_put_batched<3, 3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.B1.rowptr.p, L.B1.col.p,
+                                                                             L.B1.val.p, 0, nu, ci, cl, cg, cd, L.Ainv.p));
+      AMGC_LAUNCH(k_dense_put_batched<3, 3><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p,
+                                                                             L.B2.val.p, nu, 0, ci, cl, cg, cd, L.Ainv.p));
+    }
+  } else {
+    AMGC_LAUNCH(k_dense_put_batched<6, 6><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, 0,
+                                                                           0, ci, cl, cg, cd, L.Ainv.p));
+    if (L.nl > 0) {
+      AMGC_LAUNCH(k_dense_put_batched<6, 3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.B1.rowptr.p, L.B1.col.p,
+                                                                             L.B1.val.p, 0, nu, ci, cl, cg, cd, L.Ainv.p));
+      AMGC_LAUNCH(k_dense_put_batched<3, 6><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p,
+                                                                             L.B2.val.p, nu, 0, ci, cl, cg, cd, L.Ainv.p));
+    }
+  }
+  if (L.nl > 0)
+    AMGC_LAUNCH(k_dense_z_batched<<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.Z.p, nu, ci, cl, cg, cd, L.Ainv.p));
+  DBuf<double> f;
+  DBuf<int> piv;
+  AMGC_TRY(f.alloc(std::max(rows, 1)));
+  AMGC_TRY(piv.alloc(std::max(rows, 1)));
+  AMGC_LAUNCH(k_gj_batched<<<ni, kGjThreads, 0, s>>>(ni, cg, cd, L.Ainv.p, f.p, piv.p, h->status.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(check_status(h, "batched coarsest factorisation"));
+  AMGC_TRY(alloc_work(L));
+  return AMGC_OK;
+}
+
 int coarse_setup(amgc_hierarchy* h, int l) {
+  if (h->n_inst > 1) return coarse_setup_batched(h, l);
   cudaStream_t s = h->stream;
   Level& L = h->L[l];
   const int n = L.rows();

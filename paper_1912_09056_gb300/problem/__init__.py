@@ -271,3 +271,67 @@ def batched_workloads(count: int = 64, seed: int = 3, lo: int = 8, hi: int = 32,
                         seed=int(rng.integers(0, 2**31 - 1)),
                         top_amps=rng.uniform(-0.02, 0.0, size=4).tolist()))
     return out
+
+
+def concat_problems(probs, name: str = "batch"):
+    """Block-diagonal concatenation of independent problems (K rows, slave and master nodes).
+
+    Returns (problem, node_ptr, lm_ptr): instance q owns K block rows [node_ptr[q],
+    node_ptr[q+1]) and slave / multiplier nodes [lm_ptr[q], lm_ptr[q+1]).  Bodies of instance q
+    get ids 2q and 2q + 1.
+    """
+    node_ptr = np.cumsum([0] + [p.n_nodes for p in probs]).astype(np.int32)
+    lm_ptr = np.cumsum([0] + [p.n_s for p in probs]).astype(np.int32)
+    m_ptr = np.cumsum([0] + [p.master_node.size for p in probs])
+    kptr = np.cumsum([0] + [p.K_col.size for p in probs])
+    mnz = np.cumsum([0] + [p.M_col.size for p in probs])
+    K_rowptr = np.concatenate([probs[0].K_rowptr[:1]] + [p.K_rowptr[1:] + kptr[q] for q, p in enumerate(probs)])
+    M_rowptr = np.concatenate([probs[0].M_rowptr[:1]] + [p.M_rowptr[1:] + mnz[q] for q, p in enumerate(probs)])
+    cat = ContactProblem(
+        name=name, n_nodes=int(node_ptr[-1]),
+        K_rowptr=K_rowptr.astype(np.int32),
+        K_col=np.concatenate([p.K_col + node_ptr[q] for q, p in enumerate(probs)]).astype(np.int32),
+        K_val=np.concatenate([p.K_val for p in probs]),
+        body_id=np.concatenate([p.body_id + 2 * q for q, p in enumerate(probs)]).astype(np.int32),
+        coords=np.concatenate([p.coords for p in probs]),
+        nullspace=np.concatenate([p.nullspace for p in probs]),
+        slave_node=np.concatenate([p.slave_node + node_ptr[q] for q, p in enumerate(probs)]).astype(np.int32),
+        master_node=np.concatenate([p.master_node + node_ptr[q] for q, p in enumerate(probs)]).astype(np.int32),
+        D=np.concatenate([p.D for p in probs]),
+        M_rowptr=M_rowptr.astype(np.int32),
+        M_col=np.concatenate([p.M_col + m_ptr[q] for q, p in enumerate(probs)]).astype(np.int32),
+        M_val=np.concatenate([p.M_val for p in probs]),
+        triad=np.concatenate([p.triad for p in probs]),
+        active=np.concatenate([p.active for p in probs]),
+        f=np.concatenate([p.f for p in probs]),
+        g=np.concatenate([p.g for p in probs]),
+        extra=dict(n_inst=len(probs)))
+    return cat, node_ptr, lm_ptr
+
+
+# prescribed-displacement patterns of the batched workload (unrotated frame, scaled by the
+# instance's seeded amplitudes): compression, and compression with x, y and diagonal shear
+BATCH_PATTERNS = np.array([[0.0, 0.0, 1.0], [0.3, 0.0, 1.0], [0.0, 0.3, 1.0], [0.3, 0.3, 1.0]])
+
+
+def batched_rhs(probs, params, cat, node_ptr, lm_ptr):
+    """(nrhs, rows) right-hand sides: per instance f = L (a_k d_k), g = 0, in the concatenated order."""
+    n_u = cat.n_u
+    nrhs = BATCH_PATTERNS.shape[0]
+    out = np.zeros((nrhs, cat.n))
+    for q, (p, prm) in enumerate(zip(probs, params)):
+        L = p.extra["top_lift"]
+        for k in range(nrhs):
+            out[k, 3 * node_ptr[q]:3 * node_ptr[q + 1]] = L @ (prm["top_amps"][k] * BATCH_PATTERNS[k])
+    return out
+
+
+def batched_workload(count: int = 64, seed: int = 3, lo: int = 8, hi: int = 32):
+    """The batched set: `count` uneven instances, concatenated, with four right-hand sides each."""
+    params = batched_workloads(count, seed, lo, hi)
+    probs = []
+    for prm in params:
+        kw = {k: v for k, v in prm.items() if k != "top_amps"}
+        probs.append(two_block_problem(**kw))
+    cat, node_ptr, lm_ptr = concat_problems(probs)
+    return cat, node_ptr, lm_ptr, batched_rhs(probs, params, cat, node_ptr, lm_ptr), probs, params
