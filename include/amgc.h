@@ -86,6 +86,9 @@ typedef struct {
   double jacobi_omega;       /* <= 0: (4/3) / lambda_max(D^-1 K) per level                     */
   double simple_alpha;       /* SIMPLE damping alpha of the multiplier correction              */
   double tol;                /* relative residual tolerance ||r_k|| / ||r_0||                  */
+  int32_t autotune;          /* 1: time the row mappings of every level's K, P and R apply at
+                                setup and keep the fastest (warp per row, SELL with one or two
+                                threads per row), separately for the FP64 and FP32 cycle     */
 } amgc_options;
 
 typedef struct {
@@ -109,7 +112,7 @@ typedef struct {
 
 /* Fills the defaults: levels_max 10, coarse_max_rows 5000, SA, 1 sweep, 1 Jacobi sweep,
  * SIMPLE (diag K), FP64, restart 50, maxit 1000, seed 0x5EED, sa_omega 4/3, jacobi_omega
- * automatic, alpha 0.8, tol 1e-8 (Sec. 6.2 settings, Eq. ch7_linearstoppingcriterion). */
+ * automatic, alpha 0.8, tol 1e-8 (Sec. 6.2 settings, Eq. ch7_linearstoppingcriterion), autotune 0. */
 void amgc_default_options(amgc_options* opts);
 
 /* Builds the hierarchy (Sec. 4: segregated aggregation with Algorithm 1, transfers of

@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("smoother_sweeps", C.c_int32), ("jacobi_sweeps", C.c_int32), ("simplec", C.c_int32),
                 ("precision", C.c_int32), ("fgmres_restart", C.c_int32), ("fgmres_maxit", C.c_int32),
                 ("seed", C.c_uint32), ("sa_omega", C.c_double), ("jacobi_omega", C.c_double),
-                ("simple_alpha", C.c_double), ("tol", C.c_double)]
+                ("simple_alpha", C.c_double), ("tol", C.c_double), ("autotune", C.c_int32)]
 
 
 class Stats(C.Structure):

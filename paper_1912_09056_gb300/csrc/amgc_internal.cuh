@@ -102,7 +102,7 @@ struct Sell {
 
 // FP32 mirrors of the cycle data of one level (values only; index arrays are shared).
 struct LevelF32 {
-  DBuf<float> K, B1, B2, P, R, Z, Ks, Ps, jdinv, atinv, pl_w;
+  DBuf<float> K, B1, B2, P, R, Z, Ks, Ps, Rs, jdinv, atinv, pl_w;
   DBuf<float> x, b, r, t, dlam;
 };
 
@@ -130,7 +130,8 @@ struct LevelV {
   int rows() const { return nn * bu + 3 * nl; }
   double omega_j = 0.0;
   BsrV<T> K, B1, B2, P, R;
-  SellV<T> Ks, Ps;
+  SellV<T> Ks, Ps, Rs;
+  int kmap = -1, pmap = -1, rmap = -1;   // row mappings (see Level)
   const T* Z = nullptr;
   const double* Sinv = nullptr;    // FP64 in both precisions
   const T* dinv = nullptr;
@@ -171,7 +172,10 @@ struct Level {
   int rows() const { return nn * bu + 3 * nl; }
 
   DBsr K, B1, B2;          // saddle blocks
-  Sell Ks, Ps;             // SELL-32 copies of K and P (finest level)
+  Sell Ks, Ps, Rs;         // SELL-32 copies of K, P, R (finest level; others when autotuned)
+  // row mapping of the K, P, R applies per precision (0: FP64, 1: FP32):
+  // 0 = warp per row, 1 = SELL one thread per row, 2 = SELL two threads per row, -1 = default
+  int kmap[2] = {-1, -1}, pmap[2] = {-1, -1}, rmap[2] = {-1, -1};
   DBuf<double> Z;          // nl*9
   DBuf<int> body;          // nn
   DBuf<double> B;          // nullspace nu*6
@@ -240,6 +244,11 @@ struct amgc_hierarchy {
   std::vector<amgc::LevelV<float>> v32;    // cycle views, FP32 (precision 32)
   bool transposed = false;                 // FGMRES/cycle act on A^T (adjoint solve)
   int n_inst = 1;                          // instances of a batched hierarchy
+  // CUDA graphs of the forward V-cycle core (index 0: FP64, 1: FP32), captured on first use
+  cudaGraphExec_t cycle_graph[2] = {nullptr, nullptr};
+  long long cycle_graph_kernels[2] = {0, 0};
+  cudaStream_t capture_stream = nullptr;
+  amgc::DBuf<double> cyc_in, cyc_out;      // fixed FP64 input/output of the captured FP64 cycle
   // batched FGMRES workspace
   amgc::DBuf<int> b_chunk_row0, b_chunk_row1, b_chunk_ptr, b_row_inst;
   int b_nchunk = 0;
@@ -278,6 +287,8 @@ int build_fine_level(amgc_hierarchy* h, const amgc_bsr* K, const double* D, cons
 int coarsen_level(amgc_hierarchy* h, int l);
 int smoother_setup(amgc_hierarchy* h, int l);
 int build_sell(amgc_hierarchy* h, int l);
+int build_sell_of(amgc_hierarchy* h, const DBsr& A, Sell& S);
+int autotune(amgc_hierarchy* h);
 int coarse_setup(amgc_hierarchy* h, int l);
 int check_status(amgc_hierarchy* h, const char* where);
 int transposed_setup(amgc_hierarchy* h);

@@ -72,6 +72,7 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
     PhaseTimer pt(h, 9);
     if (lc > 0) AMGC_TRY(build_sell(h, 0));
     AMGC_TRY(make_views(h));
+    if (o.autotune && lc > 0) AMGC_TRY(autotune(h));
   }
   AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
   // statistics
@@ -163,6 +164,7 @@ void amgc_default_options(amgc_options* o) {
   o->jacobi_omega = 0.0;
   o->simple_alpha = 0.8;
   o->tol = 1e-8;
+  o->autotune = 0;
 }
 
 int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const int32_t* slave_node,
@@ -466,6 +468,9 @@ void amgc_destroy(struct amgc_hierarchy* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   for (auto& e : h->prof_ev) cudaEventDestroy(e);
+  for (auto& g : h->cycle_graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   delete h;
 }

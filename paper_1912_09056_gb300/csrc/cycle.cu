@@ -182,27 +182,45 @@ k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, cons
   for (int q = 0; q < BR; ++q) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * BR + q, acc[q]);
 }
 
+template <int BR, int BC, int MODE, class T, int TPR>
+static void launch_sell(const SellV<T>& S, int nbr, const int* rp2, const int* c2, const T* v2, const T* x,
+                        const T* x2, const T* b, const T* x0, const T* dinv, double omega, T* y, cudaStream_t s) {
+  const int g = div_up((int64_t)nbr * TPR, kSellThreads);
+  AMGC_LAUNCH(k_sell<BR, BC, MODE, T, TPR><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2,
+                                                                      x2, b, x0, dinv, (T)omega, y));
+}
+
+// tpr <= 0: the default (one thread per row in FP64, which is FMA-bound; two in FP32)
 template <int MODE, class T>
 static int sell_apply(const SellV<T>& S, int nbr, const BsrV<T>* A2, const T* x, const T* x2, const T* b, const T* x0,
-                      const T* dinv, double omega, T* y, cudaStream_t s) {
-  constexpr int TPR = sizeof(T) == 8 ? 1 : 2;
-  const int g = div_up((int64_t)nbr * TPR, kSellThreads);
+                      const T* dinv, double omega, T* y, cudaStream_t s, int tpr = 0) {
+  if (tpr <= 0) tpr = sizeof(T) == 8 ? 1 : 2;
   const int* rp2 = A2 ? A2->rp : nullptr;
   const int* c2 = A2 ? A2->col : nullptr;
   const T* v2 = A2 ? A2->val : nullptr;
   if (nbr == 0) return AMGC_OK;
-  if (S.br == 3 && S.bc == 3)
-    AMGC_LAUNCH(k_sell<3, 3, MODE, T, TPR><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
-                                                                 b, x0, dinv, (T)omega, y));
-  else if (S.br == 3 && S.bc == 6)
-    AMGC_LAUNCH(k_sell<3, 6, MODE, T, TPR><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
-                                                                 b, x0, dinv, (T)omega, y));
-  else {
-    set_error("sell_apply: unsupported block shape");
-    return AMGC_EINVAL;
+#define AMGC_SELL_CASE(R, C)                                                                         \
+  if (S.br == R && S.bc == C) {                                                                      \
+    if (tpr == 1) launch_sell<R, C, MODE, T, 1>(S, nbr, rp2, c2, v2, x, x2, b, x0, dinv, omega, y, s); \
+    else launch_sell<R, C, MODE, T, 2>(S, nbr, rp2, c2, v2, x, x2, b, x0, dinv, omega, y, s);          \
+    AMGC_CUDA_TRY(cudaGetLastError());                                                               \
+    return AMGC_OK;                                                                                  \
   }
-  AMGC_CUDA_TRY(cudaGetLastError());
-  return AMGC_OK;
+  AMGC_SELL_CASE(3, 3)
+  AMGC_SELL_CASE(3, 6)
+  AMGC_SELL_CASE(6, 3)
+  AMGC_SELL_CASE(6, 6)
+#undef AMGC_SELL_CASE
+  set_error("sell_apply: unsupported block shape");
+  return AMGC_EINVAL;
+}
+
+// Applies of K (with the multiplier coupling A2), P and R with the level's chosen row mapping.
+template <int MODE, class T>
+static int mapped_apply(const BsrV<T>& A, const SellV<T>& S, int map, const BsrV<T>* A2, const T* x, const T* x2,
+                        const T* b, const T* x0, const T* dinv, double omega, T* y, cudaStream_t s) {
+  if (S.nslice > 0 && map != 0) return sell_apply<MODE, T>(S, A.nbr, A2, x, x2, b, x0, dinv, omega, y, s, map);
+  return rowop<MODE, T>(A, x, A2, x2, b, x0, dinv, omega, y, s);
 }
 
 // ------------------------------------------------------------------ multiplier-node kernels
@@ -392,10 +410,7 @@ static int k_apply(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* x1, co
   // K is symmetric on every level (elasticity and Galerkin products), so A^T shares it;
   // the multiplier coupling of the u rows is B1 for A and B2^T for A^T.
   const BsrV<T>* B1 = L.nl ? (transposed ? &L.B2T : &L.B1) : nullptr;
-  if (L.Ks.nslice > 0)
-    AMGC_TRY((sell_apply<MODE, T>(L.Ks, L.nn, B1, x1, lam, b, x0, L.dinv, L.omega_j, y, h->stream)));
-  else
-    AMGC_TRY((rowop<MODE, T>(L.K, x1, B1, lam, b, x0, L.dinv, L.omega_j, y, h->stream)));
+  AMGC_TRY((mapped_apply<MODE, T>(L.K, L.Ks, L.kmap, B1, x1, lam, b, x0, L.dinv, L.omega_j, y, h->stream)));
   if (t)
     AMGC_TRY(prof_end(h, kind, k_apply_bytes(L, MODE == 3 ? 3 : (MODE == 2 ? 1 : 0)),
                       2.0 * ((double)L.K.nnzb * L.bu * L.bu + (double)L.B1.nnzb * L.bu * 3)));
@@ -477,7 +492,7 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
   for (int k = 0; k < sweeps; ++k) AMGC_TRY(smooth<T>(h, L, l, b, x, k == 0));
   AMGC_TRY(residual<T>(h, L, l, b, x, L.r));
   // restrict: C.b = [R r_u ; R^lambda r_lambda]
-  AMGC_TRY((rowop<0, T>(L.R, L.r, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, C.b, s)));
+  AMGC_TRY((mapped_apply<0, T>(L.R, L.Rs, L.rmap, nullptr, L.r, nullptr, nullptr, nullptr, nullptr, 0.0, C.b, s)));
   if (C.nl > 0) {
     AMGC_LAUNCH(k_restrict_lm<T><<<div_up(C.nl, 128), 128, 0, s>>>(C.nl, L.rl_ptr, L.rl_idx, L.pl_w, L.r + nu,
                                                                    C.b + C.nu()));
@@ -485,10 +500,7 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
   }
   AMGC_TRY(vcycle_t<T>(h, V, l + 1, C.b, C.x));
   // prolongate and add
-  if (L.Ps.nslice > 0)
-    AMGC_TRY((sell_apply<1, T>(L.Ps, L.nn, nullptr, C.x, nullptr, nullptr, nullptr, nullptr, 0.0, x, s)));
-  else
-    AMGC_TRY((rowop<1, T>(L.P, C.x, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, x, s)));
+  AMGC_TRY((mapped_apply<1, T>(L.P, L.Ps, L.pmap, nullptr, C.x, nullptr, nullptr, nullptr, nullptr, 0.0, x, s)));
   if (L.nl > 0) {
     AMGC_LAUNCH(k_prolong_lm<T><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.lagg, L.pl_w, C.x + C.nu(), x + nu));
     AMGC_CUDA_TRY(cudaGetLastError());
@@ -629,21 +641,73 @@ int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y) {
 }
 
 // One V-cycle with FP64 input and output; the FP32 cycle converts at entry and exit.
+// Captures the forward cycle core (fixed input and output buffers) into a CUDA graph on a
+// private stream; the caller's stream then replays it with one launch.
+static int capture_cycle(amgc_hierarchy* h, int idx) {
+  if (!h->capture_stream) AMGC_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+  const int64_t n = h->L[0].rows();
+  if (idx == 0 && h->cyc_in.n == 0) {
+    AMGC_TRY(h->cyc_in.alloc(n));
+    AMGC_TRY(h->cyc_out.alloc(n));
+  }
+  cudaStream_t saved = h->stream;
+  h->stream = h->capture_stream;
+  const long long k0 = g_launches.load();
+  cudaGraph_t graph = nullptr;
+  AMGC_CUDA_TRY(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+  int st = idx == 0 ? vcycle_t<double>(h, h->v64, 0, h->cyc_in.p, h->cyc_out.p)
+                    : vcycle_t<float>(h, h->v32, 0, h->L[0].f.b.p, h->L[0].f.x.p);
+  cudaError_t e = cudaStreamEndCapture(h->capture_stream, &graph);
+  h->stream = saved;
+  if (st != AMGC_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    set_error(std::string("cycle capture: ") + cudaGetErrorString(e));
+    return AMGC_ECUDA;
+  }
+  e = cudaGraphInstantiate(&h->cycle_graph[idx], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->cycle_graph[idx] = nullptr;
+    set_error(std::string("cycle graph instantiation: ") + cudaGetErrorString(e));
+    return AMGC_ECUDA;
+  }
+  h->cycle_graph_kernels[idx] = g_launches.load() - k0;
+  return AMGC_OK;
+}
+
+static int replay_cycle(amgc_hierarchy* h, int idx) {
+  if (!h->cycle_graph[idx]) AMGC_TRY(capture_cycle(h, idx));
+  AMGC_CUDA_TRY(cudaGraphLaunch(h->cycle_graph[idx], h->stream));
+  g_launches.fetch_add(h->cycle_graph_kernels[idx], std::memory_order_relaxed);
+  return AMGC_OK;
+}
+
+// One V-cycle with FP64 input and output; the FP32 cycle converts at entry and exit.  Outside
+// kernel timing the cycle core runs as a captured CUDA graph.
 int precond_apply(amgc_hierarchy* h, const double* r, double* z) {
   if (h->transposed) return vcycle_transposed(h, 0, r, z);
+  const bool graph = h->prof == 0;
+  const int64_t n = h->L[0].rows();
+  const int th = 256;
   if (h->opts.precision == 32) {
-    LevelV<float>& L0 = h->v32[0];
-    const int64_t n = L0.rows();
-    const int th = 256;
     float* bf = h->L[0].f.b.p;
     float* xf = h->L[0].f.x.p;
     AMGC_LAUNCH((k_convert<double, float><<<div_up(n, th), th, 0, h->stream>>>(n, r, bf)));
-    AMGC_TRY(vcycle_t<float>(h, h->v32, 0, bf, xf));
+    if (graph) AMGC_TRY(replay_cycle(h, 1));
+    else AMGC_TRY(vcycle_t<float>(h, h->v32, 0, bf, xf));
     AMGC_LAUNCH((k_convert<float, double><<<div_up(n, th), th, 0, h->stream>>>(n, xf, z)));
     AMGC_CUDA_TRY(cudaGetLastError());
     return AMGC_OK;
   }
-  return vcycle_t<double>(h, h->v64, 0, r, z);
+  if (!graph) return vcycle_t<double>(h, h->v64, 0, r, z);
+  if (!h->cycle_graph[0]) AMGC_TRY(capture_cycle(h, 0));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(h->cyc_in.p, r, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  AMGC_TRY(replay_cycle(h, 0));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(z, h->cyc_out.p, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  return AMGC_OK;
 }
 
 // ------------------------------------------------------------------ views and FP32 mirrors
@@ -695,6 +759,8 @@ int make_views(amgc_hierarchy* h) {
     v.R = bview<double>(L.R, L.R.val.p);
     v.Ks = sview<double>(L.Ks, L.Ks.val.p);
     v.Ps = sview<double>(L.Ps, L.Ps.val.p);
+    v.Rs = sview<double>(L.Rs, L.Rs.val.p);
+    v.kmap = L.kmap[0]; v.pmap = L.pmap[0]; v.rmap = L.rmap[0];
     v.Z = L.Z.p; v.dinv = L.jdinv.p; v.atinv = L.atinv.p; v.pl_w = L.pl_w.p;
     v.x = L.x.p; v.b = L.b.p; v.r = L.r.p; v.t = L.t.p; v.dlam = L.dlam.p;
     if (L.has_transposed) {
@@ -721,8 +787,9 @@ int make_views(amgc_hierarchy* h) {
       AMGC_TRY(to_f32(h, L.atinv.p, (size_t)L.nu(), F.atinv));
       AMGC_TRY(to_f32(h, L.pl_w.p, (size_t)L.nl, F.pl_w));
     }
-    if (L.Ks.nslice > 0) AMGC_TRY(to_f32(h, L.Ks.val.p, (size_t)L.Ks.slots * 32 * 9, F.Ks));
-    if (L.Ps.nslice > 0) AMGC_TRY(to_f32(h, L.Ps.val.p, (size_t)L.Ps.slots * 32 * 18, F.Ps));
+    if (L.Ks.nslice > 0) AMGC_TRY(to_f32(h, L.Ks.val.p, L.Ks.val.n, F.Ks));
+    if (L.Ps.nslice > 0) AMGC_TRY(to_f32(h, L.Ps.val.p, L.Ps.val.n, F.Ps));
+    if (L.Rs.nslice > 0) AMGC_TRY(to_f32(h, L.Rs.val.p, L.Rs.val.n, F.Rs));
     const size_t n = std::max(L.rows(), 1);
     AMGC_TRY(F.x.alloc(n));
     AMGC_TRY(F.b.alloc(n));
@@ -737,12 +804,92 @@ int make_views(amgc_hierarchy* h) {
     v.R = bview<float>(L.R, F.R.p);
     v.Ks = sview<float>(L.Ks, F.Ks.p);
     v.Ps = sview<float>(L.Ps, F.Ps.p);
+    v.Rs = sview<float>(L.Rs, F.Rs.p);
+    v.kmap = L.kmap[1]; v.pmap = L.pmap[1]; v.rmap = L.rmap[1];
     v.Z = F.Z.p; v.dinv = F.jdinv.p; v.atinv = F.atinv.p; v.pl_w = F.pl_w.p;
     v.x = F.x.p; v.b = F.b.p; v.r = F.r.p; v.t = F.t.p; v.dlam = F.dlam.p;
     h->v32.push_back(v);
   }
   AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
   return AMGC_OK;
+}
+
+// ------------------------------------------------------------------ row-mapping autotuner
+// Times every candidate row mapping of one apply (2 warm-up launches, 5 timed, CUDA events on
+// the hierarchy's stream) and returns the fastest: 0 warp per row, 1/2 SELL threads per row.
+template <int MODE, class T>
+static int tune_one(amgc_hierarchy* h, const BsrV<T>& A, const SellV<T>& S, const BsrV<T>* A2, const T* x,
+                    const T* x2, const T* b, const T* dinv, T* y, int* best) {
+  cudaEvent_t e0, e1;
+  AMGC_CUDA_TRY(cudaEventCreate(&e0));
+  AMGC_CUDA_TRY(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  *best = 0;
+  for (int cand = 0; cand < 3; ++cand) {
+    if (cand > 0 && S.nslice == 0) break;
+    for (int rep = 0; rep < 7; ++rep) {
+      if (rep == 2) AMGC_CUDA_TRY(cudaEventRecord(e0, h->stream));
+      AMGC_TRY((mapped_apply<MODE, T>(A, S, cand, A2, x, x2, b, x, dinv, 1.0, y, h->stream)));
+    }
+    AMGC_CUDA_TRY(cudaEventRecord(e1, h->stream));
+    AMGC_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMGC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      *best = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return AMGC_OK;
+}
+
+template <class T>
+static int tune_views(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int pidx) {
+  for (int l = 0; l + 1 < (int)V.size(); ++l) {
+    LevelV<T>& L = V[l];
+    const LevelV<T>& C = V[l + 1];
+    const BsrV<T>* B1 = L.nl ? &L.B1 : nullptr;
+    int km = 0, pm = 0, rm = 0;
+    AMGC_TRY((tune_one<2, T>(h, L.K, L.Ks, B1, L.x, L.x + L.nu(), L.b, L.dinv, L.r, &km)));
+    AMGC_TRY((tune_one<1, T>(h, L.P, L.Ps, nullptr, C.x, nullptr, nullptr, nullptr, L.t, &pm)));
+    AMGC_TRY((tune_one<0, T>(h, L.R, L.Rs, nullptr, L.r, nullptr, nullptr, nullptr, C.b, &rm)));
+    L.kmap = km; L.pmap = pm; L.rmap = rm;
+    Level& LL = h->L[l];
+    LL.kmap[pidx] = km; LL.pmap[pidx] = pm; LL.rmap[pidx] = rm;
+  }
+  return AMGC_OK;
+}
+
+// Builds SELL copies of K, P, R on every level that has a next one, then times the mappings.
+int autotune(amgc_hierarchy* h) {
+  const int nlev = (int)h->L.size();
+  for (int l = 0; l + 1 < nlev; ++l) {
+    Level& L = h->L[l];
+    if (L.Ks.nslice == 0) AMGC_TRY(build_sell_of(h, L.K, L.Ks));
+    if (L.Ps.nslice == 0) AMGC_TRY(build_sell_of(h, L.P, L.Ps));
+    if (L.Rs.nslice == 0) AMGC_TRY(build_sell_of(h, L.R, L.Rs));
+  }
+  AMGC_TRY(make_views(h));
+  const int64_t n0 = h->L[0].rows();
+  (void)n0;
+  // zero the work vectors the timings read (values do not matter, finiteness does)
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = h->L[l];
+    AMGC_CUDA_TRY(cudaMemsetAsync(L.x.p, 0, L.x.bytes(), h->stream));
+    AMGC_CUDA_TRY(cudaMemsetAsync(L.b.p, 0, L.b.bytes(), h->stream));
+    AMGC_CUDA_TRY(cudaMemsetAsync(L.r.p, 0, L.r.bytes(), h->stream));
+    if (h->opts.precision == 32) {
+      AMGC_CUDA_TRY(cudaMemsetAsync(L.f.x.p, 0, L.f.x.bytes(), h->stream));
+      AMGC_CUDA_TRY(cudaMemsetAsync(L.f.b.p, 0, L.f.b.bytes(), h->stream));
+      AMGC_CUDA_TRY(cudaMemsetAsync(L.f.r.p, 0, L.f.r.bytes(), h->stream));
+    }
+  }
+  AMGC_TRY(tune_views<double>(h, h->v64, 0));
+  if (h->opts.precision == 32) AMGC_TRY(tune_views<float>(h, h->v32, 1));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return make_views(h);
 }
 
 // ------------------------------------------------------------------ dot products, lambda_max

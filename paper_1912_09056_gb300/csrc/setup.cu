@@ -1183,7 +1183,7 @@ __global__ void k_sell_fill(int nbr, int nslice, int bs, const int* __restrict__
   }
 }
 
-static int build_sell_of(amgc_hierarchy* h, const DBsr& A, Sell& S) {
+int build_sell_of(amgc_hierarchy* h, const DBsr& A, Sell& S) {
   cudaStream_t s = h->stream;
   const int ns = div_up(A.nbr, 32);
   const int bs = A.br * A.bc;

@@ -196,3 +196,24 @@ def test_fp32_cycle_matches_oracle_and_solves(case):
     assert it32 <= it64 + 3, (it32, it64)
     h64.close()
     h32.close()
+
+
+def test_autotuned_mappings_and_graph_replay_give_the_same_cycle():
+    """Row-mapping choices and CUDA-graph replay change scheduling, not arithmetic results beyond rounding."""
+    make, opts = CASES["small_tilted_partial_SA"]
+    prob = make()
+    h0 = amgc.setup(prob, **opts)
+    h1 = amgc.setup(prob, autotune=1, **opts)
+    rng = np.random.default_rng(5)
+    r = torch.from_numpy(rng.standard_normal(prob.n)).cuda()
+    z0, z1, z2 = torch.empty_like(r), torch.empty_like(r), torch.empty_like(r)
+    h0.vcycle(r, z0)            # graph replay
+    h0.profile(1)               # timing mode runs the kernels directly
+    h0.vcycle(r, z2)
+    h0.profile(0)
+    h1.vcycle(r, z1)
+    torch.cuda.synchronize()
+    assert torch.equal(z0, z2)
+    assert (torch.linalg.norm(z0 - z1) / torch.linalg.norm(z0)).item() <= 1e-13
+    h0.close()
+    h1.close()
