@@ -220,6 +220,22 @@ int amgc_grad_elements(int32_t ne, const int32_t* conn, const int32_t* shape, co
                        const int32_t* node_free, const double* adj, const double* x, const double* uD,
                        const uint8_t* lift_mask, const double* E, double* gE, double* gt, void* stream);
 
+/* amgc_grad_elements without any device allocation, for callers that cannot allocate when
+ * they need the gradients: code that owns all device memory up front (a framework's memory
+ * pool with a hard cap leaves no room for the library's own allocations), or a latency-bound
+ * loop that must stay out of the driver's allocator and its implicit synchronisation.  The
+ * paper has no counterpart; this is a property of the library.
+ * Same arguments and results as amgc_grad_elements.  Its scratch is one file-scope device
+ * array of 3 x 262144 doubles (6 MiB) that every GPU loading the library holds until the
+ * process exits: ne above 262144 is rejected with AMGC_EINVAL.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device current, so make
+ * that first call before any stream capture.  All calls share the array and each call
+ * overwrites the part it reads, so calls that overlap on the GPU (different streams, no
+ * ordering between them) race: order them. */
+int amgc_grad_elements_noalloc(int32_t ne, const int32_t* conn, const int32_t* shape, const double* Khat,
+                               const int32_t* node_free, const double* adj, const double* x, const double* uD,
+                               const uint8_t* lift_mask, const double* E, double* gE, double* gt, void* stream);
+
 int amgc_stats(const struct amgc_hierarchy* h, amgc_stats_t* out);
 
 /* Copies one internal array of level `level` to the host buffer dst (capacity `bytes`).

@@ -110,6 +110,8 @@ def load():
     lib.amgc_setup_batched.restype = C.c_int
     lib.amgc_solve_batched.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp]
     lib.amgc_solve_batched.restype = C.c_int
+    lib.amgc_grad_elements_noalloc.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.amgc_grad_elements_noalloc.restype = C.c_int
     lib.amgc_destroy.argtypes = [vp]
     lib.amgc_destroy.restype = None
     lib.amgc_strerror.argtypes = [C.c_int]
@@ -295,6 +297,16 @@ def grad_elements(conn, shape, Khat, node_free, adj, x, uD, E, gE, lift_mask=Non
     _check(lib.amgc_grad_elements(ne, _ptr(conn), _ptr(shape), _ptr(Khat), _ptr(node_free), _ptr(adj), _ptr(x),
                                   _ptr(uD), _ptr(lift_mask), _ptr(E), _ptr(gE), _ptr(gt), _stream_ptr(stream)),
            "amgc_grad_elements")
+    return gE, gt
+
+
+def grad_elements_noalloc(conn, shape, Khat, node_free, adj, x, uD, E, gE, lift_mask=None, gt=None, stream=None):
+    """amgc_grad_elements_noalloc: the element gradients with static device scratch (no allocation)."""
+    lib = load()
+    ne = int(conn.shape[0])
+    _check(lib.amgc_grad_elements_noalloc(ne, _ptr(conn), _ptr(shape), _ptr(Khat), _ptr(node_free), _ptr(adj),
+                                          _ptr(x), _ptr(uD), _ptr(lift_mask), _ptr(E), _ptr(gE), _ptr(gt),
+                                          _stream_ptr(stream)), "amgc_grad_elements_noalloc")
     return gE, gt
 
 
