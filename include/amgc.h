@@ -121,7 +121,9 @@ void amgc_default_options(amgc_options* opts);
  *   K           n x n nodal 3x3 BSR, Dirichlet nodes already eliminated; every row must hold
  *               its diagonal block.
  *   D_diag      n_s diagonal entries of the dual-mortar D (slave node j <-> multiplier node j).
- *   M           n_s x n_m scalar CSR mortar matrix (slave rows, master columns).
+ *   M           n_s x n_m scalar CSR mortar matrix (slave rows, master columns); n_s >= 1:
+ *               a system without a contact interface has no multiplier block and is refused
+ *               (AMGC_EINVAL); every instance of a batch needs at least one slave node too.
  *   slave_node  n_s   K block row of slave interface node j.
  *   master_node n_m   K block row of master interface node l.
  *   triad       n_s x 3 x 3, rows (n, tau_xi, tau_eta) of each slave node, orthonormal.

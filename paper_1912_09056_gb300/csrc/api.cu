@@ -176,11 +176,12 @@ int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const
   }
   *out = nullptr;
   if (!K || !M || !opts || !K->rowptr || !K->col || !K->val || !body_id || !nullspace || !M->rowptr ||
-      K->br != 3 || K->bc != 3 || K->n_brow != K->n_bcol || K->n_brow <= 0 || M->n_row < 0 || M->n_col < 0 ||
+      K->br != 3 || K->bc != 3 || K->n_brow != K->n_bcol || K->n_brow <= 0 || M->n_row < 1 || M->n_col < 0 ||
       (M->n_row > 0 && (!D_diag || !slave_node || !triad || !active)) || (M->n_col > 0 && !master_node) ||
       opts->levels_max < 1 || opts->smoother_sweeps < 0 || opts->jacobi_sweeps < 1 || opts->fgmres_restart < 1 ||
       opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 || !(opts->tol > 0.0) || (opts->precision != 64 && opts->precision != 32)) {
-    set_error("amgc_setup: invalid argument");
+    set_error(M && M->n_row < 1 ? "amgc_setup: no slave interface nodes (the system has no multiplier block)"
+                                : "amgc_setup: invalid argument");
     return AMGC_EINVAL;
   }
   amgc_hierarchy* h = new (std::nothrow) amgc_hierarchy();
@@ -211,9 +212,9 @@ int amgc_setup_batched(const amgc_bsr* K, const double* D_diag, const amgc_csr* 
   *out = nullptr;
   std::vector<int> np(node_ptr, node_ptr + n_inst + 1), lp(lm_ptr, lm_ptr + n_inst + 1);
   bool ok = np[0] == 0 && lp[0] == 0 && np[n_inst] == K->n_brow && lp[n_inst] == M->n_row;
-  for (int q = 0; q < n_inst && ok; ++q) ok = np[q + 1] > np[q] && lp[q + 1] >= lp[q];
+  for (int q = 0; q < n_inst && ok; ++q) ok = np[q + 1] > np[q] && lp[q + 1] > lp[q];
   if (!ok) {
-    set_error("amgc_setup_batched: node_ptr / lm_ptr must be ascending and cover K and M");
+    set_error("amgc_setup_batched: node_ptr / lm_ptr must be strictly ascending and cover K and M");
     return AMGC_EINVAL;
   }
   if (n_inst == 1)
