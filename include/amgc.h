@@ -89,6 +89,13 @@ typedef struct {
   int32_t autotune;          /* 1: time the row mappings of every level's K, P and R apply at
                                 setup and keep the fastest (warp per row, SELL with one or two
                                 threads per row), separately for the FP64 and FP32 cycle     */
+  int32_t schur_damping;     /* 0: the multiplier correction is damped by simple_alpha alone
+                                (Sec. 5.2).  1: per level (per instance when batched) it is
+                                damped by min(simple_alpha, (4/3) / rho), rho = spectral radius
+                                of S_bd^-1 S_hat estimated by 30 power steps, which keeps the
+                                block-diagonal Schur step a contraction where a slave mesh much
+                                finer than its master couples many slave nodes through one
+                                master node (rho >> 2)                                       */
 } amgc_options;
 
 typedef struct {
@@ -112,7 +119,8 @@ typedef struct {
 
 /* Fills the defaults: levels_max 10, coarse_max_rows 5000, SA, 1 sweep, 1 Jacobi sweep,
  * SIMPLE (diag K), FP64, restart 50, maxit 1000, seed 0x5EED, sa_omega 4/3, jacobi_omega
- * automatic, alpha 0.8, tol 1e-8 (Sec. 6.2 settings, Eq. ch7_linearstoppingcriterion), autotune 0. */
+ * automatic, alpha 0.8, tol 1e-8 (Sec. 6.2 settings, Eq. ch7_linearstoppingcriterion), autotune 0,
+ * schur_damping 0. */
 void amgc_default_options(amgc_options* opts);
 
 /* Builds the hierarchy (Sec. 4: segregated aggregation with Algorithm 1, transfers of
@@ -264,8 +272,11 @@ enum {
   AMGC_EXPORT_PL_W = 18,      /* double[lm_nodes]    multiplier tentative-transfer weights     */
   AMGC_EXPORT_ATINV = 19,     /* double[dofs]        A~^-1                                     */
   AMGC_EXPORT_OMEGA = 20,     /* double[2]           (lambda_max, omega_J)                     */
-  AMGC_EXPORT_COARSE_INV = 21 /* double[rows*rows]   inverse of the coarsest saddle matrix
+  AMGC_EXPORT_COARSE_INV = 21, /* double[rows*rows]  inverse of the coarsest saddle matrix
                                  (batched: the instances' inverses one after the other)   */
+  AMGC_EXPORT_SCHUR_RHO = 22  /* double[instances]  rho of S_bd^-1 S_hat (schur_damping = 1;
+                                 empty otherwise); SINV then holds the blocks already scaled
+                                 by min(alpha, (4/3)/rho) / alpha                          */
 };
 int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what, void* dst,
                     int64_t bytes);

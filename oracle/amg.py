@@ -8,7 +8,8 @@ Setup (Sec. 3.1.2, Sec. 4, Algorithm 1): on every level but the coarsest,
      multiplier node L only to the displacement aggregate it was derived from);
   3. tentative transfers, optionally smoothed displacement prolongator (SA), R = P^T;
   4. segregated Galerkin products for K, B1, B2, Z;
-  5. CheapSIMPLE data: omega_J, D_K^{-1}, A_tilde^{-1} and the inverted nodal blocks of S_hat.
+  5. CheapSIMPLE data: omega_J, D_K^{-1}, A_tilde^{-1} and the inverted nodal blocks of S_hat
+     (optionally the Schur-step damping min(alpha, (4/3)/rho(S_bd^{-1} S_hat)), Sec. 5.2).
 Coarsening stops at ``levels_max`` levels or once the saddle system has fewer than
 ``coarse_max_rows`` rows (Sec. 6.2 setup); the coarsest level is merged into one dense
 matrix [K_c B1_c; B2_c -Z_c] and solved by LU with partial pivoting (Sec. 6.2 setup).
@@ -27,7 +28,7 @@ import scipy.sparse as sp
 
 from .aggregate import aggregate_nodes, aggregation_graph, lagmult_aggregation
 from .saddle import BlockMat, block_diag3, build_saddle
-from .smoother import atilde_diag, cheap_simple_sweep, schur_blocks
+from .smoother import atilde_diag, cheap_simple_sweep, schur_blocks, schur_rho
 from .transfer import galerkin, lambda_max, smoothed_prolongator, tentative_lagmult, tentative_prolongator, transpose
 
 
@@ -43,6 +44,7 @@ class Options:
     simple_alpha: float = 0.8
     simplec: int = 0             # 0: A_tilde = diag(K), 1: absolute row sums (SIMPLEC)
     seed: int = 0x5EED
+    schur_damping: int = 0       # 1: alpha -> min(alpha, (4/3)/rho(S_bd^-1 S_hat)) per level
     fgmres_restart: int = 50
     fgmres_maxit: int = 1000
     tol: float = 1e-8
@@ -76,6 +78,8 @@ class Level:
     at_inv: Optional[np.ndarray] = None
     S_blocks: Optional[np.ndarray] = None
     S_inv: Optional[np.ndarray] = None
+    alpha: float = 0.0           # damping of the multiplier correction on this level
+    schur_rho: float = 0.0
     # coarsest
     lu: Optional[tuple] = None
     extra: dict = field(default_factory=dict)
@@ -141,7 +145,7 @@ class Hierarchy:
             return np.einsum("lij,lj->li", L.S_inv, r.reshape(-1, 3)).ravel()
         for _ in range(o.smoother_sweeps):
             u, lam = cheap_simple_sweep(L.K.val, L.B1.val, L.B2.val, Zf, u, lam, f, g, L.dinv,
-                                        L.omega_j, o.jacobi_sweeps, L.at_inv, s_inv, o.simple_alpha)
+                                        L.omega_j, o.jacobi_sweeps, L.at_inv, s_inv, L.alpha)
         return u, lam
 
     def residual(self, L: Level, u, lam, f, g):
@@ -208,6 +212,10 @@ def setup(prob, opts: Optional[Options] = None) -> Hierarchy:
         L.at_inv = 1.0 / atilde_diag(L.K.val, bool(o.simplec))
         L.S_blocks = schur_blocks(L.B1.val, L.B2.val, L.Z, L.at_inv)
         L.S_inv = np.linalg.inv(L.S_blocks)
+        L.alpha = o.simple_alpha
+        if o.schur_damping and L.nl > 0:
+            L.schur_rho = schur_rho(L.B1.val, L.B2.val, L.Z, L.at_inv, L.S_inv)
+            L.alpha = min(o.simple_alpha, (4.0 / 3.0) / L.schur_rho)
     Lc = levels[-1]
     Lc.lu = sla.lu_factor(Lc.A().toarray())
     return Hierarchy(levels, o)

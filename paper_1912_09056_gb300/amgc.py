@@ -23,7 +23,7 @@ AMGC_BREAKDOWN, AMGC_TIMEOUT, AMGC_ECUDA, AMGC_ENOMEM = -4, -5, -6, -7
 
 EXPORT = dict(agg=1, lagg=2, p_rowptr=3, p_col=4, p_val=5, k_rowptr=6, k_col=7, k_val=8, b1_rowptr=9,
               b1_col=10, b1_val=11, b2_rowptr=12, b2_col=13, b2_val=14, z=15, sinv=16, nullspace=17,
-              pl_w=18, atinv=19, omega=20, coarse_inv=21)
+              pl_w=18, atinv=19, omega=20, coarse_inv=21, schur_rho=22)
 _EXPORT_DTYPE = {k: (np.int32 if k in ("agg", "lagg") or k.endswith(("rowptr", "col")) else np.float64)
                  for k in EXPORT}
 
@@ -43,7 +43,8 @@ class Options(C.Structure):
                 ("smoother_sweeps", C.c_int32), ("jacobi_sweeps", C.c_int32), ("simplec", C.c_int32),
                 ("precision", C.c_int32), ("fgmres_restart", C.c_int32), ("fgmres_maxit", C.c_int32),
                 ("seed", C.c_uint32), ("sa_omega", C.c_double), ("jacobi_omega", C.c_double),
-                ("simple_alpha", C.c_double), ("tol", C.c_double), ("autotune", C.c_int32)]
+                ("simple_alpha", C.c_double), ("tol", C.c_double), ("autotune", C.c_int32),
+                ("schur_damping", C.c_int32)]
 
 
 class Stats(C.Structure):

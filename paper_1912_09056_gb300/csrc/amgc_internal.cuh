@@ -196,6 +196,7 @@ struct Level {
   DBuf<double> kdiag, dinv, atinv;  // nu: pointwise diagonal of K, its inverse, A~^-1
   DBuf<double> jdinv;               // nu: omega_J D^-1 (omega_J per instance when batched)
   std::vector<double> inst_lam_max; // per instance (batched hierarchies)
+  std::vector<double> schur_rho;    // per instance: rho(S_bd^-1 S_hat) when schur_damping = 1
   DBuf<int> key_base;               // batched: first node of the node's instance (MIS-2 keys)
   DBuf<double> Sinv;         // nl*9
   DBuf<int> b1_rows;         // displacement nodes with B1 entries
@@ -310,6 +311,7 @@ int prof_flush(amgc_hierarchy* h);
 int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
 int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out);
 int lambda_max_instances(amgc_hierarchy* h, Level& L, std::vector<double>& lam);
+int schur_damping_setup(amgc_hierarchy* h, Level& L);
 int dot(amgc_hierarchy* h, int64_t n, const double* a, const double* b, const double* wgt, double* out_dev);
 // V-cycle (cycle.cu)
 int make_views(amgc_hierarchy* h);

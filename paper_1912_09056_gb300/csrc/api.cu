@@ -165,6 +165,7 @@ void amgc_default_options(amgc_options* o) {
   o->simple_alpha = 0.8;
   o->tol = 1e-8;
   o->autotune = 0;
+  o->schur_damping = 0;
 }
 
 int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const int32_t* slave_node,
@@ -179,7 +180,8 @@ int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const
       K->br != 3 || K->bc != 3 || K->n_brow != K->n_bcol || K->n_brow <= 0 || M->n_row < 1 || M->n_col < 0 ||
       (M->n_row > 0 && (!D_diag || !slave_node || !triad || !active)) || (M->n_col > 0 && !master_node) ||
       opts->levels_max < 1 || opts->smoother_sweeps < 0 || opts->jacobi_sweeps < 1 || opts->fgmres_restart < 1 ||
-      opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 || !(opts->tol > 0.0) || (opts->precision != 64 && opts->precision != 32)) {
+      opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 || !(opts->tol > 0.0) || (opts->precision != 64 && opts->precision != 32) ||
+      (opts->schur_damping != 0 && opts->schur_damping != 1)) {
     set_error(M && M->n_row < 1 ? "amgc_setup: no slave interface nodes (the system has no multiplier block)"
                                 : "amgc_setup: invalid argument");
     return AMGC_EINVAL;
@@ -223,7 +225,8 @@ int amgc_setup_batched(const amgc_bsr* K, const double* D_diag, const amgc_csr* 
       K->n_brow != K->n_bcol || (M->n_row > 0 && (!D_diag || !slave_node || !triad || !active)) ||
       (M->n_col > 0 && !master_node) || opts->levels_max < 1 || opts->smoother_sweeps < 0 ||
       opts->jacobi_sweeps < 1 || opts->fgmres_restart < 1 || opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 ||
-      !(opts->tol > 0.0) || (opts->precision != 64 && opts->precision != 32)) {
+      !(opts->tol > 0.0) || (opts->precision != 64 && opts->precision != 32) ||
+      (opts->schur_damping != 0 && opts->schur_damping != 1)) {
     set_error("amgc_setup_batched: invalid argument");
     return AMGC_EINVAL;
   }
@@ -425,6 +428,7 @@ int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what,
     case AMGC_EXPORT_ATINV: src = L.atinv.p; nb = L.atinv.p ? (int64_t)L.nu() * 8 : 0; break;
     case AMGC_EXPORT_OMEGA: src = scal; nb = 16; break;
     case AMGC_EXPORT_COARSE_INV: src = L.Ainv.p; nb = L.Ainv.p ? (int64_t)L.Ainv.n * 8 : 0; break;
+    case AMGC_EXPORT_SCHUR_RHO: src = L.schur_rho.data(); nb = (int64_t)L.schur_rho.size() * 8; break;
     default: set_error("amgc_export: unknown array"); return AMGC_EINVAL;
   }
   if (!dst || nb == 0) return nb;

@@ -1018,6 +1018,129 @@ int lambda_max_instances(amgc_hierarchy* h, Level& L, std::vector<double>& lam) 
   return AMGC_OK;
 }
 
+// ---------------------------------------------------------------- Schur-step damping
+// One step of the power iteration on S_bd^-1 S_hat, S_hat = Z + B2 A~^-1 B1 (the operator whose
+// block-diagonal approximation the CheapSIMPLE corrector inverts, Sec. 5.2).
+// First t_i = A~^-1_i (B1 x)_i on the displacement rows that hold B1 blocks.
+template <int BU>
+__global__ void k_schur_b1(int nrows, const int* __restrict__ rows, const int* __restrict__ rp,
+                           const int* __restrict__ col, const double* __restrict__ val,
+                           const double* __restrict__ atinv, const double* __restrict__ x, double* __restrict__ t) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nrows) return;
+  const int i = rows[k];
+  double acc[BU];
+#pragma unroll
+  for (int m = 0; m < BU; ++m) acc[m] = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const int l = col[e];
+    const double* b = val + (int64_t)e * BU * 3;
+    const double x0 = x[3 * (int64_t)l], x1 = x[3 * (int64_t)l + 1], x2 = x[3 * (int64_t)l + 2];
+#pragma unroll
+    for (int m = 0; m < BU; ++m) acc[m] = fma(b[m * 3], x0, fma(b[m * 3 + 1], x1, fma(b[m * 3 + 2], x2, acc[m])));
+  }
+#pragma unroll
+  for (int m = 0; m < BU; ++m) t[(int64_t)i * BU + m] = atinv[(int64_t)i * BU + m] * acc[m];
+}
+// then y_l = S_bd,l^-1 (Z_l x_l + sum_i B2_li t_i) per multiplier node l
+template <int BU>
+__global__ void k_schur_apply(int nl, const int* __restrict__ rp, const int* __restrict__ col,
+                              const double* __restrict__ val, const double* __restrict__ t, const double* __restrict__ Z,
+                              const double* __restrict__ Sinv, const double* __restrict__ x, double* __restrict__ y) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const double* z = Z + (int64_t)l * 9;
+  const double x0 = x[3 * (int64_t)l], x1 = x[3 * (int64_t)l + 1], x2 = x[3 * (int64_t)l + 2];
+  double r[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) r[a] = fma(z[a * 3], x0, fma(z[a * 3 + 1], x1, z[a * 3 + 2] * x2));
+  for (int e = rp[l]; e < rp[l + 1]; ++e) {
+    const int i = col[e];
+    const double* b = val + (int64_t)e * 3 * BU;
+#pragma unroll
+    for (int m = 0; m < BU; ++m) {
+      const double tv = t[(int64_t)i * BU + m];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) r[a] = fma(b[a * BU + m], tv, r[a]);
+    }
+  }
+  const double* si = Sinv + (int64_t)l * 9;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) y[3 * (int64_t)l + a] = fma(si[a * 3], r[0], fma(si[a * 3 + 1], r[1], si[a * 3 + 2] * r[2]));
+}
+// Sinv_l *= f[l]
+__global__ void k_scale_sinv(int nl, const double* __restrict__ f, double* __restrict__ Sinv) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nl * 9) return;
+  Sinv[t] *= f[t / 9];
+}
+
+// rho_q of S_bd^-1 S_hat per instance q: 30 power steps from the normalised ones vector (per
+// instance), rho = the norm of the last product.  The multiplier correction of instance q is then
+// damped by alpha_q = min(alpha, (4/3)/rho_q), applied by scaling its inverted Schur blocks by
+// alpha_q / alpha (the sweep kernels keep multiplying by alpha).
+int schur_damping_setup(amgc_hierarchy* h, Level& L) {
+  cudaStream_t s = h->stream;
+  const int ni = h->n_inst;
+  const int nl = L.nl;
+  const int64_t n = 3 * (int64_t)nl;
+  const int th = 256;
+  std::vector<int> lp = ni > 1 ? L.lptr : std::vector<int>{0, nl};
+  DBuf<double> xv, yv, tv, sc;
+  DBuf<int> dptr;
+  AMGC_TRY(xv.alloc(n));
+  AMGC_TRY(yv.alloc(n));
+  AMGC_TRY(tv.alloc((size_t)std::max(L.nu(), 1)));
+  AMGC_TRY(sc.alloc(ni));
+  AMGC_TRY(dptr.alloc(ni + 1));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(dptr.p, lp.data(), (ni + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaMemsetAsync(tv.p, 0, (size_t)std::max(L.nu(), 1) * sizeof(double), s));
+  AMGC_LAUNCH(k_fill<<<div_up(n, th), th, 0, s>>>(n, 1.0, xv.p));
+  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, 3, dptr.p, xv.p, xv.p, nullptr, sc.p));
+  const dim3 gs(16, ni);
+  AMGC_LAUNCH(k_segnormalize<<<gs, th, 0, s>>>(ni, 3, dptr.p, sc.p, xv.p, xv.p));
+  for (int it = 0; it < 30; ++it) {
+    if (L.n_b1_rows > 0) {
+      if (L.bu == 3)
+        AMGC_LAUNCH(k_schur_b1<3><<<div_up(L.n_b1_rows, 128), 128, 0, s>>>(L.n_b1_rows, L.b1_rows.p, L.B1.rowptr.p,
+                                                                          L.B1.col.p, L.B1.val.p, L.atinv.p, xv.p, tv.p));
+      else
+        AMGC_LAUNCH(k_schur_b1<6><<<div_up(L.n_b1_rows, 128), 128, 0, s>>>(L.n_b1_rows, L.b1_rows.p, L.B1.rowptr.p,
+                                                                          L.B1.col.p, L.B1.val.p, L.atinv.p, xv.p, tv.p));
+    }
+    if (L.bu == 3)
+      AMGC_LAUNCH(k_schur_apply<3><<<div_up(nl, 128), 128, 0, s>>>(nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, tv.p,
+                                                                   L.Z.p, L.Sinv.p, xv.p, yv.p));
+    else
+      AMGC_LAUNCH(k_schur_apply<6><<<div_up(nl, 128), 128, 0, s>>>(nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, tv.p,
+                                                                   L.Z.p, L.Sinv.p, xv.p, yv.p));
+    AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, 3, dptr.p, yv.p, yv.p, nullptr, sc.p));
+    if (it < 29) AMGC_LAUNCH(k_segnormalize<<<gs, th, 0, s>>>(ni, 3, dptr.p, sc.p, yv.p, xv.p));
+  }
+  AMGC_CUDA_TRY(cudaGetLastError());
+  std::vector<double> hs(ni);
+  AMGC_CUDA_TRY(cudaMemcpyAsync(hs.data(), sc.p, ni * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  const double alpha = h->opts.simple_alpha;
+  L.schur_rho.assign(ni, 0.0);
+  std::vector<double> f(nl, 1.0);
+  for (int q = 0; q < ni; ++q) {
+    const double rho = std::sqrt(hs[q]);
+    if (!(rho > 0.0) || !std::isfinite(rho)) {
+      set_error("schur_damping: power iteration on S_bd^-1 S_hat broke down");
+      return AMGC_ESINGULAR;
+    }
+    L.schur_rho[q] = rho;
+    const double fq = alpha > 0.0 ? std::min(alpha, (4.0 / 3.0) / rho) / alpha : 1.0;
+    for (int l = lp[q]; l < lp[q + 1]; ++l) f[l] = fq;
+  }
+  AMGC_CUDA_TRY(cudaMemcpyAsync(yv.p, f.data(), nl * sizeof(double), cudaMemcpyHostToDevice, s));
+  AMGC_LAUNCH(k_scale_sinv<<<div_up((int64_t)nl * 9, th), th, 0, s>>>(nl, yv.p, L.Sinv.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMGC_OK;
+}
+
 // lambda_max(D^{-1} K): 20 power steps from the normalised ones vector, then the generalised
 // Rayleigh quotient (x^T K x)/(x^T D x) with D the pointwise diagonal of K (kdiag).
 int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out) {

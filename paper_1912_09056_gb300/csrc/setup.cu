@@ -1147,6 +1147,7 @@ int smoother_setup(amgc_hierarchy* h, int l) {
     AMGC_CUDA_TRY(cudaGetLastError());
     AMGC_CUDA_TRY(cudaStreamSynchronize(s));
   }
+  if (h->opts.schur_damping && L.nl > 0) AMGC_TRY(schur_damping_setup(h, L));
   AMGC_TRY(alloc_work(L));
   return AMGC_OK;
 }

@@ -18,11 +18,17 @@ def _split(v, npt, lpt, n_u):
             for q in range(len(npt) - 1)]
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_batch_equals_instances(precision):
+@pytest.mark.parametrize("precision, schur_damping", [(64, 0), (32, 0), (64, 1), (32, 1)])
+def test_batch_equals_instances(precision, schur_damping):
     cat, npt, lpt, rhs, probs, _ = batched_workload(5, seed=9, lo=5, hi=9)
-    hb = amgc.setup(cat, node_ptr=npt, lm_ptr=lpt, precision=precision, **OPTS)
-    hs = [amgc.setup(p, precision=precision, **OPTS) for p in probs]
+    hb = amgc.setup(cat, node_ptr=npt, lm_ptr=lpt, precision=precision, schur_damping=schur_damping, **OPTS)
+    hs = [amgc.setup(p, precision=precision, schur_damping=schur_damping, **OPTS) for p in probs]
+    if schur_damping:
+        # per-instance Schur radii equal the instances' own, level by level
+        for l in range(hb.stats()["n_levels"] - 1):
+            rb = hb.export(l, "schur_rho")
+            ri = np.array([h.export(l, "schur_rho")[0] for h in hs])
+            assert rb.size == len(probs) and np.allclose(rb, ri, rtol=1e-10, atol=0.0), (l, rb, ri)
     # aggregates and multiplier aggregates: identical per instance (bit for bit, up to the offset)
     agg_b, lagg_b = hb.export(0, "agg"), hb.export(0, "lagg")
     for q, h in enumerate(hs):

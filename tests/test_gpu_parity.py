@@ -59,7 +59,15 @@ def compare_hierarchy(h, ref):
             assert abs(lam_max - L.lam_max) <= 1e-12 * L.lam_max
             assert abs(omega - L.omega_j) <= 1e-12 * L.omega_j
             assert rel(h.export(l, "atinv"), L.at_inv) <= RTOL
-            assert rel(h.export(l, "sinv").reshape(-1, 3, 3), L.S_inv) <= RTOL
+            # with the Schur-step damping the library folds alpha_l / alpha into the inverted blocks
+            a = ref.opts.simple_alpha
+            fac = L.alpha / a if a > 0 else 1.0
+            assert rel(h.export(l, "sinv").reshape(-1, 3, 3), L.S_inv * fac) <= RTOL
+            if ref.opts.schur_damping and L.nl > 0:
+                rho = h.export(l, "schur_rho")
+                assert rho.size == 1 and abs(rho[0] - L.schur_rho) <= 1e-10 * L.schur_rho
+            else:
+                assert h.export(l, "schur_rho").size == 0
             w = np.asarray(L.Pl.val.sum(axis=1)).ravel()[0::3]
             assert rel(h.export(l, "pl_w"), w) <= RTOL
             Bn = h.export(l + 1, "nullspace").reshape(-1, 6)
@@ -98,6 +106,11 @@ CASES = {
     "small_simplec_2sweeps": (
         lambda: two_block_problem(master_n=(9, 9, 9), slave_n=(8, 8, 8), seed=5, active_fraction=0.5),
         dict(levels_max=3, coarse_max_rows=0, transfer=1, simplec=1, smoother_sweeps=2, jacobi_sweeps=2)),
+    # slave mesh 2.3x finer than the master: rho(S_bd^-1 S_hat) ~ 10, Schur-step damping on
+    "slave_finer_schur_damped": (
+        lambda: two_block_problem(master_n=(6, 6, 4), slave_n=(14, 14, 6), E_slave=40.0, tilt_deg=6.0, seed=13,
+                                  active_fraction=0.8),
+        dict(levels_max=3, coarse_max_rows=0, transfer=1, schur_damping=1)),
 }
 
 
@@ -175,7 +188,8 @@ def test_rejects_bad_input():
 FP32_CYCLE_RTOL = 1e-4
 
 
-@pytest.mark.parametrize("case", ["tiny_SA_3lvl", "small_tilted_partial_SA", "small_simplec_2sweeps"])
+@pytest.mark.parametrize("case", ["tiny_SA_3lvl", "small_tilted_partial_SA", "small_simplec_2sweeps",
+                                  "slave_finer_schur_damped"])
 def test_fp32_cycle_matches_oracle_and_solves(case):
     make, opts = CASES[case]
     prob = make()

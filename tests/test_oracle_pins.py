@@ -9,7 +9,7 @@ from oracle.aggregate import (ROOT, aggregate_nodes, aggregation_graph, fmix32, 
 from oracle.amg import Options, d_rows, setup
 from oracle.krylov import fgmres
 from oracle.saddle import block_diag3, build_saddle, pattern
-from oracle.smoother import atilde_diag, cheap_simple_sweep
+from oracle.smoother import atilde_diag, cheap_simple_sweep, schur_blocks, schur_rho
 from oracle.transfer import galerkin, lambda_max, smoothed_prolongator, tentative_lagmult, tentative_prolongator
 
 
@@ -265,3 +265,51 @@ def test_amg_fgmres_solves_tiny_contact_problem(cfg0):
     lam = x[cfg0.n_u:].reshape(-1, 3)
     ln = np.einsum("ji,ji->j", lam, cfg0.triad[:, 0])
     assert ln.mean() > 0
+
+
+def _schur_operator(prob):
+    S = build_saddle(prob)
+    K, B1, B2 = S.K.val.tocsr(), S.B1.val.tocsr(), S.B2.val.tocsr()
+    at = 1.0 / atilde_diag(K, False)
+    S_inv = np.linalg.inv(schur_blocks(B1, B2, S.Z, at))
+    Sh = (block_diag3(S.Z) + B2 @ sp.diags(at) @ B1).toarray()
+    return B1, B2, S.Z, at, S_inv, block_diag3(S_inv).toarray() @ Sh
+
+
+@pytest.mark.parametrize("master_n, slave_n, E_s", [((3, 3, 2), (9, 9, 2), 50.0), ((2, 2, 2), (8, 8, 2), 80.0)])
+def test_schur_damping_makes_the_multiplier_step_a_contraction(master_n, slave_n, E_s):
+    """Slave mesh 3-4x finer than the master: rho(S_bd^-1 S_hat) >> 2, the undamped step
+    (alpha = 0.8) amplifies, the damped one min(alpha, (4/3)/rho) contracts (dense eigenvalues)."""
+    from paper_1912_09056_gb300.problem import two_block_problem
+    p = two_block_problem(master_n=master_n, slave_n=slave_n, E_slave=E_s, tilt_deg=4.0, seed=3, active_fraction=0.8)
+    B1, B2, Z, at, S_inv, M = _schur_operator(p)
+    ev = np.linalg.eigvals(M)
+    rho_true = np.abs(ev).max()
+    rho = schur_rho(B1, B2, Z, at, S_inv)
+    assert abs(rho - rho_true) <= 1e-3 * rho_true
+    assert rho_true > 10.0
+    assert np.abs(1.0 - 0.8 * ev).max() > 5.0
+    a = min(0.8, (4.0 / 3.0) / rho)
+    assert np.abs(1.0 - a * ev).max() < 1.0
+    # the hierarchy applies it per level
+    h = setup(p, Options(levels_max=2, coarse_max_rows=0, schur_damping=1))
+    assert h.levels[0].alpha == pytest.approx(a, rel=1e-12)
+    h0 = setup(p, Options(levels_max=2, coarse_max_rows=0))
+    assert h0.levels[0].alpha == 0.8
+
+
+def test_schur_rho_is_one_without_active_nodes_and_keeps_alpha_on_matched_meshes():
+    from paper_1912_09056_gb300.problem import two_block_problem
+    p = two_block_problem(master_n=(4, 4, 2), slave_n=(3, 3, 2), seed=1)
+    p.active = np.zeros_like(p.active)        # S_hat = Z = -I: S_bd^-1 S_hat = I
+    B1, B2, Z, at, S_inv, M = _schur_operator(p)
+    assert schur_rho(B1, B2, Z, at, S_inv) == pytest.approx(1.0, abs=1e-14)
+    # slave coarser than the master: rho < 5/3, so min(0.8, (4/3)/rho) = 0.8 (the paper's alpha)
+    p = two_block_problem(master_n=(6, 6, 2), slave_n=(5, 5, 2), E_slave=10.0, tilt_deg=4.0, seed=3,
+                          active_fraction=0.8)
+    B1, B2, Z, at, S_inv, M = _schur_operator(p)
+    rho = schur_rho(B1, B2, Z, at, S_inv)
+    assert abs(rho - np.abs(np.linalg.eigvals(M)).max()) <= 1e-3 * rho
+    assert rho < 5.0 / 3.0
+    h = setup(p, Options(levels_max=2, coarse_max_rows=0, schur_damping=1))
+    assert h.levels[0].alpha == 0.8
