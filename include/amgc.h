@@ -300,6 +300,13 @@ const char* amgc_last_error(void);
 /* Number of CUDA kernels this library has launched in the calling process so far. */
 int64_t amgc_launch_count(void);
 
+/* Device memory of the library comes from a stream-ordered memory pool per device: buffers are
+ * allocated and freed in order on the stream of the call (no device synchronisation on free),
+ * and freed memory stays in the pool for later calls.  amgc_trim_memory waits for the current
+ * device to finish its work and returns the pool's unused memory to the driver.  (Library
+ * mechanics; the paper has no counterpart.)  Errors: AMGC_ECUDA. */
+int amgc_trim_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

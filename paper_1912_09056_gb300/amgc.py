@@ -121,6 +121,8 @@ def load():
     lib.amgc_last_error.restype = C.c_char_p
     lib.amgc_launch_count.argtypes = []
     lib.amgc_launch_count.restype = C.c_int64
+    lib.amgc_trim_memory.argtypes = []
+    lib.amgc_trim_memory.restype = C.c_int
     _lib = lib
     return lib
 
@@ -135,6 +137,11 @@ def header_symbols(path: str = HEADER):
 def launch_count() -> int:
     """Kernels launched by libamgc in this process so far."""
     return int(load().amgc_launch_count())
+
+
+def trim_memory():
+    """Returns the unused device memory of the library's pool on the current device (amgc_trim_memory)."""
+    _check(load().amgc_trim_memory(), "amgc_trim_memory")
 
 
 def default_options(**kw) -> Options:

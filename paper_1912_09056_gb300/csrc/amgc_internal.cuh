@@ -45,7 +45,19 @@ enum : int {
 };
 
 // ------------------------------------------------------------------ device memory
-// Owning device buffer (cudaMalloc/cudaFree); the hierarchy keeps these alive.
+// Device buffers come from a stream-ordered memory pool of the current device (created on first
+// use; freed memory stays in the pool for reuse until amgc_trim_memory).  Allocations and frees
+// are ordered on the stream of the entry point in progress (StreamScope), so releasing a
+// temporary never synchronises the device.
+struct StreamScope {
+  cudaStream_t prev;
+  explicit StreamScope(cudaStream_t s);
+  ~StreamScope();
+};
+int pool_alloc(void** p, size_t bytes);
+void pool_free(void* p);
+
+// Owning device buffer; the hierarchy keeps these alive.
 template <class T>
 struct DBuf {
   T* p = nullptr;
@@ -60,7 +72,7 @@ struct DBuf {
   }
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) pool_free(p);
     p = nullptr;
     n = 0;
   }
@@ -68,13 +80,13 @@ struct DBuf {
     release();
     n = count;
     if (count == 0) return AMGC_OK;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-    if (e != cudaSuccess) {
-      p = nullptr;
+    void* q = nullptr;
+    const int st = pool_alloc(&q, count * sizeof(T));
+    if (st != AMGC_OK) {
       n = 0;
-      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-      return AMGC_ENOMEM;
+      return st;
     }
+    p = static_cast<T*>(q);
     return AMGC_OK;
   }
   size_t bytes() const { return n * sizeof(T); }

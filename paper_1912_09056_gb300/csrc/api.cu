@@ -4,11 +4,65 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <mutex>
 
 namespace amgc {
 
 static thread_local std::string g_last_error;
 std::atomic<long long> g_launches{0};
+
+// ---- stream-ordered device memory
+static thread_local cudaStream_t g_alloc_stream = nullptr;
+StreamScope::StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+StreamScope::~StreamScope() { g_alloc_stream = prev; }
+
+constexpr int kMaxPoolDevices = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+// The library's memory pool on the current device (created on first use, nothing released to
+// the driver until amgc_trim_memory); nullptr with the error set if it cannot be had.
+static cudaMemPool_t device_pool() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxPoolDevices) {
+    set_error("memory pool: no usable current device");
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaMemPoolCreate: ") + cudaGetErrorString(e));
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
+int pool_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  cudaMemPool_t pool = device_pool();
+  if (!pool) return AMGC_ECUDA;
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, g_alloc_stream);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error(std::string("device allocation of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    return AMGC_ENOMEM;
+  }
+  return AMGC_OK;
+}
+
+void pool_free(void* p) { cudaFreeAsync(p, g_alloc_stream); }
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 // Largest coarsest system solved with the dense explicit inverse.
@@ -190,9 +244,14 @@ int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const
   if (!h) return AMGC_ENOMEM;
   h->opts = *opts;
   h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
   h->n_inst = 1;
   std::vector<int> np = {0, K->n_brow}, lp = {0, M->n_row};
   int st = build(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace, np, lp);
+  if (st == AMGC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    set_error("setup: stream synchronisation failed");
+    st = AMGC_ECUDA;
+  }
   if (st != AMGC_OK) {
     cudaStreamSynchronize(h->stream);
     amgc_destroy(h);
@@ -234,8 +293,13 @@ int amgc_setup_batched(const amgc_bsr* K, const double* D_diag, const amgc_csr* 
   if (!h) return AMGC_ENOMEM;
   h->opts = *opts;
   h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
   h->n_inst = n_inst;
   int st = build(h, K, D_diag, M, slave_node, master_node, triad, active, body_id, nullspace, np, lp);
+  if (st == AMGC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    set_error("setup: stream synchronisation failed");
+    st = AMGC_ECUDA;
+  }
   if (st != AMGC_OK) {
     cudaStreamSynchronize(h->stream);
     amgc_destroy(h);
@@ -252,6 +316,7 @@ int amgc_solve_batched(struct amgc_hierarchy* h, int32_t nrhs, const double* rhs
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
   return fgmres_batched(h, nrhs, rhs, x, iters, relres);
 }
 
@@ -261,6 +326,7 @@ int amgc_vcycle(struct amgc_hierarchy* h, const double* r, double* z, void* stre
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
   return precond_apply(h, r, z);
 }
 
@@ -270,6 +336,7 @@ int amgc_apply(struct amgc_hierarchy* h, const double* x, double* y, void* strea
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
   return saddle_apply(h, 0, x, y);
 }
 
@@ -279,6 +346,7 @@ int amgc_solve(struct amgc_hierarchy* h, const double* rhs, double* x, int32_t* 
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
   int it = 0;
   double rr = 0.0;
   int st = fgmres(h, rhs, x, 0.0, &it, &rr);
@@ -294,6 +362,7 @@ int amgc_solve_host(struct amgc_hierarchy* h, const double* rhs_host, double* x_
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
   const size_t n = (size_t)h->L[0].rows();
   DBuf<double> b, x;
   AMGC_TRY(b.alloc(n));
@@ -324,6 +393,7 @@ static int enter_transposed(amgc_hierarchy* h, void* stream, const char* where) 
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
   if (!h->L[0].has_transposed) AMGC_TRY(transposed_setup(h));
   h->transposed = true;
   return AMGC_OK;
@@ -374,6 +444,7 @@ int amgc_grad_scatter(struct amgc_hierarchy* h, const double* adj, const double*
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
   return grad_scatter(h, adj, x, gK, gB1, gB2);
 }
 
@@ -385,6 +456,7 @@ int amgc_grad_elements(int32_t ne, const int32_t* conn, const int32_t* shape, co
     set_error("amgc_grad_elements: invalid argument");
     return AMGC_EINVAL;
   }
+  StreamScope scope_((cudaStream_t)stream);
   return grad_elements(ne, conn, shape, Khat, node_free, adj, x, uD, lift_mask, E, gE, gt, (cudaStream_t)stream);
 }
 
@@ -471,6 +543,7 @@ int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launc
 
 void amgc_destroy(struct amgc_hierarchy* h) {
   if (!h) return;
+  StreamScope scope_(h->stream);
   cudaStreamSynchronize(h->stream);
   for (auto& e : h->prof_ev) cudaEventDestroy(e);
   for (auto& g : h->cycle_graph)
@@ -497,5 +570,13 @@ const char* amgc_strerror(int code) {
 const char* amgc_last_error(void) { return g_last_error.c_str(); }
 
 int64_t amgc_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+int amgc_trim_memory(void) {
+  cudaMemPool_t pool = device_pool();
+  if (!pool) return AMGC_ECUDA;
+  AMGC_CUDA_TRY(cudaDeviceSynchronize());
+  AMGC_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
+  return AMGC_OK;
+}
 
 }  // extern "C"

@@ -188,10 +188,12 @@ static int batch_tables(amgc_hierarchy* h) {
   AMGC_TRY(h->b_chunk_row1.alloc(nc));
   AMGC_TRY(h->b_chunk_ptr.alloc(ni + 1));
   AMGC_TRY(h->b_row_inst.alloc(n));
-  AMGC_CUDA_TRY(cudaMemcpy(h->b_chunk_row0.p, r0.data(), nc * sizeof(int), cudaMemcpyHostToDevice));
-  AMGC_CUDA_TRY(cudaMemcpy(h->b_chunk_row1.p, r1.data(), nc * sizeof(int), cudaMemcpyHostToDevice));
-  AMGC_CUDA_TRY(cudaMemcpy(h->b_chunk_ptr.p, cptr.data(), (ni + 1) * sizeof(int), cudaMemcpyHostToDevice));
-  AMGC_CUDA_TRY(cudaMemcpy(h->b_row_inst.p, inst.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  cudaStream_t s = h->stream;
+  AMGC_CUDA_TRY(cudaMemcpyAsync(h->b_chunk_row0.p, r0.data(), nc * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(h->b_chunk_row1.p, r1.data(), nc * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(h->b_chunk_ptr.p, cptr.data(), (ni + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(h->b_row_inst.p, inst.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
   h->b_nchunk = nc;
   return AMGC_OK;
 }

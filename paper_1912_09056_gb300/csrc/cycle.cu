@@ -30,13 +30,15 @@ __device__ __forceinline__ T ldcs(const T* p) { return __ldcs(p); }
 // MODE 1: y += A1 x1
 // MODE 2: y  = b - A1 x1 - A2 x2                        (residual)
 // MODE 3: y  = x0 + omega * dinv * (b - A1 x1 - A2 x2)    (damped Jacobi, out of place)
+// MODE 4: y  = dinv * (A1 x1 + A2 x2)                     (power step on D^-1 K)
 template <int MODE, class T>
 __device__ __forceinline__ void store_row(T* __restrict__ y, const T* __restrict__ b, const T* __restrict__ x0,
                                           const T* __restrict__ dinv, T omega, int64_t o, T s) {
   if (MODE == 0) y[o] = s;
   else if (MODE == 1) y[o] += s;
   else if (MODE == 2) y[o] = b[o] - s;
-  else y[o] = x0[o] + omega * dinv[o] * (b[o] - s);
+  else if (MODE == 3) y[o] = x0[o] + omega * dinv[o] * (b[o] - s);
+  else y[o] = dinv[o] * s;
 }
 
 // lane-per-block accumulation of one block row: acc[r] += sum_c A[b][r][c] x[col[b]][c]
@@ -80,10 +82,51 @@ k_rowop(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const 
   if (lane < BR) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * BR + lane, out);
 }
 
+// Warp per block row for 6-row blocks: lane 6s + r (s = 0..4, r = 0..5) owns block row r of
+// every fifth block of the row starting at slot s, so the six lanes of a slot read one block's
+// 6 x BC values contiguously and share the x gather; lanes 30 and 31 idle.  The five partial
+// sums of each block row are then added across slots (lanes r, r+6, ..., r+24).
+template <int BC, class T>
+__device__ __forceinline__ void slot_blocks6(int b0, int b1, const int* __restrict__ col, const T* __restrict__ val,
+                                             const T* __restrict__ x, int s, int r, T& acc) {
+  if (s >= 5) return;
+  for (int b = b0 + s; b < b1; b += 5) {
+    const T* xc = x + (int64_t)__ldg(col + b) * BC;
+    const T* v = val + (int64_t)b * (6 * BC) + r * BC;
+#pragma unroll
+    for (int c = 0; c < BC; ++c) acc = fma(ldg(v + c), ldg(xc + c), acc);
+  }
+}
+template <int BC1, int BC2, int MODE, class T>
+__global__ void __launch_bounds__(kRowWarps * 32)
+k_rowop6(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const T* __restrict__ v1,
+         const T* __restrict__ x1, const int* __restrict__ rp2, const int* __restrict__ c2, const T* __restrict__ v2,
+         const T* __restrict__ x2, const T* __restrict__ b, const T* __restrict__ x0, const T* __restrict__ dinv,
+         T omega, T* __restrict__ y) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row = blockIdx.x * kRowWarps + wid;
+  if (row >= nbr) return;
+  const int s = lane / 6, r = lane - 6 * (lane / 6);
+  T acc = T(0);
+  slot_blocks6<BC1, T>(rp1[row], rp1[row + 1], c1, v1, x1, s, r, acc);
+  if (rp2 != nullptr) slot_blocks6<BC2, T>(rp2[row], rp2[row + 1], c2, v2, x2, s, r, acc);
+  const T a1 = acc + __shfl_down_sync(0xffffffffu, acc, 6);
+  const T a2 = a1 + __shfl_down_sync(0xffffffffu, a1, 12);
+  const T out = a2 + __shfl_down_sync(0xffffffffu, acc, 24);
+  if (lane < 6) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * 6 + lane, out);
+}
+
 template <int BR, int BC1, int BC2, int MODE, class T>
 static int launch_rowop(const BsrV<T>& A1, const T* x1, const BsrV<T>* A2, const T* x2, const T* b, const T* x0,
                         const T* dinv, double omega, T* y, cudaStream_t s) {
   if (A1.nbr == 0) return AMGC_OK;
+  if (BR == 6 && BC1 == 6) {
+    AMGC_LAUNCH(k_rowop6<BC1, BC2, MODE, T><<<div_up(A1.nbr, kRowWarps), kRowWarps * 32, 0, s>>>(
+        A1.nbr, A1.rp, A1.col, A1.val, x1, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr, A2 ? A2->val : nullptr, x2,
+        b, x0, dinv, (T)omega, y));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    return AMGC_OK;
+  }
   AMGC_LAUNCH(k_rowop<BR, BC1, BC2, MODE, T><<<div_up(A1.nbr, kRowWarps), kRowWarps * 32, 0, s>>>(
       A1.nbr, A1.rp, A1.col, A1.val, x1, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr, A2 ? A2->val : nullptr, x2,
       b, x0, dinv, (T)omega, y));
@@ -1161,11 +1204,25 @@ int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out) {
     }
     return bsr_spmv(L.K, xin, yout, 1.0, 0.0, s);
   };
+  // y = D^-1 K x in one launch; the iterate is normalised after steps 10 and 20 only (the
+  // direction, and with it the Rayleigh quotient, does not depend on the intermediate scaling,
+  // and 10 steps cannot overflow for any lambda_max below 1e30)
+  const BsrV<double> kv = view_of(L.K);
+  auto step = [&](const double* xin, double* yout) -> int {
+    if (L.Ks.nslice > 0) {
+      const SellV<double> sv = sview<double>(L.Ks, L.Ks.val.p);
+      return sell_apply<4, double>(sv, L.nn, nullptr, xin, nullptr, nullptr, nullptr, L.dinv.p, 0.0, yout, s);
+    }
+    return rowop<4, double>(kv, xin, nullptr, nullptr, nullptr, nullptr, L.dinv.p, 0.0, yout, s);
+  };
   for (int it = 0; it < 20; ++it) {
-    AMGC_TRY(spmv(xv.p, yv.p));
-    AMGC_LAUNCH(k_scale_dinv<<<div_up(n, th), th, 0, s>>>(n, L.dinv.p, yv.p));
-    AMGC_TRY(dot(h, n, yv.p, yv.p, nullptr, sc.p));
-    AMGC_LAUNCH(k_normalize<<<div_up(n, th), th, 0, s>>>(n, sc.p, yv.p, xv.p));
+    AMGC_TRY(step(xv.p, yv.p));
+    if (it == 9 || it == 19) {
+      AMGC_TRY(dot(h, n, yv.p, yv.p, nullptr, sc.p));
+      AMGC_LAUNCH(k_normalize<<<div_up(n, th), th, 0, s>>>(n, sc.p, yv.p, xv.p));
+    } else {
+      std::swap(xv, yv);
+    }
     AMGC_CUDA_TRY(cudaGetLastError());
   }
   AMGC_TRY(spmv(xv.p, yv.p));

@@ -12,19 +12,20 @@
 namespace amgc {
 
 constexpr int kMdThreads = 256;
+constexpr int kMdWarps = kMdThreads / 32;
 constexpr int kMdBlocks = 608;   // 4 x 152 SMs
+constexpr int kUpThreads = 256;
 constexpr int kMaxRestart = 256;
 
-// part[b * ldp + k] = sum over block b's row chunk of V[k][i] * w[i], k = 0..nk-1.
+// part[b * nk + k] = sum over block b's row chunk of V[k][i] * w[i], k = 0..nk-1.
 // Warp q of the block takes the basis vectors k = q, q + 8, ...; lanes stream the chunk.
 __global__ void __launch_bounds__(kMdThreads)
-k_multidot(int64_t n, int nk, const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ part,
-           int ldp) {
+k_multidot(int64_t n, int nk, const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ part) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = blockIdx.x * chunk;
   const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
-  for (int k = wid; k < nk; k += kMdThreads / 32) {
+  for (int k = wid; k < nk; k += kMdWarps) {
     const double* v = V + (int64_t)k * n;
     double s0 = 0.0, s1 = 0.0;
     int64_t i = b0 + lane;
@@ -34,34 +35,96 @@ k_multidot(int64_t n, int nk, const double* __restrict__ V, const double* __rest
     }
     if (i < b1) s0 = fma(v[i], w[i], s0);
     const double t = warp_sum(s0 + s1);
-    if (lane == 0) part[(int64_t)blockIdx.x * ldp + k] = t;
+    if (lane == 0) part[(int64_t)blockIdx.x * nk + k] = t;
   }
 }
-// out[k*ldo] (+)= sum_b part[b*ldp + k], one warp per k (fixed order: deterministic)
-__global__ void k_multidot_final(int nk, int nb, const double* __restrict__ part, int ldp, double* __restrict__ out,
-                                 int ldo, int accumulate, double* __restrict__ hk) {
+// out[k*ldo] (+)= sum_b part[b*nk + k], one warp per k (fixed order: deterministic)
+__global__ void k_multidot_final(int nk, int nb, const double* __restrict__ part, double* __restrict__ out, int ldo,
+                                 int accumulate, double* __restrict__ hk) {
   const int lane = threadIdx.x & 31;
   const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (k >= nk) return;
   double s = 0.0;
-  for (int b = lane; b < nb; b += 32) s += part[(int64_t)b * ldp + k];
+  for (int b = lane; b < nb; b += 32) s += part[(int64_t)b * nk + k];
   s = warp_sum(s);
   if (lane == 0) {
     if (hk) hk[k] = s;
     out[(int64_t)k * ldo] = accumulate ? out[(int64_t)k * ldo] + s : s;
   }
 }
-// w[i] -= sum_k V[k][i] h[k]
-__global__ void k_basis_update(int64_t n, int nk, const double* __restrict__ V, const double* __restrict__ h,
-                               double* __restrict__ w) {
+
+// w[i] -= sum_k V[k][i] h[k]; with norm != nullptr also one partial of ||w||^2 per block.
+__global__ void __launch_bounds__(kUpThreads)
+k_basis_update(int64_t n, int nk, const double* __restrict__ V, const double* __restrict__ h, double* __restrict__ w,
+               double* __restrict__ norm) {
   __shared__ double hs[kMaxRestart + 1];
+  __shared__ double red[kUpThreads / 32];
   for (int k = threadIdx.x; k < nk; k += blockDim.x) hs[k] = h[k];
   __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double s = w[i];
-  for (int k = 0; k < nk; ++k) s = fma(-V[(int64_t)k * n + i], hs[k], s);
-  w[i] = s;
+  double s = 0.0;
+  if (i < n) {
+    s = w[i];
+    for (int k = 0; k < nk; ++k) s = fma(-V[(int64_t)k * n + i], hs[k], s);
+    w[i] = s;
+  }
+  if (norm == nullptr) return;
+  const double t = warp_sum(s * s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+#pragma unroll
+    for (int q = 0; q < kUpThreads / 32; ++q) u += red[q];
+    norm[blockIdx.x] = u;
+  }
+}
+
+// ||w||^2 from nb block partials (fixed order) into scal[2], H[j+1][j] = ||w||, then the Givens
+// rotations of column j (one block; column j and the rotations are staged in shared memory so
+// that the sequential part reads no global memory)
+__global__ void __launch_bounds__(kUpThreads)
+k_norm_givens(int nb, const double* __restrict__ part, int j, int m, double* H, double* cs, double* sn, double* g,
+              double beta0, double* scal) {
+  __shared__ double red[kUpThreads / 32];
+  __shared__ double hc[kMaxRestart + 1], c[kMaxRestart], sv[kMaxRestart];
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kUpThreads) t += part[b];
+  for (int i = threadIdx.x; i <= j; i += kUpThreads) hc[i] = H[(int64_t)i * m + j];
+  for (int i = threadIdx.x; i < j; i += kUpThreads) {
+    c[i] = cs[i];
+    sv[i] = sn[i];
+  }
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double nrm2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < kUpThreads / 32; ++q) nrm2 += red[q];
+    scal[2] = nrm2;
+    hc[j + 1] = sqrt(nrm2);
+    for (int i = 0; i < j; ++i) {
+      const double a = hc[i], b = hc[i + 1];
+      hc[i] = c[i] * a + sv[i] * b;
+      hc[i + 1] = -sv[i] * a + c[i] * b;
+    }
+    const double a = hc[j], b = hc[j + 1];
+    const double den = hypot(a, b);
+    const double cj = den > 0.0 ? a / den : 1.0;
+    const double sj = den > 0.0 ? b / den : 0.0;
+    cs[j] = cj;
+    sn[j] = sj;
+    hc[j] = den;
+    hc[j + 1] = 0.0;
+    const double gj = g[j];
+    g[j + 1] = -sj * gj;
+    g[j] = cj * gj;
+    scal[0] = fabs(g[j + 1]) / beta0;
+    scal[1] = isfinite(den) && isfinite(g[j + 1]) ? 0.0 : 1.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += kUpThreads) H[(int64_t)i * m + j] = hc[i];
 }
 // x[i] += sum_k Zs[k][i] y[k]
 __global__ void k_solution_update(int64_t n, int nk, const double* __restrict__ Zs, const double* __restrict__ y,
@@ -75,12 +138,11 @@ __global__ void k_solution_update(int64_t n, int nk, const double* __restrict__ 
   for (int k = 0; k < nk; ++k) s = fma(Zs[(int64_t)k * n + i], ys[k], s);
   x[i] = s;
 }
-// v = w / sqrt(nrm2) (zero vector on breakdown); H[j+1][j] = sqrt(nrm2)
+// v = w / sqrt(nrm2) (zero vector on breakdown)
 __global__ void k_arnoldi_normalize(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ w,
-                                    double* __restrict__ v, double* __restrict__ hsub) {
+                                    double* __restrict__ v) {
   const double nr = sqrt(*nrm2);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i == 0) *hsub = nr;
   if (i < n) v[i] = nr > 0.0 ? w[i] / nr : 0.0;
 }
 // start of a cycle: v0 = r / beta, g = (beta, 0, ...)
@@ -90,29 +152,6 @@ __global__ void k_cycle_start(int64_t n, const double* __restrict__ nrm2, const 
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) v0[i] = r[i] / beta;
   if (i <= m) g[i] = i == 0 ? beta : 0.0;
-}
-// Givens update of column j (single thread); scal[0] = |g_{j+1}| / beta0
-__global__ void k_givens(int j, int m, double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
-                         double* __restrict__ g, double beta0, double* __restrict__ scal) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = 0; i < j; ++i) {
-    const double a = H[i * m + j], b = H[(i + 1) * m + j];
-    H[i * m + j] = cs[i] * a + sn[i] * b;
-    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
-  }
-  const double a = H[j * m + j], b = H[(j + 1) * m + j];
-  const double den = hypot(a, b);
-  const double c = den > 0.0 ? a / den : 1.0;
-  const double s = den > 0.0 ? b / den : 0.0;
-  cs[j] = c;
-  sn[j] = s;
-  H[j * m + j] = den;
-  H[(j + 1) * m + j] = 0.0;
-  const double gj = g[j];
-  g[j + 1] = -s * gj;
-  g[j] = c * gj;
-  scal[0] = fabs(g[j + 1]) / beta0;
-  scal[1] = isfinite(den) && isfinite(g[j + 1]) ? 0.0 : 1.0;
 }
 // back substitution H(0:k,0:k) y = g(0:k) (single thread)
 __global__ void k_backsolve(int k, int m, const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y) {
@@ -140,7 +179,7 @@ static int ensure_workspace(amgc_hierarchy* h, int64_t n, int m) {
   AMGC_TRY(h->givens.alloc((size_t)2 * m));
   AMGC_TRY(h->gvec.alloc(m + 1));
   AMGC_TRY(h->y.alloc(m + 1));
-  AMGC_TRY(h->wk.alloc((size_t)kMdBlocks * (m + 1)));
+  AMGC_TRY(h->wk.alloc(std::max((size_t)kMdBlocks * (m + 1), (size_t)div_up(n, kUpThreads))));
   AMGC_TRY(h->rk.alloc(n));
   AMGC_TRY(h->xk.alloc(8));
   h->m_alloc = m;
@@ -151,9 +190,9 @@ static int ensure_workspace(amgc_hierarchy* h, int64_t n, int m) {
 static int multidot(amgc_hierarchy* h, int64_t n, int nk, const double* V, const double* w, double* Hcol, int m,
                     int accumulate, double* hk) {
   cudaStream_t s = h->stream;
-  AMGC_LAUNCH(k_multidot<<<kMdBlocks, kMdThreads, 0, s>>>(n, nk, V, w, h->wk.p, nk));
-  AMGC_LAUNCH(k_multidot_final<<<div_up((int64_t)nk * 32, 128), 128, 0, s>>>(nk, kMdBlocks, h->wk.p, nk, Hcol, m,
-                                                                            accumulate, hk));
+  AMGC_LAUNCH(k_multidot<<<kMdBlocks, kMdThreads, 0, s>>>(n, nk, V, w, h->wk.p));
+  AMGC_LAUNCH(k_multidot_final<<<div_up((int64_t)nk * 32, 128), 128, 0, s>>>(nk, kMdBlocks, h->wk.p, Hcol, m, accumulate,
+                                                                            hk));
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
@@ -167,6 +206,7 @@ int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol_in, int* 
   AMGC_TRY(ensure_workspace(h, n, m));
   const int th = 256;
   const int gn = div_up(n, th);
+  const int gu = div_up(n, kUpThreads);
   double* scal = h->xk.p;          // [0] residual estimate, [1] breakdown flag, [2] norm^2, [3] scratch
   double* hk = h->y.p;             // reuse: projection coefficients of the current pass
   DBuf<double> hbuf;
@@ -207,12 +247,11 @@ int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol_in, int* 
       // CGS2
       for (int pass = 0; pass < 2; ++pass) {
         AMGC_TRY(multidot(h, n, j + 1, h->V.p, w, h->H.p + j, m, pass, hbuf.p));
-        AMGC_LAUNCH(k_basis_update<<<gn, th, 0, s>>>(n, j + 1, h->V.p, hbuf.p, w));
+        AMGC_LAUNCH(k_basis_update<<<gu, kUpThreads, 0, s>>>(n, j + 1, h->V.p, hbuf.p, w, pass ? h->wk.p : nullptr));
         AMGC_CUDA_TRY(cudaGetLastError());
       }
-      AMGC_TRY(dot(h, n, w, w, nullptr, scal + 2));
-      AMGC_LAUNCH(k_arnoldi_normalize<<<gn, th, 0, s>>>(n, scal + 2, w, w, h->H.p + (int64_t)(j + 1) * m + j));
-      AMGC_LAUNCH(k_givens<<<1, 32, 0, s>>>(j, m, h->H.p, cs, sn, h->gvec.p, beta0, scal));
+      AMGC_LAUNCH(k_norm_givens<<<1, kUpThreads, 0, s>>>(gu, h->wk.p, j, m, h->H.p, cs, sn, h->gvec.p, beta0, scal));
+      AMGC_LAUNCH(k_arnoldi_normalize<<<gn, th, 0, s>>>(n, scal + 2, w, w));
       AMGC_CUDA_TRY(cudaGetLastError());
       AMGC_CUDA_TRY(cudaMemcpyAsync(pin, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       AMGC_CUDA_TRY(cudaStreamSynchronize(s));

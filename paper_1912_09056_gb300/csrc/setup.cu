@@ -3,6 +3,8 @@
 // Galerkin products, CheapSIMPLE data and the coarsest dense inverse.
 #include "amgc_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -782,37 +784,111 @@ k_spgemm_symbolic(int nrow, const int* __restrict__ arp, const int* __restrict__
   }
 }
 
-template <int BR, int BK, int BC>
-__global__ void __launch_bounds__(kGemmWarps * 32)
-k_spgemm_numeric(int nrow, const int* __restrict__ arp, const int* __restrict__ acol, const double* __restrict__ aval,
-                 const int* __restrict__ brp, const int* __restrict__ bcol, const double* __restrict__ bval,
-                 const int* __restrict__ crp, const int* __restrict__ ccol, double* __restrict__ cval) {
-  constexpr int NQ = BR * BC;   // output elements per block product
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int row = blockIdx.x * kGemmWarps + wid;
+// ---- SpGEMM over work units.  A unit is a range [ue0, ue1) of A entries of one C row urow
+// (without unit tables: unit u is the whole row u).  Products with few C rows (the Galerkin
+// products of the coarse levels) split their long rows over several units, so that enough warps
+// work at once; the split rows are added up afterwards in unit order (deterministic).
+constexpr int kSplitRows = 8192;          // products with fewer C rows use unit tables
+constexpr int kTargetUnits = 4096;        // about this many units per split product
+constexpr int kUnitSmem = 96 * 1024;      // shared memory per CTA for the row accumulators
+constexpr size_t kUnitSmemWarp = 8 * 1024; // largest row accumulator per warp in shared memory
+
+// symbolic phase of a split product: bm[row * wpr + c / 32] gets bit c % 32 for every column c
+// of B reached from the unit's A entries (a set union, so the result does not depend on order)
+__global__ void k_sym_bitmap(int nunits, const int* __restrict__ urow, const int* __restrict__ ue0,
+                             const int* __restrict__ ue1, const int* __restrict__ acol, const int* __restrict__ brp,
+                             const int* __restrict__ bcol, int wpr, unsigned* __restrict__ bm) {
+  const int lane = threadIdx.x & 31;
+  const int u = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (u >= nunits) return;
+  unsigned* b = bm + (int64_t)urow[u] * wpr;
+  for (int e = ue0[u]; e < ue1[u]; ++e) {
+    const int k = acol[e];
+    for (int t = brp[k] + lane; t < brp[k + 1]; t += 32) {
+      const int c = bcol[t];
+      atomicOr(b + (c >> 5), 1u << (c & 31));
+    }
+  }
+}
+// per row (one warp): the number of set bits into cnt[row], or with ccol the set columns in
+// ascending order at ccol[crp[row]...]
+__global__ void k_bitmap_cols(int nrow, int wpr, const unsigned* __restrict__ bm, int* __restrict__ cnt,
+                              const int* __restrict__ crp, int* __restrict__ ccol) {
+  const int lane = threadIdx.x & 31;
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (row >= nrow) return;
+  const unsigned* b = bm + (int64_t)row * wpr;
+  int total = 0;
+  const int base = ccol ? crp[row] : 0;
+  for (int w0 = 0; w0 < wpr; w0 += 32) {
+    unsigned word = w0 + lane < wpr ? b[w0 + lane] : 0u;
+    const int c = __popc(word);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (ccol) {
+      int pos = base + total + incl - c;
+      while (word) {
+        const int bit = __ffs(word) - 1;
+        ccol[pos++] = (w0 + lane) * 32 + bit;
+        word &= word - 1u;
+      }
+    }
+    total += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (!ccol && lane == 0) cnt[row] = total;
+}
+__global__ void k_row_maxlen(int nrow, const int* __restrict__ rp, int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nrow) atomicMax(out, rp[i + 1] - rp[i]);
+}
+// numeric phase: one warp per unit accumulates its products into a zeroed copy of the C row and
+// leaves the row in cval, or, for a split row, its partial in scratch + uout[u].  For every A
+// entry (in order) the B row is taken 32 entries at a time: each lane finds the C position of
+// one B entry's column, then the lanes share the (B entry, output element) work items; items
+// of one group touch distinct C values (a B row has distinct columns).  SMEM: the copy lives in shared memory and is
+// written out at the end; otherwise the warp accumulates in place in global memory (rows too
+// long for enough warps per CTA).
+template <int BR, int BK, int BC, bool SMEM>
+__global__ void __launch_bounds__(256)
+k_spgemm_units(int nunits, const int* __restrict__ urow, const int* __restrict__ ue0, const int* __restrict__ ue1,
+               const int64_t* __restrict__ uout, const int* __restrict__ arp, const int* __restrict__ acol,
+               const double* __restrict__ aval, const int* __restrict__ brp, const int* __restrict__ bcol,
+               const double* __restrict__ bval, const int* __restrict__ crp, const int* __restrict__ ccol,
+               double* __restrict__ cval, double* __restrict__ scratch, int cmax) {
+  constexpr int NQ = BR * BC;
+  extern __shared__ double sp_acc[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int u = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (u >= nunits) return;
+  const int row = urow ? urow[u] : u;
+  const int e0 = urow ? ue0[u] : arp[row], e1 = urow ? ue1[u] : arp[row + 1];
   const int c0 = crp[row], c1 = crp[row + 1];
-  for (int64_t q = (int64_t)c0 * NQ + lane; q < (int64_t)c1 * NQ; q += 32) cval[q] = 0.0;
+  const int len = c1 - c0;
+  double* out = (uout == nullptr || uout[u] < 0) ? cval + (int64_t)c0 * NQ : scratch + uout[u];
+  double* acc = SMEM ? sp_acc + (size_t)wid * cmax * NQ : out;
+  for (int q = lane; q < len * NQ; q += 32) acc[q] = 0.0;
   __syncwarp();
-  for (int e = arp[row]; e < arp[row + 1]; ++e) {
+  for (int e = e0; e < e1; ++e) {
     const int k = acol[e];
     const double* ae = aval + (int64_t)e * BR * BK;
     const int t0 = brp[k], t1 = brp[k + 1];
     for (int tc = t0; tc < t1; tc += 32) {
-      // position in C's row of the block column of B entry tc + lane
       int pos = 0;
       if (tc + lane < t1) {
         const int c = bcol[tc + lane];
         int lo = c0, hi = c1 - 1;
         while (lo < hi) {
-          int mid = (lo + hi) >> 1;
+          const int mid = (lo + hi) >> 1;
           if (ccol[mid] < c) lo = mid + 1;
           else hi = mid;
         }
-        pos = lo;
+        pos = lo - c0;
       }
       const int nt = min(32, t1 - tc);
-      // work items (B entry t, output element qe); distinct items touch distinct C values
       for (int wb = 0; wb < nt * NQ; wb += 32) {
         const int w = wb + lane;
         const int t = w / NQ;
@@ -822,21 +898,104 @@ k_spgemm_numeric(int nrow, const int* __restrict__ arp, const int* __restrict__ 
           const int i = qe / BC, j = qe - i * BC;
           const double* bb = bval + (int64_t)(tc + t) * BK * BC + j;
           const double* ai = ae + i * BK;
-          double sacc = cval[(int64_t)p * NQ + qe];
+          double sacc = acc[p * NQ + qe];
 #pragma unroll
           for (int m = 0; m < BK; ++m) sacc = fma(__ldg(ai + m), __ldg(bb + m * BC), sacc);
-          cval[(int64_t)p * NQ + qe] = sacc;
+          acc[p * NQ + qe] = sacc;
         }
       }
       __syncwarp();
     }
   }
+  if (SMEM)
+    for (int q = lane; q < len * NQ; q += 32) out[q] = acc[q];
+}
+// rows split over units [su0[r], su1[r]): C row = sum of the partials in unit order
+__global__ void k_spgemm_reduce(int nsplit, const int* __restrict__ srow, const int* __restrict__ su0,
+                                const int* __restrict__ su1, const int64_t* __restrict__ uout,
+                                const int* __restrict__ crp, int nq, const double* __restrict__ scratch,
+                                double* __restrict__ cval) {
+  const int lane = threadIdx.x & 31;
+  const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (r >= nsplit) return;
+  const int row = srow[r];
+  const int64_t c0 = crp[row];
+  const int len = (crp[row + 1] - crp[row]) * nq;
+  for (int q = lane; q < len; q += 32) {
+    double t = 0.0;
+    for (int u = su0[r]; u < su1[r]; ++u) t += scratch[uout[u] + q];
+    cval[c0 * nq + q] = t;
+  }
 }
 
+// Work units of a split product (host tables, copied to the device).
+struct SpUnits {
+  std::vector<int> row, e0, e1, srow, su0, su1;
+  std::vector<int64_t> out;
+  int64_t scratch = 0;
+  DBuf<int> d_row, d_e0, d_e1, d_srow, d_su0, d_su1;
+  DBuf<int64_t> d_out;
+};
+// rows longer than seg A entries are cut into pieces of at most seg entries
+static void build_units(const std::vector<int>& arp, int seg, SpUnits& U) {
+  const int n = (int)arp.size() - 1;
+  for (int r = 0; r < n; ++r) {
+    const int a = arp[r], b = arp[r + 1];
+    if (b - a <= seg) {
+      U.row.push_back(r);
+      U.e0.push_back(a);
+      U.e1.push_back(b);
+      continue;
+    }
+    U.srow.push_back(r);
+    U.su0.push_back((int)U.row.size());
+    for (int e = a; e < b; e += seg) {
+      U.row.push_back(r);
+      U.e0.push_back(e);
+      U.e1.push_back(std::min(b, e + seg));
+    }
+    U.su1.push_back((int)U.row.size());
+  }
+}
+template <class T>
+static int upload(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+  AMGC_TRY(d.alloc(std::max<size_t>(h.size(), 1)));
+  if (!h.empty()) AMGC_CUDA_TRY(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return AMGC_OK;
+}
+
+// C values: with shared-memory row accumulators when the longest C row fits (cmax), over the
+// unit tables U when the product is split, else with the global-memory accumulation kernel.
 template <int BR, int BK, int BC>
-static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, cudaStream_t s) {
-  AMGC_LAUNCH(k_spgemm_numeric<BR, BK, BC><<<div_up(A.nbr, kGemmWarps), kGemmWarps * 32, 0, s>>>(
-      A.nbr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p));
+static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, int cmax, SpUnits* U, cudaStream_t s) {
+  constexpr int NQ = BR * BC;
+  const size_t per_warp = (size_t)std::max(cmax, 1) * NQ * sizeof(double);
+  // shared-memory accumulators only for short C rows (eight warps in at most 64 KB, so that
+  // three CTAs share an SM); longer rows accumulate in global memory, where more warps per SM
+  // hide the latency of the position searches better than shared memory saves
+  const bool smem_acc = per_warp <= kUnitSmemWarp;
+  const int wpb = smem_acc ? 8 : kGemmWarps;
+  const size_t smem = smem_acc ? (size_t)wpb * per_warp : 0;
+  if (smem_acc)
+    AMGC_CUDA_TRY(cudaFuncSetAttribute(k_spgemm_units<BR, BK, BC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kUnitSmem));
+  auto kern = smem_acc ? k_spgemm_units<BR, BK, BC, true> : k_spgemm_units<BR, BK, BC, false>;
+  DBuf<double> scratch;
+  if (U) {
+    const int nu = (int)U->row.size();
+    if (U->scratch > 0) AMGC_TRY(scratch.alloc((size_t)U->scratch));
+    AMGC_LAUNCH(kern<<<div_up(nu, wpb), wpb * 32, smem, s>>>(
+        nu, U->d_row.p, U->d_e0.p, U->d_e1.p, U->d_out.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
+        C.rowptr.p, C.col.p, C.val.p, scratch.p, cmax));
+    const int ns = (int)U->srow.size();
+    if (ns > 0)
+      AMGC_LAUNCH(k_spgemm_reduce<<<div_up((int64_t)ns * 32, 128), 128, 0, s>>>(
+          ns, U->d_srow.p, U->d_su0.p, U->d_su1.p, U->d_out.p, C.rowptr.p, NQ, scratch.p, C.val.p));
+  } else {
+    AMGC_LAUNCH(kern<<<div_up(A.nbr, wpb), wpb * 32, smem, s>>>(
+        A.nbr, nullptr, nullptr, nullptr, nullptr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
+        C.rowptr.p, C.col.p, C.val.p, nullptr, cmax));
+  }
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
@@ -853,10 +1012,34 @@ static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C) {
   C.bc = B.bc;
   AMGC_TRY(C.rowptr.alloc(A.nbr + 1));
   AMGC_CUDA_TRY(cudaMemsetAsync(C.rowptr.p, 0, (A.nbr + 1) * sizeof(int), s));
+  const int wpr = (B.nbc + 31) / 32;
+  // few C rows: unit tables (long rows split) and a bitmap symbolic phase
+  const bool split = A.nbr > 0 && A.nbr < kSplitRows && (int64_t)A.nbr * wpr <= (int64_t)(64 << 20);
+  std::unique_ptr<SpUnits> U;
+  DBuf<unsigned> bm;
   const int g = div_up(A.nbr, kGemmWarps);
-  if (A.nbr > 0)
-    AMGC_LAUNCH(k_spgemm_symbolic<0><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p, C.rowptr.p,
-                                                       nullptr, nullptr, h->status.p));
+  if (split) {
+    U.reset(new SpUnits());
+    std::vector<int> arp(A.nbr + 1);
+    AMGC_CUDA_TRY(cudaMemcpyAsync(arp.data(), A.rowptr.p, (A.nbr + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t nnza = arp[A.nbr];
+    const int seg = (int)std::max<int64_t>(4, (nnza + kTargetUnits - 1) / kTargetUnits);
+    build_units(arp, seg, *U);
+    AMGC_TRY(upload(U->d_row, U->row, s));
+    AMGC_TRY(upload(U->d_e0, U->e0, s));
+    AMGC_TRY(upload(U->d_e1, U->e1, s));
+    AMGC_TRY(bm.alloc((size_t)A.nbr * std::max(wpr, 1)));
+    AMGC_CUDA_TRY(cudaMemsetAsync(bm.p, 0, (size_t)A.nbr * std::max(wpr, 1) * sizeof(unsigned), s));
+    const int nu = (int)U->row.size();
+    AMGC_LAUNCH(k_sym_bitmap<<<div_up((int64_t)nu * 32, 256), 256, 0, s>>>(nu, U->d_row.p, U->d_e0.p, U->d_e1.p,
+                                                                            A.col.p, B.rowptr.p, B.col.p, wpr, bm.p));
+    AMGC_LAUNCH(k_bitmap_cols<<<div_up((int64_t)A.nbr * 32, 256), 256, 0, s>>>(A.nbr, wpr, bm.p, C.rowptr.p, nullptr,
+                                                                                 nullptr));
+  } else if (A.nbr > 0) {
+    AMGC_LAUNCH(k_spgemm_symbolic<0><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p,
+                                                                  C.rowptr.p, nullptr, nullptr, h->status.p));
+  }
   AMGC_CUDA_TRY(cudaGetLastError());
   AMGC_TRY(check_status(h, "spgemm symbolic"));
   int nnz = 0;
@@ -864,14 +1047,44 @@ static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C) {
   C.nnzb = nnz;
   AMGC_TRY(C.col.alloc(std::max(nnz, 1)));
   AMGC_TRY(C.val.alloc((size_t)std::max(nnz, 1) * C.br * C.bc));
-  if (A.nbr > 0)
-    AMGC_LAUNCH(k_spgemm_symbolic<1><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p, nullptr,
-                                                       C.rowptr.p, C.col.p, h->status.p));
-  AMGC_CUDA_TRY(cudaGetLastError());
   if (A.nbr == 0) return AMGC_OK;
+  int cmax = 0;
+  if (split) {
+    AMGC_LAUNCH(k_bitmap_cols<<<div_up((int64_t)A.nbr * 32, 256), 256, 0, s>>>(A.nbr, wpr, bm.p, nullptr, C.rowptr.p,
+                                                                                 C.col.p));
+    // C row lengths give the scratch slices of the split rows
+    std::vector<int> crp(A.nbr + 1);
+    AMGC_CUDA_TRY(cudaMemcpyAsync(crp.data(), C.rowptr.p, (A.nbr + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int r = 0; r < A.nbr; ++r) cmax = std::max(cmax, crp[r + 1] - crp[r]);
+    const int64_t nq = (int64_t)C.br * C.bc;
+    U->out.assign(U->row.size(), -1);
+    for (size_t q = 0; q < U->srow.size(); ++q) {
+      const int r = U->srow[q];
+      for (int u = U->su0[q]; u < U->su1[q]; ++u) {
+        U->out[u] = U->scratch;
+        U->scratch += (int64_t)(crp[r + 1] - crp[r]) * nq;
+      }
+    }
+    AMGC_TRY(upload(U->d_out, U->out, s));
+    AMGC_TRY(upload(U->d_srow, U->srow, s));
+    AMGC_TRY(upload(U->d_su0, U->su0, s));
+    AMGC_TRY(upload(U->d_su1, U->su1, s));
+  } else {
+    AMGC_LAUNCH(k_spgemm_symbolic<1><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p,
+                                                                  nullptr, C.rowptr.p, C.col.p, h->status.p));
+    DBuf<int> mx;
+    AMGC_TRY(mx.alloc(1));
+    AMGC_CUDA_TRY(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
+    AMGC_LAUNCH(k_row_maxlen<<<div_up(A.nbr, 256), 256, 0, s>>>(A.nbr, C.rowptr.p, mx.p));
+    AMGC_CUDA_TRY(cudaMemcpyAsync(&cmax, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  AMGC_CUDA_TRY(cudaGetLastError());
   const int br = A.br, bk = A.bc, bc = B.bc;
+  SpUnits* up = U.get();
 #define AMGC_GEMM_CASE(R, K, C_)                                   \
-  if (br == R && bk == K && bc == C_) return spgemm_numeric<R, K, C_>(A, B, C, s);
+  if (br == R && bk == K && bc == C_) return spgemm_numeric<R, K, C_>(A, B, C, cmax, up, s);
   AMGC_GEMM_CASE(3, 3, 6)
   AMGC_GEMM_CASE(6, 3, 6)
   AMGC_GEMM_CASE(3, 3, 3)
@@ -1546,6 +1759,254 @@ __global__ void k_gj_unscramble(int n, const int* __restrict__ piv, double* __re
   }
 }
 
+// Gauss-Jordan inverse with partial pivoting in one cooperative launch: every step is one
+// grid-wide pass, separated by grid barriers, between two n x n buffers (cur -> nxt).  Step k:
+// every CTA finds the same pivot p = argmax_{i >= k} |cur[i][k]| (ties to the smallest i), keeps
+// rows p and k of cur in shared memory, and writes its own rows of nxt:
+//   row k  = row p / pv, with pv^-1 in column k;
+//   row p  = row k - row k[k] * (new row k), with -row k[k] / pv in column k (p != k);
+//   row i  = row i - row i[k] * (new row k), with -row i[k] / pv in column k.
+// This is the in-place elimination of the single-block kernels with the interchange applied to
+// whole rows; afterwards the columns are permuted back (interchanges in reverse order) into the
+// other buffer.  Reads of cur bypass L1 (other CTAs wrote it before the barrier).
+constexpr int kGjcThreads = 256;
+__global__ void __launch_bounds__(kGjcThreads)
+k_gj_coop(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __restrict__ piv, int* st) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double gj_sh[];   // [0, n): row p of cur, [n, 2n): row k of cur
+  __shared__ double bv[kGjcThreads];
+  __shared__ int bi[kGjcThreads];
+  const int per = (n + gridDim.x - 1) / gridDim.x;
+  const int r0 = min(n, (int)blockIdx.x * per), r1 = min(n, r0 + per);
+  double* cur = Aa;
+  double* nxt = Ab;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int besti = n;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = fabs(__ldcg(cur + (int64_t)i * n + k));
+      if (v > best || (v == best && i < besti)) { best = v; besti = i; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = besti;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        const double v = bv[threadIdx.x + o];
+        const int ii = bi[threadIdx.x + o];
+        if (v > bv[threadIdx.x] || (v == bv[threadIdx.x] && ii < bi[threadIdx.x])) {
+          bv[threadIdx.x] = v;
+          bi[threadIdx.x] = ii;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = bi[0] < n ? bi[0] : k;
+    const double pmax = bv[0];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      gj_sh[j] = __ldcg(cur + (int64_t)p * n + j);
+      gj_sh[n + j] = __ldcg(cur + (int64_t)k * n + j);
+    }
+    __syncthreads();
+    double pv = gj_sh[k];
+    if (!(pmax > 0.0) || !isfinite(pv)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(st, ST_SINGULAR);
+      pv = 1.0;
+    }
+    const double inv = 1.0 / pv;
+    for (int i = r0; i < r1; ++i) {
+      double* dst = nxt + (int64_t)i * n;
+      if (i == k) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = j == k ? inv : gj_sh[j] * inv;
+      } else {
+        const double* src = i == p ? gj_sh + n : cur + (int64_t)i * n;
+        const double a = i == p ? gj_sh[n + k] : __ldcg(src + k);
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+          const double v = i == p ? src[j] : __ldcg(src + j);
+          dst[j] = j == k ? -a * inv : v - a * (gj_sh[j] * inv);
+        }
+      }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) piv[k] = p;
+    grid.sync();
+    double* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  int* perm = reinterpret_cast<int*>(gj_sh);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) perm[j] = j;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = __ldcg(piv + k);
+      if (p != k) {
+        const int t = perm[k];
+        perm[k] = perm[p];
+        perm[p] = t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = r0; i < r1; ++i)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) nxt[(int64_t)i * n + j] = __ldcg(cur + (int64_t)i * n + perm[j]);
+}
+
+// The same inverse with kGjB pivots per grid barrier (n up to kGjBlockedMax).  Per super-step
+// every CTA (redundantly) eliminates the panel of columns K..K+b-1 for all rows in shared memory,
+// recording the pivot rows' entities, the pivots and every row's multipliers a_e(t) (its panel
+// value in column K+t just before step t).  The rows of the other columns then follow from the
+// pivot rows of the super-step,
+//   q_t = (row_{pi_t} - sum_{s<t} a_{pi_t}(s) q_s) / pv_t,
+//   row_e <- row_e - sum_t a_e(t) q_t          (pivot row pi_s: q_s - sum_{t>s} a_{pi_s}(t) q_t),
+// which is the per-column elimination with the same operations grouped per super-step.  Each CTA
+// writes its own rows of the next buffer in the row order after the super-step's interchanges.
+constexpr int kGjB = 8;
+constexpr int kGjBlockedMax = 960;
+__device__ __forceinline__ void argmax_pair(double& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+}
+__global__ void __launch_bounds__(kGjcThreads)
+k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __restrict__ piv, int* st) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double gjb_sh[];
+  double* panel = gjb_sh;                 // [n][kGjB]   panel values per entity (row of cur)
+  double* mult = panel + n * kGjB;        // [n][kGjB]   multipliers a_e(t)
+  double* q = mult + n * kGjB;            // [kGjB][n]   transformed pivot rows (columns outside the panel)
+  int* p2e = reinterpret_cast<int*>(q + kGjB * n);   // [n] position -> entity
+  int* estep = p2e + n;                   // [n] super-step pivot index of an entity, -1 otherwise
+  __shared__ double ppan[kGjB], pinv[kGjB], wv[kGjcThreads / 32];
+  __shared__ int pent[kGjB], wi[kGjcThreads / 32], ppos;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int per = (n + gridDim.x - 1) / gridDim.x;
+  const int r0 = min(n, (int)blockIdx.x * per), r1 = min(n, r0 + per);
+  double* cur = Aa;
+  double* nxt = Ab;
+  for (int K = 0; K < n; K += kGjB) {
+    const int nb = min(kGjB, n - K);
+    for (int idx = tid; idx < n * nb; idx += kGjcThreads) {
+      const int e = idx / nb, t = idx - e * nb;
+      panel[e * kGjB + t] = __ldcg(cur + (int64_t)e * n + K + t);
+    }
+    for (int e = tid; e < n; e += kGjcThreads) {
+      p2e[e] = e;
+      estep[e] = -1;
+    }
+    __syncthreads();
+    for (int t = 0; t < nb; ++t) {
+      const int k = K + t;
+      double bv = -1.0;
+      int bi = n;
+      for (int i = k + tid; i < n; i += kGjcThreads) {
+        const double v = fabs(panel[p2e[i] * kGjB + t]);
+        if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+      }
+      argmax_pair(bv, bi);
+      if (lane == 0) { wv[wid] = bv; wi[wid] = bi; }
+      __syncthreads();
+      if (wid == 0) {
+        double v = lane < kGjcThreads / 32 ? wv[lane] : -1.0;
+        int i = lane < kGjcThreads / 32 ? wi[lane] : n;
+        argmax_pair(v, i);
+        if (lane == 0) {
+          const int p = i < n ? i : k;
+          const int ep = p2e[p];
+          double pv = panel[ep * kGjB + t];
+          if (!(v > 0.0) || !isfinite(pv)) {
+            if (blockIdx.x == 0) set_status(st, ST_SINGULAR);
+            pv = 1.0;
+          }
+          ppos = p;
+          pent[t] = ep;
+          pinv[t] = 1.0 / pv;
+          estep[ep] = t;
+          if (blockIdx.x == 0) piv[k] = p;
+        }
+      }
+      __syncthreads();
+      const int ep = pent[t];
+      const double inv = pinv[t];
+      for (int c = tid; c < nb; c += kGjcThreads) ppan[c] = panel[ep * kGjB + c];
+      for (int e = tid; e < n; e += kGjcThreads) mult[e * kGjB + t] = panel[e * kGjB + t];
+      __syncthreads();
+      for (int idx = tid; idx < n * nb; idx += kGjcThreads) {
+        const int e = idx / nb, c = idx - e * nb;
+        double* pe = panel + e * kGjB + c;
+        if (e == ep) *pe = c == t ? inv : ppan[c] * inv;
+        else {
+          const double a = mult[e * kGjB + t];
+          *pe = c == t ? -a * inv : *pe - a * (ppan[c] * inv);
+        }
+      }
+      if (tid == 0) {
+        const int p = ppos;
+        const int tmp = p2e[k];
+        p2e[k] = p2e[p];
+        p2e[p] = tmp;
+      }
+      __syncthreads();
+    }
+    // transformed pivot rows outside the panel
+    for (int j = tid; j < n; j += kGjcThreads) {
+      if (j >= K && j < K + nb) continue;
+      for (int t = 0; t < nb; ++t) {
+        const int ep = pent[t];
+        double v = __ldcg(cur + (int64_t)ep * n + j);
+        for (int s2 = 0; s2 < t; ++s2) v -= mult[ep * kGjB + s2] * q[s2 * n + j];
+        q[t * n + j] = v * pinv[t];
+      }
+    }
+    __syncthreads();
+    for (int i = r0; i < r1; ++i) {
+      const int e = p2e[i];
+      const int se = estep[e];
+      double* dst = nxt + (int64_t)i * n;
+      for (int j = tid; j < n; j += kGjcThreads) {
+        double v;
+        if (j >= K && j < K + nb) {
+          v = panel[e * kGjB + (j - K)];
+        } else if (se >= 0) {
+          v = q[se * n + j];
+          for (int t = se + 1; t < nb; ++t) v -= mult[e * kGjB + t] * q[t * n + j];
+        } else {
+          v = __ldcg(cur + (int64_t)e * n + j);
+          for (int t = 0; t < nb; ++t) v -= mult[e * kGjB + t] * q[t * n + j];
+        }
+        dst[j] = v;
+      }
+    }
+    grid.sync();
+    double* tb = cur;
+    cur = nxt;
+    nxt = tb;
+  }
+  int* perm = p2e;
+  for (int j = tid; j < n; j += kGjcThreads) perm[j] = j;
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = __ldcg(piv + k);
+      if (p != k) {
+        const int t = perm[k];
+        perm[k] = perm[p];
+        perm[p] = t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = r0; i < r1; ++i)
+    for (int j = tid; j < n; j += kGjcThreads) nxt[(int64_t)i * n + j] = __ldcg(cur + (int64_t)i * n + perm[j]);
+}
+
 // ---- batched coarsest level: one dense block per instance
 template <int BR, int BC>
 __global__ void k_dense_put_batched(int nbr, const int* __restrict__ rp, const int* __restrict__ col,
@@ -1761,16 +2222,50 @@ int coarse_setup(amgc_hierarchy* h, int l) {
   if (L.nl > 0) AMGC_LAUNCH(k_dense_z<<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.Z.p, nu, n, L.Ainv.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   DBuf<int> piv;
-  DBuf<double> f;
   AMGC_TRY(piv.alloc(n));
-  AMGC_TRY(f.alloc(n));
-  const int64_t nn2 = (int64_t)n * n;
-  for (int k = 0; k < n; ++k) {
-    AMGC_LAUNCH(k_gj_pivot<<<1, 1024, 0, s>>>(n, k, L.Ainv.p, piv.p, f.p, h->status.p));
-    AMGC_LAUNCH(k_gj_update<<<div_up(nn2, 256), 256, 0, s>>>(n, k, L.Ainv.p, f.p));
+  // one cooperative launch when the device supports it and two rows fit in shared memory,
+  // else one pivot launch and one update launch per column
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  AMGC_CUDA_TRY(cudaGetDevice(&dev));
+  AMGC_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  AMGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // kGjB pivots per barrier while the panel tables fit in shared memory, else one per barrier
+  const bool blocked = n <= kGjBlockedMax;
+  const void* kern = blocked ? (const void*)k_gj_blocked : (const void*)k_gj_coop;
+  const size_t smem = blocked ? (size_t)n * (3 * kGjB * sizeof(double) + 2 * sizeof(int))
+                              : 2 * (size_t)n * sizeof(double);
+  if (coop && smem <= 200 * 1024) {
+    if (smem > 48 * 1024) AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AMGC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGjcThreads, smem));
   }
-  AMGC_LAUNCH(k_gj_unscramble<<<div_up(n, 128), 128, 0, s>>>(n, piv.p, L.Ainv.p));
-  AMGC_CUDA_TRY(cudaGetLastError());
+  if (per_sm > 0) {
+    // the blocked kernel repeats the panel elimination in every CTA: one CTA per SM
+    const int grid = std::min(n, blocked ? sms : sms * std::min(per_sm, 2));
+    DBuf<double> tmp;
+    AMGC_TRY(tmp.alloc((size_t)n * n));
+    int nn = n;
+    double* a = L.Ainv.p;
+    double* b = tmp.p;
+    int* pv = piv.p;
+    int* st = h->status.p;
+    void* args[] = {&nn, &a, &b, &pv, &st};
+    AMGC_CUDA_TRY(AMGC_LAUNCH(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kGjcThreads), args, smem, s)));
+    // the buffers alternate once per barrier; the permuted result is in the other one
+    const int passes = blocked ? (n + kGjB - 1) / kGjB : n;
+    if (passes % 2 == 0)
+      AMGC_CUDA_TRY(cudaMemcpyAsync(L.Ainv.p, tmp.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  } else {
+    DBuf<double> f;
+    AMGC_TRY(f.alloc(n));
+    const int64_t nn2 = (int64_t)n * n;
+    for (int k = 0; k < n; ++k) {
+      AMGC_LAUNCH(k_gj_pivot<<<1, 1024, 0, s>>>(n, k, L.Ainv.p, piv.p, f.p, h->status.p));
+      AMGC_LAUNCH(k_gj_update<<<div_up(nn2, 256), 256, 0, s>>>(n, k, L.Ainv.p, f.p));
+    }
+    AMGC_LAUNCH(k_gj_unscramble<<<div_up(n, 128), 128, 0, s>>>(n, piv.p, L.Ainv.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
   AMGC_TRY(check_status(h, "coarsest factorisation"));
   AMGC_TRY(alloc_work(L));
   return AMGC_OK;
