@@ -116,10 +116,64 @@ k_rowop6(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const
   if (lane < 6) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * 6 + lane, out);
 }
 
+// CTA per block row for few, long rows of 6-row blocks (the restriction to the coarsest levels:
+// about 60 rows of several hundred blocks).  Warp w takes slots 5w .. 5w+4 of every group of
+// 5 * kLongWarps consecutive blocks with the lane mapping of k_rowop6; the warps' row sums are
+// added in warp order (deterministic).
+constexpr int kLongWarps = 8;
+template <int BC1, int BC2, int MODE, class T>
+__global__ void __launch_bounds__(kLongWarps * 32)
+k_rowop6_long(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const T* __restrict__ v1,
+              const T* __restrict__ x1, const int* __restrict__ rp2, const int* __restrict__ c2,
+              const T* __restrict__ v2, const T* __restrict__ x2, const T* __restrict__ b, const T* __restrict__ x0,
+              const T* __restrict__ dinv, T omega, T* __restrict__ y) {
+  __shared__ T part[kLongWarps][6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row = blockIdx.x;
+  if (row >= nbr) return;
+  const int s = lane / 6, r = lane - 6 * (lane / 6);
+  T acc = T(0);
+  if (s < 5) {
+    const int stride = 5 * kLongWarps;
+    for (int blk = rp1[row] + 5 * wid + s; blk < rp1[row + 1]; blk += stride) {
+      const T* xc = x1 + (int64_t)__ldg(c1 + blk) * BC1;
+      const T* v = v1 + (int64_t)blk * (6 * BC1) + r * BC1;
+#pragma unroll
+      for (int c = 0; c < BC1; ++c) acc = fma(ldg(v + c), ldg(xc + c), acc);
+    }
+    if (rp2 != nullptr) {
+      for (int blk = rp2[row] + 5 * wid + s; blk < rp2[row + 1]; blk += stride) {
+        const T* xc = x2 + (int64_t)__ldg(c2 + blk) * BC2;
+        const T* v = v2 + (int64_t)blk * (6 * BC2) + r * BC2;
+#pragma unroll
+        for (int c = 0; c < BC2; ++c) acc = fma(ldg(v + c), ldg(xc + c), acc);
+      }
+    }
+  }
+  const T a1 = acc + __shfl_down_sync(0xffffffffu, acc, 6);
+  const T a2 = a1 + __shfl_down_sync(0xffffffffu, a1, 12);
+  const T w = a2 + __shfl_down_sync(0xffffffffu, acc, 24);
+  if (lane < 6) part[wid][lane] = w;
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    T out = T(0);
+#pragma unroll
+    for (int q = 0; q < kLongWarps; ++q) out += part[q][threadIdx.x];
+    store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * 6 + threadIdx.x, out);
+  }
+}
+
 template <int BR, int BC1, int BC2, int MODE, class T>
 static int launch_rowop(const BsrV<T>& A1, const T* x1, const BsrV<T>* A2, const T* x2, const T* b, const T* x0,
                         const T* dinv, double omega, T* y, cudaStream_t s) {
   if (A1.nbr == 0) return AMGC_OK;
+  if (BR == 6 && A1.nbr < 2048 && A1.nnzb > 96 * (int64_t)A1.nbr) {   // few long rows: a CTA per row
+    AMGC_LAUNCH(k_rowop6_long<BC1, BC2, MODE, T><<<A1.nbr, kLongWarps * 32, 0, s>>>(
+        A1.nbr, A1.rp, A1.col, A1.val, x1, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr, A2 ? A2->val : nullptr, x2,
+        b, x0, dinv, (T)omega, y));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    return AMGC_OK;
+  }
   if (BR == 6 && BC1 == 6) {
     AMGC_LAUNCH(k_rowop6<BC1, BC2, MODE, T><<<div_up(A1.nbr, kRowWarps), kRowWarps * 32, 0, s>>>(
         A1.nbr, A1.rp, A1.col, A1.val, x1, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr, A2 ? A2->val : nullptr, x2,

@@ -910,22 +910,22 @@ k_spgemm_units(int nunits, const int* __restrict__ urow, const int* __restrict__
   if (SMEM)
     for (int q = lane; q < len * NQ; q += 32) out[q] = acc[q];
 }
-// rows split over units [su0[r], su1[r]): C row = sum of the partials in unit order
+// rows split over units [su0[r], su1[r]): C row = sum of the partials in unit order; one thread
+// per value of a split row (grid.y = split row)
 __global__ void k_spgemm_reduce(int nsplit, const int* __restrict__ srow, const int* __restrict__ su0,
                                 const int* __restrict__ su1, const int64_t* __restrict__ uout,
                                 const int* __restrict__ crp, int nq, const double* __restrict__ scratch,
                                 double* __restrict__ cval) {
-  const int lane = threadIdx.x & 31;
-  const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int r = blockIdx.y;
   if (r >= nsplit) return;
   const int row = srow[r];
   const int64_t c0 = crp[row];
   const int len = (crp[row + 1] - crp[row]) * nq;
-  for (int q = lane; q < len; q += 32) {
-    double t = 0.0;
-    for (int u = su0[r]; u < su1[r]; ++u) t += scratch[uout[u] + q];
-    cval[c0 * nq + q] = t;
-  }
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= len) return;
+  double t = 0.0;
+  for (int u = su0[r]; u < su1[r]; ++u) t += scratch[uout[u] + q];
+  cval[c0 * nq + q] = t;
 }
 
 // Work units of a split product (host tables, copied to the device).
@@ -988,8 +988,8 @@ static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, int cmax, SpUni
         nu, U->d_row.p, U->d_e0.p, U->d_e1.p, U->d_out.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
         C.rowptr.p, C.col.p, C.val.p, scratch.p, cmax));
     const int ns = (int)U->srow.size();
-    if (ns > 0)
-      AMGC_LAUNCH(k_spgemm_reduce<<<div_up((int64_t)ns * 32, 128), 128, 0, s>>>(
+    if (ns > 0 && cmax > 0)   // (an empty product, cmax = 0, has nothing to add up)
+      AMGC_LAUNCH(k_spgemm_reduce<<<dim3(div_up((int64_t)cmax * NQ, 128), ns), 128, 0, s>>>(
           ns, U->d_srow.p, U->d_su0.p, U->d_su1.p, U->d_out.p, C.rowptr.p, NQ, scratch.p, C.val.p));
   } else {
     AMGC_LAUNCH(kern<<<div_up(A.nbr, wpb), wpb * 32, smem, s>>>(
@@ -1196,16 +1196,19 @@ __global__ void k_diag(int nn, const int* __restrict__ rp, const int* __restrict
     atinv[(int64_t)i * BU + r] = 1.0 / (simplec ? as[r] : dg[r]);
   }
 }
-// S_l = Z_l + sum_i B2[l,i] diag(atinv_i) B1[i,l]; Sinv_l = S_l^{-1}
+// S_l = Z_l + sum_i B2[l,i] diag(atinv_i) B1[i,l]; Sinv_l = S_l^{-1}.  One warp per multiplier
+// node: the lanes take the B2 entries of the row (coarse rows have many), the nine partial sums
+// are added across the warp, and lane 0 inverts the block.
 template <int BU>
 __global__ void k_schur(int nl, const int* __restrict__ rp2, const int* __restrict__ c2, const double* __restrict__ v2,
                         const int* __restrict__ rp1, const int* __restrict__ c1, const double* __restrict__ v1,
                         const double* __restrict__ atinv, const double* __restrict__ Z, double* __restrict__ Sinv, int* st) {
-  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int l = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (l >= nl) return;
   double S[9];
-  for (int t = 0; t < 9; ++t) S[t] = Z[(int64_t)l * 9 + t];
-  for (int e = rp2[l]; e < rp2[l + 1]; ++e) {
+  for (int t = 0; t < 9; ++t) S[t] = 0.0;
+  for (int e = rp2[l] + lane; e < rp2[l + 1]; e += 32) {
     const int i = c2[e];
     // find block (i, l) of B1
     int lo = rp1[i], hi = rp1[i + 1] - 1, pos = -1;
@@ -1227,6 +1230,10 @@ __global__ void k_schur(int nl, const int* __restrict__ rp2, const int* __restri
       }
     }
   }
+#pragma unroll
+  for (int t = 0; t < 9; ++t) S[t] = warp_sum(S[t]);
+  if (lane != 0) return;
+  for (int t = 0; t < 9; ++t) S[t] += Z[(int64_t)l * 9 + t];
   // 3x3 inverse by cofactors
   const double c00 = S[4] * S[8] - S[5] * S[7];
   const double c01 = S[5] * S[6] - S[3] * S[8];
@@ -1311,10 +1318,10 @@ int smoother_setup(amgc_hierarchy* h, int l) {
   AMGC_TRY(L.Sinv.alloc((size_t)std::max(L.nl, 1) * 9));
   if (L.nl > 0) {
     if (L.bu == 3)
-      AMGC_LAUNCH(k_schur<3><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, L.B1.rowptr.p,
+      AMGC_LAUNCH(k_schur<3><<<div_up((int64_t)L.nl * 32, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, L.B1.rowptr.p,
                                                    L.B1.col.p, L.B1.val.p, L.atinv.p, L.Z.p, L.Sinv.p, h->status.p));
     else
-      AMGC_LAUNCH(k_schur<6><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, L.B1.rowptr.p,
+      AMGC_LAUNCH(k_schur<6><<<div_up((int64_t)L.nl * 32, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, L.B1.rowptr.p,
                                                    L.B1.col.p, L.B1.val.p, L.atinv.p, L.Z.p, L.Sinv.p, h->status.p));
     AMGC_CUDA_TRY(cudaGetLastError());
     AMGC_TRY(check_status(h, "Schur blocks"));
@@ -1861,8 +1868,7 @@ k_gj_coop(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __restri
 //   row_e <- row_e - sum_t a_e(t) q_t          (pivot row pi_s: q_s - sum_{t>s} a_{pi_s}(t) q_t),
 // which is the per-column elimination with the same operations grouped per super-step.  Each CTA
 // writes its own rows of the next buffer in the row order after the super-step's interchanges.
-constexpr int kGjB = 8;
-constexpr int kGjBlockedMax = 960;
+constexpr int kGjBlockedMax = 960;   // n limit of the blocked kernel (8 pivots per barrier)
 __device__ __forceinline__ void argmax_pair(double& v, int& i) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1874,6 +1880,7 @@ __device__ __forceinline__ void argmax_pair(double& v, int& i) {
     }
   }
 }
+template <int kGjB>
 __global__ void __launch_bounds__(kGjcThreads)
 k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __restrict__ piv, int* st) {
   namespace cg = cooperative_groups;
@@ -1958,11 +1965,17 @@ k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __res
     // transformed pivot rows outside the panel
     for (int j = tid; j < n; j += kGjcThreads) {
       if (j >= K && j < K + nb) continue;
-      for (int t = 0; t < nb; ++t) {
-        const int ep = pent[t];
-        double v = __ldcg(cur + (int64_t)ep * n + j);
-        for (int s2 = 0; s2 < t; ++s2) v -= mult[ep * kGjB + s2] * q[s2 * n + j];
-        q[t * n + j] = v * pinv[t];
+      double orig[kGjB];   // the pivot rows' values in column j, loaded together
+#pragma unroll
+      for (int t = 0; t < kGjB; ++t) orig[t] = t < nb ? __ldcg(cur + (int64_t)pent[t] * n + j) : 0.0;
+#pragma unroll
+      for (int t = 0; t < kGjB; ++t) {
+        if (t < nb) {
+          const int ep = pent[t];
+          double v = orig[t];
+          for (int s2 = 0; s2 < t; ++s2) v -= mult[ep * kGjB + s2] * q[s2 * n + j];
+          q[t * n + j] = v * pinv[t];
+        }
       }
     }
     __syncthreads();
@@ -2231,8 +2244,9 @@ int coarse_setup(amgc_hierarchy* h, int l) {
   AMGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   // kGjB pivots per barrier while the panel tables fit in shared memory, else one per barrier
   const bool blocked = n <= kGjBlockedMax;
-  const void* kern = blocked ? (const void*)k_gj_blocked : (const void*)k_gj_coop;
-  const size_t smem = blocked ? (size_t)n * (3 * kGjB * sizeof(double) + 2 * sizeof(int))
+  const int gjb = 8;
+  const void* kern = !blocked ? (const void*)k_gj_coop : (const void*)k_gj_blocked<8>;
+  const size_t smem = blocked ? (size_t)n * (3 * gjb * sizeof(double) + 2 * sizeof(int))
                               : 2 * (size_t)n * sizeof(double);
   if (coop && smem <= 200 * 1024) {
     if (smem > 48 * 1024) AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2251,7 +2265,7 @@ int coarse_setup(amgc_hierarchy* h, int l) {
     void* args[] = {&nn, &a, &b, &pv, &st};
     AMGC_CUDA_TRY(AMGC_LAUNCH(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kGjcThreads), args, smem, s)));
     // the buffers alternate once per barrier; the permuted result is in the other one
-    const int passes = blocked ? (n + kGjB - 1) / kGjB : n;
+    const int passes = blocked ? (n + gjb - 1) / gjb : n;
     if (passes % 2 == 0)
       AMGC_CUDA_TRY(cudaMemcpyAsync(L.Ainv.p, tmp.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     AMGC_CUDA_TRY(cudaStreamSynchronize(s));
