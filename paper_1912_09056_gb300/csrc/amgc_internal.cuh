@@ -42,6 +42,7 @@ enum : int {
   ST_RANK = 8,
   ST_ROW_TOO_DENSE = 16,
   ST_NONFINITE = 32,
+  ST_TIMEOUT = 64,           // a bounded wait on an asynchronous copy gave up
 };
 
 // ------------------------------------------------------------------ device memory
@@ -134,6 +135,8 @@ struct SellV {
   const int* len = nullptr;
   const int* col = nullptr;
   const T* val = nullptr;
+  unsigned* ctr = nullptr;   // slice counter of the staged FP32 kernel (fine level), else null
+  int* st = nullptr;         // status word for its bounded waits
 };
 template <class T>
 struct LevelV {
@@ -252,6 +255,7 @@ struct amgc_hierarchy {
   // FGMRES workspace
   int m_alloc = 0;
   amgc::DBuf<double> V, Zs, H, givens, gvec, y, wk, xk, rk;
+  amgc::DBuf<unsigned> tma_ctr;    // slice counter of the staged FP32 fine-level apply
   amgc::DBuf<double> partial;      // per-block partial dot products
   std::vector<amgc::LevelV<double>> v64;   // cycle views, FP64
   std::vector<amgc::LevelV<float>> v32;    // cycle views, FP32 (precision 32)

@@ -62,15 +62,21 @@ __global__ void k_bbasis_update(int64_t n, int nrhs, int nk, const double* __res
   for (int k = 0; k < nk; ++k) s = fma(-V[((int64_t)k * nrhs + r) * n + i], h[k], s);
   w[t] = s;
 }
-// v = w / sqrt(nrm2[sys]) (0 on breakdown)
-__global__ void k_bnormalize(int64_t n, int nrhs, const int* __restrict__ row_inst, const double* __restrict__ nrm2,
+// inv[sys] = 1 / sqrt(nrm2[sys]) (0 for a zero norm), so that the vector kernels multiply
+__global__ void k_brsqrt(int nsys, const double* __restrict__ nrm2, double* __restrict__ inv) {
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= nsys) return;
+  const double nr = sqrt(nrm2[sys]);
+  inv[sys] = nr > 0.0 ? 1.0 / nr : 0.0;
+}
+// v = w / sqrt(nrm2[sys]) with inv = k_brsqrt(nrm2) (0 on breakdown)
+__global__ void k_bnormalize(int64_t n, int nrhs, const int* __restrict__ row_inst, const double* __restrict__ inv,
                              const double* __restrict__ w, double* __restrict__ v) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * nrhs) return;
   const int r = (int)(t / n);
   const int64_t i = t - (int64_t)r * n;
-  const double nr = sqrt(nrm2[row_inst[i] * nrhs + r]);
-  v[t] = nr > 0.0 ? w[t] / nr : 0.0;
+  v[t] = w[t] * inv[row_inst[i] * nrhs + r];
 }
 // H[sys][j+1][j] = sqrt(nrm2[sys])
 __global__ void k_bsubdiag(int nsys, int j, int m, const double* __restrict__ nrm2, double* __restrict__ H) {
@@ -141,15 +147,14 @@ __global__ void k_bsolution_update(int64_t n, int nrhs, int nk, const double* __
   for (int k = 0; k < nk; ++k) s = fma(Zs[((int64_t)k * nrhs + r) * n + i], ys[k], s);
   x[t] = s;
 }
-// start of a cycle for the live systems: v0 = r / beta, g = (beta, 0, ...)
-__global__ void k_bcycle_start(int64_t n, int nrhs, const int* __restrict__ row_inst, const double* __restrict__ nrm2,
+// start of a cycle for the live systems: v0 = r / beta with inv = k_brsqrt(beta^2)
+__global__ void k_bcycle_start(int64_t n, int nrhs, const int* __restrict__ row_inst, const double* __restrict__ inv,
                                const double* __restrict__ r, double* __restrict__ v0) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * nrhs) return;
   const int rr = (int)(t / n);
   const int64_t i = t - (int64_t)rr * n;
-  const double b = sqrt(nrm2[row_inst[i] * nrhs + rr]);
-  v0[t] = b > 0.0 ? r[t] / b : 0.0;
+  v0[t] = r[t] * inv[row_inst[i] * nrhs + rr];
 }
 __global__ void k_bgvec(int nsys, int m, const double* __restrict__ nrm2, double* __restrict__ g, int* __restrict__ jd) {
   const int sys = blockIdx.x * blockDim.x + threadIdx.x;
@@ -212,7 +217,7 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
   const int th = 256;
   const int gv = div_up(nv, th);
   const int gs = div_up(nsys, 128);
-  DBuf<double> V, Zs, H, cs, sn, g, y, hk, part, nrm2, beta0, rv;
+  DBuf<double> V, Zs, H, cs, sn, g, y, hk, part, nrm2, beta0, rv, rinv;
   DBuf<int> done, jd, it, cnt;
   AMGC_TRY(V.alloc((size_t)(m + 1) * nv));
   AMGC_TRY(Zs.alloc((size_t)m * nv));
@@ -224,6 +229,7 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
   AMGC_TRY(hk.alloc((size_t)nsys * (m + 1)));
   AMGC_TRY(part.alloc((size_t)(m + 1) * nrhs * nc));
   AMGC_TRY(nrm2.alloc(nsys));
+  AMGC_TRY(rinv.alloc(nsys));
   AMGC_TRY(beta0.alloc(nsys));
   AMGC_TRY(rv.alloc(nv));
   AMGC_TRY(done.alloc(nsys));
@@ -270,7 +276,8 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
   while (total < maxit && live > 0) {
     // cycle start on the current residual rv
     AMGC_TRY(segnorm2(rv.p, nrm2.p));
-    AMGC_LAUNCH(k_bcycle_start<<<gv, th, 0, s>>>(n, nrhs, ri, nrm2.p, rv.p, V.p));
+    AMGC_LAUNCH(k_brsqrt<<<gs, 128, 0, s>>>(nsys, nrm2.p, rinv.p));
+    AMGC_LAUNCH(k_bcycle_start<<<gv, th, 0, s>>>(n, nrhs, ri, rinv.p, rv.p, V.p));
     AMGC_LAUNCH(k_bgvec<<<gs, 128, 0, s>>>(nsys, m, nrm2.p, g.p, jd.p));
     AMGC_CUDA_TRY(cudaMemsetAsync(H.p, 0, (size_t)nsys * (m + 1) * m * sizeof(double), s));
     int jmax = 0;
@@ -289,7 +296,8 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
       }
       AMGC_TRY(segnorm2(w, nrm2.p));
       AMGC_LAUNCH(k_bsubdiag<<<gs, 128, 0, s>>>(nsys, j, m, nrm2.p, H.p));
-      AMGC_LAUNCH(k_bnormalize<<<gv, th, 0, s>>>(n, nrhs, ri, nrm2.p, w, w));
+      AMGC_LAUNCH(k_brsqrt<<<gs, 128, 0, s>>>(nsys, nrm2.p, rinv.p));
+      AMGC_LAUNCH(k_bnormalize<<<gv, th, 0, s>>>(n, nrhs, ri, rinv.p, w, w));
       ++total;
       AMGC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int), s));
       AMGC_LAUNCH(k_bgivens<<<gs, 128, 0, s>>>(nsys, j, m, H.p, cs.p, sn.p, g.p, beta0.p, done.p, jd.p, it.p, total,
@@ -332,6 +340,7 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
     all = all && hd[q];
   }
   h->stats.last_iters = total;
+  if (h->opts.precision == 32) AMGC_TRY(check_status(h, "fgmres_batched"));   // bounded waits of the FP32 cycle
   if (!all) {
     set_error("fgmres_batched: iteration limit reached for some systems");
     return AMGC_NOT_CONVERGED;

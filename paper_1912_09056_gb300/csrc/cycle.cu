@@ -287,6 +287,192 @@ static void launch_sell(const SellV<T>& S, int nbr, const int* rp2, const int* c
                                                                       x2, b, x0, dinv, (T)omega, y));
 }
 
+// ---------------------------------------------------------------- TMA-staged FP32 fine-level apply
+// The FP32 cycle's fine-level K apply streams 200 MB per launch and is bound by memory latency
+// when every lane loads its own values.  Here each warp owns whole 32-row slices and a two-stage
+// shared-memory pipeline: lane 0 moves the next chunk of kTmaChunk slots of the slice (values
+// and block columns, contiguous in the SELL layout) with one bulk asynchronous copy per array,
+// completing on an mbarrier, while the warp computes the current chunk from shared memory.  Only
+// the x gathers go to global memory.  Every wait is bounded: a wait that gives up sets
+// ST_TIMEOUT, drains the copies still in flight (bounded again) and returns.
+constexpr int kTmaChunk = 4;                       // slots per stage
+constexpr int kTmaStages = 3;                      // stages per warp (copies run two chunks ahead)
+constexpr int kTmaWarps = 6;                       // warps per CTA
+constexpr int kTmaStageBytes = kTmaChunk * 9 * 32 * 4 + kTmaChunk * 32 * 4;   // 3x3 FP32 values + columns
+constexpr int kTmaSmem = kTmaWarps * kTmaStages * kTmaStageBytes;
+constexpr unsigned kTmaSpin = 1u << 26;           // polls before a wait gives up
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// true once the phase with the given parity has completed; false after kTmaSpin polls (the
+// non-blocking test, so that the limit bounds the time: about a second at most)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < kTmaSpin; ++it) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+struct TmaMeta {
+  int valid, s, t0, n, last;
+};
+
+// y = op(K x [+ B1 lam]) over the FP32 SELL copy of a 3x3-block matrix (op as in store_row);
+// slices are taken in order from the counter *ctr (zero at launch) by lane 0 of each warp.
+template <int MODE>
+__global__ void __launch_bounds__(kTmaWarps * 32)
+k_sell_tma(int nbr, int nslice, const int* __restrict__ soff, const int* __restrict__ slen,
+           const int* __restrict__ scol, const float* __restrict__ sval, const float* __restrict__ x,
+           const int* __restrict__ rp2, const int* __restrict__ c2, const float* __restrict__ v2,
+           const float* __restrict__ x2, const float* __restrict__ b, const float* __restrict__ x0,
+           const float* __restrict__ dinv, float omega, float* __restrict__ y, unsigned* __restrict__ ctr,
+           int* __restrict__ st) {
+  extern __shared__ __align__(128) unsigned char tma_sh[];
+  __shared__ uint64_t bars[kTmaWarps][kTmaStages];
+  __shared__ TmaMeta meta[kTmaWarps][kTmaStages];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char* stage_base = tma_sh + (size_t)wid * kTmaStages * kTmaStageBytes;
+  uint64_t* bar = bars[wid];
+  TmaMeta* mt = meta[wid];
+  // issue state (lane 0 only)
+  int is_s = 0, is_t0 = 0, is_len = 0;
+  bool is_have = false;
+  auto fetch = [&]() {
+    const int s = (int)atomicAdd(ctr, 1u);
+    is_have = s < nslice;
+    if (is_have) {
+      is_s = s;
+      is_t0 = 0;
+      is_len = slen[s];
+    }
+  };
+  auto issue = [&](int stg) {
+    TmaMeta m{0, 0, 0, 0, 0};
+    if (is_have) {
+      const int n = min(kTmaChunk, is_len - is_t0);
+      m = TmaMeta{1, is_s, is_t0, n, is_t0 + n >= is_len ? 1 : 0};
+      const int64_t g = (int64_t)soff[is_s] + is_t0;
+      unsigned char* dv = stage_base + (size_t)stg * kTmaStageBytes;
+      unsigned char* dc = dv + kTmaChunk * 9 * 32 * 4;
+      const unsigned bv = (unsigned)n * 9u * 32u * 4u, bc = (unsigned)n * 32u * 4u;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar[stg], bv + bc);
+      if (n > 0) {
+        bulk_g2s(dv, sval + g * 288, bv, &bar[stg]);
+        bulk_g2s(dc, scol + g * 32, bc, &bar[stg]);
+      }
+      is_t0 += n;
+      if (is_t0 >= is_len) fetch();
+    }
+    mt[stg] = m;
+  };
+  if (lane == 0) {
+    for (int q = 0; q < kTmaStages; ++q) mbar_init(&bar[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fetch();
+    for (int q = 0; q + 1 < kTmaStages; ++q) issue(q);
+  }
+  __syncwarp();
+  unsigned phase = 0u;   // bit q: parity of the next phase of stage q
+  float acc[3] = {0.f, 0.f, 0.f};
+  for (int k = 0;; ++k) {
+    const int stg = k % kTmaStages;
+    const TmaMeta m = mt[stg];
+    if (!m.valid) break;
+    if (lane == 0) issue((k + kTmaStages - 1) % kTmaStages);   // the stage chunk k-1 used
+    __syncwarp();
+    if (!mbar_wait(&bar[stg], (phase >> stg) & 1u)) {
+      // give up: record it, wait (bounded) for this warp's copies still in flight, leave
+      if (lane == 0) {
+        atomicOr(st, ST_TIMEOUT);
+        for (int q = 0; q < kTmaStages; ++q)
+          if (mt[q].valid) mbar_wait(&bar[q], (phase >> q) & 1u);
+      }
+      __syncwarp();
+      return;
+    }
+    phase ^= 1u << stg;
+    const float* vs = reinterpret_cast<const float*>(stage_base + (size_t)stg * kTmaStageBytes);
+    const int* cs = reinterpret_cast<const int*>(vs + kTmaChunk * 9 * 32);
+    // all x gathers of the chunk first (slots past n read x[0..2], never used), then the FMAs
+    float xr[kTmaChunk][3];
+#pragma unroll
+    for (int t = 0; t < kTmaChunk; ++t) {
+      const float* xc = x + 3 * (int64_t)(t < m.n ? cs[t * 32 + lane] : 0);
+      xr[t][0] = __ldg(xc);
+      xr[t][1] = __ldg(xc + 1);
+      xr[t][2] = __ldg(xc + 2);
+    }
+#pragma unroll
+    for (int t = 0; t < kTmaChunk; ++t) {
+      if (t < m.n) {
+        const float* v = vs + t * 288 + lane;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          acc[q] = fmaf(v[(3 * q) * 32], xr[t][0], acc[q]);
+          acc[q] = fmaf(v[(3 * q + 1) * 32], xr[t][1], acc[q]);
+          acc[q] = fmaf(v[(3 * q + 2) * 32], xr[t][2], acc[q]);
+        }
+      }
+    }
+    if (m.last) {
+      const int row = m.s * 32 + lane;
+      if (row < nbr) {
+        if (rp2 != nullptr) {
+          for (int e = rp2[row]; e < rp2[row + 1]; ++e) {
+            const float* blk = v2 + (int64_t)e * 9;
+            const float* d = x2 + 3 * (int64_t)c2[e];
+            const float d0 = d[0], d1 = d[1], dd2 = d[2];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[q] = fmaf(blk[3 * q], d0, fmaf(blk[3 * q + 1], d1, fmaf(blk[3 * q + 2], dd2, acc[q])));
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) store_row<MODE, float>(y, b, x0, dinv, omega, (int64_t)row * 3 + q, acc[q]);
+      }
+      acc[0] = acc[1] = acc[2] = 0.f;
+    }
+    __syncwarp();
+  }
+}
+
+template <int MODE>
+static int launch_sell_tma(const SellV<float>& S, int nbr, const BsrV<float>* A2, const float* x, const float* x2,
+                           const float* b, const float* x0, const float* dinv, double omega, float* y,
+                           cudaStream_t s) {
+  int dev = 0, sms = 0, per_sm = 0;
+  AMGC_CUDA_TRY(cudaGetDevice(&dev));
+  AMGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  AMGC_CUDA_TRY(cudaFuncSetAttribute(k_sell_tma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmaSmem));
+  AMGC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell_tma<MODE>, kTmaWarps * 32, kTmaSmem));
+  const int grid = std::max(1, std::min(div_up(S.nslice, kTmaWarps), sms * std::max(per_sm, 1)));
+  AMGC_CUDA_TRY(cudaMemsetAsync(S.ctr, 0, sizeof(unsigned), s));
+  AMGC_LAUNCH(k_sell_tma<MODE><<<grid, kTmaWarps * 32, kTmaSmem, s>>>(
+      nbr, S.nslice, S.off, S.len, S.col, S.val, x, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr,
+      A2 ? A2->val : nullptr, x2, b, x0, dinv, (float)omega, y, S.ctr, S.st));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
 // tpr <= 0: the default (one thread per row in FP64, which is FMA-bound; two in FP32)
 template <int MODE, class T>
 static int sell_apply(const SellV<T>& S, int nbr, const BsrV<T>* A2, const T* x, const T* x2, const T* b, const T* x0,
@@ -316,6 +502,12 @@ static int sell_apply(const SellV<T>& S, int nbr, const BsrV<T>* A2, const T* x,
 template <int MODE, class T>
 static int mapped_apply(const BsrV<T>& A, const SellV<T>& S, int map, const BsrV<T>* A2, const T* x, const T* x2,
                         const T* b, const T* x0, const T* dinv, double omega, T* y, cudaStream_t s) {
+  // map 3: the staged kernel for the FP32 fine-level 3x3 K (an autotuner candidate)
+  if constexpr (sizeof(T) == 4 && MODE != 1 && MODE != 4) {
+    if (map == 3 && S.ctr != nullptr && S.nslice > 0 && S.br == 3 && S.bc == 3)
+      return launch_sell_tma<MODE>(S, A.nbr, A2, x, x2, b, x0, dinv, omega, y, s);
+  }
+  if (map == 3) map = -1;
   if (S.nslice > 0 && map != 0) return sell_apply<MODE, T>(S, A.nbr, A2, x, x2, b, x0, dinv, omega, y, s, map);
   return rowop<MODE, T>(A, x, A2, x2, b, x0, dinv, omega, y, s);
 }
@@ -900,6 +1092,11 @@ int make_views(amgc_hierarchy* h) {
     v.P = bview<float>(L.P, F.P.p);
     v.R = bview<float>(L.R, F.R.p);
     v.Ks = sview<float>(L.Ks, F.Ks.p);
+    if (l == 0 && L.Ks.nslice > 0 && L.Ks.br == 3 && L.Ks.bc == 3) {
+      if (!h->tma_ctr.p) AMGC_TRY(h->tma_ctr.alloc(1));
+      v.Ks.ctr = h->tma_ctr.p;
+      v.Ks.st = h->status.p;
+    }
     v.Ps = sview<float>(L.Ps, F.Ps.p);
     v.Rs = sview<float>(L.Rs, F.Rs.p);
     v.kmap = L.kmap[1]; v.pmap = L.pmap[1]; v.rmap = L.rmap[1];
@@ -913,7 +1110,8 @@ int make_views(amgc_hierarchy* h) {
 
 // ------------------------------------------------------------------ row-mapping autotuner
 // Times every candidate row mapping of one apply (2 warm-up launches, 5 timed, CUDA events on
-// the hierarchy's stream) and returns the fastest: 0 warp per row, 1/2 SELL threads per row.
+// the hierarchy's stream) and returns the fastest: 0 warp per row, 1/2 SELL threads per row,
+// 3 the staged FP32 kernel (fine-level 3x3 K only).
 template <int MODE, class T>
 static int tune_one(amgc_hierarchy* h, const BsrV<T>& A, const SellV<T>& S, const BsrV<T>* A2, const T* x,
                     const T* x2, const T* b, const T* dinv, T* y, int* best) {
@@ -922,8 +1120,9 @@ static int tune_one(amgc_hierarchy* h, const BsrV<T>& A, const SellV<T>& S, cons
   AMGC_CUDA_TRY(cudaEventCreate(&e1));
   float best_ms = 1e30f;
   *best = 0;
-  for (int cand = 0; cand < 3; ++cand) {
+  for (int cand = 0; cand < 4; ++cand) {
     if (cand > 0 && S.nslice == 0) break;
+    if (cand == 3 && S.ctr == nullptr) break;
     for (int rep = 0; rep < 7; ++rep) {
       if (rep == 2) AMGC_CUDA_TRY(cudaEventRecord(e0, h->stream));
       AMGC_TRY((mapped_apply<MODE, T>(A, S, cand, A2, x, x2, b, x, dinv, 1.0, y, h->stream)));
@@ -1029,11 +1228,14 @@ __global__ void k_dot_final(int nparts, const double* __restrict__ part, double*
     if (threadIdx.x == 0) *out = v;
   }
 }
-// y = src / sqrt(*nrm2)
+// y = src / sqrt(*nrm2), the reciprocal formed once per block
 __global__ void k_normalize(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ src,
                             double* __restrict__ y) {
+  __shared__ double inv;
+  if (threadIdx.x == 0) inv = 1.0 / sqrt(*nrm2);
+  __syncthreads();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = src[i] / sqrt(*nrm2);
+  if (i < n) y[i] = src[i] * inv;
 }
 
 int dot(amgc_hierarchy* h, int64_t n, const double* a, const double* b, const double* wgt, double* out_dev) {

@@ -138,20 +138,31 @@ __global__ void k_solution_update(int64_t n, int nk, const double* __restrict__ 
   for (int k = 0; k < nk; ++k) s = fma(Zs[(int64_t)k * n + i], ys[k], s);
   x[i] = s;
 }
+// 1 / sqrt(nrm2) formed once per block (an FP64 division per element would cost more than the
+// memory traffic of these kernels); 0 when nrm2 is 0
+__device__ __forceinline__ double block_rsqrt(const double* nrm2) {
+  __shared__ double inv;
+  if (threadIdx.x == 0) {
+    const double nr = sqrt(*nrm2);
+    inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  }
+  __syncthreads();
+  return inv;
+}
 // v = w / sqrt(nrm2) (zero vector on breakdown)
 __global__ void k_arnoldi_normalize(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ w,
                                     double* __restrict__ v) {
-  const double nr = sqrt(*nrm2);
+  const double inv = block_rsqrt(nrm2);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) v[i] = nr > 0.0 ? w[i] / nr : 0.0;
+  if (i < n) v[i] = w[i] * inv;
 }
 // start of a cycle: v0 = r / beta, g = (beta, 0, ...)
 __global__ void k_cycle_start(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ r,
                               double* __restrict__ v0, double* __restrict__ g, int m) {
-  const double beta = sqrt(*nrm2);
+  const double inv = block_rsqrt(nrm2);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) v0[i] = r[i] / beta;
-  if (i <= m) g[i] = i == 0 ? beta : 0.0;
+  if (i < n) v0[i] = r[i] * inv;
+  if (i <= m) g[i] = i == 0 ? sqrt(*nrm2) : 0.0;
 }
 // back substitution H(0:k,0:k) y = g(0:k) (single thread)
 __global__ void k_backsolve(int k, int m, const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y) {

@@ -134,7 +134,9 @@ int check_status(amgc_hierarchy* h, const char* where) {
   if (st & ST_RANK) m += " rank-deficient nullspace on an aggregate;";
   if (st & ST_ROW_TOO_DENSE) m += " product row exceeds the hash capacity;";
   if (st & ST_NONFINITE) m += " non-finite value;";
+  if (st & ST_TIMEOUT) m += " a bounded wait on an asynchronous copy gave up;";
   set_error(m);
+  if (st & ST_TIMEOUT) return AMGC_TIMEOUT;
   if (st & (ST_SINGULAR | ST_RANK)) return AMGC_ESINGULAR;
   return AMGC_EINVAL;
 }

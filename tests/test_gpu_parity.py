@@ -231,3 +231,21 @@ def test_autotuned_mappings_and_graph_replay_give_the_same_cycle():
     assert (torch.linalg.norm(z0 - z1) / torch.linalg.norm(z0)).item() <= 1e-13
     h0.close()
     h1.close()
+
+
+def test_fp32_autotuned_mappings_give_the_same_cycle():
+    """The FP32 row-mapping candidates (warp, SELL with one or two threads, the shared-memory
+    staged kernel) differ only in FP32 rounding of the same sums."""
+    make, opts = CASES["small_tilted_partial_SA"]
+    prob = make()
+    h0 = amgc.setup(prob, precision=32, **opts)
+    h1 = amgc.setup(prob, precision=32, autotune=1, **opts)
+    rng = np.random.default_rng(6)
+    r = torch.from_numpy(rng.standard_normal(prob.n)).cuda()
+    z0, z1 = torch.empty_like(r), torch.empty_like(r)
+    h0.vcycle(r, z0)
+    h1.vcycle(r, z1)
+    torch.cuda.synchronize()
+    assert (torch.linalg.norm(z0 - z1) / torch.linalg.norm(z0)).item() <= 1e-5
+    h0.close()
+    h1.close()
