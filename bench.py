@@ -51,6 +51,17 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest value over all ranks: replicas run side by side, the slowest sets the time."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_name():
     from paper_1912_09056_gb300.problem import WORKLOADS
     return WORKLOADS[WORKLOAD]["name"]
@@ -217,10 +228,7 @@ def main_gpu(args):
         dist.barrier()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     clk = clocks.stop() if clocks else None
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
 
     # ---- breakdown on one hierarchy (outside the timed region)
     h = amgc.setup(dprob, opts)
@@ -403,10 +411,7 @@ def main_gpu(args):
         he.close()
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
