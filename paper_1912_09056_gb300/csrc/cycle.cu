@@ -618,22 +618,29 @@ k_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp,
   if (lane < BU) u[(int64_t)i * BU + lane] -= alpha * atinv[(int64_t)i * BU + lane] * out;
 }
 // multiplier restriction / prolongation through P-hat^lambda (weights w_l, aggregate lagg_l)
+// (restriction: one warp per coarse multiplier node, the lanes over its members)
 template <class T>
 __global__ void k_restrict_lm(int nlc, const int* __restrict__ ptr, const int* __restrict__ idx, const T* __restrict__ w,
                               const T* __restrict__ r, T* __restrict__ out) {
-  const int L = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int L = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (L >= nlc) return;
   T s0 = 0, s1 = 0, s2 = 0;
-  for (int e = ptr[L]; e < ptr[L + 1]; ++e) {
+  for (int e = ptr[L] + lane; e < ptr[L + 1]; e += 32) {
     const int l = idx[e];
     const T wl = w[l];
     s0 += wl * r[3 * l];
     s1 += wl * r[3 * l + 1];
     s2 += wl * r[3 * l + 2];
   }
-  out[3 * L] = s0;
-  out[3 * L + 1] = s1;
-  out[3 * L + 2] = s2;
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    out[3 * L] = s0;
+    out[3 * L + 1] = s1;
+    out[3 * L + 2] = s2;
+  }
 }
 template <class T>
 __global__ void k_prolong_lm(int nl, const int* __restrict__ lagg, const T* __restrict__ w, const T* __restrict__ c,
@@ -783,7 +790,7 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
   // restrict: C.b = [R r_u ; R^lambda r_lambda]
   AMGC_TRY((mapped_apply<0, T>(L.R, L.Rs, L.rmap, nullptr, L.r, nullptr, nullptr, nullptr, nullptr, 0.0, C.b, s)));
   if (C.nl > 0) {
-    AMGC_LAUNCH(k_restrict_lm<T><<<div_up(C.nl, 128), 128, 0, s>>>(C.nl, L.rl_ptr, L.rl_idx, L.pl_w, L.r + nu,
+    AMGC_LAUNCH(k_restrict_lm<T><<<div_up((int64_t)C.nl * 32, 128), 128, 0, s>>>(C.nl, L.rl_ptr, L.rl_idx, L.pl_w, L.r + nu,
                                                                    C.b + C.nu()));
     AMGC_CUDA_TRY(cudaGetLastError());
   }
@@ -905,7 +912,7 @@ static int vcycle_transposed(amgc_hierarchy* h, int l, const double* y, double* 
   AMGC_TRY((lm_op<0, double>(L, x, y + nu, x + nu, 0.0, L.r + nu, s, true)));
   AMGC_TRY((rowop<0, double>(L.R, L.r, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, C.b, s)));
   if (C.nl > 0)
-    AMGC_LAUNCH(k_restrict_lm<double><<<div_up(C.nl, 128), 128, 0, s>>>(C.nl, L.rl_ptr, L.rl_idx, L.pl_w, L.r + nu,
+    AMGC_LAUNCH(k_restrict_lm<double><<<div_up((int64_t)C.nl * 32, 128), 128, 0, s>>>(C.nl, L.rl_ptr, L.rl_idx, L.pl_w, L.r + nu,
                                                                         C.b + C.nu()));
   AMGC_TRY(vcycle_transposed(h, l + 1, C.b, C.x));
   if (L.Ps.nslice > 0)

@@ -1947,13 +1947,16 @@ k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __res
       for (int c = tid; c < nb; c += kGjcThreads) ppan[c] = panel[ep * kGjB + c];
       for (int e = tid; e < n; e += kGjcThreads) mult[e * kGjB + t] = panel[e * kGjB + t];
       __syncthreads();
-      for (int idx = tid; idx < n * nb; idx += kGjcThreads) {
-        const int e = idx / nb, c = idx - e * nb;
+      // (a full panel is the common case: constant stride, no division in the index)
+      const int w = nb == kGjB ? kGjB : nb;
+      for (int idx = tid; idx < n * w; idx += kGjcThreads) {
+        const int e = nb == kGjB ? idx / kGjB : idx / w;
+        const int c = idx - e * w;
         double* pe = panel + e * kGjB + c;
         if (e == ep) *pe = c == t ? inv : ppan[c] * inv;
         else {
           const double a = mult[e * kGjB + t];
-          *pe = c == t ? -a * inv : *pe - a * (ppan[c] * inv);
+          *pe = c == t ? -a * inv : fma(-a, ppan[c] * inv, *pe);
         }
       }
       if (tid == 0) {
