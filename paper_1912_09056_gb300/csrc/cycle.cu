@@ -289,11 +289,11 @@ static void launch_sell(const SellV<T>& S, int nbr, const int* rp2, const int* c
 
 // ---------------------------------------------------------------- TMA-staged FP32 fine-level apply
 // The FP32 cycle's fine-level K apply streams 200 MB per launch and is bound by memory latency
-// when every lane loads its own values.  Here each warp owns whole 32-row slices and a two-stage
-// shared-memory pipeline: lane 0 moves the next chunk of kTmaChunk slots of the slice (values
-// and block columns, contiguous in the SELL layout) with one bulk asynchronous copy per array,
-// completing on an mbarrier, while the warp computes the current chunk from shared memory.  Only
-// the x gathers go to global memory.  Every wait is bounded: a wait that gives up sets
+// when every lane loads its own values.  Here each warp owns whole 32-row slices and a
+// kTmaStages-deep shared-memory pipeline: lane 0 moves the next chunks of kTmaChunk slots of the
+// slice (values and block columns, contiguous in the SELL layout) with one bulk asynchronous copy
+// per array, completing on an mbarrier, while the warp computes the current chunk from shared
+// memory.  Only the x gathers go to global memory.  Every wait is bounded: a wait that gives up sets
 // ST_TIMEOUT, drains the copies still in flight (bounded again) and returns.
 constexpr int kTmaChunk = 4;                       // slots per stage
 constexpr int kTmaStages = 3;                      // stages per warp (copies run two chunks ahead)
