@@ -1944,7 +1944,7 @@ k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __res
       __syncthreads();
       const int ep = pent[t];
       const double inv = pinv[t];
-      for (int c = tid; c < nb; c += kGjcThreads) ppan[c] = panel[ep * kGjB + c];
+      for (int c = tid; c < nb; c += kGjcThreads) ppan[c] = c == t ? inv : panel[ep * kGjB + c] * inv;   // new pivot row
       for (int e = tid; e < n; e += kGjcThreads) mult[e * kGjB + t] = panel[e * kGjB + t];
       __syncthreads();
       // (a full panel is the common case: constant stride, no division in the index)
@@ -1953,10 +1953,10 @@ k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __res
         const int e = nb == kGjB ? idx / kGjB : idx / w;
         const int c = idx - e * w;
         double* pe = panel + e * kGjB + c;
-        if (e == ep) *pe = c == t ? inv : ppan[c] * inv;
+        if (e == ep) *pe = ppan[c];
         else {
           const double a = mult[e * kGjB + t];
-          *pe = c == t ? -a * inv : fma(-a, ppan[c] * inv, *pe);
+          *pe = c == t ? -a * inv : fma(-a, ppan[c], *pe);
         }
       }
       if (tid == 0) {
