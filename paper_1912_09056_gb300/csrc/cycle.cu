@@ -235,7 +235,7 @@ k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, cons
        const T* __restrict__ dinv, T omega, T* __restrict__ y) {
   constexpr int BS = BR * BC;
   constexpr int RPW = 32 / TPR;                                // rows per warp
-  const int gt = blockIdx.x * kSellThreads + threadIdx.x;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int part = lane / RPW;                                 // slot residue handled by this lane
   const int row = (gt >> 5) * RPW + (lane % RPW);
@@ -282,9 +282,12 @@ k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, cons
 template <int BR, int BC, int MODE, class T, int TPR>
 static void launch_sell(const SellV<T>& S, int nbr, const int* rp2, const int* c2, const T* v2, const T* x,
                         const T* x2, const T* b, const T* x0, const T* dinv, double omega, T* y, cudaStream_t s) {
-  const int g = div_up((int64_t)nbr * TPR, kSellThreads);
-  AMGC_LAUNCH(k_sell<BR, BC, MODE, T, TPR><<<g, kSellThreads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2,
-                                                                      x2, b, x0, dinv, (T)omega, y));
+  // FP64 is bound by each SM's FMA rate and all CTAs fit at once: two-warp CTAs spread the row
+  // groups over the SMs more evenly than four-warp ones
+  const int threads = sizeof(T) == 8 ? kSellThreads / 2 : kSellThreads;
+  const int g = div_up((int64_t)nbr * TPR, threads);
+  AMGC_LAUNCH(k_sell<BR, BC, MODE, T, TPR><<<g, threads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
+                                                                 b, x0, dinv, (T)omega, y));
 }
 
 // ---------------------------------------------------------------- TMA-staged FP32 fine-level apply

@@ -854,7 +854,10 @@ __global__ void k_row_maxlen(int nrow, const int* __restrict__ rp, int* __restri
 // of one group touch distinct C values (a B row has distinct columns).  SMEM: the copy lives in shared memory and is
 // written out at the end; otherwise the warp accumulates in place in global memory (rows too
 // long for enough warps per CTA).
-template <int BR, int BK, int BC, bool SMEM>
+// SYM (square blocks, C known to be block-symmetric): only the blocks on and above the diagonal
+// are formed (B entries with a column below the row are skipped before the work items are
+// dealt out); k_sym_mirror then fills the lower blocks with the transposed upper ones.
+template <int BR, int BK, int BC, bool SMEM, bool SYM>
 __global__ void __launch_bounds__(256)
 k_spgemm_units(int nunits, const int* __restrict__ urow, const int* __restrict__ ue0, const int* __restrict__ ue1,
                const int64_t* __restrict__ uout, const int* __restrict__ arp, const int* __restrict__ acol,
@@ -863,6 +866,7 @@ k_spgemm_units(int nunits, const int* __restrict__ urow, const int* __restrict__
                double* __restrict__ cval, double* __restrict__ scratch, int cmax) {
   constexpr int NQ = BR * BC;
   extern __shared__ double sp_acc[];
+  __shared__ int taken[8][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int u = blockIdx.x * (blockDim.x >> 5) + wid;
   if (u >= nunits) return;
@@ -880,8 +884,10 @@ k_spgemm_units(int nunits, const int* __restrict__ urow, const int* __restrict__
     const int t0 = brp[k], t1 = brp[k + 1];
     for (int tc = t0; tc < t1; tc += 32) {
       int pos = 0;
+      bool use = false;
       if (tc + lane < t1) {
         const int c = bcol[tc + lane];
+        use = !SYM || c >= row;
         int lo = c0, hi = c1 - 1;
         while (lo < hi) {
           const int mid = (lo + hi) >> 1;
@@ -890,15 +896,20 @@ k_spgemm_units(int nunits, const int* __restrict__ urow, const int* __restrict__
         }
         pos = lo - c0;
       }
-      const int nt = min(32, t1 - tc);
+      // the entries taken (all of them unless SYM), listed in lane order
+      const unsigned take = __ballot_sync(0xffffffffu, use);
+      const int nt = __popc(take);
+      if (use) taken[wid][__popc(take & ((1u << lane) - 1u))] = lane;
+      __syncwarp();
       for (int wb = 0; wb < nt * NQ; wb += 32) {
         const int w = wb + lane;
         const int t = w / NQ;
-        const int p = __shfl_sync(0xffffffffu, pos, t < nt ? t : 0);
+        const int src = t < nt ? taken[wid][t] : 0;   // lane holding the t-th entry taken
+        const int p = __shfl_sync(0xffffffffu, pos, src);
         if (w < nt * NQ) {
           const int qe = w - t * NQ;
           const int i = qe / BC, j = qe - i * BC;
-          const double* bb = bval + (int64_t)(tc + t) * BK * BC + j;
+          const double* bb = bval + (int64_t)(tc + src) * BK * BC + j;
           const double* ai = ae + i * BK;
           double sacc = acc[p * NQ + qe];
 #pragma unroll
@@ -928,6 +939,29 @@ __global__ void k_spgemm_reduce(int nsplit, const int* __restrict__ srow, const 
   double t = 0.0;
   for (int u = su0[r]; u < su1[r]; ++u) t += scratch[uout[u] + q];
   cval[c0 * nq + q] = t;
+}
+
+// lower blocks of a block-symmetric product: C[I][J] = C[J][I]^T for J < I (one warp per row)
+template <int B>
+__global__ void k_sym_mirror(int nrow, const int* __restrict__ crp, const int* __restrict__ ccol,
+                             double* __restrict__ cval) {
+  const int lane = threadIdx.x & 31;
+  const int I = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (I >= nrow) return;
+  for (int e = crp[I] + lane; e < crp[I + 1]; e += 32) {
+    const int J = ccol[e];
+    if (J >= I) continue;
+    int lo = crp[J], hi = crp[J + 1] - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ccol[mid] < I) lo = mid + 1;
+      else hi = mid;
+    }
+    const double* up = cval + (int64_t)lo * B * B;
+    double* dn = cval + (int64_t)e * B * B;
+    for (int r = 0; r < B; ++r)
+      for (int c = 0; c < B; ++c) dn[r * B + c] = up[c * B + r];
+  }
 }
 
 // Work units of a split product (host tables, copied to the device).
@@ -968,7 +1002,7 @@ static int upload(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
 
 // C values: with shared-memory row accumulators when the longest C row fits (cmax), over the
 // unit tables U when the product is split, else with the global-memory accumulation kernel.
-template <int BR, int BK, int BC>
+template <int BR, int BK, int BC, bool SYM = false>
 static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, int cmax, SpUnits* U, cudaStream_t s) {
   constexpr int NQ = BR * BC;
   const size_t per_warp = (size_t)std::max(cmax, 1) * NQ * sizeof(double);
@@ -979,9 +1013,9 @@ static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, int cmax, SpUni
   const int wpb = smem_acc ? 8 : kGemmWarps;
   const size_t smem = smem_acc ? (size_t)wpb * per_warp : 0;
   if (smem_acc)
-    AMGC_CUDA_TRY(cudaFuncSetAttribute(k_spgemm_units<BR, BK, BC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kUnitSmem));
-  auto kern = smem_acc ? k_spgemm_units<BR, BK, BC, true> : k_spgemm_units<BR, BK, BC, false>;
+    AMGC_CUDA_TRY(cudaFuncSetAttribute(k_spgemm_units<BR, BK, BC, true, SYM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kUnitSmem));
+  auto kern = smem_acc ? k_spgemm_units<BR, BK, BC, true, SYM> : k_spgemm_units<BR, BK, BC, false, SYM>;
   DBuf<double> scratch;
   if (U) {
     const int nu = (int)U->row.size();
@@ -998,11 +1032,14 @@ static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, int cmax, SpUni
         A.nbr, nullptr, nullptr, nullptr, nullptr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
         C.rowptr.p, C.col.p, C.val.p, nullptr, cmax));
   }
+  if (SYM)
+    AMGC_LAUNCH(k_sym_mirror<BR><<<div_up((int64_t)A.nbr * 32, 128), 128, 0, s>>>(A.nbr, C.rowptr.p, C.col.p, C.val.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
 
-static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C) {
+// sym: C = A B is known to be block-symmetric (a Galerkin product P^T K P): square blocks only
+static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C, bool sym = false) {
   cudaStream_t s = h->stream;
   if (A.bc != B.br || A.nbc != B.nbr) {
     set_error("spgemm: shape mismatch");
@@ -1085,6 +1122,8 @@ static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C) {
   AMGC_CUDA_TRY(cudaGetLastError());
   const int br = A.br, bk = A.bc, bc = B.bc;
   SpUnits* up = U.get();
+  if (sym && br == 6 && bk == 3 && bc == 6) return spgemm_numeric<6, 3, 6, true>(A, B, C, cmax, up, s);
+  if (sym && br == 6 && bk == 6 && bc == 6) return spgemm_numeric<6, 6, 6, true>(A, B, C, cmax, up, s);
 #define AMGC_GEMM_CASE(R, K, C_)                                   \
   if (br == R && bk == K && bc == C_) return spgemm_numeric<R, K, C_>(A, B, C, cmax, up, s);
   AMGC_GEMM_CASE(3, 3, 6)
@@ -1588,7 +1627,7 @@ int coarsen_level(amgc_hierarchy* h, int l) {
   {
     DBsr AP;
     AMGC_TRY(spgemm(h, L.K, L.P, AP));
-    AMGC_TRY(spgemm(h, L.R, AP, C.K));
+    AMGC_TRY(spgemm(h, L.R, AP, C.K, true));   // K_c = P^T K P is symmetric
   }
   if (L.nl > 0) {
     DBsr B1P, B2P;
