@@ -27,14 +27,16 @@ k_multidot(int64_t n, int nk, const double* __restrict__ V, const double* __rest
   const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
   for (int k = wid; k < nk; k += kMdWarps) {
     const double* v = V + (int64_t)k * n;
-    double s0 = 0.0, s1 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four independent chains: 8 loads in flight
     int64_t i = b0 + lane;
-    for (; i + 32 < b1; i += 64) {
+    for (; i + 96 < b1; i += 128) {
       s0 = fma(v[i], w[i], s0);
       s1 = fma(v[i + 32], w[i + 32], s1);
+      s2 = fma(v[i + 64], w[i + 64], s2);
+      s3 = fma(v[i + 96], w[i + 96], s3);
     }
-    if (i < b1) s0 = fma(v[i], w[i], s0);
-    const double t = warp_sum(s0 + s1);
+    for (; i < b1; i += 32) s0 = fma(v[i], w[i], s0);
+    const double t = warp_sum((s0 + s1) + (s2 + s3));
     if (lane == 0) part[(int64_t)blockIdx.x * nk + k] = t;
   }
 }
@@ -65,6 +67,7 @@ k_basis_update(int64_t n, int nk, const double* __restrict__ V, const double* __
   double s = 0.0;
   if (i < n) {
     s = w[i];
+#pragma unroll 8
     for (int k = 0; k < nk; ++k) s = fma(-V[(int64_t)k * n + i], hs[k], s);
     w[i] = s;
   }
