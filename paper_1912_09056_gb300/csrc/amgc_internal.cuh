@@ -208,6 +208,11 @@ struct Level {
 
   // CheapSIMPLE data
   double lam_max = 0.0, omega_j = 0.0;
+  // lambda_max power iteration running on the auxiliary stream (single-instance levels): its
+  // buffers, and the event that marks its end; joined before the smoothed prolongator
+  DBuf<double> lmx_x, lmx_y, lmx_sc, lmx_part;
+  cudaEvent_t lmx_done = nullptr;
+  bool smoother_pending = false;
   DBuf<double> kdiag, dinv, atinv;  // nu: pointwise diagonal of K, its inverse, A~^-1
   DBuf<double> jdinv;               // nu: omega_J D^-1 (omega_J per instance when batched)
   std::vector<double> inst_lam_max; // per instance (batched hierarchies)
@@ -265,6 +270,7 @@ struct amgc_hierarchy {
   cudaGraphExec_t cycle_graph[2] = {nullptr, nullptr};
   long long cycle_graph_kernels[2] = {0, 0};
   cudaStream_t capture_stream = nullptr;
+  cudaStream_t aux_stream = nullptr;    // setup work overlapped with the main stream
   amgc::DBuf<double> cyc_in, cyc_out;      // fixed FP64 input/output of the captured FP64 cycle
   // batched FGMRES workspace
   amgc::DBuf<int> b_chunk_row0, b_chunk_row1, b_chunk_ptr, b_row_inst;
@@ -326,6 +332,9 @@ int prof_flush(amgc_hierarchy* h);
 // sparse kernels (cycle.cu)
 int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
 int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out);
+int lambda_max_start(amgc_hierarchy* h, Level& L);
+int lambda_max_finish(amgc_hierarchy* h, Level& L, double* out);
+int smoother_finish(amgc_hierarchy* h, int l);
 int lambda_max_instances(amgc_hierarchy* h, Level& L, std::vector<double>& lam);
 int schur_damping_setup(amgc_hierarchy* h, Level& L);
 int dot(amgc_hierarchy* h, int64_t n, const double* a, const double* b, const double* wgt, double* out_dev);

@@ -545,6 +545,12 @@ void amgc_destroy(struct amgc_hierarchy* h) {
   if (!h) return;
   StreamScope scope_(h->stream);
   cudaStreamSynchronize(h->stream);
+  if (h->aux_stream) {
+    cudaStreamSynchronize(h->aux_stream);
+    cudaStreamDestroy(h->aux_stream);
+  }
+  for (auto& L : h->L)
+    if (L.lmx_done) cudaEventDestroy(L.lmx_done);
   for (auto& e : h->prof_ev) cudaEventDestroy(e);
   for (auto& g : h->cycle_graph)
     if (g) cudaGraphExecDestroy(g);

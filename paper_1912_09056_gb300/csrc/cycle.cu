@@ -1450,26 +1450,39 @@ int schur_damping_setup(amgc_hierarchy* h, Level& L) {
   return AMGC_OK;
 }
 
+static int dot_on(cudaStream_t s, double* part, int64_t n, const double* a, const double* b, const double* wgt,
+                  double* out_dev) {
+  int blocks = (int)std::min<int64_t>(kDotBlocks, std::max<int64_t>(1, div_up(n, kDotThreads)));
+  AMGC_LAUNCH(k_dot_partial<<<blocks, kDotThreads, 0, s>>>(n, a, b, wgt, part));
+  AMGC_LAUNCH(k_dot_final<<<1, 1024, 0, s>>>(blocks, part, out_dev));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
 // lambda_max(D^{-1} K): 20 power steps from the normalised ones vector, then the generalised
-// Rayleigh quotient (x^T K x)/(x^T D x) with D the pointwise diagonal of K (kdiag).
-int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out) {
-  cudaStream_t s = h->stream;
+// Rayleigh quotient (x^T K x)/(x^T D x) with D the pointwise diagonal of K (kdiag).  Started on
+// the auxiliary stream after the level's diagonal is ready (lambda_max_start), so that it runs
+// beside the aggregation and the tentative transfers; lambda_max_finish joins it.
+int lambda_max_start(amgc_hierarchy* h, Level& L) {
   const int64_t n = L.nu();
   const int th = 256;
-  DBuf<double> xv, yv, sc;
-  AMGC_TRY(xv.alloc(n));
-  AMGC_TRY(yv.alloc(n));
-  AMGC_TRY(sc.alloc(4));
-  AMGC_LAUNCH(k_fill<<<div_up(n, th), th, 0, s>>>(n, 1.0 / sqrt((double)n), xv.p));
+  if (!h->aux_stream) AMGC_CUDA_TRY(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+  cudaStream_t s = h->aux_stream;
+  AMGC_TRY(L.lmx_x.alloc(n));
+  AMGC_TRY(L.lmx_y.alloc(n));
+  AMGC_TRY(L.lmx_sc.alloc(4));
+  AMGC_TRY(L.lmx_part.alloc(kDotBlocks));
+  cudaEvent_t ready;
+  AMGC_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  AMGC_CUDA_TRY(cudaEventRecord(ready, h->stream));   // diagonal, SELL copy and buffers in place
+  AMGC_CUDA_TRY(cudaStreamWaitEvent(s, ready, 0));
+  cudaEventDestroy(ready);
+  double* xv = L.lmx_x.p;
+  double* yv = L.lmx_y.p;
+  double* sc = L.lmx_sc.p;
+  double* part = L.lmx_part.p;
+  AMGC_LAUNCH(k_fill<<<div_up(n, th), th, 0, s>>>(n, 1.0 / sqrt((double)n), xv));
   AMGC_CUDA_TRY(cudaGetLastError());
-  // y = K x on the SELL copy when the level has one, else on the BSR rows
-  auto spmv = [&](const double* xin, double* yout) -> int {
-    if (L.Ks.nslice > 0) {
-      const SellV<double> sv = sview<double>(L.Ks, L.Ks.val.p);
-      return sell_apply<0, double>(sv, L.nn, nullptr, xin, nullptr, nullptr, nullptr, nullptr, 0.0, yout, s);
-    }
-    return bsr_spmv(L.K, xin, yout, 1.0, 0.0, s);
-  };
   // y = D^-1 K x in one launch; the iterate is normalised after steps 10 and 20 only (the
   // direction, and with it the Rayleigh quotient, does not depend on the intermediate scaling,
   // and 10 steps cannot overflow for any lambda_max below 1e30)
@@ -1482,27 +1495,51 @@ int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out) {
     return rowop<4, double>(kv, xin, nullptr, nullptr, nullptr, nullptr, L.dinv.p, 0.0, yout, s);
   };
   for (int it = 0; it < 20; ++it) {
-    AMGC_TRY(step(xv.p, yv.p));
+    AMGC_TRY(step(xv, yv));
     if (it == 9 || it == 19) {
-      AMGC_TRY(dot(h, n, yv.p, yv.p, nullptr, sc.p));
-      AMGC_LAUNCH(k_normalize<<<div_up(n, th), th, 0, s>>>(n, sc.p, yv.p, xv.p));
+      AMGC_TRY(dot_on(s, part, n, yv, yv, nullptr, sc));
+      AMGC_LAUNCH(k_normalize<<<div_up(n, th), th, 0, s>>>(n, sc, yv, xv));
     } else {
       std::swap(xv, yv);
     }
     AMGC_CUDA_TRY(cudaGetLastError());
   }
-  AMGC_TRY(spmv(xv.p, yv.p));
-  AMGC_TRY(dot(h, n, xv.p, yv.p, nullptr, sc.p));             // x^T K x
-  AMGC_TRY(dot(h, n, xv.p, xv.p, L.kdiag.p, sc.p + 1));       // x^T D x
+  // y = K x on the SELL copy when the level has one, else on the BSR rows
+  if (L.Ks.nslice > 0) {
+    const SellV<double> sv = sview<double>(L.Ks, L.Ks.val.p);
+    AMGC_TRY((sell_apply<0, double>(sv, L.nn, nullptr, xv, nullptr, nullptr, nullptr, nullptr, 0.0, yv, s)));
+  } else {
+    AMGC_TRY((rowop<0, double>(kv, xv, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, yv, s)));
+  }
+  AMGC_TRY(dot_on(s, part, n, xv, yv, nullptr, sc));             // x^T K x
+  AMGC_TRY(dot_on(s, part, n, xv, xv, L.kdiag.p, sc + 1));       // x^T D x
+  if (!L.lmx_done) AMGC_CUDA_TRY(cudaEventCreateWithFlags(&L.lmx_done, cudaEventDisableTiming));
+  AMGC_CUDA_TRY(cudaEventRecord(L.lmx_done, s));
+  return AMGC_OK;
+}
+
+int lambda_max_finish(amgc_hierarchy* h, Level& L, double* out) {
+  cudaStream_t s = h->stream;
+  AMGC_CUDA_TRY(cudaStreamWaitEvent(s, L.lmx_done, 0));
   double hs[2] = {0.0, 0.0};
-  AMGC_CUDA_TRY(cudaMemcpyAsync(hs, sc.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(hs, L.lmx_sc.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  // the buffers are released in order on the main stream, after the join
+  L.lmx_x.release();
+  L.lmx_y.release();
+  L.lmx_sc.release();
+  L.lmx_part.release();
   if (!(hs[1] > 0.0) || !std::isfinite(hs[0] / hs[1])) {
     set_error("lambda_max: non-positive or non-finite Rayleigh quotient");
     return AMGC_ESINGULAR;
   }
   *out = hs[0] / hs[1];
   return AMGC_OK;
+}
+
+int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out) {
+  AMGC_TRY(lambda_max_start(h, L));
+  return lambda_max_finish(h, L, out);
 }
 
 }  // namespace amgc

@@ -1341,6 +1341,8 @@ static int alloc_work(Level& L) {
   return AMGC_OK;
 }
 
+static int smoother_rest(amgc_hierarchy* h, Level& L);
+
 int smoother_setup(amgc_hierarchy* h, int l) {
   cudaStream_t s = h->stream;
   Level& L = h->L[l];
@@ -1382,9 +1384,30 @@ int smoother_setup(amgc_hierarchy* h, int l) {
       AMGC_TRY(lambda_max_instances(h, L, L.inst_lam_max));
       L.lam_max = L.inst_lam_max[0];
     } else {
-      AMGC_TRY(lambda_max_estimate(h, L, &L.lam_max));
+      // single instance: the power iteration runs on the auxiliary stream; the rest of the
+      // smoother data waits for it in smoother_finish
+      AMGC_TRY(lambda_max_start(h, L));
+      L.smoother_pending = true;
+      return AMGC_OK;
     }
   }
+  return smoother_rest(h, L);
+}
+
+// Joins a pending lambda_max of level l and completes its smoother data (no-op otherwise).
+int smoother_finish(amgc_hierarchy* h, int l) {
+  Level& L = h->L[l];
+  if (!L.smoother_pending) return AMGC_OK;
+  L.smoother_pending = false;
+  AMGC_TRY(lambda_max_finish(h, L, &L.lam_max));
+  return smoother_rest(h, L);
+}
+
+// omega_J, the scaled Jacobi diagonal, the Schur-step damping and the work vectors of a level
+// whose lambda_max is known
+static int smoother_rest(amgc_hierarchy* h, Level& L) {
+  cudaStream_t s = h->stream;
+  const int nu = L.nu();
   L.omega_j = h->opts.jacobi_omega > 0.0 ? h->opts.jacobi_omega : (4.0 / 3.0) / L.lam_max;
   // omega_J D^-1 per DOF (omega_J per instance when batched)
   {
@@ -1595,6 +1618,7 @@ int coarsen_level(amgc_hierarchy* h, int l) {
   // --- lambda_max and smoothed prolongator
   ptm.reset(new PhaseTimer(h, 5));
   if (L.kdiag.p == nullptr) AMGC_TRY(smoother_setup(h, l));
+  AMGC_TRY(smoother_finish(h, l));
   if (h->opts.transfer == 1) {
     AMGC_TRY(spgemm(h, L.K, Phat, L.P));
     const double omega = h->opts.sa_omega / L.lam_max;
