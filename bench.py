@@ -62,6 +62,34 @@ def max_over_ranks(x: float, world: int, device="cpu") -> float:
     return float(t.item())
 
 
+def vcycle_bytes(h, s: int) -> float:
+    """Algorithmic bytes of one V-cycle with storage size s (8: FP64 cycle, 4: FP32): every matrix
+    value and index streamed once per use and every vector once per kernel that touches it.
+    Per level: two K applies (residual, Jacobi predictor) with the B1 rows, three multiplier-row
+    passes (two Schur corrections and the residual), two B1 corrections, the zero-guess predictor,
+    restriction and prolongation; the coarsest level reads its dense FP64 inverse once."""
+    st = h.stats()
+    total = 0.0
+    nlev = st["n_levels"]
+    for l in range(nlev):
+        bu, nn, nl, n = st["dofs_per_node"][l], st["disp_nodes"][l], st["lm_nodes"][l], st["rows"][l]
+        nu = bu * nn
+        if l == nlev - 1:
+            total += n * n * 8.0 + 2.0 * n * s
+            continue
+        kb = h.export_size(l, "k_col")
+        b1 = h.export_size(l, "b1_col")
+        b2 = h.export_size(l, "b2_col")
+        pb = h.export_size(l, "p_col")
+        k_apply = kb * (bu * bu * s + 4) + b1 * (3 * bu * s + 4) + 8.0 * (nn + 1)
+        total += 2 * k_apply + (3 * nu + 3 * nl) * s + (5 * nu + 3 * nl) * s
+        total += 3 * (b2 * (3 * bu * s + 4) + nl * (9 * s + 72) + 4 * 3 * nl * s)
+        total += 2 * (b1 * (3 * bu * s + 4) + 2 * 3 * nl * s)
+        total += 3 * nu * s
+        total += 2 * (pb * (bu * 6 * s + 4)) + 3 * nu * s
+    return total
+
+
 def workload_name():
     from paper_1912_09056_gb300.problem import WORKLOADS
     return WORKLOADS[WORKLOAD]["name"]
@@ -169,6 +197,30 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- GPU leg
+def host_arrays(prob) -> dict:
+    """The input arrays of amgc_setup of a ContactProblem, by field name."""
+    return dict(K_rowptr=prob.K_rowptr, K_col=prob.K_col, K_val=prob.K_val, D=prob.D, M_rowptr=prob.M_rowptr,
+                M_col=prob.M_col, M_val=prob.M_val, slave_node=prob.slave_node, master_node=prob.master_node,
+                triad=prob.triad, active=prob.active, body_id=prob.body_id, nullspace=prob.nullspace)
+
+
+class SetupInputs:
+    """The fields of a ContactProblem that amgc.setup reads, as tensors of one kind."""
+
+    def __init__(self, prob, tensors: dict):
+        self.n_nodes, self.n_s = prob.n_nodes, prob.n_s
+        for k, v in tensors.items():
+            setattr(self, k, v)
+
+
+def device_problem(prob, dev):
+    """A copy of the setup inputs resident on the device (timed steps start from HBM)."""
+    import numpy as np
+    import torch
+    return SetupInputs(prob, {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+                              for k, v in host_arrays(prob).items()})
+
+
 def main_gpu(args):
     import numpy as np
     import torch
@@ -185,16 +237,8 @@ def main_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prob = workload(WORKLOAD)
-    host = dict(K_rowptr=prob.K_rowptr, K_col=prob.K_col, K_val=prob.K_val, D=prob.D, M_rowptr=prob.M_rowptr,
-                M_col=prob.M_col, M_val=prob.M_val, slave_node=prob.slave_node, master_node=prob.master_node,
-                triad=prob.triad, active=prob.active, body_id=prob.body_id, nullspace=prob.nullspace)
-
-    class P:
-        pass
-    dprob = P()
-    dprob.n_nodes, dprob.n_s = prob.n_nodes, prob.n_s
-    for k, v in host.items():
-        setattr(dprob, k, torch.from_numpy(np.ascontiguousarray(v)).to(dev))
+    host = host_arrays(prob)
+    dprob = device_problem(prob, dev)
     rhs_d = torch.from_numpy(prob.rhs).to(dev)
     x_d = torch.zeros_like(rhs_d)
     opts = amgc.default_options(**OPTS)
@@ -256,6 +300,7 @@ def main_gpu(args):
     torch.cuda.synchronize()
     solve_ms = ev[0].elapsed_time(ev[1]) / reps
     vcycle_ms = ev[2].elapsed_time(ev[3]) / nv
+    vc_bytes64 = vcycle_bytes(h, 8)
     # ---- FP32 cycle (FP32 storage and arithmetic inside the V-cycle, FP64 FGMRES)
     opts32 = amgc.default_options(precision=32, **OPTS)
     h32 = amgc.setup(dprob, opts32)
@@ -272,6 +317,7 @@ def main_gpu(args):
         h32.vcycle(r, z)
     ev32[3].record()
     torch.cuda.synchronize()
+    vc_bytes32 = vcycle_bytes(h32, 4)
     h32.profile(2)                      # the FP32 cycle's fine-level K applies only
     h32.solve(rhs_d, x32)
     kms32, kl32, kb32, _ = h32.profile_read()
@@ -299,8 +345,12 @@ def main_gpu(args):
     fp32 = {"step_ms": round(step32_ms, 3), "solve_ms": round(ev32[0].elapsed_time(ev32[1]) / reps, 3),
             "solve_ms_autotuned": round(tuned_solve_ms, 3),
             "iters": it32, "relres": rr32, "vcycle_ms": round(ev32[2].elapsed_time(ev32[3]) / nv, 4),
+            "vcycle_gbs": round(vc_bytes32 / (ev32[2].elapsed_time(ev32[3]) / nv * 1e-3) / 1e9, 1),
             "k_apply_us": round(1e3 * kms32 / kl32, 2) if kl32 else None,
             "k_apply_gbs": round((kb32 / kl32) / (kms32 / kl32 * 1e-3) / 1e9, 1) if kl32 else None}
+    fp32["vcycle_hbm_frac"] = round(fp32["vcycle_gbs"] / float(
+        json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else fp32["vcycle_gbs"] / 6800.0, 4)
     if kl32:
         fp32["k_apply_hbm_frac"] = round(fp32["k_apply_gbs"] / float(
             json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
@@ -338,6 +388,7 @@ def main_gpu(args):
     if not args.no_batch:
         from paper_1912_09056_gb300.problem import batched_workload
         cat, npt, lpt, brhs, bprobs, _ = batched_workload(64, seed=3)
+        dcat = device_problem(cat, dev)   # inputs resident in HBM, as for the medium step
         # the set includes slave meshes up to 4x finer than their master, where rho(S_bd^-1 S_hat)
         # reaches ~20 and the undamped Schur step (alpha = 0.8) amplifies: Schur damping on
         optsb = amgc.default_options(precision=32, levels_max=4, coarse_max_rows=400, transfer=1, schur_damping=1,
@@ -345,13 +396,13 @@ def main_gpu(args):
         Rb = torch.from_numpy(np.ascontiguousarray(brhs)).to(dev)
         Xb = torch.zeros_like(Rb)
         nsys = len(bprobs) * brhs.shape[0]
-        hb = amgc.setup(cat, optsb, node_ptr=npt, lm_ptr=lpt)
+        hb = amgc.setup(dcat, optsb, node_ptr=npt, lm_ptr=lpt)
         hb.solve_batched(Rb, Xb, n_sys=nsys, check=False)
         hb.close()
         torch.cuda.synchronize()
         eb = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         eb[0].record()
-        hb = amgc.setup(cat, optsb, node_ptr=npt, lm_ptr=lpt)
+        hb = amgc.setup(dcat, optsb, node_ptr=npt, lm_ptr=lpt)
         eb[1].record()
         itb, rrb, codeb = hb.solve_batched(Rb, Xb, n_sys=nsys, check=False)
         eb[2].record()
@@ -365,7 +416,7 @@ def main_gpu(args):
                       "cycle": "FP32, 3 CheapSIMPLE sweeps, Schur damping, restart 50, autotuned row mappings",
                       "step": "amgc_setup_batched + amgc_solve_batched"}
         hb.close()
-        del cat, bprobs, Rb, Xb
+        del cat, dcat, bprobs, Rb, Xb
     # ---- dominant kernel: fine-level K apply, timed by events on its launching stream
     h.profile(1)
     for _ in range(reps):
@@ -395,10 +446,7 @@ def main_gpu(args):
 
     # ---- end to end through the host-buffer API: inputs copied in, solution copied out
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
-    hprob = P()
-    hprob.n_nodes, hprob.n_s = prob.n_nodes, prob.n_s
-    for k, v in pin.items():
-        setattr(hprob, k, v)
+    hprob = SetupInputs(prob, pin)
     rhs_pin = torch.from_numpy(prob.rhs).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in pin.values()) + rhs_pin.numel() * 8
     d2h = rhs_pin.numel() * 8
@@ -436,6 +484,9 @@ def main_gpu(args):
             "iters": iters[-1], "relres": relres[-1], "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
             "setup_phase_ms": {k: round(v, 3) for k, v in st["setup_phase_ms"].items()},
             "vcycle_ms": round(vcycle_ms, 4),
+            "vcycle_hbm": {"bytes": int(vc_bytes64), "gbs": round(vc_bytes64 / (vcycle_ms * 1e-3) / 1e9, 1),
+                           "frac": round(vc_bytes64 / (vcycle_ms * 1e-3) / 1e9 / hbm_peak, 4),
+                           "model": "algorithmic bytes of one V-cycle (bench.vcycle_bytes), of measured"},
             "fp32_cycle": fp32,
             "adjoint": adj_info,
             "batched": batch_info,

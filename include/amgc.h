@@ -246,6 +246,9 @@ int amgc_grad_elements_noalloc(int32_t ne, const int32_t* conn, const int32_t* s
                                const int32_t* node_free, const double* adj, const double* x, const double* uD,
                                const uint8_t* lift_mask, const double* E, double* gE, double* gt, void* stream);
 
+/* Copies the hierarchy's summary (levels, sizes, operator complexity, lambda_max per level, setup
+ * time and phase times, the last solve's iterations and residual) into *out.  Host only; no
+ * device work.  Errors: AMGC_EINVAL (null argument). */
 int amgc_stats(const struct amgc_hierarchy* h, amgc_stats_t* out);
 
 /* Copies one internal array of level `level` to the host buffer dst (capacity `bytes`).
@@ -293,8 +296,14 @@ int amgc_profile(struct amgc_hierarchy* h, int32_t enable);
 int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes,
                       double* flops);
 
+/* Waits for the hierarchy's stream (and its auxiliary setup stream), then frees every device and
+ * host resource the hierarchy owns (device memory goes back to the library's pool).  NULL is
+ * accepted.  The handle must not be used afterwards. */
 void amgc_destroy(struct amgc_hierarchy* h);
+/* Static description of a status code (never NULL). */
 const char* amgc_strerror(int code);
+/* Detail of the last failure in the calling thread (empty string if none); valid until the
+ * thread's next failing call. */
 const char* amgc_last_error(void);
 
 /* Number of CUDA kernels this library has launched in the calling process so far. */

@@ -220,6 +220,13 @@ class Hierarchy:
                 raise AmgcError(int(r), "amgc_export")
         return out
 
+    def export_size(self, level: int, what: str) -> int:
+        """Number of elements amgc_export would copy (no copy is made)."""
+        nb = self._lib.amgc_export(self._h, level, EXPORT[what], None, 0)
+        if nb < 0:
+            raise AmgcError(int(nb), "amgc_export")
+        return int(nb) // np.dtype(_EXPORT_DTYPE[what]).itemsize
+
     def profile(self, enable=True):
         """enable: True/3 = FP64 and FP32 applies, 1 = FP64 only, 2 = FP32 only, False/0 = off."""
         mask = 3 if enable is True else int(enable)

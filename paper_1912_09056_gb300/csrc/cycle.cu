@@ -593,10 +593,14 @@ __global__ void k_zero(int64_t n, T* __restrict__ y) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = T(0);
 }
+// Jacobi sweep from a zero guess, y = omega D^-1 f, with the multipliers' zero guess (lam = 0)
+// set in the same launch
 template <class T>
-__global__ void k_jacobi_zero(int64_t n, const T* __restrict__ f, const T* __restrict__ dinv, T omega, T* __restrict__ y) {
+__global__ void k_jacobi_zero(int64_t n, int64_t nlam, const T* __restrict__ f, const T* __restrict__ dinv, T omega,
+                              T* __restrict__ y, T* __restrict__ lam) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = omega * dinv[i] * f[i];
+  if (i < nlam) lam[i] = T(0);
 }
 // u_i -= alpha atinv_i (B1 dlam)_i over the rows of B1 with entries, one warp per row
 template <int BU, class T>
@@ -619,6 +623,37 @@ k_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp,
     if (lane == r) out = v;
   }
   if (lane < BU) u[(int64_t)i * BU + lane] -= alpha * atinv[(int64_t)i * BU + lane] * out;
+}
+// u = uh - alpha atinv (B1 dlam) in one launch: blocks below ncopy copy uh into u on the rows
+// without B1 entries (one thread per DOF), the others update the rows of B1 as k_b1_update does,
+// reading uh
+template <int BU, class T>
+__global__ void __launch_bounds__(128)
+k_copy_b1(int64_t nu, int ncopy, const T* __restrict__ uh, int nrows, const int* __restrict__ rows,
+          const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+          const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha, T* __restrict__ u) {
+  if ((int)blockIdx.x < ncopy) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nu) return;
+    const int64_t node = i / BU;
+    if (rp[node + 1] == rp[node]) u[i] = uh[i];
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int t = (int)(((blockIdx.x - ncopy) * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (t >= nrows) return;
+  const int i = rows[t];
+  T acc[BU];
+#pragma unroll
+  for (int r = 0; r < BU; ++r) acc[r] = T(0);
+  lane_blocks<BU, 3, T>(rp[i], rp[i + 1], col, val, dlam, lane, acc);
+  T out = T(0);
+#pragma unroll
+  for (int r = 0; r < BU; ++r) {
+    const T v = warp_sum(acc[r]);
+    if (lane == r) out = v;
+  }
+  if (lane < BU) u[(int64_t)i * BU + lane] = uh[(int64_t)i * BU + lane] - alpha * atinv[(int64_t)i * BU + lane] * out;
 }
 // multiplier restriction / prolongation through P-hat^lambda (weights w_l, aggregate lagg_l)
 // (restriction: one warp per coarse multiplier node, the lanes over its members)
@@ -724,29 +759,41 @@ static int smooth(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, T* x
   const T* g = b + nu;
   T* u = x;
   T* lam = x + nu;
-  T* t = L.t;   // u_half
+  T* t = L.t;
   const int th = 256;
-  for (int j = 0; j < h->opts.jacobi_sweeps; ++j) {
-    T* src = (j % 2 == 0) ? u : t;
-    T* dst = (j % 2 == 0) ? t : u;
+  const int J = h->opts.jacobi_sweeps;
+  // sweep j reads the iterate of sweep j-1 and writes the other buffer; from a zero guess the
+  // first sweep reads no iterate, and its buffer is chosen so that the last sweep ends in u
+  T* cur = u;
+  for (int j = 0; j < J; ++j) {
     if (zero_guess && j == 0) {
-      AMGC_LAUNCH(k_zero<T><<<div_up(3 * (int64_t)L.nl, th), th, 0, s>>>(3 * (int64_t)L.nl, lam));
-      AMGC_LAUNCH(k_jacobi_zero<T><<<div_up(nu, th), th, 0, s>>>(nu, f, L.dinv, (T)L.omega_j, dst));
+      T* dst = (J % 2 == 1) ? u : t;
+      const int64_t nlam = 3 * (int64_t)L.nl;
+      AMGC_LAUNCH(k_jacobi_zero<T><<<div_up(std::max<int64_t>(nu, nlam), th), th, 0, s>>>(nu, nlam, f, L.dinv,
+                                                                                      (T)L.omega_j, dst, lam));
       AMGC_CUDA_TRY(cudaGetLastError());
+      cur = dst;
     } else {
-      AMGC_TRY((k_apply<3, T>(h, L, l, src, lam, f, src, dst)));
+      T* dst = cur == u ? t : u;
+      AMGC_TRY((k_apply<3, T>(h, L, l, cur, lam, f, cur, dst)));
+      cur = dst;
     }
   }
-  T* uh = (h->opts.jacobi_sweeps % 2 == 1) ? t : u;
+  T* uh = cur;   // u_half
   // corrector on the multipliers: dlam = -S^-1 (g - B2 uh + Z lam), lam += alpha dlam
   AMGC_TRY((lm_op<1, T>(L, uh, g, lam, h->opts.simple_alpha, L.dlam, s)));
   // u = uh - alpha A~^-1 B1 dlam
+  const int gb = div_up((int64_t)L.n_b1_rows * 32, 128);
   if (uh != u) {
-    AMGC_LAUNCH(k_copy<T><<<div_up(nu, th), th, 0, s>>>(nu, uh, u));
+    const int nc = div_up(nu, 128);
+    if (L.bu == 3)
+      AMGC_LAUNCH(k_copy_b1<3, T><<<nc + gb, 128, 0, s>>>(nu, nc, uh, L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col,
+                                                          L.B1.val, L.dlam, L.atinv, (T)h->opts.simple_alpha, u));
+    else
+      AMGC_LAUNCH(k_copy_b1<6, T><<<nc + gb, 128, 0, s>>>(nu, nc, uh, L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col,
+                                                          L.B1.val, L.dlam, L.atinv, (T)h->opts.simple_alpha, u));
     AMGC_CUDA_TRY(cudaGetLastError());
-  }
-  if (L.n_b1_rows > 0) {
-    const int gb = div_up((int64_t)L.n_b1_rows * 32, 128);
+  } else if (L.n_b1_rows > 0) {
     if (L.bu == 3)
       AMGC_LAUNCH(k_b1_update<3, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
                                                        L.atinv, (T)h->opts.simple_alpha, u));
@@ -1119,7 +1166,7 @@ int make_views(amgc_hierarchy* h) {
 }
 
 // ------------------------------------------------------------------ row-mapping autotuner
-// Times every candidate row mapping of one apply (2 warm-up launches, 5 timed, CUDA events on
+// Times every candidate row mapping of one apply (1 warm-up launch, 3 timed, CUDA events on
 // the hierarchy's stream) and returns the fastest: 0 warp per row, 1/2 SELL threads per row,
 // 3 the staged FP32 kernel (fine-level 3x3 K only).
 template <int MODE, class T>
@@ -1133,8 +1180,8 @@ static int tune_one(amgc_hierarchy* h, const BsrV<T>& A, const SellV<T>& S, cons
   for (int cand = 0; cand < 4; ++cand) {
     if (cand > 0 && S.nslice == 0) break;
     if (cand == 3 && S.ctr == nullptr) break;
-    for (int rep = 0; rep < 7; ++rep) {
-      if (rep == 2) AMGC_CUDA_TRY(cudaEventRecord(e0, h->stream));
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) AMGC_CUDA_TRY(cudaEventRecord(e0, h->stream));
       AMGC_TRY((mapped_apply<MODE, T>(A, S, cand, A2, x, x2, b, x, dinv, 1.0, y, h->stream)));
     }
     AMGC_CUDA_TRY(cudaEventRecord(e1, h->stream));
@@ -1151,19 +1198,24 @@ static int tune_one(amgc_hierarchy* h, const BsrV<T>& A, const SellV<T>& S, cons
   return AMGC_OK;
 }
 
+// fine_k_only: only the finest K (the Krylov operator apply) is tuned; the other maps keep
+// their defaults (the FP64 views of a hierarchy whose cycle runs in FP32)
 template <class T>
-static int tune_views(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int pidx) {
+static int tune_views(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int pidx, bool fine_k_only) {
   for (int l = 0; l + 1 < (int)V.size(); ++l) {
     LevelV<T>& L = V[l];
     const LevelV<T>& C = V[l + 1];
     const BsrV<T>* B1 = L.nl ? &L.B1 : nullptr;
-    int km = 0, pm = 0, rm = 0;
-    AMGC_TRY((tune_one<2, T>(h, L.K, L.Ks, B1, L.x, L.x + L.nu(), L.b, L.dinv, L.r, &km)));
-    AMGC_TRY((tune_one<1, T>(h, L.P, L.Ps, nullptr, C.x, nullptr, nullptr, nullptr, L.t, &pm)));
-    AMGC_TRY((tune_one<0, T>(h, L.R, L.Rs, nullptr, L.r, nullptr, nullptr, nullptr, C.b, &rm)));
-    L.kmap = km; L.pmap = pm; L.rmap = rm;
     Level& LL = h->L[l];
+    int km = LL.kmap[pidx], pm = LL.pmap[pidx], rm = LL.rmap[pidx];
+    AMGC_TRY((tune_one<2, T>(h, L.K, L.Ks, B1, L.x, L.x + L.nu(), L.b, L.dinv, L.r, &km)));
+    if (!fine_k_only) {
+      AMGC_TRY((tune_one<1, T>(h, L.P, L.Ps, nullptr, C.x, nullptr, nullptr, nullptr, L.t, &pm)));
+      AMGC_TRY((tune_one<0, T>(h, L.R, L.Rs, nullptr, L.r, nullptr, nullptr, nullptr, C.b, &rm)));
+    }
+    L.kmap = km; L.pmap = pm; L.rmap = rm;
     LL.kmap[pidx] = km; LL.pmap[pidx] = pm; LL.rmap[pidx] = rm;
+    if (fine_k_only) break;
   }
   return AMGC_OK;
 }
@@ -1192,8 +1244,9 @@ int autotune(amgc_hierarchy* h) {
       AMGC_CUDA_TRY(cudaMemsetAsync(L.f.r.p, 0, L.f.r.bytes(), h->stream));
     }
   }
-  AMGC_TRY(tune_views<double>(h, h->v64, 0));
-  if (h->opts.precision == 32) AMGC_TRY(tune_views<float>(h, h->v32, 1));
+  // an FP32 cycle uses the FP64 views for the Krylov operator apply only
+  AMGC_TRY(tune_views<double>(h, h->v64, 0, h->opts.precision == 32));
+  if (h->opts.precision == 32) AMGC_TRY(tune_views<float>(h, h->v32, 1, false));
   AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
   return make_views(h);
 }
@@ -1286,32 +1339,52 @@ __global__ void k_segnormalize(int ni, int bu, const int* __restrict__ nptr, con
     y[i] = src[i] * inv;
 }
 
-// The same power iteration per instance of a batched level: lam[q] for every instance.
+// y = D^-1 K x (scaled) or y = K x, on the level's SELL copy when it has one, else on its BSR rows
+static int power_apply(const Level& L, bool scaled, const double* x, double* y, cudaStream_t s) {
+  if (L.Ks.nslice > 0) {
+    const SellV<double> sv = sview<double>(L.Ks, L.Ks.val.p);
+    return scaled ? sell_apply<4, double>(sv, L.nn, nullptr, x, nullptr, nullptr, nullptr, L.dinv.p, 0.0, y, s)
+                  : sell_apply<0, double>(sv, L.nn, nullptr, x, nullptr, nullptr, nullptr, nullptr, 0.0, y, s);
+  }
+  const BsrV<double> kv = view_of(L.K);
+  return scaled ? rowop<4, double>(kv, x, nullptr, nullptr, nullptr, nullptr, L.dinv.p, 0.0, y, s)
+                : rowop<0, double>(kv, x, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, y, s);
+}
+
+// The same power iteration per instance of a batched level: lam[q] for every instance.  The
+// instances are decoupled blocks of D^-1 K, so each instance's part of the iterate keeps its own
+// direction under any per-instance scaling: the iterate is normalised per instance after steps
+// 10 and 20 only, as in the single-instance iteration.
 int lambda_max_instances(amgc_hierarchy* h, Level& L, std::vector<double>& lam) {
   cudaStream_t s = h->stream;
   const int ni = h->n_inst;
   const int64_t n = L.nu();
   const int th = 256;
-  DBuf<double> xv, yv, sc;
+  DBuf<double> xb, yb, sc;
   DBuf<int> dptr;
-  AMGC_TRY(xv.alloc(n));
-  AMGC_TRY(yv.alloc(n));
+  AMGC_TRY(xb.alloc(n));
+  AMGC_TRY(yb.alloc(n));
   AMGC_TRY(sc.alloc(2 * ni));
   AMGC_TRY(dptr.alloc(ni + 1));
   AMGC_CUDA_TRY(cudaMemcpyAsync(dptr.p, L.nptr.data(), (ni + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-  AMGC_LAUNCH(k_fill<<<div_up(n, th), th, 0, s>>>(n, 1.0, xv.p));
-  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, xv.p, xv.p, nullptr, sc.p));
+  double* xv = xb.p;
+  double* yv = yb.p;
   const dim3 gs(64, ni);
-  AMGC_LAUNCH(k_segnormalize<<<gs, th, 0, s>>>(ni, L.bu, dptr.p, sc.p, xv.p, xv.p));
+  AMGC_LAUNCH(k_fill<<<div_up(n, th), th, 0, s>>>(n, 1.0, xv));
+  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, xv, xv, nullptr, sc.p));
+  AMGC_LAUNCH(k_segnormalize<<<gs, th, 0, s>>>(ni, L.bu, dptr.p, sc.p, xv, xv));
   for (int it = 0; it < 20; ++it) {
-    AMGC_TRY(bsr_spmv(L.K, xv.p, yv.p, 1.0, 0.0, s));
-    AMGC_LAUNCH(k_scale_dinv<<<div_up(n, th), th, 0, s>>>(n, L.dinv.p, yv.p));
-    AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, yv.p, yv.p, nullptr, sc.p));
-    AMGC_LAUNCH(k_segnormalize<<<gs, th, 0, s>>>(ni, L.bu, dptr.p, sc.p, yv.p, xv.p));
+    AMGC_TRY(power_apply(L, true, xv, yv, s));
+    if (it == 9 || it == 19) {
+      AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, yv, yv, nullptr, sc.p));
+      AMGC_LAUNCH(k_segnormalize<<<gs, th, 0, s>>>(ni, L.bu, dptr.p, sc.p, yv, xv));
+    } else {
+      std::swap(xv, yv);
+    }
   }
-  AMGC_TRY(bsr_spmv(L.K, xv.p, yv.p, 1.0, 0.0, s));
-  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, xv.p, yv.p, nullptr, sc.p));
-  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, xv.p, xv.p, L.kdiag.p, sc.p + ni));
+  AMGC_TRY(power_apply(L, false, xv, yv, s));
+  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, xv, yv, nullptr, sc.p));
+  AMGC_LAUNCH(k_segdot<<<ni, 512, 0, s>>>(ni, L.bu, dptr.p, xv, xv, L.kdiag.p, sc.p + ni));
   AMGC_CUDA_TRY(cudaGetLastError());
   std::vector<double> hs(2 * ni);
   AMGC_CUDA_TRY(cudaMemcpyAsync(hs.data(), sc.p, 2 * ni * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1486,16 +1559,8 @@ int lambda_max_start(amgc_hierarchy* h, Level& L) {
   // y = D^-1 K x in one launch; the iterate is normalised after steps 10 and 20 only (the
   // direction, and with it the Rayleigh quotient, does not depend on the intermediate scaling,
   // and 10 steps cannot overflow for any lambda_max below 1e30)
-  const BsrV<double> kv = view_of(L.K);
-  auto step = [&](const double* xin, double* yout) -> int {
-    if (L.Ks.nslice > 0) {
-      const SellV<double> sv = sview<double>(L.Ks, L.Ks.val.p);
-      return sell_apply<4, double>(sv, L.nn, nullptr, xin, nullptr, nullptr, nullptr, L.dinv.p, 0.0, yout, s);
-    }
-    return rowop<4, double>(kv, xin, nullptr, nullptr, nullptr, nullptr, L.dinv.p, 0.0, yout, s);
-  };
   for (int it = 0; it < 20; ++it) {
-    AMGC_TRY(step(xv, yv));
+    AMGC_TRY(power_apply(L, true, xv, yv, s));
     if (it == 9 || it == 19) {
       AMGC_TRY(dot_on(s, part, n, yv, yv, nullptr, sc));
       AMGC_LAUNCH(k_normalize<<<div_up(n, th), th, 0, s>>>(n, sc, yv, xv));
@@ -1504,13 +1569,7 @@ int lambda_max_start(amgc_hierarchy* h, Level& L) {
     }
     AMGC_CUDA_TRY(cudaGetLastError());
   }
-  // y = K x on the SELL copy when the level has one, else on the BSR rows
-  if (L.Ks.nslice > 0) {
-    const SellV<double> sv = sview<double>(L.Ks, L.Ks.val.p);
-    AMGC_TRY((sell_apply<0, double>(sv, L.nn, nullptr, xv, nullptr, nullptr, nullptr, nullptr, 0.0, yv, s)));
-  } else {
-    AMGC_TRY((rowop<0, double>(kv, xv, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, yv, s)));
-  }
+  AMGC_TRY(power_apply(L, false, xv, yv, s));
   AMGC_TRY(dot_on(s, part, n, xv, yv, nullptr, sc));             // x^T K x
   AMGC_TRY(dot_on(s, part, n, xv, xv, L.kdiag.p, sc + 1));       // x^T D x
   if (!L.lmx_done) AMGC_CUDA_TRY(cudaEventCreateWithFlags(&L.lmx_done, cudaEventDisableTiming));

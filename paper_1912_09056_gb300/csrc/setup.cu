@@ -1190,51 +1190,66 @@ static int bsr_transpose(amgc_hierarchy* h, const DBsr& A, DBsr& T) {
 
 // ======================================================================== smoothed prolongator
 // P = P-hat - omega D^{-1} (K P-hat) on the pattern of K P-hat (K holds its diagonal blocks,
-// so that pattern contains P-hat's).
+// so that pattern contains P-hat's).  One warp per node row; the lanes take the row's values
+// (its blocks are contiguous), so that loads and stores are coalesced.
 template <int BU>
 __global__ void k_sa_values(int nn, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ agg,
                             const double* __restrict__ phat, const double* __restrict__ dinv, double omega,
                             const double* __restrict__ omega_dof, double* __restrict__ val) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int NQ = BU * 6;
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (i >= nn) return;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) {
-    double* v = val + (int64_t)e * BU * 6;
-    const bool own = col[e] == agg[i];
-    for (int r = 0; r < BU; ++r) {
-      const double d = (omega_dof ? omega_dof[(int64_t)i * BU + r] : omega) * dinv[(int64_t)i * BU + r];
-      for (int c = 0; c < 6; ++c) {
-        double p = own ? phat[((int64_t)i * BU + r) * 6 + c] : 0.0;
-        v[r * 6 + c] = p - d * v[r * 6 + c];
-      }
-    }
+  const int e0 = rp[i], nq = (rp[i + 1] - e0) * NQ;
+  const int a = agg[i];
+  double* v = val + (int64_t)e0 * NQ;
+  for (int q = lane; q < nq; q += 32) {
+    const int eb = q / NQ;
+    const int w = q - eb * NQ;
+    const int r = w / 6, c = w - r * 6;
+    const int64_t dof = (int64_t)i * BU + r;
+    const double d = (omega_dof ? omega_dof[dof] : omega) * dinv[dof];
+    const double p = col[e0 + eb] == a ? phat[dof * 6 + c] : 0.0;
+    v[q] = p - d * v[q];
   }
 }
 
 // ======================================================================== smoother data
+// Pointwise diagonal of K, its inverse and the inverse of A~ (the diagonal, or with SIMPLEC the
+// absolute row sums).  One warp per node row: for block row r the lanes take the row's (block,
+// column) pairs, and the absolute values are added across the warp.
 template <int BU>
 __global__ void k_diag(int nn, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
                        int simplec, double* __restrict__ kdiag, double* __restrict__ dinv, double* __restrict__ atinv,
                        int* st) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (i >= nn) return;
-  double dg[BU], as[BU];
-  for (int r = 0; r < BU; ++r) { dg[r] = 0.0; as[r] = 0.0; }
-  bool found = false;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) {
-    const double* v = val + (int64_t)e * BU * BU;
-    if (col[e] == i) {
-      found = true;
-      for (int r = 0; r < BU; ++r) dg[r] = v[r * BU + r];
-    }
-    for (int r = 0; r < BU; ++r)
-      for (int c = 0; c < BU; ++c) as[r] += fabs(v[r * BU + c]);
+  const int e0 = rp[i], e1 = rp[i + 1];
+  // the diagonal block (columns ascending: a binary search)
+  int lo = e0, hi = e1 - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (col[mid] < i) lo = mid + 1;
+    else hi = mid;
   }
-  if (!found) set_status(st, ST_NO_DIAG);
+  const bool found = e1 > e0 && col[lo] == i;
+  if (!found && lane == 0) set_status(st, ST_NO_DIAG);
+  const int nq = (e1 - e0) * BU;
   for (int r = 0; r < BU; ++r) {
-    if (!(dg[r] > 0.0) || !isfinite(dg[r])) set_status(st, ST_SINGULAR);
-    kdiag[(int64_t)i * BU + r] = dg[r];
-    dinv[(int64_t)i * BU + r] = 1.0 / dg[r];
-    atinv[(int64_t)i * BU + r] = 1.0 / (simplec ? as[r] : dg[r]);
+    double as = 0.0;
+    for (int q = lane; q < nq; q += 32) {
+      const int eb = q / BU, c = q - eb * BU;
+      as += fabs(val[((int64_t)(e0 + eb) * BU + r) * BU + c]);
+    }
+    as = warp_sum(as);
+    if (lane == 0) {
+      const double dg = found ? val[((int64_t)lo * BU + r) * BU + r] : 0.0;
+      if (!(dg > 0.0) || !isfinite(dg)) set_status(st, ST_SINGULAR);
+      kdiag[(int64_t)i * BU + r] = dg;
+      dinv[(int64_t)i * BU + r] = 1.0 / dg;
+      atinv[(int64_t)i * BU + r] = 1.0 / (simplec ? as : dg);
+    }
   }
 }
 // S_l = Z_l + sum_i B2[l,i] diag(atinv_i) B1[i,l]; Sinv_l = S_l^{-1}.  One warp per multiplier
@@ -1351,10 +1366,10 @@ int smoother_setup(amgc_hierarchy* h, int l) {
   AMGC_TRY(L.dinv.alloc(nu));
   AMGC_TRY(L.atinv.alloc(nu));
   if (L.bu == 3)
-    AMGC_LAUNCH(k_diag<3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
+    AMGC_LAUNCH(k_diag<3><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
                                                 L.dinv.p, L.atinv.p, h->status.p));
   else
-    AMGC_LAUNCH(k_diag<6><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
+    AMGC_LAUNCH(k_diag<6><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
                                                 L.dinv.p, L.atinv.p, h->status.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   AMGC_TRY(check_status(h, "K diagonal"));
@@ -1632,10 +1647,10 @@ int coarsen_level(amgc_hierarchy* h, int l) {
       AMGC_CUDA_TRY(cudaStreamSynchronize(s));
     }
     if (L.bu == 3)
-      AMGC_LAUNCH(k_sa_values<3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.P.rowptr.p, L.P.col.p, L.agg.p, Phat.val.p, L.dinv.p,
+      AMGC_LAUNCH(k_sa_values<3><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.P.rowptr.p, L.P.col.p, L.agg.p, Phat.val.p, L.dinv.p,
                                                        omega, wdof.p, L.P.val.p));
     else
-      AMGC_LAUNCH(k_sa_values<6><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.P.rowptr.p, L.P.col.p, L.agg.p, Phat.val.p, L.dinv.p,
+      AMGC_LAUNCH(k_sa_values<6><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.P.rowptr.p, L.P.col.p, L.agg.p, Phat.val.p, L.dinv.p,
                                                        omega, wdof.p, L.P.val.p));
     AMGC_CUDA_TRY(cudaGetLastError());
   } else {
@@ -1736,16 +1751,21 @@ int transposed_setup(amgc_hierarchy* h) {
 }
 
 // ======================================================================== coarsest level: dense inverse
+// dense copy of a BSR matrix into rows row0.., columns col0.. of A (row-major, n columns); one
+// warp per block row, the lanes over the row's values
 template <int BR, int BC>
 __global__ void k_dense_put(int nbr, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
                             int row0, int col0, double sign, int n, double* __restrict__ A) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int NQ = BR * BC;
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (i >= nbr) return;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) {
-    const double* v = val + (int64_t)e * BR * BC;
-    for (int r = 0; r < BR; ++r)
-      for (int c = 0; c < BC; ++c)
-        A[(int64_t)(row0 + i * BR + r) * n + col0 + col[e] * BC + c] = sign * v[r * BC + c];
+  const int e0 = rp[i], nq = (rp[i + 1] - e0) * NQ;
+  for (int q = lane; q < nq; q += 32) {
+    const int eb = q / NQ;
+    const int w = q - eb * NQ;
+    const int r = w / BC, c = w - r * BC;
+    A[(int64_t)(row0 + i * BR + r) * n + col0 + col[e0 + eb] * BC + c] = sign * val[(int64_t)e0 * NQ + q];
   }
 }
 __global__ void k_dense_z(int nl, const double* __restrict__ Z, int off, int n, double* __restrict__ A) {
@@ -1925,19 +1945,32 @@ k_gj_coop(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __restri
 }
 
 // The same inverse with kGjB pivots per grid barrier (n up to kGjBlockedMax).  Per super-step
-// every CTA (redundantly) eliminates the panel of columns K..K+b-1 for all rows in shared memory,
-// recording the pivot rows' entities, the pivots and every row's multipliers a_e(t) (its panel
-// value in column K+t just before step t).  The rows of the other columns then follow from the
-// pivot rows of the super-step,
+// every CTA (redundantly) eliminates the panel of columns K..K+b-1 in shared memory, recording
+// the pivot rows' entities, the pivots and every row's multipliers a_e(t) (its panel value in
+// column K+t just before step t).  The rows of the other columns then follow from the pivot rows
+// of the super-step,
 //   q_t = (row_{pi_t} - sum_{s<t} a_{pi_t}(s) q_s) / pv_t,
 //   row_e <- row_e - sum_t a_e(t) q_t          (pivot row pi_s: q_s - sum_{t>s} a_{pi_s}(t) q_t),
 // which is the per-column elimination with the same operations grouped per super-step.  Each CTA
 // writes its own rows of the next buffer in the row order after the super-step's interchanges.
+//
+// GB300 issues FP64 at 2 FMA per clock and SM, so the redundant panel work is kept small: step t
+// updates, for every row, only the columns right of t (what later pivot searches and
+// multipliers read); column t of a row is left at its multiplier a_e(t).  The panel columns left
+// of the pivot (the inverse's part) are formed only where they are needed, by replaying the
+// step updates on the frozen multipliers: for the pivot row of each step (its scaled row is
+// kept in ppan[t][.]) and, at the end of the super-step, for the CTA's own rows.  Every value
+// is formed by the same operations, in the same order, as in the per-column elimination.  The
+// pivot search compares magnitudes as integers (the bit patterns of non-negative doubles are
+// ordered like their values), which keeps it off the FP64 pipe.
 constexpr int kGjBlockedMax = 960;   // n limit of the blocked kernel (8 pivots per barrier)
-__device__ __forceinline__ void argmax_pair(double& v, int& i) {
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ void argmax_key(unsigned long long& v, int& i) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const unsigned long long ov = __shfl_xor_sync(0xffffffffu, v, o);
     const int oi = __shfl_xor_sync(0xffffffffu, i, o);
     if (ov > v || (ov == v && oi < i)) {
       v = ov;
@@ -1951,13 +1984,13 @@ k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __res
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   extern __shared__ double gjb_sh[];
-  double* panel = gjb_sh;                 // [n][kGjB]   panel values per entity (row of cur)
-  double* mult = panel + n * kGjB;        // [n][kGjB]   multipliers a_e(t)
-  double* q = mult + n * kGjB;            // [kGjB][n]   transformed pivot rows (columns outside the panel)
+  double* panel = gjb_sh;                 // [kGjB][n] panel column c of entity e at c * n + e
+  double* q = panel + n * kGjB;           // [kGjB][n] transformed pivot rows (columns outside the panel)
   int* p2e = reinterpret_cast<int*>(q + kGjB * n);   // [n] position -> entity
   int* estep = p2e + n;                   // [n] super-step pivot index of an entity, -1 otherwise
-  __shared__ double ppan[kGjB], pinv[kGjB], wv[kGjcThreads / 32];
-  __shared__ int pent[kGjB], wi[kGjcThreads / 32], ppos;
+  __shared__ double ppan[kGjB][kGjB], pinv[kGjB];
+  __shared__ unsigned long long wv[kGjcThreads / 32];
+  __shared__ int pent[kGjB], wi[kGjcThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int per = (n + gridDim.x - 1) / gridDim.x;
   const int r0 = min(n, (int)blockIdx.x * per), r1 = min(n, r0 + per);
@@ -1966,8 +1999,8 @@ k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __res
   for (int K = 0; K < n; K += kGjB) {
     const int nb = min(kGjB, n - K);
     for (int idx = tid; idx < n * nb; idx += kGjcThreads) {
-      const int e = idx / nb, t = idx - e * nb;
-      panel[e * kGjB + t] = __ldcg(cur + (int64_t)e * n + K + t);
+      const int e = idx / nb, c = idx - e * nb;
+      panel[c * n + e] = __ldcg(cur + (int64_t)e * n + K + c);
     }
     for (int e = tid; e < n; e += kGjcThreads) {
       p2e[e] = e;
@@ -1976,57 +2009,59 @@ k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __res
     __syncthreads();
     for (int t = 0; t < nb; ++t) {
       const int k = K + t;
-      double bv = -1.0;
+      const double* col_t = panel + t * n;
+      unsigned long long bv = 0ULL;
       int bi = n;
       for (int i = k + tid; i < n; i += kGjcThreads) {
-        const double v = fabs(panel[p2e[i] * kGjB + t]);
+        const unsigned long long v = abs_key(col_t[p2e[i]]);
         if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
       }
-      argmax_pair(bv, bi);
+      argmax_key(bv, bi);
       if (lane == 0) { wv[wid] = bv; wi[wid] = bi; }
       __syncthreads();
       if (wid == 0) {
-        double v = lane < kGjcThreads / 32 ? wv[lane] : -1.0;
+        unsigned long long v = lane < kGjcThreads / 32 ? wv[lane] : 0ULL;
         int i = lane < kGjcThreads / 32 ? wi[lane] : n;
-        argmax_pair(v, i);
+        argmax_key(v, i);   // every lane holds the winner
+        const int p = i < n ? i : k;
+        const int ep = p2e[p];
+        const double pv = col_t[ep];
+        const bool bad = !(fabs(pv) > 0.0) || !isfinite(pv);
+        const double inv = 1.0 / (bad ? 1.0 : pv);
+        // the pivot row scaled: columns left of t replayed from its multipliers, t itself the
+        // reciprocal, columns right of t from the panel
+        if (lane < t) {
+          double f = -panel[lane * n + ep] * pinv[lane];
+          for (int s2 = lane + 1; s2 < t; ++s2) f = fma(-panel[s2 * n + ep], ppan[s2][lane], f);
+          ppan[t][lane] = f * inv;
+        } else if (lane < nb) {
+          ppan[t][lane] = lane == t ? inv : panel[lane * n + ep] * inv;
+        }
+        __syncwarp();   // every lane has read p2e before lane 0 interchanges
         if (lane == 0) {
-          const int p = i < n ? i : k;
-          const int ep = p2e[p];
-          double pv = panel[ep * kGjB + t];
-          if (!(v > 0.0) || !isfinite(pv)) {
-            if (blockIdx.x == 0) set_status(st, ST_SINGULAR);
-            pv = 1.0;
-          }
-          ppos = p;
+          if (bad && blockIdx.x == 0) set_status(st, ST_SINGULAR);
           pent[t] = ep;
-          pinv[t] = 1.0 / pv;
+          pinv[t] = inv;
           estep[ep] = t;
           if (blockIdx.x == 0) piv[k] = p;
+          // row interchange of positions k and p
+          p2e[p] = p2e[k];
+          p2e[k] = ep;
         }
       }
       __syncthreads();
+      // columns right of t: every row but the pivot row takes a_e(t) times the pivot row off;
+      // the pivot row becomes the scaled row
       const int ep = pent[t];
-      const double inv = pinv[t];
-      for (int c = tid; c < nb; c += kGjcThreads) ppan[c] = c == t ? inv : panel[ep * kGjB + c] * inv;   // new pivot row
-      for (int e = tid; e < n; e += kGjcThreads) mult[e * kGjB + t] = panel[e * kGjB + t];
-      __syncthreads();
-      // (a full panel is the common case: constant stride, no division in the index)
-      const int w = nb == kGjB ? kGjB : nb;
-      for (int idx = tid; idx < n * w; idx += kGjcThreads) {
-        const int e = nb == kGjB ? idx / kGjB : idx / w;
-        const int c = idx - e * w;
-        double* pe = panel + e * kGjB + c;
-        if (e == ep) *pe = ppan[c];
-        else {
-          const double a = mult[e * kGjB + t];
-          *pe = c == t ? -a * inv : fma(-a, ppan[c], *pe);
+      if (t + 1 < nb) {
+        for (int e = tid; e < n; e += kGjcThreads) {
+          if (e == ep) {
+            for (int c = t + 1; c < nb; ++c) panel[c * n + e] = ppan[t][c];
+          } else {
+            const double a = col_t[e];
+            for (int c = t + 1; c < nb; ++c) panel[c * n + e] = fma(-a, ppan[t][c], panel[c * n + e]);
+          }
         }
-      }
-      if (tid == 0) {
-        const int p = ppos;
-        const int tmp = p2e[k];
-        p2e[k] = p2e[p];
-        p2e[p] = tmp;
       }
       __syncthreads();
     }
@@ -2041,7 +2076,7 @@ k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __res
         if (t < nb) {
           const int ep = pent[t];
           double v = orig[t];
-          for (int s2 = 0; s2 < t; ++s2) v -= mult[ep * kGjB + s2] * q[s2 * n + j];
+          for (int s2 = 0; s2 < t; ++s2) v -= panel[s2 * n + ep] * q[s2 * n + j];
           q[t * n + j] = v * pinv[t];
         }
       }
@@ -2054,13 +2089,24 @@ k_gj_blocked(int n, double* __restrict__ Aa, double* __restrict__ Ab, int* __res
       for (int j = tid; j < n; j += kGjcThreads) {
         double v;
         if (j >= K && j < K + nb) {
-          v = panel[e * kGjB + (j - K)];
+          // panel column c: from the scaled pivot row (a pivot row, c <= its step) or from the
+          // frozen multiplier a_e(c), then the later steps' updates
+          const int c = j - K;
+          int s0;
+          if (se >= 0 && c <= se) {
+            v = ppan[se][c];
+            s0 = se + 1;
+          } else {
+            v = -panel[c * n + e] * pinv[c];
+            s0 = c + 1;
+          }
+          for (int s2 = s0; s2 < nb; ++s2) v = fma(-panel[s2 * n + e], ppan[s2][c], v);
         } else if (se >= 0) {
           v = q[se * n + j];
-          for (int t = se + 1; t < nb; ++t) v -= mult[e * kGjB + t] * q[t * n + j];
+          for (int t = se + 1; t < nb; ++t) v -= panel[t * n + e] * q[t * n + j];
         } else {
           v = __ldcg(cur + (int64_t)e * n + j);
-          for (int t = 0; t < nb; ++t) v -= mult[e * kGjB + t] * q[t * n + j];
+          for (int t = 0; t < nb; ++t) v -= panel[t * n + e] * q[t * n + j];
         }
         dst[j] = v;
       }
@@ -2284,19 +2330,19 @@ int coarse_setup(amgc_hierarchy* h, int l) {
   AMGC_TRY(L.Ainv.alloc((size_t)n * n));
   AMGC_CUDA_TRY(cudaMemsetAsync(L.Ainv.p, 0, (size_t)n * n * sizeof(double), s));
   if (L.bu == 3) {
-    AMGC_LAUNCH(k_dense_put<3, 3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, 0, 0, 1.0, n, L.Ainv.p));
+    AMGC_LAUNCH(k_dense_put<3, 3><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, 0, 0, 1.0, n, L.Ainv.p));
     if (L.nl > 0) {
-      AMGC_LAUNCH(k_dense_put<3, 3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.B1.rowptr.p, L.B1.col.p, L.B1.val.p, 0, nu, 1.0, n,
+      AMGC_LAUNCH(k_dense_put<3, 3><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.B1.rowptr.p, L.B1.col.p, L.B1.val.p, 0, nu, 1.0, n,
                                                           L.Ainv.p));
-      AMGC_LAUNCH(k_dense_put<3, 3><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, nu, 0, 1.0, n,
+      AMGC_LAUNCH(k_dense_put<3, 3><<<div_up((int64_t)L.nl * 32, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, nu, 0, 1.0, n,
                                                           L.Ainv.p));
     }
   } else {
-    AMGC_LAUNCH(k_dense_put<6, 6><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, 0, 0, 1.0, n, L.Ainv.p));
+    AMGC_LAUNCH(k_dense_put<6, 6><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, 0, 0, 1.0, n, L.Ainv.p));
     if (L.nl > 0) {
-      AMGC_LAUNCH(k_dense_put<6, 3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.B1.rowptr.p, L.B1.col.p, L.B1.val.p, 0, nu, 1.0, n,
+      AMGC_LAUNCH(k_dense_put<6, 3><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.B1.rowptr.p, L.B1.col.p, L.B1.val.p, 0, nu, 1.0, n,
                                                           L.Ainv.p));
-      AMGC_LAUNCH(k_dense_put<3, 6><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, nu, 0, 1.0, n,
+      AMGC_LAUNCH(k_dense_put<3, 6><<<div_up((int64_t)L.nl * 32, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p, nu, 0, 1.0, n,
                                                           L.Ainv.p));
     }
   }
@@ -2314,7 +2360,7 @@ int coarse_setup(amgc_hierarchy* h, int l) {
   const bool blocked = n <= kGjBlockedMax;
   const int gjb = 8;
   const void* kern = !blocked ? (const void*)k_gj_coop : (const void*)k_gj_blocked<8>;
-  const size_t smem = blocked ? (size_t)n * (3 * gjb * sizeof(double) + 2 * sizeof(int))
+  const size_t smem = blocked ? (size_t)n * (2 * gjb * sizeof(double) + 2 * sizeof(int))
                               : 2 * (size_t)n * sizeof(double);
   if (coop && smem <= 200 * 1024) {
     if (smem > 48 * 1024) AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
