@@ -316,6 +316,13 @@ int64_t amgc_launch_count(void);
  * mechanics; the paper has no counterpart.)  Errors: AMGC_ECUDA. */
 int amgc_trim_memory(void);
 
+/* y[i] = x[i] rounded to FP32, to nearest with ties to even (the value a C cast gives), for
+ * i < n: the conversion that feeds the FP32 cycle its input and forms the FP32 copies of the
+ * hierarchy and of the Krylov basis.  x, y: device arrays of n elements, not overlapping; the
+ * work is enqueued on stream (NULL: the default stream).  (Library mechanics; the paper has no
+ * counterpart.)  Errors: AMGC_EINVAL for n < 0 or a NULL array with n > 0; AMGC_ECUDA. */
+int amgc_f64_to_f32(int64_t n, const double* x, float* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -123,6 +123,8 @@ def load():
     lib.amgc_launch_count.restype = C.c_int64
     lib.amgc_trim_memory.argtypes = []
     lib.amgc_trim_memory.restype = C.c_int
+    lib.amgc_f64_to_f32.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.amgc_f64_to_f32.restype = C.c_int
     _lib = lib
     return lib
 
@@ -142,6 +144,16 @@ def launch_count() -> int:
 def trim_memory():
     """Returns the unused device memory of the library's pool on the current device (amgc_trim_memory)."""
     _check(load().amgc_trim_memory(), "amgc_trim_memory")
+
+
+def f64_to_f32(x, y, stream=None):
+    """amgc_f64_to_f32: y = x rounded to FP32 (contiguous CUDA tensors, float64 -> float32)."""
+    import torch
+    if x.dtype != torch.float64 or y.dtype != torch.float32 or x.numel() != y.numel():
+        raise TypeError("f64_to_f32: float64 input and float32 output of one size")
+    if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+        raise TypeError("f64_to_f32: contiguous CUDA tensors")
+    _check(load().amgc_f64_to_f32(x.numel(), x.data_ptr(), y.data_ptr(), _stream_ptr(stream)), "amgc_f64_to_f32")
 
 
 def default_options(**kw) -> Options:

@@ -260,6 +260,7 @@ struct amgc_hierarchy {
   // FGMRES workspace
   int m_alloc = 0;
   amgc::DBuf<double> V, Zs, H, givens, gvec, y, wk, xk, rk;
+  amgc::DBuf<float> Vf;             // FP32 copy of the Arnoldi basis (first projection pass)
   amgc::DBuf<unsigned> tma_ctr;    // slice counter of the staged FP32 fine-level apply
   amgc::DBuf<double> partial;      // per-block partial dot products
   std::vector<amgc::LevelV<double>> v64;   // cycle views, FP64
@@ -297,6 +298,26 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// FP64 -> FP32, rounded to nearest even, on the integer pipe for results in FP32's normal range
+// (GB300 issues the FP64 -> FP32 conversion instruction at a small fraction of its integer
+// rate).  The sign is kept, the exponent rebiased (1023 -> 127), the 52-bit fraction cut to 23
+// bits and rounded on the 29 dropped bits, a carry running into the exponent (to infinity above
+// FP32's largest value, as the conversion does).  Inputs whose FP32 result is zero, subnormal,
+// infinite or NaN outside that path take the conversion instruction.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned int hi = static_cast<unsigned int>(b >> 32);
+  const int e = static_cast<int>((hi >> 20) & 0x7ffu);   // biased FP64 exponent
+  if (e < 897 || e > 1150) {                              // outside FP32's normal exponents
+    if ((b << 1) == 0ULL) return __uint_as_float(hi & 0x80000000u);   // signed zero
+    return static_cast<float>(x);
+  }
+  const unsigned int keep = static_cast<unsigned int>((b >> 29) & 0x7fffffu);
+  const unsigned int rest = static_cast<unsigned int>(b & 0x1fffffffu);
+  unsigned int f = (static_cast<unsigned int>(e - 896) << 23) | keep;
+  if (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) f += 1u;
+  return __uint_as_float((hi & 0x80000000u) | f);
+}
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -332,6 +353,7 @@ int prof_flush(amgc_hierarchy* h);
 // sparse kernels (cycle.cu)
 int bsr_spmv(const DBsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
 int lambda_max_estimate(amgc_hierarchy* h, Level& L, double* out);
+int convert_f64_f32(int64_t n, const double* x, float* y, cudaStream_t s);
 int lambda_max_start(amgc_hierarchy* h, Level& L);
 int lambda_max_finish(amgc_hierarchy* h, Level& L, double* out);
 int smoother_finish(amgc_hierarchy* h, int l);

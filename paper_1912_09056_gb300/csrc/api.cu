@@ -577,6 +577,14 @@ const char* amgc_last_error(void) { return g_last_error.c_str(); }
 
 int64_t amgc_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
+int amgc_f64_to_f32(int64_t n, const double* x, float* y, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) {
+    set_error("amgc_f64_to_f32: invalid argument");
+    return AMGC_EINVAL;
+  }
+  return convert_f64_f32(n, x, y, (cudaStream_t)stream);
+}
+
 int amgc_trim_memory(void) {
   cudaMemPool_t pool = device_pool();
   if (!pool) return AMGC_ECUDA;

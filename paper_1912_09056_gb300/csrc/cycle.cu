@@ -583,10 +583,16 @@ __global__ void k_copy(int64_t n, const T* __restrict__ a, T* __restrict__ y) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = a[i];
 }
+template <class Tb>
+__device__ __forceinline__ Tb convert_to(double v) { return (Tb)v; }
+template <>
+__device__ __forceinline__ float convert_to<float>(double v) { return f64_to_f32_rn(v); }
+template <class Tb>
+__device__ __forceinline__ Tb convert_to(float v) { return (Tb)v; }
 template <class Ta, class Tb>
 __global__ void k_convert(int64_t n, const Ta* __restrict__ a, Tb* __restrict__ y) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = (Tb)a[i];
+  if (i < n) y[i] = convert_to<Tb>(a[i]);
 }
 template <class T>
 __global__ void k_zero(int64_t n, T* __restrict__ y) {
@@ -1057,6 +1063,13 @@ int precond_apply(amgc_hierarchy* h, const double* r, double* z) {
 }
 
 // ------------------------------------------------------------------ views and FP32 mirrors
+int convert_f64_f32(int64_t n, const double* x, float* y, cudaStream_t s) {
+  if (n == 0) return AMGC_OK;
+  AMGC_LAUNCH((k_convert<double, float><<<div_up(n, 256), 256, 0, s>>>(n, x, y)));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
 static int to_f32(amgc_hierarchy* h, const double* src, size_t n, DBuf<float>& dst) {
   AMGC_TRY(dst.alloc(std::max<size_t>(n, 1)));
   if (n == 0) return AMGC_OK;

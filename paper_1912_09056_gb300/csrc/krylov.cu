@@ -4,6 +4,15 @@
 // single streaming multi-dot plus a single streaming update over the basis.  Hessenberg
 // columns, Givens rotations and the residual estimate live on the device; the host reads one
 // scalar per iteration to decide whether to stop.
+//
+// The first pass's projection coefficients h1 are taken from FP32 copies of the basis and of w
+// (FP32 arithmetic, FP64 partial sums); every update w -= V h and the second projection run in
+// FP64.  After the exact FP64 update w1 = w - V h1, the second pass measures what h1 missed,
+// h2 = V^T w1, so the Hessenberg column h1 + h2 and the Arnoldi relation w = V (h1 + h2) + w2
+// hold to FP64 rounding whatever h1's accuracy; h1 only has to be close enough for the second
+// pass to finish the orthogonalisation (its error is at FP32 level).  On GB300 the FP64 pipe
+// bounds every Arnoldi sweep, and the first projection then reads half the bytes and issues no
+// FP64 multiply-adds.
 #include "amgc_internal.cuh"
 
 #include <algorithm>
@@ -39,6 +48,34 @@ k_multidot(int64_t n, int nk, const double* __restrict__ V, const double* __rest
     const double t = warp_sum((s0 + s1) + (s2 + s3));
     if (lane == 0) part[(int64_t)blockIdx.x * nk + k] = t;
   }
+}
+// The same partial dot products from FP32 copies of the basis and of w: FP32 products and
+// per-lane FP32 sums over the block's chunk, FP64 sums across the warp.
+__global__ void __launch_bounds__(kMdThreads)
+k_multidot_f32(int64_t n, int nk, const float* __restrict__ V, const float* __restrict__ w, double* __restrict__ part) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = blockIdx.x * chunk;
+  const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+  for (int k = wid; k < nk; k += kMdWarps) {
+    const float* v = V + (int64_t)k * n;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int64_t i = b0 + lane;
+    for (; i + 96 < b1; i += 128) {
+      s0 = fmaf(v[i], w[i], s0);
+      s1 = fmaf(v[i + 32], w[i + 32], s1);
+      s2 = fmaf(v[i + 64], w[i + 64], s2);
+      s3 = fmaf(v[i + 96], w[i + 96], s3);
+    }
+    for (; i < b1; i += 32) s0 = fmaf(v[i], w[i], s0);
+    const double t = warp_sum((double)((s0 + s1) + (s2 + s3)));
+    if (lane == 0) part[(int64_t)blockIdx.x * nk + k] = t;
+  }
+}
+// y = fp32(x)
+__global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = f64_to_f32_rn(x[i]);
 }
 // out[k*ldo] (+)= sum_b part[b*nk + k], one warp per k (fixed order: deterministic)
 __global__ void k_multidot_final(int nk, int nb, const double* __restrict__ part, double* __restrict__ out, int ldo,
@@ -152,19 +189,27 @@ __device__ __forceinline__ double block_rsqrt(const double* nrm2) {
   __syncthreads();
   return inv;
 }
-// v = w / sqrt(nrm2) (zero vector on breakdown)
+// v = w / sqrt(nrm2) (zero vector on breakdown), with its FP32 copy vf
 __global__ void k_arnoldi_normalize(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ w,
-                                    double* __restrict__ v) {
+                                    double* __restrict__ v, float* __restrict__ vf) {
   const double inv = block_rsqrt(nrm2);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) v[i] = w[i] * inv;
+  if (i < n) {
+    const double t = w[i] * inv;
+    v[i] = t;
+    vf[i] = f64_to_f32_rn(t);
+  }
 }
-// start of a cycle: v0 = r / beta, g = (beta, 0, ...)
+// start of a cycle: v0 = r / beta (and its FP32 copy), g = (beta, 0, ...)
 __global__ void k_cycle_start(int64_t n, const double* __restrict__ nrm2, const double* __restrict__ r,
-                              double* __restrict__ v0, double* __restrict__ g, int m) {
+                              double* __restrict__ v0, float* __restrict__ v0f, double* __restrict__ g, int m) {
   const double inv = block_rsqrt(nrm2);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) v0[i] = r[i] * inv;
+  if (i < n) {
+    const double t = r[i] * inv;
+    v0[i] = t;
+    v0f[i] = f64_to_f32_rn(t);
+  }
   if (i <= m) g[i] = i == 0 ? sqrt(*nrm2) : 0.0;
 }
 // back substitution H(0:k,0:k) y = g(0:k) (single thread)
@@ -188,6 +233,7 @@ __global__ void k_zero_vec(int64_t n, double* __restrict__ y) {
 static int ensure_workspace(amgc_hierarchy* h, int64_t n, int m) {
   if (h->m_alloc == m && h->V.n == (size_t)(m + 1) * n) return AMGC_OK;
   AMGC_TRY(h->V.alloc((size_t)(m + 1) * n));
+  AMGC_TRY(h->Vf.alloc((size_t)(m + 1) * n));
   AMGC_TRY(h->Zs.alloc((size_t)m * n));
   AMGC_TRY(h->H.alloc((size_t)(m + 1) * m));
   AMGC_TRY(h->givens.alloc((size_t)2 * m));
@@ -249,7 +295,8 @@ int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol_in, int* 
   double relres = 1.0;
   while (total < maxit && !converged) {
     // ||r||^2 is in scal[2]
-    AMGC_LAUNCH(k_cycle_start<<<div_up(std::max<int64_t>(n, m + 1), th), th, 0, s>>>(n, scal + 2, h->rk.p, h->V.p, h->gvec.p, m));
+    AMGC_LAUNCH(k_cycle_start<<<div_up(std::max<int64_t>(n, m + 1), th), th, 0, s>>>(n, scal + 2, h->rk.p, h->V.p,
+                                                                                   h->Vf.p, h->gvec.p, m));
     AMGC_CUDA_TRY(cudaMemsetAsync(h->H.p, 0, (size_t)(m + 1) * m * sizeof(double), s));
     int jd = 0;
     for (int j = 0; j < m && total < maxit; ++j) {
@@ -258,14 +305,19 @@ int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol_in, int* 
       double* w = h->V.p + (int64_t)(j + 1) * n;
       AMGC_TRY(precond_apply(h, vj, zj));
       AMGC_TRY(saddle_apply(h, 0, zj, w));
-      // CGS2
-      for (int pass = 0; pass < 2; ++pass) {
-        AMGC_TRY(multidot(h, n, j + 1, h->V.p, w, h->H.p + j, m, pass, hbuf.p));
-        AMGC_LAUNCH(k_basis_update<<<gu, kUpThreads, 0, s>>>(n, j + 1, h->V.p, hbuf.p, w, pass ? h->wk.p : nullptr));
-        AMGC_CUDA_TRY(cudaGetLastError());
-      }
+      // CGS2: first projection from the FP32 copies (w's copy in the slot of v_{j+1}), then
+      // FP64 update, FP64 projection, FP64 update with the partial norms of the result
+      float* wf = h->Vf.p + (int64_t)(j + 1) * n;
+      AMGC_LAUNCH(k_to_f32<<<gn, th, 0, s>>>(n, w, wf));
+      AMGC_LAUNCH(k_multidot_f32<<<kMdBlocks, kMdThreads, 0, s>>>(n, j + 1, h->Vf.p, wf, h->wk.p));
+      AMGC_LAUNCH(k_multidot_final<<<div_up((int64_t)(j + 1) * 32, 128), 128, 0, s>>>(j + 1, kMdBlocks, h->wk.p,
+                                                                                     h->H.p + j, m, 0, hbuf.p));
+      AMGC_LAUNCH(k_basis_update<<<gu, kUpThreads, 0, s>>>(n, j + 1, h->V.p, hbuf.p, w, nullptr));
+      AMGC_TRY(multidot(h, n, j + 1, h->V.p, w, h->H.p + j, m, 1, hbuf.p));
+      AMGC_LAUNCH(k_basis_update<<<gu, kUpThreads, 0, s>>>(n, j + 1, h->V.p, hbuf.p, w, h->wk.p));
+      AMGC_CUDA_TRY(cudaGetLastError());
       AMGC_LAUNCH(k_norm_givens<<<1, kUpThreads, 0, s>>>(gu, h->wk.p, j, m, h->H.p, cs, sn, h->gvec.p, beta0, scal));
-      AMGC_LAUNCH(k_arnoldi_normalize<<<gn, th, 0, s>>>(n, scal + 2, w, w));
+      AMGC_LAUNCH(k_arnoldi_normalize<<<gn, th, 0, s>>>(n, scal + 2, w, w, wf));
       AMGC_CUDA_TRY(cudaGetLastError());
       AMGC_CUDA_TRY(cudaMemcpyAsync(pin, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       AMGC_CUDA_TRY(cudaStreamSynchronize(s));
