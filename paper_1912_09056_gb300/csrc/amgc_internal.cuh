@@ -272,6 +272,8 @@ struct amgc_hierarchy {
   long long cycle_graph_kernels[2] = {0, 0};
   cudaStream_t capture_stream = nullptr;
   cudaStream_t aux_stream = nullptr;    // setup work overlapped with the main stream
+  cudaStream_t side_stream = nullptr;   // short multiplier-row kernels beside the long ones
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   amgc::DBuf<double> cyc_in, cyc_out;      // fixed FP64 input/output of the captured FP64 cycle
   // batched FGMRES workspace
   amgc::DBuf<int> b_chunk_row0, b_chunk_row1, b_chunk_ptr, b_row_inst;

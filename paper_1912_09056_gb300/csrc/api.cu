@@ -555,6 +555,12 @@ void amgc_destroy(struct amgc_hierarchy* h) {
   for (auto& g : h->cycle_graph)
     if (g) cudaGraphExecDestroy(g);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->side_stream) {
+    cudaStreamSynchronize(h->side_stream);
+    cudaStreamDestroy(h->side_stream);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->join_ev) cudaEventDestroy(h->join_ev);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   delete h;
 }

@@ -757,6 +757,26 @@ static int k_apply(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* x1, co
   return AMGC_OK;
 }
 
+// Runs side(stream) on the hierarchy's side stream beside main() on its stream: a fork and a
+// join through events, which a stream capture records as two parallel graph branches.  Used
+// where a short kernel on the multiplier rows and a long one on the displacement rows read the
+// same inputs and write disjoint outputs.
+template <class FMain, class FSide>
+static int fork_join(amgc_hierarchy* h, FMain&& main_fn, FSide&& side_fn) {
+  if (!h->side_stream) {
+    AMGC_CUDA_TRY(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+    AMGC_CUDA_TRY(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+    AMGC_CUDA_TRY(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+  }
+  AMGC_CUDA_TRY(cudaEventRecord(h->fork_ev, h->stream));
+  AMGC_CUDA_TRY(cudaStreamWaitEvent(h->side_stream, h->fork_ev, 0));
+  AMGC_TRY(side_fn(h->side_stream));
+  AMGC_CUDA_TRY(cudaEventRecord(h->join_ev, h->side_stream));
+  AMGC_TRY(main_fn());
+  AMGC_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->join_ev, 0));
+  return AMGC_OK;
+}
+
 template <class T>
 static int smooth(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, T* x, bool zero_guess) {
   cudaStream_t s = h->stream;
@@ -814,9 +834,9 @@ static int smooth(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, T* x
 template <class T>
 static int residual(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, const T* x, T* r) {
   const int nu = L.nu();
-  AMGC_TRY((k_apply<2, T>(h, L, l, x, x + nu, b, nullptr, r)));
-  AMGC_TRY((lm_op<0, T>(L, x, b + nu, const_cast<T*>(x + nu), 0.0, r + nu, h->stream)));
-  return AMGC_OK;
+  return fork_join(
+      h, [&]() { return k_apply<2, T>(h, L, l, x, x + nu, b, nullptr, r); },
+      [&](cudaStream_t ss) { return lm_op<0, T>(L, x, b + nu, const_cast<T*>(x + nu), 0.0, r + nu, ss); });
 }
 
 template <class T>
@@ -843,20 +863,28 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
   }
   for (int k = 0; k < sweeps; ++k) AMGC_TRY(smooth<T>(h, L, l, b, x, k == 0));
   AMGC_TRY(residual<T>(h, L, l, b, x, L.r));
-  // restrict: C.b = [R r_u ; R^lambda r_lambda]
-  AMGC_TRY((mapped_apply<0, T>(L.R, L.Rs, L.rmap, nullptr, L.r, nullptr, nullptr, nullptr, nullptr, 0.0, C.b, s)));
-  if (C.nl > 0) {
-    AMGC_LAUNCH(k_restrict_lm<T><<<div_up((int64_t)C.nl * 32, 128), 128, 0, s>>>(C.nl, L.rl_ptr, L.rl_idx, L.pl_w, L.r + nu,
-                                                                   C.b + C.nu()));
-    AMGC_CUDA_TRY(cudaGetLastError());
-  }
+  // restrict: C.b = [R r_u ; R^lambda r_lambda] (the multiplier part beside the displacement part)
+  AMGC_TRY(fork_join(
+      h, [&]() { return mapped_apply<0, T>(L.R, L.Rs, L.rmap, nullptr, L.r, nullptr, nullptr, nullptr, nullptr, 0.0, C.b, s); },
+      [&](cudaStream_t ss) -> int {
+        if (C.nl > 0) {
+          AMGC_LAUNCH(k_restrict_lm<T><<<div_up((int64_t)C.nl * 32, 128), 128, 0, ss>>>(C.nl, L.rl_ptr, L.rl_idx, L.pl_w,
+                                                                                       L.r + nu, C.b + C.nu()));
+          AMGC_CUDA_TRY(cudaGetLastError());
+        }
+        return AMGC_OK;
+      }));
   AMGC_TRY(vcycle_t<T>(h, V, l + 1, C.b, C.x));
-  // prolongate and add
-  AMGC_TRY((mapped_apply<1, T>(L.P, L.Ps, L.pmap, nullptr, C.x, nullptr, nullptr, nullptr, nullptr, 0.0, x, s)));
-  if (L.nl > 0) {
-    AMGC_LAUNCH(k_prolong_lm<T><<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.lagg, L.pl_w, C.x + C.nu(), x + nu));
-    AMGC_CUDA_TRY(cudaGetLastError());
-  }
+  // prolongate and add (the multiplier part beside the displacement part)
+  AMGC_TRY(fork_join(
+      h, [&]() { return mapped_apply<1, T>(L.P, L.Ps, L.pmap, nullptr, C.x, nullptr, nullptr, nullptr, nullptr, 0.0, x, s); },
+      [&](cudaStream_t ss) -> int {
+        if (L.nl > 0) {
+          AMGC_LAUNCH(k_prolong_lm<T><<<div_up(L.nl, 128), 128, 0, ss>>>(L.nl, L.lagg, L.pl_w, C.x + C.nu(), x + nu));
+          AMGC_CUDA_TRY(cudaGetLastError());
+        }
+        return AMGC_OK;
+      }));
   for (int k = 0; k < sweeps; ++k) AMGC_TRY(smooth<T>(h, L, l, b, x, false));
   return AMGC_OK;
 }
@@ -987,9 +1015,9 @@ int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y) {
   const LevelV<double>& L = h->v64[l];
   const int nu = L.nu();
   const bool tr = h->transposed;
-  AMGC_TRY((k_apply<0, double>(h, L, l, x, x + nu, nullptr, nullptr, y, tr)));
-  AMGC_TRY((lm_op<2, double>(L, x, nullptr, const_cast<double*>(x + nu), 0.0, y + nu, h->stream, tr)));
-  return AMGC_OK;
+  return fork_join(
+      h, [&]() { return k_apply<0, double>(h, L, l, x, x + nu, nullptr, nullptr, y, tr); },
+      [&](cudaStream_t ss) { return lm_op<2, double>(L, x, nullptr, const_cast<double*>(x + nu), 0.0, y + nu, ss, tr); });
 }
 
 // One V-cycle with FP64 input and output; the FP32 cycle converts at entry and exit.
