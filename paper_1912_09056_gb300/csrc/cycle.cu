@@ -116,17 +116,18 @@ k_rowop6(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const
   if (lane < 6) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * 6 + lane, out);
 }
 
-// CTA per block row for few, long rows of 6-row blocks (the restriction to the coarsest levels:
-// about 60 rows of several hundred blocks).  Warp w takes slots 5w .. 5w+4 of every group of
-// 5 * kLongWarps consecutive blocks with the lane mapping of k_rowop6; the warps' row sums are
+// CTA of W warps per block row for long rows of 6-row blocks (the restrictions, about 180
+// blocks per row from the finest level and several hundred to the coarsest, with W = 8; the
+// coarse K, about 40 blocks per row, with W = 2).  Warp w takes slots 5w .. 5w+4 of every
+// group of 5 W consecutive blocks with the lane mapping of k_rowop6; the warps' row sums are
 // added in warp order (deterministic).
-constexpr int kLongWarps = 8;
-template <int BC1, int BC2, int MODE, class T>
-__global__ void __launch_bounds__(kLongWarps * 32)
+template <int W, int BC1, int BC2, int MODE, class T>
+__global__ void __launch_bounds__(W * 32)
 k_rowop6_long(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const T* __restrict__ v1,
               const T* __restrict__ x1, const int* __restrict__ rp2, const int* __restrict__ c2,
               const T* __restrict__ v2, const T* __restrict__ x2, const T* __restrict__ b, const T* __restrict__ x0,
               const T* __restrict__ dinv, T omega, T* __restrict__ y) {
+  constexpr int kLongWarps = W;
   __shared__ T part[kLongWarps][6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int row = blockIdx.x;
@@ -167,10 +168,18 @@ template <int BR, int BC1, int BC2, int MODE, class T>
 static int launch_rowop(const BsrV<T>& A1, const T* x1, const BsrV<T>* A2, const T* x2, const T* b, const T* x0,
                         const T* dinv, double omega, T* y, cudaStream_t s) {
   if (A1.nbr == 0) return AMGC_OK;
-  if (BR == 6 && A1.nbr < 2048 && A1.nnzb > 96 * (int64_t)A1.nbr) {   // few long rows: a CTA per row
-    AMGC_LAUNCH(k_rowop6_long<BC1, BC2, MODE, T><<<A1.nbr, kLongWarps * 32, 0, s>>>(
-        A1.nbr, A1.rp, A1.col, A1.val, x1, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr, A2 ? A2->val : nullptr, x2,
-        b, x0, dinv, (T)omega, y));
+  // long rows of 6-row blocks: a CTA of 8 (more than 96 blocks per row) or 2 (more than 24)
+  // warps per row, so that the SMs hold enough warps
+  if (BR == 6 && A1.nbr < (1 << 16) && A1.nnzb > 24 * (int64_t)A1.nbr) {
+    const int* r2 = A2 ? A2->rp : nullptr;
+    const int* k2 = A2 ? A2->col : nullptr;
+    const T* w2 = A2 ? A2->val : nullptr;
+    if (A1.nnzb > 96 * (int64_t)A1.nbr)
+      AMGC_LAUNCH(k_rowop6_long<8, BC1, BC2, MODE, T><<<A1.nbr, 8 * 32, 0, s>>>(
+          A1.nbr, A1.rp, A1.col, A1.val, x1, r2, k2, w2, x2, b, x0, dinv, (T)omega, y));
+    else
+      AMGC_LAUNCH(k_rowop6_long<2, BC1, BC2, MODE, T><<<A1.nbr, 2 * 32, 0, s>>>(
+          A1.nbr, A1.rp, A1.col, A1.val, x1, r2, k2, w2, x2, b, x0, dinv, (T)omega, y));
     AMGC_CUDA_TRY(cudaGetLastError());
     return AMGC_OK;
   }

@@ -714,40 +714,59 @@ __global__ void k_zc(int nlc, const int* __restrict__ ptr, const int* __restrict
 constexpr int kHashCap = 1024;
 constexpr int kGemmWarps = 4;
 
-__device__ __forceinline__ int hash_insert(int* tab, int key) {
-  unsigned slot = ((unsigned)key * 2654435761u) & (kHashCap - 1);
-  for (int probe = 0; probe < kHashCap; ++probe) {
+__device__ __forceinline__ int hash_insert(int* tab, int cap, int key) {
+  unsigned slot = ((unsigned)key * 2654435761u) & (unsigned)(cap - 1);
+  for (int probe = 0; probe < cap; ++probe) {
     int prev = atomicCAS(tab + slot, -1, key);
     if (prev == -1) return 1;
     if (prev == key) return 0;
-    slot = (slot + 1) & (kHashCap - 1);
+    slot = (slot + 1) & (unsigned)(cap - 1);
   }
   return -1;
 }
 
-// MODE 0: count unique columns per row into cnt; MODE 1: write sorted unique columns into ccol
+// MODE 0: count unique columns per row into cnt; MODE 1: write sorted unique columns into ccol.
+// One warp per C row with an open-addressing table in shared memory, sized per row: a power of
+// two of at least twice the row's candidate count (the sum of the B row lengths its A entries
+// reach; at most kHashCap), so that clearing and compacting the table cost what the row needs.
+// The lanes take lpe lanes per A entry (32 / lpe A entries at once), each lane a strided part
+// of its B row.
 template <int MODE>
 __global__ void __launch_bounds__(kGemmWarps * 32)
-k_spgemm_symbolic(int nrow, const int* __restrict__ arp, const int* __restrict__ acol, const int* __restrict__ brp,
+k_spgemm_symbolic(int nrow, int lpe, const int* __restrict__ arp, const int* __restrict__ acol, const int* __restrict__ brp,
                   const int* __restrict__ bcol, int* __restrict__ cnt, const int* __restrict__ crp,
                   int* __restrict__ ccol, int* st) {
   __shared__ int tab[kGemmWarps][kHashCap];
-  __shared__ int lst[kGemmWarps][kHashCap];
   __shared__ int nlist[kGemmWarps];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int row = blockIdx.x * kGemmWarps + wid;
   if (row >= nrow) return;
+  const int a0 = arp[row], a1 = arp[row + 1];
+  int bound = 0;
+  for (int e = a0 + lane; e < a1; e += 32) {
+    const int k = acol[e];
+    bound += brp[k + 1] - brp[k];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bound += __shfl_xor_sync(0xffffffffu, bound, o);
+  int cap = 64;
+  while (cap < kHashCap && cap < 2 * bound) cap <<= 1;
   int* T = tab[wid];
-  for (int k = lane; k < kHashCap; k += 32) T[k] = -1;
+  for (int k = lane; k < cap; k += 32) T[k] = -1;
   __syncwarp();
   int mine = 0;
   bool overflow = false;
-  for (int e = arp[row]; e < arp[row + 1]; ++e) {
-    const int k = acol[e];
-    for (int t = brp[k] + lane; t < brp[k + 1]; t += 32) {
-      int r = hash_insert(T, bcol[t]);
-      if (r < 0) overflow = true;
-      else mine += r;
+  const int per = 32 / lpe;   // A entries per pass
+  const int sub = lane % lpe;
+  for (int e0 = a0; e0 < a1; e0 += per) {
+    const int e = e0 + lane / lpe;
+    if (e < a1) {
+      const int k = acol[e];
+      for (int t = brp[k] + sub; t < brp[k + 1]; t += lpe) {
+        const int r = hash_insert(T, cap, bcol[t]);
+        if (r < 0) overflow = true;
+        else mine += r;
+      }
     }
   }
   __syncwarp();
@@ -763,11 +782,12 @@ k_spgemm_symbolic(int nrow, const int* __restrict__ arp, const int* __restrict__
     if (lane == 0) cnt[row] = total;
     return;
   }
-  // compact the keys, then rank them
-  int* Ls = lst[wid];
+  // compact the keys in place (a key moves to a slot at or below its own, already read), then
+  // rank them
+  int* Ls = T;
   if (lane == 0) nlist[wid] = 0;
   __syncwarp();
-  for (int base = 0; base < kHashCap; base += 32) {
+  for (int base = 0; base < cap; base += 32) {
     int key = T[base + lane];
     unsigned m = __ballot_sync(0xffffffffu, key >= 0);
     int pos = nlist[wid] + __popc(m & ((1u << lane) - 1u));
@@ -784,6 +804,14 @@ k_spgemm_symbolic(int nrow, const int* __restrict__ arp, const int* __restrict__
     for (int r = 0; r < nk; ++r) rank += Ls[r] < key;
     ccol[off + rank] = key;
   }
+}
+
+// lanes per A entry in the symbolic phase: the power of two at or above B's mean row length
+static int lanes_per_entry(const DBsr& B) {
+  const int64_t mean = B.nbr > 0 ? (B.nnzb + B.nbr - 1) / B.nbr : 1;
+  int l = 1;
+  while (l < 32 && l < mean) l <<= 1;
+  return l;
 }
 
 // ---- SpGEMM over work units.  A unit is a range [ue0, ue1) of A entries of one C row urow
@@ -1076,7 +1104,8 @@ static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C, bool
     AMGC_LAUNCH(k_bitmap_cols<<<div_up((int64_t)A.nbr * 32, 256), 256, 0, s>>>(A.nbr, wpr, bm.p, C.rowptr.p, nullptr,
                                                                                  nullptr));
   } else if (A.nbr > 0) {
-    AMGC_LAUNCH(k_spgemm_symbolic<0><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p,
+    AMGC_LAUNCH(k_spgemm_symbolic<0><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, lanes_per_entry(B), A.rowptr.p, A.col.p,
+                                                                  B.rowptr.p, B.col.p,
                                                                   C.rowptr.p, nullptr, nullptr, h->status.p));
   }
   AMGC_CUDA_TRY(cudaGetLastError());
@@ -1110,7 +1139,8 @@ static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C, bool
     AMGC_TRY(upload(U->d_su0, U->su0, s));
     AMGC_TRY(upload(U->d_su1, U->su1, s));
   } else {
-    AMGC_LAUNCH(k_spgemm_symbolic<1><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p,
+    AMGC_LAUNCH(k_spgemm_symbolic<1><<<g, kGemmWarps * 32, 0, s>>>(A.nbr, lanes_per_entry(B), A.rowptr.p, A.col.p,
+                                                                  B.rowptr.p, B.col.p,
                                                                   nullptr, C.rowptr.p, C.col.p, h->status.p));
     DBuf<int> mx;
     AMGC_TRY(mx.alloc(1));
