@@ -480,16 +480,23 @@ __global__ void k_agg_phase2(int n, const int* __restrict__ rp, const int* __res
   }
   agg[i] = a;
 }
-// phase 3: unassigned node -> phase-2 aggregate with most shared edges, ties to the smallest id
+// phase 3: unassigned node -> phase-2 aggregate with most shared edges, ties to the smallest id.
+// One warp per node: each lane scores the candidates of its share of the neighbours (every
+// neighbour is counted for every candidate), then the warp keeps the best (count, id) pair.
 __global__ void k_agg_phase3(int n, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ body,
                              const int* __restrict__ agg2, int* __restrict__ agg, int* st) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (i >= n) return;
-  if (agg2[i] >= 0) { agg[i] = agg2[i]; return; }
+  const int own = agg2[i];
+  if (own >= 0) {
+    if (lane == 0) agg[i] = own;
+    return;
+  }
   const int bi = body[i];
   int best = -1, best_cnt = 0;
   const int b = rp[i], e = rp[i + 1];
-  for (int q = b; q < e; ++q) {
+  for (int q = b + lane; q < e; q += 32) {
     int j = col[q];
     if (j == i || body[j] != bi) continue;
     int a = agg2[j];
@@ -502,8 +509,16 @@ __global__ void k_agg_phase3(int n, const int* __restrict__ rp, const int* __res
     }
     if (cnt > best_cnt || (cnt == best_cnt && a < best)) { best = a; best_cnt = cnt; }
   }
-  if (best < 0) set_status(st, ST_BAD_INDEX);
-  agg[i] = best;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int oc = __shfl_xor_sync(0xffffffffu, best_cnt, o);
+    const int oa = __shfl_xor_sync(0xffffffffu, best, o);
+    if (oc > best_cnt || (oc == best_cnt && oa >= 0 && (best < 0 || oa < best))) { best = oa; best_cnt = oc; }
+  }
+  if (lane == 0) {
+    if (best < 0) set_status(st, ST_BAD_INDEX);
+    agg[i] = best;
+  }
 }
 
 static int mis2_aggregate(amgc_hierarchy* h, Level& L, DBuf<int>& roots, int* n_agg) {
@@ -551,7 +566,7 @@ static int mis2_aggregate(amgc_hierarchy* h, Level& L, DBuf<int>& roots, int* n_
   AMGC_TRY(roots.alloc(na));
   AMGC_LAUNCH(k_agg_phase2<<<g, 256, 0, s>>>(n, rp, col, body, state.p, nr.p, a1.p, roots.p));
   AMGC_TRY(L.agg.alloc(n));
-  AMGC_LAUNCH(k_agg_phase3<<<g, 256, 0, s>>>(n, rp, col, body, a1.p, L.agg.p, h->status.p));
+  AMGC_LAUNCH(k_agg_phase3<<<div_up((int64_t)n * 32, 256), 256, 0, s>>>(n, rp, col, body, a1.p, L.agg.p, h->status.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   AMGC_TRY(check_status(h, "aggregation"));
   *n_agg = na;
@@ -891,12 +906,13 @@ k_spgemm_units(int nunits, const int* __restrict__ urow, const int* __restrict__
                const int64_t* __restrict__ uout, const int* __restrict__ arp, const int* __restrict__ acol,
                const double* __restrict__ aval, const int* __restrict__ brp, const int* __restrict__ bcol,
                const double* __restrict__ bval, const int* __restrict__ crp, const int* __restrict__ ccol,
-               double* __restrict__ cval, double* __restrict__ scratch, int cmax) {
+               double* __restrict__ cval, double* __restrict__ scratch, int cmax, int cache_cols) {
   constexpr int NQ = BR * BC;
   extern __shared__ double sp_acc[];
   __shared__ int taken[8][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int u = blockIdx.x * (blockDim.x >> 5) + wid;
+  const int nw = blockDim.x >> 5;
+  const int u = blockIdx.x * nw + wid;
   if (u >= nunits) return;
   const int row = urow ? urow[u] : u;
   const int e0 = urow ? ue0[u] : arp[row], e1 = urow ? ue1[u] : arp[row + 1];
@@ -905,6 +921,13 @@ k_spgemm_units(int nunits, const int* __restrict__ urow, const int* __restrict__
   double* out = (uout == nullptr || uout[u] < 0) ? cval + (int64_t)c0 * NQ : scratch + uout[u];
   double* acc = SMEM ? sp_acc + (size_t)wid * cmax * NQ : out;
   for (int q = lane; q < len * NQ; q += 32) acc[q] = 0.0;
+  // the C row's columns, searched once per B entry, from shared memory when they fit
+  const int* cs = ccol + c0;
+  if (cache_cols) {
+    int* cc = reinterpret_cast<int*>(sp_acc + (SMEM ? (size_t)nw * cmax * NQ : 0)) + (size_t)wid * cmax;
+    for (int q = lane; q < len; q += 32) cc[q] = ccol[c0 + q];
+    cs = cc;
+  }
   __syncwarp();
   for (int e = e0; e < e1; ++e) {
     const int k = acol[e];
@@ -916,13 +939,15 @@ k_spgemm_units(int nunits, const int* __restrict__ urow, const int* __restrict__
       if (tc + lane < t1) {
         const int c = bcol[tc + lane];
         use = !SYM || c >= row;
-        int lo = c0, hi = c1 - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (ccol[mid] < c) lo = mid + 1;
-          else hi = mid;
+        if (use) {
+          int lo = 0, hi = len - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cs[mid] < c) lo = mid + 1;
+            else hi = mid;
+          }
+          pos = lo;
         }
-        pos = lo - c0;
       }
       // the entries taken (all of them unless SYM), listed in lane order
       const unsigned take = __ballot_sync(0xffffffffu, use);
@@ -1039,18 +1064,20 @@ static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, int cmax, SpUni
   // hide the latency of the position searches better than shared memory saves
   const bool smem_acc = per_warp <= kUnitSmemWarp;
   const int wpb = smem_acc ? 8 : kGemmWarps;
-  const size_t smem = smem_acc ? (size_t)wpb * per_warp : 0;
-  if (smem_acc)
-    AMGC_CUDA_TRY(cudaFuncSetAttribute(k_spgemm_units<BR, BK, BC, true, SYM>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kUnitSmem));
+  // plus each warp's copy of its C row's columns when that stays within the CTA's budget
+  const size_t acc_bytes = smem_acc ? (size_t)wpb * per_warp : 0;
+  const size_t col_bytes = (size_t)wpb * std::max(cmax, 1) * sizeof(int);
+  const int cache_cols = acc_bytes + col_bytes <= (size_t)kUnitSmem ? 1 : 0;
+  const size_t smem = acc_bytes + (cache_cols ? col_bytes : 0);
   auto kern = smem_acc ? k_spgemm_units<BR, BK, BC, true, SYM> : k_spgemm_units<BR, BK, BC, false, SYM>;
+  if (smem > 48 * 1024) AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kUnitSmem));
   DBuf<double> scratch;
   if (U) {
     const int nu = (int)U->row.size();
     if (U->scratch > 0) AMGC_TRY(scratch.alloc((size_t)U->scratch));
     AMGC_LAUNCH(kern<<<div_up(nu, wpb), wpb * 32, smem, s>>>(
         nu, U->d_row.p, U->d_e0.p, U->d_e1.p, U->d_out.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
-        C.rowptr.p, C.col.p, C.val.p, scratch.p, cmax));
+        C.rowptr.p, C.col.p, C.val.p, scratch.p, cmax, cache_cols));
     const int ns = (int)U->srow.size();
     if (ns > 0 && cmax > 0)   // (an empty product, cmax = 0, has nothing to add up)
       AMGC_LAUNCH(k_spgemm_reduce<<<dim3(div_up((int64_t)cmax * NQ, 128), ns), 128, 0, s>>>(
@@ -1058,7 +1085,7 @@ static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, int cmax, SpUni
   } else {
     AMGC_LAUNCH(kern<<<div_up(A.nbr, wpb), wpb * 32, smem, s>>>(
         A.nbr, nullptr, nullptr, nullptr, nullptr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
-        C.rowptr.p, C.col.p, C.val.p, nullptr, cmax));
+        C.rowptr.p, C.col.p, C.val.p, nullptr, cmax, cache_cols));
   }
   if (SYM)
     AMGC_LAUNCH(k_sym_mirror<BR><<<div_up((int64_t)A.nbr * 32, 128), 128, 0, s>>>(A.nbr, C.rowptr.p, C.col.p, C.val.p));
