@@ -599,9 +599,99 @@ __global__ void k_lm_assign(int nl, const int* __restrict__ lm_dnode, const int*
 }
 
 // ======================================================================== tentative prolongator by QR
-// One warp per aggregate: classical Gram-Schmidt with one re-orthogonalisation pass on the
-// aggregate's nullspace rows (member nodes ascending, DOF-minor); Q goes to P-hat's blocks,
-// R (positive diagonal) to the coarse nullspace.
+// One warp per aggregate, Cholesky QR applied twice (CholQR2) to the aggregate's nullspace rows
+// (member nodes ascending, DOF-minor): each pass forms the 6 x 6 Gram matrix of the current
+// rows (lanes over rows, then a warp sum: every lane ends with the same bits), its Cholesky
+// factor R_p (positive diagonal) redundantly in every lane, and the rows times R_p^-1.  Two
+// passes give orthonormal columns to rounding level for nullspaces far from rank deficiency,
+// in four sweeps over the rows instead of a sequential Gram-Schmidt chain; the product R_2 R_1
+// (positive diagonal) goes to the coarse nullspace and the rows to P-hat's blocks.  The rank
+// test reads R_1's diagonal (min / max below 1e-12, or a non-positive pivot).
+__device__ __forceinline__ int64_t qr_row_addr(const int* __restrict__ midx, int m0, int bu, int t) {
+  const int node = midx[m0 + t / bu];
+  return ((int64_t)node * bu + (t % bu)) * 6;
+}
+// one CholQR pass: rows of src (or of dst after the first pass) become rows of dst = src R^-1
+// (src and dst may be the same array: each lane reads and writes only its own rows)
+__device__ bool cholqr_pass(const int* __restrict__ midx, int m0, int bu, int nrows, const double* src, double* dst,
+                            int lane, double (&R)[6][6]) {
+  double g[21];
+#pragma unroll
+  for (int q = 0; q < 21; ++q) g[q] = 0.0;
+  for (int t = lane; t < nrows; t += 32) {
+    const double* b = src + qr_row_addr(midx, m0, bu, t);
+    double v[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v[c] = b[c];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i; j < 6; ++j) {
+        const int q = i * 6 - (i * (i - 1)) / 2 + (j - i);   // packed upper triangle, row-major
+        g[q] = fma(v[i], v[j], g[q]);
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < 21; ++q) g[q] = warp_sum(g[q]);
+  // Cholesky G = R^T R
+  bool ok = true;
+  {
+    double G[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i; j < 6; ++j) G[i][j] = g[i * 6 - (i * (i - 1)) / 2 + (j - i)];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) R[i][j] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      double d = G[i][i];
+#pragma unroll
+      for (int k = 0; k < i; ++k) d = fma(-R[k][i], R[k][i], d);
+      if (!(d > 0.0) || !isfinite(d)) { ok = false; d = 1.0; }
+      const double rii = sqrt(d);
+      R[i][i] = rii;
+      const double inv = 1.0 / rii;
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        double e = G[i][j];
+#pragma unroll
+        for (int k = 0; k < i; ++k) e = fma(-R[k][i], R[k][j], e);
+        R[i][j] = e * inv;
+      }
+    }
+  }
+  // Rinv, upper triangular: column j from R Rinv(:, j) = e_j by back substitution
+  double Ri[6][6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+      double t = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = i + 1; k < 6; ++k) t = fma(-R[i][k], Ri[k][j], t);
+      Ri[i][j] = i > j ? 0.0 : t / R[i][i];
+    }
+  }
+  for (int t = lane; t < nrows; t += 32) {
+    const int64_t o = qr_row_addr(midx, m0, bu, t);
+    double v[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v[c] = src[o + c];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      double y = 0.0;
+#pragma unroll
+      for (int i = 0; i <= j; ++i) y = fma(v[i], Ri[i][j], y);
+      dst[o + j] = y;
+    }
+  }
+  __syncwarp();
+  return ok;
+}
 __global__ void k_tentative_qr(int n_agg, int bu, const int* __restrict__ mptr, const int* __restrict__ midx,
                                const double* __restrict__ B, double* __restrict__ Pval, double* __restrict__ Bc, int* st) {
   const int lane = threadIdx.x & 31;
@@ -609,47 +699,30 @@ __global__ void k_tentative_qr(int n_agg, int bu, const int* __restrict__ mptr, 
   if (a >= n_agg) return;
   const int m0 = mptr[a], m1 = mptr[a + 1];
   const int nrows = (m1 - m0) * bu;
-  auto addr = [&](int t, int c) -> int64_t {
-    int node = midx[m0 + t / bu];
-    return ((int64_t)node * bu + (t % bu)) * 6 + c;
-  };
-  for (int t = lane; t < nrows; t += 32)
-    for (int c = 0; c < 6; ++c) Pval[addr(t, c)] = B[addr(t, c)];
-  __syncwarp();
-  double R[6][6];
-  for (int i = 0; i < 6; ++i)
-    for (int j = 0; j < 6; ++j) R[i][j] = 0.0;
-  double rmax = 0.0;
-  for (int c = 0; c < 6; ++c) {
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int k = 0; k < c; ++k) {
-        double d = 0.0;
-        for (int t = lane; t < nrows; t += 32) d = fma(Pval[addr(t, k)], Pval[addr(t, c)], d);
-        d = warp_sum(d);
-        for (int t = lane; t < nrows; t += 32) Pval[addr(t, c)] -= d * Pval[addr(t, k)];
-        __syncwarp();
-        R[k][c] += d;
-      }
-    }
-    double nr = 0.0;
-    for (int t = lane; t < nrows; t += 32) {
-      double v = Pval[addr(t, c)];
-      nr = fma(v, v, nr);
-    }
-    nr = sqrt(warp_sum(nr));
-    R[c][c] = nr;
-    rmax = fmax(rmax, nr);
-    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
-    for (int t = lane; t < nrows; t += 32) Pval[addr(t, c)] *= inv;
-    __syncwarp();
+  double R1[6][6], R2[6][6];
+  const bool ok1 = cholqr_pass(midx, m0, bu, nrows, B, Pval, lane, R1);
+  const bool ok2 = cholqr_pass(midx, m0, bu, nrows, Pval, Pval, lane, R2);
+  double rmin = R1[0][0], rmax = R1[0][0];
+#pragma unroll
+  for (int c = 1; c < 6; ++c) {
+    rmin = fmin(rmin, R1[c][c]);
+    rmax = fmax(rmax, R1[c][c]);
   }
-  double rmin = R[0][0];
-  for (int c = 1; c < 6; ++c) rmin = fmin(rmin, R[c][c]);
-  if (nrows < 6 || !(rmin > 1e-12 * rmax)) {
+  if (nrows < 6 || !ok1 || !ok2 || !(rmin > 1e-12 * rmax)) {
     if (lane == 0) set_status(st, ST_RANK);
   }
-  if (lane < 6) {
-    for (int j = 0; j < 6; ++j) Bc[((int64_t)a * 6 + lane) * 6 + j] = R[lane][j];
+  // R = R2 R1 (upper triangular), lane i < 6 writes row i
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    if (lane == i) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        double r = 0.0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r = (k >= i && k <= j) ? fma(R2[i][k], R1[k][j], r) : r;
+        Bc[((int64_t)a * 6 + i) * 6 + j] = r;
+      }
+    }
   }
 }
 __global__ void k_tentative_pattern(int nn, const int* __restrict__ agg, int* __restrict__ rp, int* __restrict__ col) {
@@ -1273,17 +1346,15 @@ __global__ void k_sa_values(int nn, const int* __restrict__ rp, const int* __res
 
 // ======================================================================== smoother data
 // Pointwise diagonal of K, its inverse and the inverse of A~ (the diagonal, or with SIMPLEC the
-// absolute row sums).  One warp per node row: for block row r the lanes take the row's (block,
-// column) pairs, and the absolute values are added across the warp.
+// absolute row sums).  One thread per node row: the diagonal block is found by binary search
+// (columns ascending), and only SIMPLEC walks the whole row.
 template <int BU>
 __global__ void k_diag(int nn, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
                        int simplec, double* __restrict__ kdiag, double* __restrict__ dinv, double* __restrict__ atinv,
                        int* st) {
-  const int lane = threadIdx.x & 31;
-  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nn) return;
   const int e0 = rp[i], e1 = rp[i + 1];
-  // the diagonal block (columns ascending: a binary search)
   int lo = e0, hi = e1 - 1;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
@@ -1291,22 +1362,25 @@ __global__ void k_diag(int nn, const int* __restrict__ rp, const int* __restrict
     else hi = mid;
   }
   const bool found = e1 > e0 && col[lo] == i;
-  if (!found && lane == 0) set_status(st, ST_NO_DIAG);
-  const int nq = (e1 - e0) * BU;
+  if (!found) set_status(st, ST_NO_DIAG);
+  double as[BU];
+#pragma unroll
+  for (int r = 0; r < BU; ++r) as[r] = 0.0;
+  if (simplec)
+    for (int e = e0; e < e1; ++e) {
+      const double* v = val + (int64_t)e * BU * BU;
+#pragma unroll
+      for (int r = 0; r < BU; ++r)
+#pragma unroll
+        for (int c = 0; c < BU; ++c) as[r] += fabs(v[r * BU + c]);
+    }
+#pragma unroll
   for (int r = 0; r < BU; ++r) {
-    double as = 0.0;
-    for (int q = lane; q < nq; q += 32) {
-      const int eb = q / BU, c = q - eb * BU;
-      as += fabs(val[((int64_t)(e0 + eb) * BU + r) * BU + c]);
-    }
-    as = warp_sum(as);
-    if (lane == 0) {
-      const double dg = found ? val[((int64_t)lo * BU + r) * BU + r] : 0.0;
-      if (!(dg > 0.0) || !isfinite(dg)) set_status(st, ST_SINGULAR);
-      kdiag[(int64_t)i * BU + r] = dg;
-      dinv[(int64_t)i * BU + r] = 1.0 / dg;
-      atinv[(int64_t)i * BU + r] = 1.0 / (simplec ? as : dg);
-    }
+    const double dg = found ? val[((int64_t)lo * BU + r) * BU + r] : 0.0;
+    if (!(dg > 0.0) || !isfinite(dg)) set_status(st, ST_SINGULAR);
+    kdiag[(int64_t)i * BU + r] = dg;
+    dinv[(int64_t)i * BU + r] = 1.0 / dg;
+    atinv[(int64_t)i * BU + r] = 1.0 / (simplec ? as[r] : dg);
   }
 }
 // S_l = Z_l + sum_i B2[l,i] diag(atinv_i) B1[i,l]; Sinv_l = S_l^{-1}.  One warp per multiplier
@@ -1423,10 +1497,10 @@ int smoother_setup(amgc_hierarchy* h, int l) {
   AMGC_TRY(L.dinv.alloc(nu));
   AMGC_TRY(L.atinv.alloc(nu));
   if (L.bu == 3)
-    AMGC_LAUNCH(k_diag<3><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
+    AMGC_LAUNCH(k_diag<3><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
                                                 L.dinv.p, L.atinv.p, h->status.p));
   else
-    AMGC_LAUNCH(k_diag<6><<<div_up((int64_t)L.nn * 32, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
+    AMGC_LAUNCH(k_diag<6><<<div_up(L.nn, 128), 128, 0, s>>>(L.nn, L.K.rowptr.p, L.K.col.p, L.K.val.p, h->opts.simplec, L.kdiag.p,
                                                 L.dinv.p, L.atinv.p, h->status.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   AMGC_TRY(check_status(h, "K diagonal"));
