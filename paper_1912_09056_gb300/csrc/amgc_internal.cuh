@@ -14,14 +14,17 @@ namespace amgc {
 
 // ------------------------------------------------------------------ error handling
 void set_error(const std::string& msg);
+// Source location of the first launch in this thread that left a launch error, if any since the
+// last report (appended to the message of the CUDA error that reports it; then cleared).
+std::string take_launch_site();
 
-#define AMGC_CUDA_TRY(expr)                                                             \
-  do {                                                                                  \
-    cudaError_t e_ = (expr);                                                            \
-    if (e_ != cudaSuccess) {                                                            \
-      ::amgc::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));            \
-      return e_ == cudaErrorMemoryAllocation ? AMGC_ENOMEM : AMGC_ECUDA;                \
-    }                                                                                   \
+#define AMGC_CUDA_TRY(expr)                                                                          \
+  do {                                                                                               \
+    cudaError_t e_ = (expr);                                                                         \
+    if (e_ != cudaSuccess) {                                                                         \
+      ::amgc::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_) + ::amgc::take_launch_site()); \
+      return e_ == cudaErrorMemoryAllocation ? AMGC_ENOMEM : AMGC_ECUDA;                             \
+    }                                                                                                \
   } while (0)
 
 #define AMGC_TRY(expr)            \
@@ -30,9 +33,19 @@ void set_error(const std::string& msg);
     if (s_ != AMGC_OK) return s_; \
   } while (0)
 
-// Every kernel launch of the library goes through AMGC_LAUNCH, which counts it.
+// Every kernel launch of the library goes through AMGC_LAUNCH, which counts it.  A LaunchSite
+// temporary lives to the end of the launch expression; its destructor notes the source line of
+// the first launch that leaves a launch error (an invalid configuration), so that the error, when
+// a later check reports it, names the launch.
 extern std::atomic<long long> g_launches;
-#define AMGC_LAUNCH(...) (::amgc::g_launches.fetch_add(1, std::memory_order_relaxed), __VA_ARGS__)
+struct LaunchSite {
+  const char* file;
+  int line;
+  LaunchSite(const char* f, int l) : file(f), line(l) {}
+  ~LaunchSite();
+};
+#define AMGC_LAUNCH(...) \
+  (::amgc::LaunchSite(__FILE__, __LINE__), ::amgc::g_launches.fetch_add(1, std::memory_order_relaxed), __VA_ARGS__)
 
 // Device status bits written by kernels that detect bad input or a singular block.
 enum : int {

@@ -65,6 +65,19 @@ int pool_alloc(void** p, size_t bytes) {
 void pool_free(void* p) { cudaFreeAsync(p, g_alloc_stream); }
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+static thread_local std::string g_launch_site;
+LaunchSite::~LaunchSite() {
+  if (g_launch_site.empty() && cudaPeekAtLastError() != cudaSuccess) {
+    const char* base = std::strrchr(file, '/');
+    g_launch_site = std::string(" (launch at ") + (base ? base + 1 : file) + ":" + std::to_string(line) + ")";
+  }
+}
+std::string take_launch_site() {
+  std::string s;
+  s.swap(g_launch_site);
+  return s;
+}
+
 // Largest coarsest system solved with the dense explicit inverse.
 constexpr int kMaxDenseRows = 16384;
 

@@ -1143,7 +1143,9 @@ static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, int cmax, SpUni
   const int cache_cols = acc_bytes + col_bytes <= (size_t)kUnitSmem ? 1 : 0;
   const size_t smem = acc_bytes + (cache_cols ? col_bytes : 0);
   auto kern = smem_acc ? k_spgemm_units<BR, BK, BC, true, SYM> : k_spgemm_units<BR, BK, BC, false, SYM>;
-  if (smem > 48 * 1024) AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kUnitSmem));
+  // (the dynamic limit is raised for every launch: the kernel's static shared memory counts
+  // against the default 48 KB too)
+  AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kUnitSmem));
   DBuf<double> scratch;
   if (U) {
     const int nu = (int)U->row.size();
@@ -2494,7 +2496,8 @@ int coarse_setup(amgc_hierarchy* h, int l) {
   const size_t smem = blocked ? (size_t)n * (2 * gjb * sizeof(double) + 2 * sizeof(int))
                               : 2 * (size_t)n * sizeof(double);
   if (coop && smem <= 200 * 1024) {
-    if (smem > 48 * 1024) AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // (raised whatever the size: the kernel's static shared memory counts against 48 KB too)
+    AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     AMGC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGjcThreads, smem));
   }
   if (per_sm > 0) {
