@@ -182,6 +182,9 @@ int amgc_apply(struct amgc_hierarchy* h, const double* x, double* y, void* strea
 
 /* Solves A x = rhs by right-preconditioned flexible GMRES with one V-cycle per iteration,
  * x_0 = 0, stopped when ||b - A x_k|| / ||b|| < tol (Eq. ch7_linearstoppingcriterion).
+ * Arnoldi: classical Gram-Schmidt with re-orthogonalisation; the first projection's
+ * coefficients come from FP32 copies of the basis, the updates and the second projection are
+ * FP64, so the Hessenberg matrix and the Arnoldi relation hold to FP64 rounding.
  * rhs, x: device vectors of length rows[0]; iters / relres may be NULL.  Returns
  * AMGC_NOT_CONVERGED (x holds the last iterate) or AMGC_BREAKDOWN on failure. */
 int amgc_solve(struct amgc_hierarchy* h, const double* rhs, double* x, int32_t* iters,

@@ -28,6 +28,7 @@ import scipy.sparse as sp
 
 from .aggregate import aggregate_nodes, aggregation_graph, lagmult_aggregation
 from .saddle import BlockMat, block_diag3, build_saddle
+from .blocksmoothers import braess_sarazin_sweep, ilu0_solver, schur_approx, sgs, simple_sweep, uzawa_sweep
 from .smoother import atilde_diag, cheap_simple_sweep, schur_blocks, schur_rho
 from .transfer import galerkin, lambda_max, smoothed_prolongator, tentative_lagmult, tentative_prolongator, transpose
 
@@ -45,6 +46,13 @@ class Options:
     simplec: int = 0             # 0: A_tilde = diag(K), 1: absolute row sums (SIMPLEC)
     seed: int = 0x5EED
     schur_damping: int = 0       # 1: alpha -> min(alpha, (4/3)/rho(S_bd^-1 S_hat)) per level
+    # level smoother: "cheap_simple" (the default above), or a cheap block smoother of Sec. 5.1 /
+    # 5.2 with SGS for K and nodal-block ILU(0) for its Schur approximation: "uzawa",
+    # "braess_sarazin", "simple_sgs" (SIMPLE, or SIMPLEC with simplec = 1)
+    smoother: str = "cheap_simple"
+    block_omega: float = 0.7     # damping of the block smoother (the paper's omega)
+    sgs_sweeps: int = 1
+    sgs_omega: float = 0.7
     fgmres_restart: int = 50
     fgmres_maxit: int = 1000
     tol: float = 1e-8
@@ -140,12 +148,42 @@ class Hierarchy:
     def smooth(self, L: Level, u, lam, f, g):
         o = self.opts
         Zf = L.Z_full()
+        K, B1, B2 = L.K.val, L.B1.val, L.B2.val
+        if o.smoother != "cheap_simple":
+            return self._block_smooth(L, u, lam, f, g, Zf)
 
         def s_inv(r):
             return np.einsum("lij,lj->li", L.S_inv, r.reshape(-1, 3)).ravel()
         for _ in range(o.smoother_sweeps):
-            u, lam = cheap_simple_sweep(L.K.val, L.B1.val, L.B2.val, Zf, u, lam, f, g, L.dinv,
+            u, lam = cheap_simple_sweep(K, B1, B2, Zf, u, lam, f, g, L.dinv,
                                         L.omega_j, o.jacobi_sweeps, L.at_inv, s_inv, L.alpha)
+        return u, lam
+
+    def _block_smooth(self, L: Level, u, lam, f, g, Zf):
+        """Cheap Uzawa, Braess-Sarazin or SIMPLE(C) sweeps (Algorithms 2-4, Sec. 5.2): SGS for K,
+        ILU(0) on the nodal 3 x 3 blocks of the Schur approximation (built on first use)."""
+        o = self.opts
+        K, B1, B2 = L.K.val, L.B1.val, L.B2.val
+        w = o.block_omega
+        if "block_s_solve" not in L.extra:
+            if L.nl == 0:
+                L.extra["block_s_solve"] = lambda r: r
+            else:
+                scale = 1.0 / w if o.smoother == "braess_sarazin" else 1.0
+                L.extra["block_s_solve"] = ilu0_solver(schur_approx(B1, B2, Zf, L.at_inv, scale), 3)
+        s_solve = L.extra["block_s_solve"]
+        zero = np.zeros(L.nu_dofs)
+        for _ in range(o.smoother_sweeps):
+            if o.smoother == "uzawa":
+                u, lam = uzawa_sweep(K, B1, B2, Zf, u, lam, f, g, w,
+                                     lambda r: sgs(K, r, zero, o.sgs_sweeps, o.sgs_omega), s_solve)
+            elif o.smoother == "braess_sarazin":
+                u, lam = braess_sarazin_sweep(K, B1, B2, Zf, u, lam, f, g, w, L.at_inv, s_solve)
+            elif o.smoother == "simple_sgs":
+                u, lam = simple_sweep(K, B1, B2, Zf, u, lam, f, g, w,
+                                      lambda r, x0: sgs(K, r, x0, o.sgs_sweeps, o.sgs_omega), L.at_inv, s_solve)
+            else:
+                raise ValueError(f"unknown smoother {o.smoother!r}")
         return u, lam
 
     def residual(self, L: Level, u, lam, f, g):
