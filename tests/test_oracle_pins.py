@@ -313,3 +313,20 @@ def test_schur_rho_is_one_without_active_nodes_and_keeps_alpha_on_matched_meshes
     assert rho < 5.0 / 3.0
     h = setup(p, Options(levels_max=2, coarse_max_rows=0, schur_damping=1))
     assert h.levels[0].alpha == 0.8
+
+
+def test_iteration_count_does_not_depend_on_the_rotation_of_the_model():
+    """The nodal block treatment of the contact rows makes the method indifferent to how the
+    interface is oriented in the Cartesian frame (the paper's rotated two-body study, Sec. 6.1):
+    rotating the whole tiny model about x by 0 to 90 degrees leaves the FGMRES count of the
+    3-level AMG within 10 % (29 to 30 iterations seen)."""
+    from oracle.krylov import fgmres
+    from paper_1912_09056_gb300.problem import workload
+    counts = []
+    for ang in (0.0, 30.0, 60.0, 90.0):
+        prob = workload(0, tilt_deg=ang)
+        h = setup(prob, Options(levels_max=3, coarse_max_rows=0, transfer=0))
+        x, it, _ = fgmres(h.A0(), prob.rhs, h.vcycle, tol=1e-8)
+        assert np.linalg.norm(prob.rhs - h.A0() @ x) <= 1e-8 * np.linalg.norm(prob.rhs)
+        counts.append(it)
+    assert max(counts) <= 1.1 * min(counts), counts
