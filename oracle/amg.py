@@ -50,6 +50,9 @@ class Options:
     # 5.2 with SGS for K and nodal-block ILU(0) for its Schur approximation: "uzawa",
     # "braess_sarazin", "simple_sgs" (SIMPLE, or SIMPLEC with simplec = 1)
     smoother: str = "cheap_simple"
+    # coarsest level: "lu" (merged dense matrix, LU with partial pivoting) or "smoother" (the level
+    # smoother's sweeps from a zero guess, no merged matrix; the paper's alternative, Sec. 6.2)
+    coarse_solver: str = "lu"
     block_omega: float = 0.7     # damping of the block smoother (the paper's omega)
     sgs_sweeps: int = 1
     sgs_omega: float = 0.7
@@ -195,6 +198,9 @@ class Hierarchy:
         L = self.levels[level]
         nu = L.nu_dofs
         if level == self.n_levels - 1:
+            if self.opts.coarse_solver == "smoother" and self.n_levels > 1:
+                u, lam = self.smooth(L, np.zeros(nu), np.zeros(b.size - nu), b[:nu], b[nu:])
+                return np.concatenate([u, lam])
             return sla.lu_solve(L.lu, b)
         f, g = b[:nu], b[nu:]
         u = np.zeros(nu)
@@ -241,8 +247,9 @@ def setup(prob, opts: Optional[Options] = None) -> Hierarchy:
         lm_dnode_c = np.array([inv_d[Lc] for Lc in range(n_lagg)], dtype=np.int64)
         levels.append(Level(K=Kc, B1=B1c, B2=B2c, Z=Zc, body=body_c, B=Bc, Bl=Blc,
                             lm_dnode=lm_dnode_c, bu=6))
-    # smoother data on all but the coarsest level
-    for L in levels[:-1]:
+    # smoother data on all but the coarsest level (on all levels when it smooths the coarsest)
+    smoothed = levels if (o.coarse_solver == "smoother" and len(levels) > 1) else levels[:-1]
+    for L in smoothed:
         if L.lam_max == 0.0:
             L.lam_max = lambda_max(L.K.val)
         L.omega_j = o.jacobi_omega if o.jacobi_omega > 0 else (4.0 / 3.0) / L.lam_max

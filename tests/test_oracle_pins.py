@@ -330,3 +330,26 @@ def test_iteration_count_does_not_depend_on_the_rotation_of_the_model():
         assert np.linalg.norm(prob.rhs - h.A0() @ x) <= 1e-8 * np.linalg.norm(prob.rhs)
         counts.append(it)
     assert max(counts) <= 1.1 * min(counts), counts
+
+
+def test_smoother_as_coarsest_solver_matches_the_papers_observations():
+    """Sec. 6.2 compares LU on the coarsest level with the level smoother there: LU gives fewer
+    iterations, and with the smoother more levels compensate.  On the tiny workload: 23 / 58
+    iterations with 2 levels, 30 / 40 with 3 (LU / smoother); the smoothed V-cycle stays linear."""
+    from oracle.krylov import fgmres
+    from paper_1912_09056_gb300.problem import workload
+    prob = workload(0)
+    its = {}
+    for lv in (2, 3):
+        for cs in ("lu", "smoother"):
+            h = setup(prob, Options(levels_max=lv, coarse_max_rows=0, transfer=0, coarse_solver=cs))
+            x, it, _ = fgmres(h.A0(), prob.rhs, h.vcycle, tol=1e-8, maxit=500)
+            assert np.linalg.norm(prob.rhs - h.A0() @ x) <= 1e-8 * np.linalg.norm(prob.rhs)
+            its[(lv, cs)] = it
+            if cs == "smoother" and lv == 3:
+                rng = np.random.default_rng(5)
+                a, b = rng.standard_normal(prob.n), rng.standard_normal(prob.n)
+                lin = h.vcycle(2.0 * a - b) - (2.0 * h.vcycle(a) - h.vcycle(b))
+                assert np.linalg.norm(lin) <= 1e-12 * np.linalg.norm(h.vcycle(a))
+    assert its[(2, "lu")] < its[(2, "smoother")] and its[(3, "lu")] < its[(3, "smoother")], its
+    assert its[(3, "smoother")] < its[(2, "smoother")], its
