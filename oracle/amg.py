@@ -219,15 +219,30 @@ class Hierarchy:
         return self.levels[0].A()
 
 
-def setup(prob, opts: Optional[Options] = None) -> Hierarchy:
-    """Build the hierarchy for a ContactProblem (all FP64)."""
+def setup(prob, opts: Optional[Options] = None, reuse: Optional[Hierarchy] = None) -> Hierarchy:
+    """Build the hierarchy for a ContactProblem (all FP64).
+
+    reuse: a hierarchy of the same problem under another active set.  Only the constraint blocks
+    B2 and Z depend on the active set; the aggregates, the transfers, lambda_max and the coarse K
+    (the expensive parts of the setup) are taken from it, and the coarse B1, B2, Z, the smoother
+    data and the coarsest factorisation are formed anew.
+    """
     o = opts or Options()
     S = build_saddle(prob)
     L0 = Level(K=S.K, B1=S.B1, B2=S.B2, Z=S.Z, body=prob.body_id.astype(np.int64),
                B=prob.nullspace.copy(), Bl=np.ones(prob.n_s), lm_dnode=prob.slave_node.astype(np.int64), bu=3)
     L0.extra["fine"] = True
     levels = [L0]
-    while len(levels) < o.levels_max and levels[-1].rows >= o.coarse_max_rows:
+    if reuse is not None:
+        for Lr in reuse.levels[:-1]:
+            L = levels[-1]
+            for name in ("agg", "n_agg", "lagg", "n_lagg", "Phat", "P", "Pl", "R", "Rl", "lam_max"):
+                setattr(L, name, getattr(Lr, name))
+            _, B1c, B2c, Zc = galerkin(L.K, L.B1, L.B2, L.Z, L.P, L.Pl, L.lagg, L.n_lagg)
+            nxt = reuse.levels[len(levels)]
+            levels.append(Level(K=nxt.K, B1=B1c, B2=B2c, Z=Zc, body=nxt.body, B=nxt.B, Bl=nxt.Bl,
+                                lm_dnode=nxt.lm_dnode, bu=nxt.bu))
+    while reuse is None and len(levels) < o.levels_max and levels[-1].rows >= o.coarse_max_rows:
         L = levels[-1]
         G = aggregation_graph(L.K.pat, L.body)
         agg, roots = aggregate_nodes(G, o.seed)
