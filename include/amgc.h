@@ -54,6 +54,9 @@ enum {
   AMGC_ENOMEM = -7           /* device allocation failed                                        */
 };
 
+/* Opaque hierarchy handle (library-owned; see amgc_setup / amgc_destroy). */
+struct amgc_hierarchy;
+
 /* Block-sparse row matrix: n_brow x n_bcol blocks of br x bc, row-major blocks,
  * rowptr[n_brow+1], col[nnzb] sorted ascending within each row, val[nnzb*br*bc]. */
 typedef struct {
@@ -96,6 +99,11 @@ typedef struct {
                                 block-diagonal Schur step a contraction where a slave mesh much
                                 finer than its master couples many slave nodes through one
                                 master node (rho >> 2)                                       */
+  int32_t coarse_solver;     /* 0: explicit dense inverse of the merged coarsest matrix (the role
+                                of the paper's LU, Sec. 6.2).  1: the level smoother's sweeps from
+                                a zero guess on the coarsest level instead, with no merged matrix
+                                (the alternative compared in Sec. 6.2; no dense-size limit).
+                                Single hierarchies only; not with the transposed entry points */
 } amgc_options;
 
 typedef struct {
@@ -120,7 +128,7 @@ typedef struct {
 /* Fills the defaults: levels_max 10, coarse_max_rows 5000, SA, 1 sweep, 1 Jacobi sweep,
  * SIMPLE (diag K), FP64, restart 50, maxit 1000, seed 0x5EED, sa_omega 4/3, jacobi_omega
  * automatic, alpha 0.8, tol 1e-8 (Sec. 6.2 settings, Eq. ch7_linearstoppingcriterion), autotune 0,
- * schur_damping 0. */
+ * schur_damping 0, coarse_solver 0. */
 void amgc_default_options(amgc_options* opts);
 
 /* Builds the hierarchy (Sec. 4: segregated aggregation with Algorithm 1, transfers of

@@ -44,7 +44,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("fgmres_restart", C.c_int32), ("fgmres_maxit", C.c_int32),
                 ("seed", C.c_uint32), ("sa_omega", C.c_double), ("jacobi_omega", C.c_double),
                 ("simple_alpha", C.c_double), ("tol", C.c_double), ("autotune", C.c_int32),
-                ("schur_damping", C.c_int32)]
+                ("schur_damping", C.c_int32), ("coarse_solver", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -126,14 +126,21 @@ static int build(amgc_hierarchy* h, const amgc_bsr* K, const double* D_diag, con
     }
   }
   const int lc = (int)h->L.size() - 1;
-  if (max_instance_rows(h, h->L[lc]) > kMaxDenseRows) {
+  // the level smoother on the coarsest level needs no merged dense matrix
+  const bool coarse_smooth = o.coarse_solver == 1 && lc > 0;
+  if (!coarse_smooth && max_instance_rows(h, h->L[lc]) > kMaxDenseRows) {
     set_error("coarsest level has " + std::to_string(h->L[lc].rows()) +
               " rows; raise levels_max or lower coarse_max_rows (dense limit " + std::to_string(kMaxDenseRows) + ")");
     return AMGC_EINVAL;
   }
   {
     PhaseTimer pt(h, 8);
-    AMGC_TRY(coarse_setup(h, lc));
+    if (coarse_smooth) {
+      AMGC_TRY(smoother_setup(h, lc));
+      AMGC_TRY(smoother_finish(h, lc));
+    } else {
+      AMGC_TRY(coarse_setup(h, lc));
+    }
   }
   {
     PhaseTimer pt(h, 9);
@@ -233,6 +240,7 @@ void amgc_default_options(amgc_options* o) {
   o->tol = 1e-8;
   o->autotune = 0;
   o->schur_damping = 0;
+  o->coarse_solver = 0;
 }
 
 int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const int32_t* slave_node,
@@ -248,7 +256,7 @@ int amgc_setup(const amgc_bsr* K, const double* D_diag, const amgc_csr* M, const
       (M->n_row > 0 && (!D_diag || !slave_node || !triad || !active)) || (M->n_col > 0 && !master_node) ||
       opts->levels_max < 1 || opts->smoother_sweeps < 0 || opts->jacobi_sweeps < 1 || opts->fgmres_restart < 1 ||
       opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 || !(opts->tol > 0.0) || (opts->precision != 64 && opts->precision != 32) ||
-      (opts->schur_damping != 0 && opts->schur_damping != 1)) {
+      (opts->schur_damping != 0 && opts->schur_damping != 1) || (opts->coarse_solver != 0 && opts->coarse_solver != 1)) {
     set_error(M && M->n_row < 1 ? "amgc_setup: no slave interface nodes (the system has no multiplier block)"
                                 : "amgc_setup: invalid argument");
     return AMGC_EINVAL;
@@ -298,8 +306,9 @@ int amgc_setup_batched(const amgc_bsr* K, const double* D_diag, const amgc_csr* 
       (M->n_col > 0 && !master_node) || opts->levels_max < 1 || opts->smoother_sweeps < 0 ||
       opts->jacobi_sweeps < 1 || opts->fgmres_restart < 1 || opts->fgmres_restart > 256 || opts->fgmres_maxit < 1 ||
       !(opts->tol > 0.0) || (opts->precision != 64 && opts->precision != 32) ||
-      (opts->schur_damping != 0 && opts->schur_damping != 1)) {
-    set_error("amgc_setup_batched: invalid argument");
+      (opts->schur_damping != 0 && opts->schur_damping != 1) || opts->coarse_solver != 0) {
+    set_error(opts->coarse_solver != 0 ? "amgc_setup_batched: coarse_solver 1 is for single hierarchies only"
+                                       : "amgc_setup_batched: invalid argument");
     return AMGC_EINVAL;
   }
   amgc_hierarchy* h = new (std::nothrow) amgc_hierarchy();
@@ -403,6 +412,10 @@ static int enter_transposed(amgc_hierarchy* h, void* stream, const char* where) 
   }
   if (h->n_inst > 1) {
     set_error(std::string(where) + ": not available for batched hierarchies");
+    return AMGC_EINVAL;
+  }
+  if (h->opts.coarse_solver != 0) {
+    set_error(std::string(where) + ": the transposed cycle needs coarse_solver 0 (the coarsest inverse)");
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;

@@ -853,6 +853,16 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
   const LevelV<T>& L = V[l];
   cudaStream_t s = h->stream;
   const int th = 256;
+  if (l == (int)V.size() - 1 && h->opts.coarse_solver == 1 && l > 0) {
+    // coarsest level without a merged matrix: the level smoother's sweeps from a zero guess
+    const int sweeps = h->opts.smoother_sweeps;
+    if (sweeps == 0) {
+      AMGC_LAUNCH(k_zero<T><<<div_up(L.rows(), th), th, 0, s>>>(L.rows(), x));
+      AMGC_CUDA_TRY(cudaGetLastError());
+    }
+    for (int k = 0; k < sweeps; ++k) AMGC_TRY(smooth<T>(h, L, l, b, x, k == 0));
+    return AMGC_OK;
+  }
   if (l == (int)V.size() - 1) {
     const int n = L.rows();
     if (L.c_inst)
@@ -1172,6 +1182,7 @@ int make_views(amgc_hierarchy* h) {
     Level& L = h->L[l];
     LevelF32& F = L.f;
     const bool last = l == nlev - 1;
+    const bool smoothed = !last || (h->opts.coarse_solver == 1 && l > 0);   // the level is smoothed
     AMGC_TRY(to_f32(h, L.K.val.p, (size_t)L.K.nnzb * L.bu * L.bu, F.K));
     AMGC_TRY(to_f32(h, L.B1.val.p, (size_t)L.B1.nnzb * L.bu * 3, F.B1));
     AMGC_TRY(to_f32(h, L.B2.val.p, (size_t)L.B2.nnzb * 3 * L.bu, F.B2));
@@ -1179,9 +1190,11 @@ int make_views(amgc_hierarchy* h) {
     if (!last) {
       AMGC_TRY(to_f32(h, L.P.val.p, (size_t)L.P.nnzb * L.P.br * L.P.bc, F.P));
       AMGC_TRY(to_f32(h, L.R.val.p, (size_t)L.R.nnzb * L.R.br * L.R.bc, F.R));
+      AMGC_TRY(to_f32(h, L.pl_w.p, (size_t)L.nl, F.pl_w));
+    }
+    if (smoothed) {
       AMGC_TRY(to_f32(h, L.jdinv.p, (size_t)L.nu(), F.jdinv));
       AMGC_TRY(to_f32(h, L.atinv.p, (size_t)L.nu(), F.atinv));
-      AMGC_TRY(to_f32(h, L.pl_w.p, (size_t)L.nl, F.pl_w));
     }
     if (L.Ks.nslice > 0) AMGC_TRY(to_f32(h, L.Ks.val.p, L.Ks.val.n, F.Ks));
     if (L.Ps.nslice > 0) AMGC_TRY(to_f32(h, L.Ps.val.p, L.Ps.val.n, F.Ps));
