@@ -28,7 +28,9 @@ import scipy.sparse as sp
 
 from .aggregate import aggregate_nodes, aggregation_graph, lagmult_aggregation
 from .saddle import BlockMat, block_diag3, build_saddle
-from .blocksmoothers import braess_sarazin_sweep, ilu0_solver, schur_approx, sgs, simple_sweep, uzawa_sweep
+from .blocksmoothers import (braess_sarazin_sweep, colored_block_sgs, ilu0_solver, jp_coloring, schur_approx,
+                             simple_sweep, uzawa_sweep)
+from .blocksmoothers import sgs as sgs_point
 from .smoother import atilde_diag, cheap_simple_sweep, schur_blocks, schur_rho
 from .transfer import galerkin, lambda_max, smoothed_prolongator, tentative_lagmult, tentative_prolongator, transpose
 
@@ -56,6 +58,8 @@ class Options:
     block_omega: float = 0.7     # damping of the block smoother (the paper's omega)
     sgs_sweeps: int = 1
     sgs_omega: float = 0.7
+    sgs_kind: str = "point"      # "point": natural-order pointwise SGS; "colored_block": nodal-block
+                                 # SGS in Jones-Plassmann colour order (the data-parallel form)
     fgmres_restart: int = 50
     fgmres_maxit: int = 1000
     tol: float = 1e-8
@@ -176,6 +180,15 @@ class Hierarchy:
                 L.extra["block_s_solve"] = ilu0_solver(schur_approx(B1, B2, Zf, L.at_inv, scale), 3)
         s_solve = L.extra["block_s_solve"]
         zero = np.zeros(L.nu_dofs)
+        sgs = sgs_point
+        if o.sgs_kind == "colored_block":
+            if "colored_sgs" not in L.extra:
+                col = jp_coloring(aggregation_graph(L.K.pat, np.zeros(L.nn, dtype=np.int64)), o.seed)
+                L.extra["colored_sgs"] = colored_block_sgs(K, col, L.bu)
+            prepared = L.extra["colored_sgs"]
+
+            def sgs(K, r, x0, sweeps, omega):
+                return prepared(r, x0, sweeps, omega)
         for _ in range(o.smoother_sweeps):
             if o.smoother == "uzawa":
                 u, lam = uzawa_sweep(K, B1, B2, Zf, u, lam, f, g, w,

@@ -59,6 +59,71 @@ def sgs(K: sp.spmatrix, b: np.ndarray, x: np.ndarray, sweeps: int = 1, omega: fl
     return x
 
 
+def jp_coloring(G: sp.spmatrix, seed: int = 0x5EED) -> np.ndarray:
+    """Colour of every node of the symmetric graph G (diagonal ignored) by Jones-Plassmann rounds:
+    an uncoloured node whose priority (the MIS-2 key, fmix32(i ^ seed) * 2^32 + i) exceeds that
+    of every uncoloured neighbour takes the smallest colour none of its coloured neighbours has.
+    The rounds are data parallel, so a GPU can reproduce the colouring exactly."""
+    from .aggregate import priorities
+    G = sp.csr_matrix(G)
+    n = G.shape[0]
+    key = priorities(n, seed)
+    color = -np.ones(n, dtype=np.int64)
+    nbrs = [G.indices[G.indptr[i]:G.indptr[i + 1]] for i in range(n)]
+    nbrs = [nb[nb != i] for i, nb in enumerate(nbrs)]
+    while (color < 0).any():
+        pick = [i for i in np.nonzero(color < 0)[0]
+                if all(color[j] >= 0 or key[j] < key[i] for j in nbrs[i])]
+        new = {}
+        for i in pick:
+            used = {int(color[j]) for j in nbrs[i] if color[j] >= 0}
+            c = 0
+            while c in used:
+                c += 1
+            new[i] = c
+        for i, c in new.items():
+            color[i] = c
+    return color
+
+
+def colored_block_sgs(K: sp.spmatrix, color: np.ndarray, bs: int = 3):
+    """Damped symmetric block Gauss-Seidel over nodal bs x bs blocks in colour order, prepared for
+    K and a colouring of its nodes: returns apply(b, x, sweeps, omega).  Each sweep visits the
+    colours ascending, then descending; within a colour every node i (no two adjacent) takes
+    x_i <- x_i + omega K_ii^{-1} (b_i - sum_j K_ij x_j) from the current x (the nodes of one colour
+    are updated together, as they do not couple)."""
+    K = sp.csr_matrix(K)
+    rows = _blocks(K, bs)
+    ncol = int(color.max()) + 1 if color.size else 0
+    parts = []
+    for c in range(ncol):
+        nodes = np.nonzero(color == c)[0]
+        idx = (nodes[:, None] * bs + np.arange(bs)[None, :]).ravel()
+        inv = np.array([np.linalg.inv(rows[i][i]) for i in nodes]).reshape(-1, bs, bs)
+        ri = np.repeat(np.arange(nodes.size * bs), bs)
+        ci = (np.arange(nodes.size)[:, None, None] * bs + np.zeros((1, bs, 1), dtype=np.int64)
+              + np.arange(bs)[None, None, :]).ravel()
+        dinv = sp.csr_matrix((inv.ravel(), (ri, ci)), shape=(nodes.size * bs, nodes.size * bs))
+        parts.append((idx, K[idx, :].tocsr(), dinv))
+    order = list(range(ncol)) + list(range(ncol - 1, -1, -1))
+
+    def apply(b: np.ndarray, x: np.ndarray, sweeps: int = 1, omega: float = 1.0) -> np.ndarray:
+        x = np.array(x, dtype=np.float64, copy=True)
+        b = np.asarray(b, dtype=np.float64)
+        for _ in range(sweeps):
+            for c in order:
+                idx, Kc, dinv = parts[c]
+                x[idx] = x[idx] + omega * (dinv @ (b[idx] - Kc @ x))
+        return x
+    return apply
+
+
+def block_sgs_colored(K: sp.spmatrix, b: np.ndarray, x: np.ndarray, color: np.ndarray, bs: int = 3,
+                      sweeps: int = 1, omega: float = 1.0) -> np.ndarray:
+    """One-off form of colored_block_sgs."""
+    return colored_block_sgs(K, color, bs)(b, x, sweeps, omega)
+
+
 def _blocks(S: sp.csr_matrix, bs: int):
     """Rows of S as {block column: bs x bs array} per block row (the block pattern of S)."""
     nb = S.shape[0] // bs
