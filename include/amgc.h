@@ -32,6 +32,9 @@
  *    DEVICE pointers unless the call says otherwise.
  *  - The hierarchy is owned by the library until amgc_destroy().  A failed amgc_setup leaves
  *    *out == NULL and frees everything it allocated.
+ *  - The library keeps per-device state for the life of the process (its memory pool, the device
+ *    address of a static scratch array).  After cudaDeviceReset on a device that state is stale:
+ *    do not call the library on that device again in the same process.
  */
 #ifndef AMGC_H
 #define AMGC_H
@@ -246,7 +249,10 @@ int amgc_grad_elements(int32_t ne, const int32_t* conn, const int32_t* shape, co
  * pool with a hard cap leaves no room for the library's own allocations), or a latency-bound
  * loop that must stay out of the driver's allocator and its implicit synchronisation.  The
  * paper has no counterpart; this is a property of the library.
- * Same arguments and results as amgc_grad_elements.  Its scratch is one file-scope device
+ * Same arguments and results as amgc_grad_elements, except that this call is asynchronous: it
+ * only enqueues its two kernels on `stream` and returns (amgc_grad_elements waits for its stream
+ * before it frees its scratch); read gE and gt after synchronising that stream.  With gt == NULL
+ * no scratch is used at all, and ne == 0 returns at once.  Its scratch is one file-scope device
  * array of 3 x 262144 doubles (6 MiB) that every GPU loading the library holds until the
  * process exits: ne above 262144 is rejected with AMGC_EINVAL.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress) with the device current, so make
@@ -306,6 +312,32 @@ int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what,
 int amgc_profile(struct amgc_hierarchy* h, int32_t enable);
 int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes,
                       double* flops);
+
+/* Overrides the row mapping of one sparse apply of the cycle (the choice the setup-time autotuner
+ * makes when opts.autotune = 1).  level: 0 .. n_levels-1; matrix: 0 = the level's K (with its B1
+ * coupling), 1 = its prolongator P, 2 = its restriction R (P and R: not on the coarsest level);
+ * precision: 64 = the FP64 views (the Krylov operator apply and the FP64 cycle), 32 = the FP32
+ * cycle (hierarchies set up with precision 32 only); mapping: -1 = the default, 0 = one warp per
+ * block row, 1 / 2 = SELL-32 with one / two threads per block row, 3 = the shared-memory staged
+ * FP32 kernel with bounded waits (level 0, K, precision 32 only).  Builds the SELL copy of the
+ * matrix if it has none and drops the captured V-cycle graphs (recaptured on the next cycle).
+ * Synchronises the hierarchy's last stream.  Errors: AMGC_EINVAL (argument out of range, or a
+ * mapping the matrix has no form for), AMGC_ENOMEM, AMGC_ECUDA.  (Library mechanics; the paper
+ * has no counterpart.) */
+int amgc_set_row_mapping(struct amgc_hierarchy* h, int32_t level, int32_t matrix, int32_t precision,
+                         int32_t mapping);
+
+/* Sets how many times each bounded device wait of the hierarchy's kernels (the mbarrier waits of
+ * the staged FP32 apply) tests its barrier before giving up: polls < 0 restores the default (2^26
+ * tests, about a second); 0 makes every such wait give up without testing (the give-up path on
+ * demand, for tests of the error handling); up to 2^32 - 1 otherwise.  A wait that gives up makes
+ * its warp stop, lets the copies the warp started land (waiting for them with the default limit),
+ * and sets a status bit: amgc_vcycle and amgc_solve then return AMGC_TIMEOUT (amgc_last_error says
+ * which call), and the output vector is incomplete.  The status is cleared when it is reported, so
+ * the next call runs normally.  Drops the captured V-cycle graphs.  Synchronises the hierarchy's
+ * last stream.  Errors: AMGC_EINVAL (h NULL, polls above 2^32 - 1), AMGC_ECUDA.  (Library
+ * mechanics; the paper has no counterpart.) */
+int amgc_set_wait_limit(struct amgc_hierarchy* h, int64_t polls);
 
 /* Waits for the hierarchy's stream (and its auxiliary setup stream), then frees every device and
  * host resource the hierarchy owns (device memory goes back to the library's pool).  NULL is

@@ -28,13 +28,22 @@ def _device_problem(prob, K_val: torch.Tensor):
 
 
 class SaddleSolve(torch.autograd.Function):
+    """The forward hierarchy is kept for the backward pass only: it is released as soon as no
+    gradient is needed (forward without grad) or once the backward pass has used it.  A second
+    backward pass through the same graph (retain_graph=True) sets the hierarchy up again."""
+
     @staticmethod
     def forward(ctx, K_val, b, prob, opts, adj_tol):
         h = amgc.setup(_device_problem(prob, K_val), opts)
         x = torch.zeros_like(b)
         h.solve(b.detach().contiguous(), x)
-        ctx.h = h
         ctx.adj_tol = adj_tol
+        ctx.rebuild = (prob, K_val.detach(), opts)
+        if any(ctx.needs_input_grad[:2]):
+            ctx.h = h
+        else:
+            h.close()
+            ctx.h = None
         ctx.save_for_backward(x)
         return x
 
@@ -42,10 +51,17 @@ class SaddleSolve(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         h = ctx.h
-        adj = torch.zeros_like(gx)
-        h.solve_transposed(gx.contiguous(), adj, tol=ctx.adj_tol)
-        gK = torch.empty((h.export(0, "k_col").size, 3, 3), dtype=torch.float64, device=x.device)
-        h.grad_scatter(adj, x, gK)
+        if h is None:
+            prob, K_val, opts = ctx.rebuild
+            h = amgc.setup(_device_problem(prob, K_val), opts)
+        ctx.h = None
+        try:
+            adj = torch.zeros_like(gx)
+            h.solve_transposed(gx.contiguous(), adj, tol=ctx.adj_tol)
+            gK = torch.empty((h.export(0, "k_col").size, 3, 3), dtype=torch.float64, device=x.device)
+            h.grad_scatter(adj, x, gK)
+        finally:
+            h.close()
         return gK, adj, None, None, None
 
 

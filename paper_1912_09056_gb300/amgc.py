@@ -113,6 +113,10 @@ def load():
     lib.amgc_solve_batched.restype = C.c_int
     lib.amgc_grad_elements_noalloc.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.amgc_grad_elements_noalloc.restype = C.c_int
+    lib.amgc_set_row_mapping.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+    lib.amgc_set_row_mapping.restype = C.c_int
+    lib.amgc_set_wait_limit.argtypes = [vp, C.c_int64]
+    lib.amgc_set_wait_limit.restype = C.c_int
     lib.amgc_destroy.argtypes = [vp]
     lib.amgc_destroy.restype = None
     lib.amgc_strerror.argtypes = [C.c_int]
@@ -252,6 +256,18 @@ class Hierarchy:
         _check(self._lib.amgc_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(b), C.byref(f)),
                "amgc_profile_read")
         return ms.value, n.value, b.value, f.value
+
+    ROW_MATRIX = dict(K=0, P=1, R=2)
+
+    def set_row_mapping(self, level: int, matrix: str, precision: int, mapping: int):
+        """amgc_set_row_mapping: matrix 'K', 'P' or 'R'; mapping -1 default, 0 warp per row,
+        1 / 2 SELL threads per row, 3 staged FP32 kernel (level-0 K, precision 32)."""
+        _check(self._lib.amgc_set_row_mapping(self._h, int(level), self.ROW_MATRIX[matrix], int(precision),
+                                              int(mapping)), "amgc_set_row_mapping")
+
+    def set_wait_limit(self, polls: int):
+        """amgc_set_wait_limit: tests per bounded device wait (< 0: the default; 0: every wait gives up)."""
+        _check(self._lib.amgc_set_wait_limit(self._h, int(polls)), "amgc_set_wait_limit")
 
     # ------------------------------------------------------------ device-vector calls
     def vcycle(self, r, z, stream=None):

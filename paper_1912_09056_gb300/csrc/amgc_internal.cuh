@@ -150,6 +150,7 @@ struct SellV {
   const T* val = nullptr;
   unsigned* ctr = nullptr;   // slice counter of the staged FP32 kernel (fine level), else null
   int* st = nullptr;         // status word for its bounded waits
+  long long polls = -1;      // poll limit of those waits (< 0: the kernel's default)
 };
 template <class T>
 struct LevelV {
@@ -275,6 +276,7 @@ struct amgc_hierarchy {
   amgc::DBuf<double> V, Zs, H, givens, gvec, y, wk, xk, rk;
   amgc::DBuf<float> Vf;             // FP32 copy of the Arnoldi basis (first projection pass)
   amgc::DBuf<unsigned> tma_ctr;    // slice counter of the staged FP32 fine-level apply
+  long long wait_polls = -1;       // poll limit of the bounded device waits (< 0: kernel default)
   amgc::DBuf<double> partial;      // per-block partial dot products
   std::vector<amgc::LevelV<double>> v64;   // cycle views, FP64
   std::vector<amgc::LevelV<float>> v32;    // cycle views, FP32 (precision 32)
@@ -378,6 +380,10 @@ int dot(amgc_hierarchy* h, int64_t n, const double* a, const double* b, const do
 // V-cycle (cycle.cu)
 int make_views(amgc_hierarchy* h);
 int precond_apply(amgc_hierarchy* h, const double* r, double* z);   // one V-cycle, FP64 in/out
+bool staged_apply_in_use(const amgc_hierarchy* h);   // the FP32 cycle's fine K runs the staged kernel
+void drop_cycle_graphs(amgc_hierarchy* h);            // forget captured cycles (their launches changed)
+int set_row_mapping(amgc_hierarchy* h, int level, int matrix, int precision, int mapping);
+int set_wait_limit(amgc_hierarchy* h, long long polls);
 int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y);
 // FGMRES (krylov.cu)
 int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol, int* iters, double* relres);
@@ -385,6 +391,11 @@ int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol, int* ite
 int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, int* iters, double* relres);
 // gradients (grad.cu)
 int grad_scatter(amgc_hierarchy* h, const double* adj, const double* x, double* gK, double* gB1, double* gB2);
+// the element-gradient kernels with caller-provided scratch `lift` (3 ne doubles, used when gt != 0),
+// enqueued on s without synchronising
+int launch_grad_elements(int ne, const int* conn, const int* shape, const double* Khat, const int* node_free,
+                         const double* adj, const double* x, const double* uD, const uint8_t* lift_mask,
+                         const double* E, double* gE, double* gt, double* lift, cudaStream_t s);
 int grad_elements(int ne, const int* conn, const int* shape, const double* Khat, const int* node_free,
                   const double* adj, const double* x, const double* uD, const uint8_t* lift_mask, const double* E,
                   double* gE, double* gt, cudaStream_t s);

@@ -349,7 +349,30 @@ int amgc_vcycle(struct amgc_hierarchy* h, const double* r, double* z, void* stre
   }
   h->stream = (cudaStream_t)stream;
   StreamScope scope_(h->stream);
-  return precond_apply(h, r, z);
+  AMGC_TRY(precond_apply(h, r, z));
+  // the staged FP32 apply's bounded waits report through the status word
+  if (staged_apply_in_use(h)) return check_status(h, "amgc_vcycle (FP32 V-cycle)");
+  return AMGC_OK;
+}
+
+int amgc_set_row_mapping(struct amgc_hierarchy* h, int32_t level, int32_t matrix, int32_t precision,
+                         int32_t mapping) {
+  if (!h) {
+    set_error("amgc_set_row_mapping: invalid argument");
+    return AMGC_EINVAL;
+  }
+  StreamScope scope_(h->stream);
+  AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return set_row_mapping(h, level, matrix, precision, mapping);
+}
+
+int amgc_set_wait_limit(struct amgc_hierarchy* h, int64_t polls) {
+  if (!h || polls > 0xffffffffLL) {
+    set_error("amgc_set_wait_limit: invalid argument");
+    return AMGC_EINVAL;
+  }
+  AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return set_wait_limit(h, polls);
 }
 
 int amgc_apply(struct amgc_hierarchy* h, const double* x, double* y, void* stream) {

@@ -305,14 +305,17 @@ static void launch_sell(const SellV<T>& S, int nbr, const int* rp2, const int* c
 // kTmaStages-deep shared-memory pipeline: lane 0 moves the next chunks of kTmaChunk slots of the
 // slice (values and block columns, contiguous in the SELL layout) with one bulk asynchronous copy
 // per array, completing on an mbarrier, while the warp computes the current chunk from shared
-// memory.  Only the x gathers go to global memory.  Every wait is bounded: a wait that gives up sets
-// ST_TIMEOUT, drains the copies still in flight (bounded again) and returns.
+// memory.  Only the x gathers go to global memory.  Every wait is bounded by `polls` tests of the
+// mbarrier (a kernel argument, kTmaSpin by default; 0 makes every wait give up without a test, which
+// exercises the give-up path deterministically): when any lane of a warp gives up, the whole warp
+// gives up (the decision is a warp vote, so the lanes never diverge), sets ST_TIMEOUT, waits for its
+// copies still in flight with the full kTmaSpin limit, and returns.
 constexpr int kTmaChunk = 4;                       // slots per stage
 constexpr int kTmaStages = 3;                      // stages per warp (copies run two chunks ahead)
 constexpr int kTmaWarps = 6;                       // warps per CTA
 constexpr int kTmaStageBytes = kTmaChunk * 9 * 32 * 4 + kTmaChunk * 32 * 4;   // 3x3 FP32 values + columns
 constexpr int kTmaSmem = kTmaWarps * kTmaStages * kTmaStageBytes;
-constexpr unsigned kTmaSpin = 1u << 26;           // polls before a wait gives up
+constexpr unsigned kTmaSpin = 1u << 26;           // default polls before a wait gives up
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -329,10 +332,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// true once the phase with the given parity has completed; false after kTmaSpin polls (the
-// non-blocking test, so that the limit bounds the time: about a second at most)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < kTmaSpin; ++it) {
+// true once the phase with the given parity has completed; false after `limit` polls (the
+// non-blocking test, so that the limit bounds the time: about a second at most for kTmaSpin)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -357,7 +360,7 @@ k_sell_tma(int nbr, int nslice, const int* __restrict__ soff, const int* __restr
            const int* __restrict__ rp2, const int* __restrict__ c2, const float* __restrict__ v2,
            const float* __restrict__ x2, const float* __restrict__ b, const float* __restrict__ x0,
            const float* __restrict__ dinv, float omega, float* __restrict__ y, unsigned* __restrict__ ctr,
-           int* __restrict__ st) {
+           int* __restrict__ st, unsigned polls) {
   extern __shared__ __align__(128) unsigned char tma_sh[];
   __shared__ uint64_t bars[kTmaWarps][kTmaStages];
   __shared__ TmaMeta meta[kTmaWarps][kTmaStages];
@@ -412,12 +415,15 @@ k_sell_tma(int nbr, int nslice, const int* __restrict__ soff, const int* __restr
     if (!m.valid) break;
     if (lane == 0) issue((k + kTmaStages - 1) % kTmaStages);   // the stage chunk k-1 used
     __syncwarp();
-    if (!mbar_wait(&bar[stg], (phase >> stg) & 1u)) {
-      // give up: record it, wait (bounded) for this warp's copies still in flight, leave
+    // every lane tests the barrier (each lane reads the copied data), the warp acts on the vote
+    const bool landed = mbar_wait(&bar[stg], (phase >> stg) & 1u, polls);
+    if (!__all_sync(0xffffffffu, landed)) {
+      // give up, as one warp: record it, wait for this warp's copies still in flight (bounded by
+      // the full limit, so that no copy lands after the CTA has left), leave
       if (lane == 0) {
         atomicOr(st, ST_TIMEOUT);
         for (int q = 0; q < kTmaStages; ++q)
-          if (mt[q].valid) mbar_wait(&bar[q], (phase >> q) & 1u);
+          if (mt[q].valid) mbar_wait(&bar[q], (phase >> q) & 1u, kTmaSpin);
       }
       __syncwarp();
       return;
@@ -480,7 +486,7 @@ static int launch_sell_tma(const SellV<float>& S, int nbr, const BsrV<float>* A2
   AMGC_CUDA_TRY(cudaMemsetAsync(S.ctr, 0, sizeof(unsigned), s));
   AMGC_LAUNCH(k_sell_tma<MODE><<<grid, kTmaWarps * 32, kTmaSmem, s>>>(
       nbr, S.nslice, S.off, S.len, S.col, S.val, x, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr,
-      A2 ? A2->val : nullptr, x2, b, x0, dinv, (float)omega, y, S.ctr, S.st));
+      A2 ? A2->val : nullptr, x2, b, x0, dinv, (float)omega, y, S.ctr, S.st, S.polls < 0 ? kTmaSpin : (unsigned)S.polls));
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
@@ -1216,6 +1222,7 @@ int make_views(amgc_hierarchy* h) {
       if (!h->tma_ctr.p) AMGC_TRY(h->tma_ctr.alloc(1));
       v.Ks.ctr = h->tma_ctr.p;
       v.Ks.st = h->status.p;
+      v.Ks.polls = h->wait_polls;
     }
     v.Ps = sview<float>(L.Ps, F.Ps.p);
     v.Rs = sview<float>(L.Rs, F.Rs.p);
@@ -1225,6 +1232,71 @@ int make_views(amgc_hierarchy* h) {
     h->v32.push_back(v);
   }
   AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return AMGC_OK;
+}
+
+// ------------------------------------------------------------------ mapping overrides, wait limit
+bool staged_apply_in_use(const amgc_hierarchy* h) {
+  return h->opts.precision == 32 && !h->v32.empty() && h->v32[0].kmap == 3;
+}
+
+void drop_cycle_graphs(amgc_hierarchy* h) {
+  for (int i = 0; i < 2; ++i) {
+    if (h->cycle_graph[i]) cudaGraphExecDestroy(h->cycle_graph[i]);
+    h->cycle_graph[i] = nullptr;
+    h->cycle_graph_kernels[i] = 0;
+  }
+}
+
+// matrix 0 = K, 1 = P, 2 = R of `level`; precision 64 or 32; mapping -1 (default), 0 (warp per
+// row), 1 / 2 (SELL, one / two threads per row), 3 (the staged FP32 kernel: level-0 K only)
+int set_row_mapping(amgc_hierarchy* h, int level, int matrix, int precision, int mapping) {
+  const int nlev = (int)h->L.size();
+  if (level < 0 || level >= nlev || matrix < 0 || matrix > 2 || (precision != 64 && precision != 32) ||
+      mapping < -1 || mapping > 3 || (matrix > 0 && level == nlev - 1)) {
+    set_error("amgc_set_row_mapping: invalid level, matrix, precision or mapping");
+    return AMGC_EINVAL;
+  }
+  if (precision == 32 && h->opts.precision != 32) {
+    set_error("amgc_set_row_mapping: the hierarchy has no FP32 cycle (precision 64)");
+    return AMGC_EINVAL;
+  }
+  if (mapping == 3 && !(level == 0 && matrix == 0 && precision == 32)) {
+    set_error("amgc_set_row_mapping: the staged kernel applies the FP32 fine-level K only");
+    return AMGC_EINVAL;
+  }
+  Level& L = h->L[level];
+  Sell& S = matrix == 0 ? L.Ks : (matrix == 1 ? L.Ps : L.Rs);
+  const DBsr& A = matrix == 0 ? L.K : (matrix == 1 ? L.P : L.R);
+  const int pidx = precision == 32 ? 1 : 0;
+  int* slot = matrix == 0 ? &L.kmap[pidx] : (matrix == 1 ? &L.pmap[pidx] : &L.rmap[pidx]);
+  if (mapping >= 1 && S.nslice == 0) {
+    AMGC_TRY(build_sell_of(h, A, S));
+    *slot = mapping;
+    AMGC_TRY(make_views(h));     // the views of the new SELL copy (and its FP32 mirror)
+  } else {
+    *slot = mapping;
+    LevelV<double>& v = h->v64[level];
+    if (precision == 64) (matrix == 0 ? v.kmap : (matrix == 1 ? v.pmap : v.rmap)) = mapping;
+    else {
+      LevelV<float>& w = h->v32[level];
+      (matrix == 0 ? w.kmap : (matrix == 1 ? w.pmap : w.rmap)) = mapping;
+    }
+  }
+  if (mapping == 3 && (h->v32.empty() || h->v32[0].Ks.ctr == nullptr)) {
+    *slot = -1;
+    AMGC_TRY(make_views(h));
+    set_error("amgc_set_row_mapping: the fine-level K has no staged FP32 form (not 3x3 SELL)");
+    return AMGC_EINVAL;
+  }
+  drop_cycle_graphs(h);
+  return AMGC_OK;
+}
+
+int set_wait_limit(amgc_hierarchy* h, long long polls) {
+  h->wait_polls = polls;
+  if (!h->v32.empty()) h->v32[0].Ks.polls = polls;
+  drop_cycle_graphs(h);
   return AMGC_OK;
 }
 

@@ -107,16 +107,25 @@ __global__ void k_sum3(int ne, const double* __restrict__ lift, double* __restri
   }
 }
 
+int launch_grad_elements(int ne, const int* conn, const int* shape, const double* Khat, const int* node_free,
+                         const double* adj, const double* x, const double* uD, const uint8_t* lift_mask,
+                         const double* E, double* gE, double* gt, double* lift, cudaStream_t s) {
+  if (ne == 0) return AMGC_OK;
+  // every lift entry k_sum3 reads is written by k_grad_elements of the same call
+  AMGC_LAUNCH(k_grad_elements<<<div_up((int64_t)ne * 32, kGradWarps * 32), kGradWarps * 32, 0, s>>>(
+      ne, conn, shape, Khat, node_free, adj, x, uD, lift_mask, E, gE, gt ? lift : nullptr));
+  if (gt) AMGC_LAUNCH(k_sum3<<<3, 1024, 0, s>>>(ne, lift, gt));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
 int grad_elements(int ne, const int* conn, const int* shape, const double* Khat, const int* node_free,
                   const double* adj, const double* x, const double* uD, const uint8_t* lift_mask, const double* E,
                   double* gE, double* gt, cudaStream_t s) {
   if (ne == 0) return AMGC_OK;
   DBuf<double> lift;
   if (gt) AMGC_TRY(lift.alloc((size_t)ne * 3));
-  AMGC_LAUNCH(k_grad_elements<<<div_up((int64_t)ne * 32, kGradWarps * 32), kGradWarps * 32, 0, s>>>(
-      ne, conn, shape, Khat, node_free, adj, x, uD, lift_mask, E, gE, gt ? lift.p : nullptr));
-  if (gt) AMGC_LAUNCH(k_sum3<<<3, 1024, 0, s>>>(ne, lift.p, gt));
-  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(launch_grad_elements(ne, conn, shape, Khat, node_free, adj, x, uD, lift_mask, E, gE, gt, lift.p, s));
   AMGC_CUDA_TRY(cudaStreamSynchronize(s));   // lift is freed on return
   return AMGC_OK;
 }

@@ -274,6 +274,10 @@ int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol_in, int* 
   double* cs = h->givens.p;
   double* sn = h->givens.p + m;
   double* pin = h->h_pinned;
+  // the staged FP32 apply reports a bounded wait that gave up in the status word, read with the
+  // iteration's residual estimate
+  const bool staged = staged_apply_in_use(h) && !h->transposed;
+  int* pst = reinterpret_cast<int*>(pin + 8);
 
   AMGC_LAUNCH(k_zero_vec<<<gn, th, 0, s>>>(n, x));
   AMGC_TRY(dot(h, n, rhs, rhs, nullptr, scal + 2));
@@ -320,7 +324,9 @@ int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol_in, int* 
       AMGC_LAUNCH(k_arnoldi_normalize<<<gn, th, 0, s>>>(n, scal + 2, w, w, wf));
       AMGC_CUDA_TRY(cudaGetLastError());
       AMGC_CUDA_TRY(cudaMemcpyAsync(pin, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (staged) AMGC_CUDA_TRY(cudaMemcpyAsync(pst, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
       AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+      if (staged && *pst != 0) return check_status(h, "fgmres (FP32 V-cycle)");
       ++total;
       jd = j + 1;
       relres = pin[0];

@@ -39,6 +39,29 @@ def test_noalloc_element_gradients_match_allocating_entry_point_twice():
         torch.cuda.synchronize()
         assert torch.allclose(gE, ref_gE, rtol=1e-12, atol=0.0)
         assert torch.allclose(gt, ref_gt, rtol=1e-12, atol=0.0)
+    # without gt no scratch is touched: gE alone, compared with the allocating call
+    gE_only = torch.full((tab.ne,), float("nan"), dtype=torch.float64, device="cuda")
+    amgc.grad_elements_noalloc(tab.conn, tab.shape, tab.Khat, tab.node_free, adj, x, tab.uD, tab.E, gE_only)
+    torch.cuda.synchronize()
+    assert torch.allclose(gE_only, ref_gE, rtol=1e-12, atol=0.0)
+    # zero elements: nothing to do, nothing written
+    empty = torch.zeros((0, 8), dtype=torch.int32, device="cuda")
+    keep = gt.clone()
+    amgc.grad_elements_noalloc(empty, tab.shape, tab.Khat, tab.node_free, adj, x, tab.uD, tab.E, gE,
+                               lift_mask=tab.top, gt=gt)
+    torch.cuda.synchronize()
+    assert torch.equal(gt, keep)
+    # on a side stream: the call only enqueues work there; results read after that stream is done
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        gE_s = torch.full((tab.ne,), float("nan"), dtype=torch.float64, device="cuda")
+        gt_s = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+        amgc.grad_elements_noalloc(tab.conn, tab.shape, tab.Khat, tab.node_free, adj, x, tab.uD, tab.E, gE_s,
+                                   lift_mask=tab.top, gt=gt_s, stream=side)
+    side.synchronize()
+    assert torch.allclose(gE_s, ref_gE, rtol=1e-12, atol=0.0)
+    assert torch.allclose(gt_s, ref_gt, rtol=1e-12, atol=0.0)
     # sizes above the static scratch are refused before any device work
     big = torch.zeros((262145, 8), dtype=torch.int32, device="cuda")
     with pytest.raises(amgc.AmgcError) as e:
