@@ -9,6 +9,7 @@ isotropic linear elasticity, 2x2x2 Gauss quadrature, assembled into a node-block
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 
 # Local node order of the hex8 element in natural coordinates.
 HEX8_XI = np.array(
@@ -97,25 +98,27 @@ def brick_mesh(nx: int, ny: int, nz: int, lo, hi):
 
 
 def block_pattern(conn: np.ndarray, n_nodes: int):
-    """Node-graph CSR (sorted columns, diagonal included) of the elements' couplings."""
+    """Node-graph CSR (sorted columns, diagonal included) of the elements' couplings: the
+    structure of E^T E for the element-node incidence matrix E.  Returns (rowptr, cols, keys)
+    with keys = row * n_nodes + col in ascending order."""
     ne = conn.shape[0]
-    r = np.repeat(conn, 8, axis=1).ravel()
-    c = np.tile(conn, (1, 8)).ravel()
-    keys = np.unique(r * n_nodes + c)
-    rows = keys // n_nodes
-    cols = keys % n_nodes
-    rowptr = np.zeros(n_nodes + 1, dtype=np.int64)
-    np.add.at(rowptr, rows + 1, 1)
-    rowptr = np.cumsum(rowptr)
-    del ne
+    inc = sp.csr_matrix((np.ones(ne * 8), (np.repeat(np.arange(ne, dtype=np.int64), 8), conn.ravel())),
+                        shape=(ne, n_nodes))
+    G = (inc.T.tocsr() @ inc).tocsr()
+    G.sort_indices()
+    rowptr = G.indptr.astype(np.int64)
+    cols = G.indices.astype(np.int64)
+    keys = np.repeat(np.arange(n_nodes, dtype=np.int64), np.diff(rowptr)) * n_nodes + cols
     return rowptr, cols, keys
 
 
-def assemble_bsr(coords, conn, E_elem, nu, n_nodes, chunk=65536):
+def assemble_bsr(coords, conn, E_elem, nu, n_nodes):
     """Assemble K as node-blocked CSR: (rowptr, col, val (nnzb,3,3)).
 
     Elements that are translates of the body's last element (all but the jittered ones on a
-    structured brick) share its unit-modulus matrix, scaled by their own E.
+    structured brick) share its unit-modulus matrix, scaled by their own E.  Contributions are
+    added one local node pair (a, b) at a time: on a brick every node is local node a of at
+    most one element, so the blocks of one pair land on distinct positions.
     """
     rowptr, cols, keys = block_pattern(conn, n_nodes)
     val = np.zeros((keys.size, 3, 3))
@@ -123,20 +126,22 @@ def assemble_bsr(coords, conn, E_elem, nu, n_nodes, chunk=65536):
     h = np.abs(rel[-1]).max()
     same = np.abs(rel - rel[-1][None]).max(axis=(1, 2)) <= 1e-12 * h
     K_ref = hex8_stiffness(coords[conn[-1:]], np.ones(1), nu)[0]
-    for s in range(0, conn.shape[0], chunk):
-        cc = conn[s:s + chunk]
-        sm = same[s:s + chunk]
-        Ke = np.empty((cc.shape[0], 24, 24))
-        Ke[sm] = K_ref[None] * E_elem[s:s + chunk][sm][:, None, None]
-        if np.any(~sm):
-            Ke[~sm] = hex8_stiffness(coords[cc[~sm]], E_elem[s:s + chunk][~sm], nu)
-        blk = Ke.reshape(-1, 8, 3, 8, 3).transpose(0, 1, 3, 2, 4)      # (ne,8,8,3,3)
-        r = np.repeat(cc, 8, axis=1).ravel()
-        c = np.tile(cc, (1, 8)).ravel()
-        pos = np.searchsorted(keys, r * n_nodes + c)
-        flat = blk.reshape(-1, 9)
-        for q in range(9):
-            val.reshape(-1, 9)[:, q] += np.bincount(pos, weights=flat[:, q], minlength=keys.size)
+    others = np.nonzero(~same)[0]
+    K_oth = hex8_stiffness(coords[conn[others]], E_elem[others], nu) if others.size else None
+    distinct = all(np.unique(conn[:, a]).size == conn.shape[0] for a in range(8))
+    Es = E_elem[same]
+    for a in range(8):
+        for b in range(8):
+            pos = np.searchsorted(keys, conn[:, a] * n_nodes + conn[:, b])
+            blk = K_ref[3 * a:3 * a + 3, 3 * b:3 * b + 3]
+            if distinct:
+                val[pos[same]] += Es[:, None, None] * blk[None]
+                if others.size:
+                    val[pos[others]] += K_oth[:, 3 * a:3 * a + 3, 3 * b:3 * b + 3]
+            else:
+                np.add.at(val, pos[same], Es[:, None, None] * blk[None])
+                if others.size:
+                    np.add.at(val, pos[others], K_oth[:, 3 * a:3 * a + 3, 3 * b:3 * b + 3])
     return rowptr, cols, val
 
 

@@ -125,6 +125,33 @@ def polygon_area(P: np.ndarray) -> float:
     return 0.5 * float(np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y))
 
 
+def quad_inverse_map_batched(X: np.ndarray, pts: np.ndarray, iters: int = 30, tol: float = 1e-14):
+    """Newton inverse of the bilinear maps of corners X (n,4,2), one map per point pts (n,2);
+    every point iterates until its own step is below tol (at most `iters` steps)."""
+    n = pts.shape[0]
+    xi = np.zeros(n)
+    eta = np.zeros(n)
+    live = np.arange(n)
+    for _ in range(iters):
+        if live.size == 0:
+            break
+        Xl = X[live]
+        N = quad_N(xi[live], eta[live])                              # (m,4)
+        x = np.einsum("mk,mkc->mc", N, Xl)
+        dxi_w = 0.25 * QUAD_XI[:, 0] * (1 + QUAD_XI[:, 1] * eta[live][:, None])
+        deta_w = 0.25 * QUAD_XI[:, 1] * (1 + QUAD_XI[:, 0] * xi[live][:, None])
+        a, b = np.einsum("mk,mk->m", dxi_w, Xl[:, :, 0]), np.einsum("mk,mk->m", deta_w, Xl[:, :, 0])
+        c, d = np.einsum("mk,mk->m", dxi_w, Xl[:, :, 1]), np.einsum("mk,mk->m", deta_w, Xl[:, :, 1])
+        r = pts[live] - x
+        det = a * d - b * c
+        dxi = (d * r[:, 0] - b * r[:, 1]) / det
+        deta = (-c * r[:, 0] + a * r[:, 1]) / det
+        xi[live] += dxi
+        eta[live] += deta
+        live = live[np.abs(dxi) + np.abs(deta) >= tol]
+    return xi, eta
+
+
 def dual_mortar(slave_xy: np.ndarray, slave_faces: np.ndarray,
                 master_origin, master_h, master_n):
     """Assemble D (diagonal, per slave node) and M (slave x master CSR).
@@ -133,20 +160,25 @@ def dual_mortar(slave_xy: np.ndarray, slave_faces: np.ndarray,
     the master surface is the structured grid with origin (x0,y0), spacing (hx,hy),
     (mx, my) faces; master node (a,b) has id a + (mx+1) b.
     Returns D (ns,), M (scipy CSR ns x nm).
+
+    Every (slave face, master face) pair with an overlap is clipped and triangulated first;
+    the quadrature of all segments (inverse maps, dual basis, products) then runs batched.
     """
     x0, y0 = master_origin
     hx, hy = master_h
     mx, my = master_n
     ns = slave_xy.shape[0]
     nm = (mx + 1) * (my + 1)
-    D = np.zeros(ns)
-    rows, cols, vals = [], [], []
-    for f in range(slave_faces.shape[0]):
+    nf = slave_faces.shape[0]
+    A_all = np.empty((nf, 4, 4))
+    seg_face, seg_r0, seg_mids, seg_npts = [], [], [], []
+    pts_all, wts_all = [], []
+    for f in range(nf):
         ids = slave_faces[f]
         X = slave_xy[ids]
         if polygon_area(X) <= 0:
             raise ValueError("slave face is not counter-clockwise")
-        A = dual_coefficients(X)
+        A_all[f] = dual_coefficients(X)
         bx0, by0 = X.min(axis=0)
         bx1, by1 = X.max(axis=0)
         a0 = max(int(np.floor((bx0 - x0) / hx)) - 1, 0)
@@ -161,30 +193,40 @@ def dual_mortar(slave_xy: np.ndarray, slave_faces: np.ndarray,
                 if len(P) < 3 or polygon_area(P) <= 1e-14 * hx * hy:
                     continue
                 c = P.mean(axis=0)
-                pts, wts = [], []
+                npts = 0
                 for t in range(len(P)):
                     p1, p2 = P[t], P[(t + 1) % len(P)]
                     area = 0.5 * ((p1[0] - c[0]) * (p2[1] - c[1]) - (p2[0] - c[0]) * (p1[1] - c[1]))
                     if area <= 0:
                         continue
-                    pts.append(TRI7_BARY[:, 0:1] * c + TRI7_BARY[:, 1:2] * p1 + TRI7_BARY[:, 2:3] * p2)
-                    wts.append(TRI7_W * area)
-                pts = np.concatenate(pts)
-                wts = np.concatenate(wts)
-                xi, eta = quad_inverse_map(X, pts)
-                psi = quad_N(xi, eta) @ A.T                  # (nq,4): psi_j at points
-                mxi = 2.0 * (pts[:, 0] - rx0) / hx - 1.0
-                meta = 2.0 * (pts[:, 1] - ry0) / hy - 1.0
-                Nm = quad_N(mxi, meta)                       # (nq,4)
-                Mloc = (psi * wts[:, None]).T @ Nm           # (4,4)
-                D[ids] += psi.T @ wts
-                mids = np.array([a + (mx + 1) * b, a + 1 + (mx + 1) * b,
-                                 a + 1 + (mx + 1) * (b + 1), a + (mx + 1) * (b + 1)])
-                rows.append(np.repeat(ids, 4))
-                cols.append(np.tile(mids, 4))
-                vals.append(Mloc.ravel())
-    M = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                      shape=(ns, nm)).tocsr()
+                    pts_all.append(TRI7_BARY[:, 0:1] * c + TRI7_BARY[:, 1:2] * p1 + TRI7_BARY[:, 2:3] * p2)
+                    wts_all.append(TRI7_W * area)
+                    npts += TRI7_W.size
+                seg_face.append(f)
+                seg_r0.append((rx0, ry0))
+                seg_mids.append((a + (mx + 1) * b, a + 1 + (mx + 1) * b, a + 1 + (mx + 1) * (b + 1),
+                                 a + (mx + 1) * (b + 1)))
+                seg_npts.append(npts)
+    seg_face = np.asarray(seg_face, dtype=np.int64)
+    seg_npts = np.asarray(seg_npts, dtype=np.int64)
+    seg_r0 = np.asarray(seg_r0)
+    seg_mids = np.asarray(seg_mids, dtype=np.int64)
+    pts = np.concatenate(pts_all)
+    wts = np.concatenate(wts_all)
+    seg_of_pt = np.repeat(np.arange(seg_face.size), seg_npts)
+    face_of_pt = seg_face[seg_of_pt]
+    xi, eta = quad_inverse_map_batched(slave_xy[slave_faces[face_of_pt]], pts)
+    psi = np.einsum("pk,pjk->pj", quad_N(xi, eta), A_all[face_of_pt])         # psi_j at the points
+    r0 = seg_r0[seg_of_pt]
+    Nm = quad_N(2.0 * (pts[:, 0] - r0[:, 0]) / hx - 1.0, 2.0 * (pts[:, 1] - r0[:, 1]) / hy - 1.0)
+    pw = psi * wts[:, None]
+    starts = np.concatenate([[0], np.cumsum(seg_npts)[:-1]])
+    Mloc = np.add.reduceat(pw[:, :, None] * Nm[:, None, :], starts, axis=0)    # (nseg,4,4)
+    D = np.zeros(ns)
+    np.add.at(D, slave_faces[face_of_pt].ravel(), pw.ravel())
+    rows = np.repeat(slave_faces[seg_face], 4, axis=1).ravel()
+    cols = np.tile(seg_mids, (1, 4)).ravel()
+    M = sp.coo_matrix((Mloc.reshape(-1), (rows, cols)), shape=(ns, nm)).tocsr()
     M.sum_duplicates()
     M.sort_indices()
     return D, M
