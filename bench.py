@@ -1,22 +1,24 @@
 #!/usr/bin/env python3
 """Benchmark of the block-AMG contact solver on one GB300 (or N replicas).
 
-A step is one pass of the whole path on the medium two-block contact workload
-(48^3 master + 41^3 slave hex8 bricks, E ratio 10, 5 degree tilt, 60 % active disc):
-amgc_setup on device-resident inputs (aggregation, transfers, Galerkin products, smoother
-data, coarsest inverse) followed by amgc_solve with FGMRES + one V-cycle per iteration to
-a 1e-8 relative residual.  Prints one JSON line.
+A step is one pass of the whole path on the large two-block contact workload (110x110x55 master
++ 97x97x49 slave hex8 bricks, E 1 / 100, nu 0.3 / 0.45, all interface nodes active, 3.47 M rows,
+4 smoothed-aggregation levels): amgc_setup on device-resident inputs (aggregation, transfers,
+Galerkin products, smoother data, coarsest inverse) followed by amgc_solve with FGMRES + one FP64
+V-cycle per iteration to a 1e-8 relative residual.  The same step with the FP32 V-cycle, the
+V-cycle times against the HBM roofline, the adjoint workload and the batched set are reported
+beside it, and the GPU solutions are compared with the FP64 oracle's.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amgc|reference]
 
---impl reference times the FP64 CPU oracle (as it stands) on the host cores on a bounded
-sample of the same workload.  Under torchrun each rank runs an independent replica.
+--impl reference times the FP64 CPU oracle (as it stands, one thread) on the same workload: its
+full setup and its full FGMRES solve to 1e-8, each measured once (no extrapolation).  Under
+torchrun each rank runs an independent replica.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import re
 import os
 import statistics
 import subprocess
@@ -29,9 +31,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "FGMRES+AMG solve ms to 1e-8 rel res (FP32-cycle vs FP64); V-cycle %HBM; adjoint ms"
-WORKLOAD = 1
-OPTS = dict(levels_max=10, coarse_max_rows=5000, transfer=1)   # SA (4/3)/lambda_max for u, PA for lambda
-ORACLE_ITER_SAMPLE = 4
+WORKLOAD = 2
+OPTS = dict(levels_max=4, coarse_max_rows=0, transfer=1)   # 4 levels, SA (4/3)/lambda_max for u, PA for lambda
 
 
 def parse():
@@ -40,9 +41,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="amgc", choices=["amgc", "reference"])
-    ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--iters", type=int, default=0, help=argparse.SUPPRESS)
-    ap.add_argument("--reps", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-worker", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--workload", type=int, default=WORKLOAD,
+                    help="workload of --profile-run (0 tiny, 1 medium, 2 large)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -96,56 +97,82 @@ def workload_name():
 
 
 # ----------------------------------------------------------------------------- oracle leg
-def oracle_worker(iters: int, reps: int) -> dict:
-    """Times the FP64 oracle: full setup plus a few FGMRES iterations, extrapolated to `iters`
-    iterations (iters <= 0: first run one full oracle solve to take its own iteration count)."""
+def oracle_worker(x_path: str) -> dict:
+    """Times the FP64 oracle on the workload, once and in full: setup, then FGMRES to 1e-8
+    (no extrapolation).  The solution goes to x_path (.npy) for the error of the GPU solutions."""
+    import platform
+
     import numpy as np
     from paper_1912_09056_gb300.problem import workload
     from oracle.amg import Options, setup
     from oracle.krylov import fgmres
     prob = workload(WORKLOAD)
     o = Options(**OPTS)
-    A = None
-    if iters <= 0:
-        h = setup(prob, o)
-        _, iters, _ = fgmres(h.A0(), prob.rhs, h.vcycle, tol=o.tol)
-        del h
-    setup_s, iter_s = [], []
-    for _ in range(max(reps, 1)):
-        t0 = time.perf_counter()
-        h = setup(prob, o)
-        t1 = time.perf_counter()
-        if A is None:
-            A = h.A0()
-        v = prob.rhs / np.linalg.norm(prob.rhs)
-        t2 = time.perf_counter()
-        for _ in range(ORACLE_ITER_SAMPLE):       # one FGMRES iteration = V-cycle + A apply + MGS
-            z = h.vcycle(v)
-            w = A @ z
-            w = w - (w @ v) * v
-            v = w / np.linalg.norm(w)
-        t3 = time.perf_counter()
-        setup_s.append(t1 - t0)
-        iter_s.append((t3 - t2) / ORACLE_ITER_SAMPLE)
-    per_step = [1e3 * (a + b * iters) for a, b in zip(setup_s, iter_s)]
-    return dict(setup_s=statistics.median(setup_s), iter_s=statistics.median(iter_s),
-                ms=statistics.median(per_step), iters=iters, steps_ms=per_step)
+    t0 = time.perf_counter()
+    h = setup(prob, o)
+    t1 = time.perf_counter()
+    A = h.A0()
+    x, iters, _ = fgmres(A, prob.rhs, h.vcycle, tol=o.tol)
+    t2 = time.perf_counter()
+    relres = float(np.linalg.norm(prob.rhs - A @ x) / np.linalg.norm(prob.rhs))
+    if x_path:
+        np.save(x_path, x)
+    cpu = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    cpu = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return dict(setup_s=t1 - t0, solve_s=t2 - t1, iters=int(iters), relres=relres, n_levels=h.n_levels,
+                nproc=os.cpu_count(), cpu=cpu, affinity=sorted(os.sched_getaffinity(0)))
 
 
-def run_oracle(iters: int, reps: int = 1) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--iters", str(iters), "--reps", str(reps)]
-    r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT, timeout=3600)
-    if r.returncode != 0:
-        raise RuntimeError("oracle worker failed:\n" + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+class OracleRun:
+    """The oracle worker as a child process on the host's last core (one thread), started before
+    the GPU work so that the two run side by side; result() waits for it."""
+
+    def __init__(self):
+        self.dir = tempfile.mkdtemp(prefix="amgc_oracle")
+        self.x_path = os.path.join(self.dir, "x.npy")
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        cores = sorted(os.sched_getaffinity(0))
+        last = cores[-1]
+
+        def pin():
+            os.sched_setaffinity(0, {last})
+        self.p = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", self.x_path],
+                                  stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT,
+                                  preexec_fn=pin if len(cores) > 1 else None)
+        self.gpu_cores = set(cores[:-1]) if len(cores) > 1 else set(cores)
+
+    def result(self, timeout: float = 3600.0):
+        out, err = self.p.communicate(timeout=timeout)
+        if self.p.returncode != 0:
+            raise RuntimeError("oracle worker failed:\n" + err[-2000:])
+        r = json.loads(out.strip().splitlines()[-1])
+        import numpy as np
+        r["x"] = np.load(self.x_path)
+        return r
+
+    def cleanup(self):
+        try:
+            if self.p.poll() is None:
+                self.p.kill()
+            for f in os.listdir(self.dir):
+                os.unlink(os.path.join(self.dir, f))
+            os.rmdir(self.dir)
+        except OSError:
+            pass
 
 
-def cpu_sample_text(iters: int) -> str:
-    return (f"oracle setup of the full workload plus {ORACLE_ITER_SAMPLE} FGMRES iterations (V-cycle + "
-            f"operator apply + orthogonalisation), per-iteration time scaled to the {iters} iterations "
-            f"of the GPU solve; 1 thread")
+def oracle_sample_text(o: dict) -> str:
+    return (f"the oracle's full setup ({o['n_levels']} levels) and its full FGMRES solve to 1e-8 "
+            f"({o['iters']} iterations) of the whole workload, each measured once (no extrapolation); "
+            f"1 thread on {o['cpu']}")
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -221,6 +248,25 @@ def device_problem(prob, dev):
                               for k, v in host_arrays(prob).items()})
 
 
+def _peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture of the
+# medium workload scaled to this workload by its block count (the kernel streams every block
+# once), keyed by the hash of the kernel source they were measured on: null once it has changed.
+NCU_TRAFFIC = {"source_sha16": None, "bytes_per_block": None}
+
+
+def _kernel_source_sha16() -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1912_09056_gb300", "csrc", "cycle.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
 def main_gpu(args):
     import numpy as np
     import torch
@@ -232,10 +278,17 @@ def main_gpu(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle = OracleRun()                  # the oracle runs on the last host core meanwhile
+        os.sched_setaffinity(0, oracle.gpu_cores)
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    peaks = _peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     prob = workload(WORKLOAD)
     host = host_arrays(prob)
     dprob = device_problem(prob, dev)
@@ -273,113 +326,105 @@ def main_gpu(args):
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     clk = clocks.stop() if clocks else None
     ms = max_over_ranks(ms, world, dev)
+    x64 = x_d.cpu().numpy()
 
     # ---- breakdown on one hierarchy (outside the timed region)
+    reps, nv = 3, 20
+
+    def timed(fn, n):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    def cycle_info(hh, label, s_bytes):
+        r = torch.randn(rhs_d.shape, dtype=torch.float64, device=dev)
+        z = torch.empty_like(r)
+        hh.vcycle(r, z)
+        vc_ms = timed(lambda: hh.vcycle(r, z), nv)
+        vb = vcycle_bytes(hh, s_bytes)
+        gbs = vb / (vc_ms * 1e-3) / 1e9
+        return {"ms": round(vc_ms, 4), "bytes": int(vb), "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 4),
+                "model": f"algorithmic bytes of one {label} V-cycle (bench.vcycle_bytes), {peak_src}"}
+
+    def kernel_info(hh, mask, solve_x):
+        hh.profile(mask)
+        hh.solve(rhs_d, solve_x)
+        kms, kl, kb, kf = hh.profile_read()
+        hh.profile(False)
+        if not kl:
+            return None
+        t = kms / kl * 1e-3
+        gbs = (kb / kl) / t / 1e9
+        return {"launches": kl, "avg_launch_us": round(1e6 * t, 2), "bytes_per_launch": round(kb / kl),
+                "flops_per_launch": round(kf / kl), "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 4),
+                "gflops": round((kf / kl) / t / 1e9, 1)}
+
     h = amgc.setup(dprob, opts)
     st = h.stats()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    reps = 3
     for _ in range(reps):
-        h2 = amgc.setup(dprob, opts)
-        h2.close()
+        amgc.setup(dprob, opts).close()
     torch.cuda.synchronize()
     setup_ms = 1e3 * (time.perf_counter() - t0) / reps
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    ev[0].record()
-    for _ in range(reps):
-        it, rr, _ = h.solve(rhs_d, x_d)
-    ev[1].record()
-    r = torch.randn(rhs_d.shape, dtype=torch.float64, device=dev)
-    z = torch.empty_like(r)
-    nv = 20
-    ev[2].record()
-    for _ in range(nv):
-        h.vcycle(r, z)
-    ev[3].record()
-    torch.cuda.synchronize()
-    solve_ms = ev[0].elapsed_time(ev[1]) / reps
-    vcycle_ms = ev[2].elapsed_time(ev[3]) / nv
-    vc_bytes64 = vcycle_bytes(h, 8)
+    solve_ms = timed(lambda: h.solve(rhs_d, x_d), reps)
+    vc64 = cycle_info(h, "FP64", 8)
+    k64 = kernel_info(h, 1, x_d)
+
     # ---- FP32 cycle (FP32 storage and arithmetic inside the V-cycle, FP64 FGMRES)
     opts32 = amgc.default_options(precision=32, **OPTS)
     h32 = amgc.setup(dprob, opts32)
-    x32 = torch.zeros_like(rhs_d)
-    h32.solve(rhs_d, x32)
+    x32_d = torch.zeros_like(rhs_d)
+    it32, rr32, _ = h32.solve(rhs_d, x32_d)
     torch.cuda.synchronize()
-    ev32 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    ev32[0].record()
-    for _ in range(reps):
-        it32, rr32, _ = h32.solve(rhs_d, x32)
-    ev32[1].record()
-    ev32[2].record()
-    for _ in range(nv):
-        h32.vcycle(r, z)
-    ev32[3].record()
-    torch.cuda.synchronize()
-    vc_bytes32 = vcycle_bytes(h32, 4)
-    h32.profile(2)                      # the FP32 cycle's fine-level K applies only
-    h32.solve(rhs_d, x32)
-    kms32, kl32, kb32, _ = h32.profile_read()
+    solve32_ms = timed(lambda: h32.solve(rhs_d, x32_d), reps)
+    vc32 = cycle_info(h32, "FP32", 4)
+    k32 = kernel_info(h32, 2, x32_d)
     h32.close()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(reps):
         hh = amgc.setup(dprob, opts32)
-        hh.solve(rhs_d, x32)
+        hh.solve(rhs_d, x32_d)
         hh.close()
     torch.cuda.synchronize()
     step32_ms = 1e3 * (time.perf_counter() - t0) / reps
-    # the same FP32 solve with the row mappings chosen by the setup-time autotuner
     h32t = amgc.setup(dprob, amgc.default_options(precision=32, autotune=1, **OPTS))
-    h32t.solve(rhs_d, x32)
-    torch.cuda.synchronize()
-    et = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    et[0].record()
-    for _ in range(reps):
-        h32t.solve(rhs_d, x32)
-    et[1].record()
-    torch.cuda.synchronize()
-    tuned_solve_ms = et[0].elapsed_time(et[1]) / reps
+    h32t.solve(rhs_d, x32_d)
+    tuned_solve_ms = timed(lambda: h32t.solve(rhs_d, x32_d), reps)
     h32t.close()
-    fp32 = {"step_ms": round(step32_ms, 3), "solve_ms": round(ev32[0].elapsed_time(ev32[1]) / reps, 3),
-            "solve_ms_autotuned": round(tuned_solve_ms, 3),
-            "iters": it32, "relres": rr32, "vcycle_ms": round(ev32[2].elapsed_time(ev32[3]) / nv, 4),
-            "vcycle_gbs": round(vc_bytes32 / (ev32[2].elapsed_time(ev32[3]) / nv * 1e-3) / 1e9, 1),
-            "k_apply_us": round(1e3 * kms32 / kl32, 2) if kl32 else None,
-            "k_apply_gbs": round((kb32 / kl32) / (kms32 / kl32 * 1e-3) / 1e9, 1) if kl32 else None}
-    fp32["vcycle_hbm_frac"] = round(fp32["vcycle_gbs"] / float(
-        json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else fp32["vcycle_gbs"] / 6800.0, 4)
-    if kl32:
-        fp32["k_apply_hbm_frac"] = round(fp32["k_apply_gbs"] / float(
-            json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else fp32["k_apply_gbs"] / 6800.0, 4)
+    x32 = x32_d.cpu().numpy()
+    fp32 = {"step_ms": round(step32_ms, 3), "solve_ms": round(solve32_ms, 3),
+            "solve_ms_autotuned": round(tuned_solve_ms, 3), "iters": it32, "relres": rr32,
+            "vcycle": vc32, "k_apply": k32,
+            "rel_diff_to_fp64_cycle_solution": float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64))}
+
     # ---- adjoint on the ~1M-row workload with a lognormal modulus field
     adj_info = None
     if not args.no_adjoint:
         from paper_1912_09056_gb300.adjoint import ElementTables, contact_gradients
         p4 = workload(4, keep_full=True)
         tab = ElementTables(p4)
-        h4 = amgc.setup(p4, amgc.default_options(**OPTS))
+        h4 = amgc.setup(p4, amgc.default_options(levels_max=10, coarse_max_rows=5000, transfer=1))
         b4 = torch.from_numpy(p4.rhs).to(dev)
         x4 = torch.zeros_like(b4)
         it4, rr4, _ = h4.solve(b4, x4)
         contact_gradients(p4, h4, x4, tab, adj_tol=1e-10)          # builds the transposed data once
         torch.cuda.synchronize()
-        ea = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ea[0].record()
-        for _ in range(reps):
-            h4.solve(b4, x4)
-        ea[1].record()
-        ea[2].record()
-        for _ in range(reps):
-            J4, gE4, gt4, _, ita = contact_gradients(p4, h4, x4, tab, adj_tol=1e-10)
-        ea[3].record()
-        torch.cuda.synchronize()
-        adj_info = {"workload": "adjoint_58^3_50^3", "rows": p4.n, "forward_ms": round(ea[0].elapsed_time(ea[1]) / reps, 3),
-                    "forward_iters": it4, "adjoint_ms": round(ea[2].elapsed_time(ea[3]) / reps, 3),
-                    "adjoint_iters": ita, "adjoint_tol": 1e-10, "n_elements": tab.ne,
+        fwd_ms = timed(lambda: h4.solve(b4, x4), reps)
+        out4 = {}
+
+        def adj_step():
+            out4["r"] = contact_gradients(p4, h4, x4, tab, adj_tol=1e-10)
+        adj_ms = timed(adj_step, reps)
+        adj_info = {"workload": "adjoint_58^3_50^3", "rows": p4.n, "forward_ms": round(fwd_ms, 3),
+                    "forward_iters": it4, "adjoint_ms": round(adj_ms, 3), "adjoint_iters": out4["r"][4],
+                    "adjoint_tol": 1e-10, "n_elements": tab.ne,
                     "step": "transposed FGMRES with the transposed hierarchy + element gradient kernel"}
         h4.close()
         del tab, p4
@@ -388,7 +433,7 @@ def main_gpu(args):
     if not args.no_batch:
         from paper_1912_09056_gb300.problem import batched_workload
         cat, npt, lpt, brhs, bprobs, _ = batched_workload(64, seed=3)
-        dcat = device_problem(cat, dev)   # inputs resident in HBM, as for the medium step
+        dcat = device_problem(cat, dev)
         # the set includes slave meshes up to 4x finer than their master, where rho(S_bd^-1 S_hat)
         # reaches ~20 and the undamped Schur step (alpha = 0.8) amplifies: Schur damping on
         optsb = amgc.default_options(precision=32, levels_max=4, coarse_max_rows=400, transfer=1, schur_damping=1,
@@ -417,32 +462,6 @@ def main_gpu(args):
                       "step": "amgc_setup_batched + amgc_solve_batched"}
         hb.close()
         del cat, dcat, bprobs, Rb, Xb
-    # ---- dominant kernel: fine-level K apply, timed by events on its launching stream
-    h.profile(1)
-    for _ in range(reps):
-        h.solve(rhs_d, x_d)
-    kms, kl, kbytes, kflops = h.profile_read()
-    h.profile(False)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    # FP64 peak from the nominal GB300 figures: 1.25 TFLOP/s = 152 SMs x 2.07 GHz x 4 FLOP/clk/SM
-    fp64_peak = 152 * 2.07 * 4.0
-    t_launch = kms / kl * 1e-3 if kl else float("nan")
-    achieved_gbs = (kbytes / kl) / t_launch / 1e9 if kl else 0.0
-    achieved_gflops = (kflops / kl) / t_launch / 1e9 if kl else 0.0
-    # DRAM bytes (read + write) of one fine-level FP64 K-residual launch, from the committed ncu
-    # summary of the current kernel (null when the summary holds none)
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "k_sell_fp64_residual_medium_48x41.md")) as fh:
-            m = re.search(r"traffic_bytes_per_launch = (\d+)", fh.read())
-        traffic = int(m.group(1)) if m else None
-    except OSError:
-        pass
 
     # ---- end to end through the host-buffer API: inputs copied in, solution copied out
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
@@ -455,22 +474,49 @@ def main_gpu(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         he = amgc.setup(hprob, opts)
-        xh, _, _, _ = he.solve_host(rhs_pin.numpy())
+        he.solve_host(rhs_pin.numpy())
         he.close()
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    # ---- the oracle: its measured setup + solve, and the GPU solutions' error against its solution
+    cpu, vs_oracle = None, None
+    if oracle is not None:
         try:
-            o = run_oracle(st["last_iters"] or iters[-1])
-            cpu = {"value": round(o["ms"], 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                   "sample": cpu_sample_text(o["iters"]), "setup_ms": round(1e3 * o["setup_s"], 1),
-                   "ms_per_iteration": round(1e3 * o["iter_s"], 2)}
+            o = oracle.result()
+            xo = o["x"]
+            nu = prob.n_u
+
+            def err(x):
+                return {"u": float(np.linalg.norm(x[:nu] - xo[:nu]) / np.linalg.norm(xo[:nu])),
+                        "lambda": float(np.linalg.norm(x[nu:] - xo[nu:]) / np.linalg.norm(xo[nu:]))}
+            vs_oracle = {"fp64_cycle": err(x64), "fp32_cycle": err(x32), "oracle_iters": o["iters"],
+                         "oracle_relres": o["relres"],
+                         "note": "relative 2-norm differences; each solution meets 1e-8 relative residual"}
+            cpu = {"value": round(1e3 * (o["setup_s"] + o["solve_s"]), 1), "unit": "ms", "cores": 1,
+                   "kind": "oracle", "sample": oracle_sample_text(o), "setup_ms": round(1e3 * o["setup_s"], 1),
+                   "solve_ms": round(1e3 * o["solve_s"], 1), "iters": o["iters"], "host_cpus": o["nproc"]}
         except Exception as ex:  # reported, not hidden
             cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+        finally:
+            oracle.cleanup()
     if rank == 0:
+        nblk = h.export_size(0, "k_col")
+        traffic = None
+        if NCU_TRAFFIC["source_sha16"] == _kernel_source_sha16() and NCU_TRAFFIC["bytes_per_block"]:
+            traffic = round(NCU_TRAFFIC["bytes_per_block"] * nblk)
+        fp64_peak = 152 * 2.07 * 4.0      # GFLOP/s: 152 SMs x 2.07 GHz x 2 FP64 FMA per clock (nominal)
+        roof = None
+        if k64:
+            roof = {"bound": "hbm", "kernel": "fine-level K apply, FP64 (k_sell<3,3,*,double,1>)",
+                    "achieved": k64["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": k64["frac"],
+                    "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)", "traffic": traffic,
+                    "launches": k64["launches"], "bytes_per_launch": k64["bytes_per_launch"],
+                    "avg_launch_us": k64["avg_launch_us"],
+                    "alu": {"achieved_gflops": k64["gflops"], "peak_gflops": round(fp64_peak, 1),
+                            "frac": round(k64["gflops"] / fp64_peak, 4),
+                            "peak_source": "FP64 FMA rate of the nominal GB300 figures (of nominal)"}}
         out = {
             "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
@@ -479,26 +525,16 @@ def main_gpu(args):
                        "rows": st["rows"][0], "levels": st["n_levels"], "level_rows": st["rows"],
                        "operator_complexity": round(st["operator_complexity"], 4),
                        "transfer": "SA (4/3)/lambda_max for u, PA for lambda", "smoother": "CheapSIMPLE(0.8) x1",
-                       "l2": "inputs larger than L2 (fine K block %.0f MB)" % (prob.K_val.nbytes / 1e6),
+                       "l2": "inputs larger than L2 (fine K blocks %.0f MB)" % (prob.K_val.nbytes / 1e6),
                        "parallelism": f"replicas x{world}"},
             "iters": iters[-1], "relres": relres[-1], "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
             "setup_phase_ms": {k: round(v, 3) for k, v in st["setup_phase_ms"].items()},
-            "vcycle_ms": round(vcycle_ms, 4),
-            "vcycle_hbm": {"bytes": int(vc_bytes64), "gbs": round(vc_bytes64 / (vcycle_ms * 1e-3) / 1e9, 1),
-                           "frac": round(vc_bytes64 / (vcycle_ms * 1e-3) / 1e9 / hbm_peak, 4),
-                           "model": "algorithmic bytes of one V-cycle (bench.vcycle_bytes), of measured"},
+            "vcycle": vc64, "k_apply": k64,
             "fp32_cycle": fp32,
+            "vs_oracle": vs_oracle,
             "adjoint": adj_info,
             "batched": batch_info,
-            "roofline": {"bound": "alu", "kernel": "fine-level K apply, FP64 (k_sell<3,3,*>)",
-                         "achieved": round(achieved_gflops, 1), "peak": round(fp64_peak, 1), "unit": "GFLOP/s",
-                         "frac": round(achieved_gflops / fp64_peak, 4),
-                         "peak_source": "FP64 FMA rate of the nominal GB300 figures (of nominal)",
-                         "traffic": traffic, "launches": kl, "bytes_per_launch": round(kbytes / kl) if kl else None,
-                         "flops_per_launch": round(kflops / kl) if kl else None,
-                         "avg_launch_us": round(1e6 * t_launch, 2) if kl else None,
-                         "hbm_achieved_gbs": round(achieved_gbs, 1), "hbm_peak_gbs": hbm_peak,
-                         "hbm_frac": round(achieved_gbs / hbm_peak, 4)},
+            "roofline": roof,
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
@@ -516,31 +552,38 @@ def main_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # one worker process: generation, one full oracle solve for the iteration count, then
-    # `steps` timed samples (setup + sampled iterations); warm-up steps are not needed on the CPU
-    o = run_oracle(0, reps=max(args.steps, 1))
-    ms = o["ms"]
+    # one worker process: generation (untimed), then the oracle's full setup and full FGMRES solve,
+    # each measured once; a CPU program has no warm-up state, and K full solves would take K times
+    # the value, so one full solve stands for every step
+    run = OracleRun()
+    try:
+        o = run.result()
+    finally:
+        run.cleanup()
+    ms = 1e3 * (o["setup_s"] + o["solve_s"])
     out = {"impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(), "step": "oracle setup + FGMRES to 1e-8 (sampled)"},
-           "iters": o["iters"],
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded two-block hex8 contact generator)",
+           "config": {"workload": workload_name(), "step": "amgc_setup + amgc_solve (FP64 V-cycle) to 1e-8"},
+           "timed_full_solves": 1, "iters": o["iters"], "relres": o["relres"],
+           "setup_ms": round(1e3 * o["setup_s"], 1), "solve_ms": round(1e3 * o["solve_s"], 1),
            "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                            "sample": cpu_sample_text(o["iters"])},
+                            "sample": oracle_sample_text(o)},
            "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def profile_run():
+def profile_run(cfg: int):
     """One FP64-cycle and one FP32-cycle setup + solve, nothing timed: the command ncu captures."""
     import torch
 
     from paper_1912_09056_gb300 import amgc
     from paper_1912_09056_gb300.problem import workload
-    prob = workload(WORKLOAD)
+    prob = workload(cfg)
+    opts = OPTS if cfg == WORKLOAD else dict(levels_max=10, coarse_max_rows=5000, transfer=1)
     b = torch.from_numpy(prob.rhs).cuda()
     for precision in (64, 32):
-        h = amgc.setup(prob, amgc.default_options(precision=precision, **OPTS))
+        h = amgc.setup(prob, amgc.default_options(precision=precision, **opts))
         x = torch.zeros_like(b)
         it, rr, _ = h.solve(b, x)
         h.close()
@@ -551,9 +594,9 @@ def profile_run():
 if __name__ == "__main__":
     a = parse()
     if a.profile_run:
-        profile_run()
+        profile_run(a.workload)
     elif a.oracle_worker:
-        print(json.dumps(oracle_worker(a.iters, a.reps)))
+        print(json.dumps(oracle_worker(a.oracle_worker)))
     elif a.impl == "reference":
         main_reference(a)
     else:

@@ -17,3 +17,10 @@ def pytest_configure(config):
 def cfg0():
     from paper_1912_09056_gb300.problem import workload
     return workload(0, keep_full=True)
+
+
+@pytest.fixture(scope="session")
+def large_problem():
+    """The large workload (110x110x55 + 97x97x49 hex8, 3.47 M rows), generated once per session."""
+    from paper_1912_09056_gb300.problem import workload
+    return workload(2)

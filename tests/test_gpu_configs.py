@@ -47,8 +47,8 @@ def _check_aggregates(h, prob):
     assert np.unique(first).size == n_lagg, "two multiplier aggregates share a displacement aggregate"
 
 
-def test_large_fp32_and_fp64_cycles_reach_the_tolerance_and_agree():
-    prob = workload(2)
+def test_large_fp32_and_fp64_cycles_reach_the_tolerance_and_agree(large_problem):
+    prob = large_problem
     opts = dict(levels_max=4, coarse_max_rows=0, transfer=1)
     b = _cuda(prob.rhs)
     xs, its = {}, {}
