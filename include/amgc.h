@@ -206,6 +206,83 @@ int amgc_solve(struct amgc_hierarchy* h, const double* rhs, double* x, int32_t* 
 int amgc_solve_host(struct amgc_hierarchy* h, const double* rhs_host, double* x_host,
                     int32_t* iters, double* relres, void* stream);
 
+/* Chooses the level smoother of the V-cycle (Sec. 5.1 block smoothers in the cheap forms of Sec. 5.2,
+ * with the inner solvers of the paper's experiments, Sec. 6.1):
+ *   kind 0: CheapSIMPLE (the default; Algorithm 4 with damped Jacobi and the nodal Schur blocks);
+ *   kind 1: Uzawa (Algorithm 2):  du = SGS(K, f - K u - B1 lam) from 0,
+ *           dlam = -ILU(S)^-1 (g - B2 u + Z lam - B2 du),  u += omega du,  lam += omega dlam;
+ *   kind 2: Braess-Sarazin (Algorithm 3):  u_h = u + A~^-1 (f - K u - B1 lam) / omega,
+ *           dlam = -ILU(S_w)^-1 (g + Z lam - B2 u_h),  lam += dlam,  u = u_h - A~^-1 B1 dlam / omega;
+ *   kind 3: SIMPLE (Algorithm 4; SIMPLEC with opts.simplec):  u_h = SGS(K, f - B1 lam) from u,
+ *           dlam = -ILU(S)^-1 (g + Z lam - B2 u_h),  lam += omega dlam,  u = u_h - omega A~^-1 B1 dlam;
+ * with S = Z + B2 A~^-1 B1, S_w = Z + B2 A~^-1 B1 / omega assembled on the nodal 3x3 multiplier
+ * blocks and factored by block ILU(0) (no fill; rows eliminated in natural order), and SGS =
+ * sgs_sweeps damped (sgs_omega) symmetric Gauss-Seidel sweeps over the nodal blocks of K in the order
+ * of a Jones-Plassmann colouring of K's node graph (colours ascending, then descending; priorities
+ * fmix32(i ^ seed) * 2^32 + i as in the aggregation).  smoother_sweeps of the options sweeps run
+ * pre and post.  The call builds, on every smoothed level, the colouring, the inverted diagonal
+ * blocks of K and the ILU(0) factors (level-scheduled), drops the captured V-cycle graphs and
+ * synchronises `stream`; amgc_update_active_set and amgc_pdass refactor the Schur part.  Kinds 1-3
+ * need a single FP64 hierarchy; the transposed calls refuse them.  The ILU(0) substitutions run
+ * level by level in one thread block, so these smoothers are for comparisons, not for speed.
+ * Errors: AMGC_EINVAL (kind, omega <= 0, sgs_sweeps < 1, sgs_omega <= 0, batched or FP32
+ * hierarchy), AMGC_ESINGULAR (singular diagonal block or ILU pivot), AMGC_ENOMEM, AMGC_ECUDA. */
+int amgc_set_smoother(struct amgc_hierarchy* h, int32_t kind, double omega, int32_t sgs_sweeps, double sgs_omega,
+                      void* stream);
+
+/* Chooses the preconditioner that amgc_vcycle applies and amgc_solve / amgc_pdass use:
+ *   kind 0: the fully coupled block AMG V-cycle (the paper's method; the default);
+ *   kind 1: nested multigrid, the comparison approach of Sec. 3.2 (Fig. mgmphmodelsA): the
+ *     coupling is treated on the finest level only, by `outer_sweeps` SIMPLE sweeps (Algorithm 4)
+ *       u_h = u + V_K (f - K u - B1 lambda)
+ *       dlambda = -S_hat^-1 (g + Z lambda - B2 u_h),  S_hat = Z + B2 A~^-1 B1 (exact, dense)
+ *       lambda += omega dlambda,  u = u_h - omega A~^-1 B1 dlambda
+ *     whose predictor V_K is one single-field AMG V-cycle on K: the displacement part of this
+ *     hierarchy (its aggregates, transfers and Galerkin K_c), damped Jacobi with omega_J
+ *     (smoother_sweeps pre and post), and the coarsest K_c by its dense inverse.
+ * The first switch to kind 1 forms the dense inverses of the coarsest K_c and of S_hat (each at
+ * most 16384 rows) and synchronises `stream`; amgc_update_active_set and amgc_pdass form S_hat
+ * again.  Kind 1 needs a single FP64 hierarchy (precision 64, not batched); the transposed
+ * calls keep the coupled cycle and refuse kind 1.  Errors: AMGC_EINVAL (kind, outer_sweeps < 1,
+ * omega <= 0, batched or FP32 hierarchy, a dense size above the limit), AMGC_ESINGULAR,
+ * AMGC_ENOMEM, AMGC_ECUDA. */
+int amgc_set_preconditioner(struct amgc_hierarchy* h, int32_t kind, int32_t outer_sweeps, double omega, void* stream);
+
+/* Replaces the hierarchy's active set (setup reuse across active-set changes, as in the Newton
+ * steps of the paper's contact simulations, Sec. 6.3-6.4).  Only the constraint blocks depend on
+ * the active set: B2 (the weighted-gap rows of active nodes) and Z (tangential rows of active
+ * nodes, the identity of inactive ones).  The call forms B2 and Z anew on the finest level from
+ * the interface data given to amgc_setup, the coarse B2_c = R^lambda B2 P and Z_c with the kept
+ * transfers, the inverted nodal Schur blocks (and their damping), and the coarsest inverse (or the
+ * coarsest smoother data); it keeps the aggregates, multiplier aggregates, transfers, lambda_max,
+ * Jacobi data, coarse K and coarse B1, which the active set does not change (Sec. 4 aggregates
+ * the displacement graph and derives the multiplier aggregates through D, not through B2).  The
+ * result equals a fresh amgc_setup with the new set and the old aggregates.
+ * active: n_s bytes (1 active, 0 inactive), host or device.  Single hierarchies only.  Drops the
+ * captured V-cycle graphs and the transposed data (formed again when next needed).  Synchronises
+ * `stream`.  Errors: AMGC_EINVAL (NULL argument, batched hierarchy), AMGC_ESINGULAR (singular Schur
+ * block or coarse pivot), AMGC_ENOMEM, AMGC_ECUDA. */
+int amgc_update_active_set(struct amgc_hierarchy* h, const uint8_t* active, void* stream);
+
+/* Primal-dual active set strategy (PDASS, Sec. 2.2) for frictionless contact with an initial
+ * normal gap: from the hierarchy's current active set, solves the saddle system of the set with
+ * FGMRES (amgc_solve's method and tolerance), right-hand side f on the displacement rows and, on an
+ * active node's normal row, D_jj g0_j (zero on every other multiplier row); then takes as next set
+ *     active_j  <=>  lambda_n,j - c g_j(u) > 0,   lambda_n,j = n_j . lambda_j,
+ *     g_j(u) = D_jj g0_j - n_j^T (D_jj u_s,j - sum_l M_jl u_m,l)   (weighted gap, Eq. ch4_discretenormalcontact),
+ * with n_j the first row of node j's triad, and updates the hierarchy as amgc_update_active_set
+ * does; it stops when a solve leaves the set unchanged (the contact conditions then hold at the
+ * solve's accuracy).
+ *   f: device, 3n displacement right-hand side; g0: device, n_s initial normal gaps; c > 0 the
+ *   complementarity parameter; max_steps >= 1 solves at most; x: device, rows[0]: the last solve's
+ *   solution [u; lambda].  active_out: host (or device) n_s bytes for the final set, or NULL;
+ *   steps: solves run; total_iters: FGMRES iterations over all solves (both may be NULL).
+ * Returns AMGC_NOT_CONVERGED if a solve failed to converge or the set still changed after
+ * max_steps solves (x and the hierarchy then hold the last step's), AMGC_EINVAL for bad
+ * arguments or a batched hierarchy; other errors as amgc_solve and amgc_update_active_set. */
+int amgc_pdass(struct amgc_hierarchy* h, const double* f, const double* g0, double c, int32_t max_steps, double* x,
+               uint8_t* active_out, int32_t* steps, int32_t* total_iters, void* stream);
+
 /* Adjoint calls (transposed system).  The first one builds, once, the transposed data of every
  * level (B1^T, B2^T, blockwise transposes of Z and of the Schur-block inverses, the transposed
  * coarsest inverse).  They need jacobi_sweeps == 1 (AMGC_EINVAL otherwise) and run in FP64.
@@ -294,9 +371,11 @@ enum {
   AMGC_EXPORT_OMEGA = 20,     /* double[2]           (lambda_max, omega_J)                     */
   AMGC_EXPORT_COARSE_INV = 21, /* double[rows*rows]  inverse of the coarsest saddle matrix
                                  (batched: the instances' inverses one after the other)   */
-  AMGC_EXPORT_SCHUR_RHO = 22  /* double[instances]  rho of S_bd^-1 S_hat (schur_damping = 1;
+  AMGC_EXPORT_SCHUR_RHO = 22, /* double[instances]  rho of S_bd^-1 S_hat (schur_damping = 1;
                                  empty otherwise); SINV then holds the blocks already scaled
                                  by min(alpha, (4/3)/rho) / alpha                          */
+  AMGC_EXPORT_COLOR = 23      /* int32[disp_nodes]  Jones-Plassmann colour of each node (block
+                                 smoothers with SGS; empty otherwise)                      */
 };
 int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what, void* dst,
                     int64_t bytes);

@@ -23,8 +23,8 @@ AMGC_BREAKDOWN, AMGC_TIMEOUT, AMGC_ECUDA, AMGC_ENOMEM = -4, -5, -6, -7
 
 EXPORT = dict(agg=1, lagg=2, p_rowptr=3, p_col=4, p_val=5, k_rowptr=6, k_col=7, k_val=8, b1_rowptr=9,
               b1_col=10, b1_val=11, b2_rowptr=12, b2_col=13, b2_val=14, z=15, sinv=16, nullspace=17,
-              pl_w=18, atinv=19, omega=20, coarse_inv=21, schur_rho=22)
-_EXPORT_DTYPE = {k: (np.int32 if k in ("agg", "lagg") or k.endswith(("rowptr", "col")) else np.float64)
+              pl_w=18, atinv=19, omega=20, coarse_inv=21, schur_rho=22, color=23)
+_EXPORT_DTYPE = {k: (np.int32 if k in ("agg", "lagg", "color") or k.endswith(("rowptr", "col")) else np.float64)
                  for k in EXPORT}
 
 
@@ -117,6 +117,15 @@ def load():
     lib.amgc_set_row_mapping.restype = C.c_int
     lib.amgc_set_wait_limit.argtypes = [vp, C.c_int64]
     lib.amgc_set_wait_limit.restype = C.c_int
+    lib.amgc_set_smoother.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, C.c_double, vp]
+    lib.amgc_set_smoother.restype = C.c_int
+    lib.amgc_set_preconditioner.argtypes = [vp, C.c_int32, C.c_int32, C.c_double, vp]
+    lib.amgc_set_preconditioner.restype = C.c_int
+    lib.amgc_update_active_set.argtypes = [vp, vp, vp]
+    lib.amgc_update_active_set.restype = C.c_int
+    lib.amgc_pdass.argtypes = [vp, vp, vp, C.c_double, C.c_int32, vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               vp]
+    lib.amgc_pdass.restype = C.c_int
     lib.amgc_destroy.argtypes = [vp]
     lib.amgc_destroy.restype = None
     lib.amgc_strerror.argtypes = [C.c_int]
@@ -320,6 +329,38 @@ class Hierarchy:
         if check:
             _check(code, "amgc_solve_batched")
         return it, rr, code
+
+    SMOOTHERS = dict(cheap_simple=0, uzawa=1, braess_sarazin=2, simple_sgs=3)
+
+    def set_smoother(self, kind, omega: float = 0.7, sgs_sweeps: int = 1, sgs_omega: float = 0.7, stream=None):
+        """amgc_set_smoother: kind 'cheap_simple', 'uzawa', 'braess_sarazin', 'simple_sgs' (or 0..3)."""
+        k = self.SMOOTHERS[kind] if isinstance(kind, str) else int(kind)
+        _check(self._lib.amgc_set_smoother(self._h, k, float(omega), int(sgs_sweeps), float(sgs_omega),
+                                           _stream_ptr(stream)), "amgc_set_smoother")
+
+    def set_preconditioner(self, kind: int, outer_sweeps: int = 1, omega: float = 0.8, stream=None):
+        """amgc_set_preconditioner: 0 the coupled V-cycle, 1 nested multigrid (outer SIMPLE sweeps)."""
+        _check(self._lib.amgc_set_preconditioner(self._h, int(kind), int(outer_sweeps), float(omega),
+                                                 _stream_ptr(stream)), "amgc_set_preconditioner")
+
+    def update_active_set(self, active, stream=None):
+        """amgc_update_active_set: active is a host uint8 array (or a device tensor) of n_s flags."""
+        if not hasattr(active, "data_ptr"):
+            active = np.ascontiguousarray(active, dtype=np.uint8)
+        _check(self._lib.amgc_update_active_set(self._h, _ptr(active), _stream_ptr(stream)), "amgc_update_active_set")
+
+    def pdass(self, f, g0, x, c: float = 1.0, max_steps: int = 50, stream=None, check: bool = True):
+        """amgc_pdass on device tensors f (3n), g0 (n_s) and x (rows); returns (final active set
+        (host uint8), solves, total FGMRES iterations, status)."""
+        n_s = int(g0.shape[0])
+        act = np.zeros(n_s, dtype=np.uint8)
+        steps = C.c_int32(0)
+        its = C.c_int32(0)
+        code = self._lib.amgc_pdass(self._h, _ptr(f), _ptr(g0), float(c), int(max_steps), _ptr(x), act.ctypes.data,
+                                    C.byref(steps), C.byref(its), _stream_ptr(stream))
+        if check:
+            _check(code, "amgc_pdass")
+        return act, steps.value, its.value, code
 
     def solve_host(self, rhs: np.ndarray, stream=None, check: bool = True):
         rhs = np.ascontiguousarray(rhs, dtype=np.float64)

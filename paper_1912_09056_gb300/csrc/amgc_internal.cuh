@@ -255,6 +255,29 @@ struct Level {
   int n_b2t_rows = 0;
   bool has_transposed = false;
 
+  // interface data of the finest level, kept for active-set updates: D, M (CSR over slave rows),
+  // slave and master node ids, triads
+  DBuf<double> if_D, if_Mv, if_T;
+  DBuf<int> if_Mrp, if_Mcol, if_Sl, if_Ms;
+  DBuf<uint8_t> if_act;    // the current active set (one byte per slave node)
+  // block smoothers other than CheapSIMPLE (Uzawa, Braess-Sarazin, SIMPLE with SGS):
+  // Jones-Plassmann colouring of K's node graph, inverted nodal diagonal blocks of K, and the
+  // assembled Schur approximation factored in place by block ILU(0) with its level schedules
+  int ncolor = 0;
+  DBuf<int> color, col_ptr, col_nodes;
+  std::vector<int> h_col_ptr;       // host copy of col_ptr (launch sizes)
+  DBuf<double> kdblk_inv;           // nn x bu x bu
+  DBsr S;                           // Schur approximation -> ILU(0) factors (L unit-lower, U)
+  DBuf<int> s_diag;                 // position of each row's diagonal block in S
+  DBuf<double> s_uinv;              // inverted diagonal blocks of U
+  int s_nlev_l = 0, s_nlev_u = 0;
+  DBuf<int> s_lptr, s_lrows, s_uptr, s_urows;   // rows of S by forward / backward level
+  DBuf<double> bs_w, bs_d;          // work vectors (nu) of the block smoothers
+  DBuf<double> bs_l, bs_m;          // work vectors (3 nl)
+  // tentative multiplier transfer to the next level and its transpose (BSR, 3x3 diagonal blocks),
+  // kept for the coarse constraint blocks of an active-set update
+  DBsr Pl, Rl;
+
   // work vectors [u; lambda]
   DBuf<double> x, b, r, t;
   DBuf<double> dlam;         // nl*3
@@ -294,6 +317,22 @@ struct amgc_hierarchy {
   amgc::DBuf<int> b_chunk_row0, b_chunk_row1, b_chunk_ptr, b_row_inst;
   int b_nchunk = 0;
   double* h_pinned = nullptr;      // pinned host scalars
+  // level smoother: 0 CheapSIMPLE, 1 Uzawa, 2 Braess-Sarazin, 3 SIMPLE with an SGS predictor
+  int smoother_kind = 0;
+  double block_omega = 0.7;        // the block smoother's damping omega
+  int sgs_sweeps = 1;
+  double sgs_omega = 0.7;
+  // preconditioner of amgc_vcycle / amgc_solve: 0 the fully coupled V-cycle, 1 nested multigrid
+  // (outer SIMPLE sweeps with a single-field AMG V-cycle on K and the exact Schur complement)
+  int prec_kind = 0;
+  int nest_sweeps = 1;
+  double nest_omega = 0.8;
+  amgc::DBuf<double> nest_Kinv;     // dense inverse of the coarsest level's K
+  amgc::DBuf<double> nest_Sinv;     // dense inverse of S_hat = Z + B2 A~^-1 B1 (finest level)
+  struct NestBufs {
+    amgc::DBuf<double> x, b, r, t;
+  };
+  std::vector<NestBufs> nest;        // per-level work vectors of the K V-cycle
   // event timing of the fine-level K applies (amgc_profile)
   int prof = 0;                    // mask: 1 FP64 applies, 2 FP32 applies
   std::vector<cudaEvent_t> prof_ev;
@@ -338,6 +377,17 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// MurmurHash3's 32-bit finaliser (A. Appleby): the hash of the node priorities
+// fmix32(i ^ seed) * 2^32 + i of the MIS-2 aggregation and of the Jones-Plassmann colouring.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
 // ------------------------------------------------------------------ host-side kernel drivers
 // scan.cu
 int exclusive_scan(const int* in, int* out, int n, cudaStream_t s, int* total_host);
@@ -351,8 +401,16 @@ int build_sell(amgc_hierarchy* h, int l);
 int build_sell_of(amgc_hierarchy* h, const DBsr& A, Sell& S);
 int autotune(amgc_hierarchy* h);
 int coarse_setup(amgc_hierarchy* h, int l);
+// block SpGEMM C = A B (BSR, sorted block columns; sym: C symmetric, formed on and above the diagonal)
+int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C, bool sym = false);
+// ptr / idx: the indices i < n grouped by bucket[i] (in [0, nb); < 0 skipped), ascending in each
+int bucket_lists(int n, const int* bucket, int nb, DBuf<int>& ptr, DBuf<int>& idx, cudaStream_t s);
 int check_status(amgc_hierarchy* h, const char* where);
 int transposed_setup(amgc_hierarchy* h);
+// new active set of the slave nodes (device or host bytes, n_s of them): rebuilds the constraint
+// blocks B2 and Z on every level, the Schur-block inverses (and their damping), the coarsest
+// inverse and the views; keeps aggregates, transfers, lambda_max, coarse K and B1
+int update_active_set(amgc_hierarchy* h, const uint8_t* active);
 // setup phase timer: synchronises the stream and adds the elapsed wall time to a phase
 struct PhaseTimer {
   amgc_hierarchy* h;
@@ -384,6 +442,11 @@ bool staged_apply_in_use(const amgc_hierarchy* h);   // the FP32 cycle's fine K 
 void drop_cycle_graphs(amgc_hierarchy* h);            // forget captured cycles (their launches changed)
 int set_row_mapping(amgc_hierarchy* h, int level, int matrix, int precision, int mapping);
 int set_wait_limit(amgc_hierarchy* h, long long polls);
+int nested_setup(amgc_hierarchy* h);   // dense K_c and S_hat inverses, work vectors (prec_kind 1)
+// colouring, diagonal-block inverses and Schur ILU(0) of every smoothed level (smoother_kind != 0);
+// schur_only: the Schur part alone (after an active-set change)
+int block_smoother_setup(amgc_hierarchy* h, bool schur_only);
+int dense_inverse(amgc_hierarchy* h, double* A, int n);   // in place, Gauss-Jordan (setup.cu)
 int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y);
 // FGMRES (krylov.cu)
 int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol, int* iters, double* relres);

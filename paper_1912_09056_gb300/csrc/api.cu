@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -366,6 +367,56 @@ int amgc_set_row_mapping(struct amgc_hierarchy* h, int32_t level, int32_t matrix
   return set_row_mapping(h, level, matrix, precision, mapping);
 }
 
+int amgc_set_smoother(struct amgc_hierarchy* h, int32_t kind, double omega, int32_t sgs_sweeps, double sgs_omega,
+                      void* stream) {
+  if (!h || kind < 0 || kind > 3 ||
+      (kind != 0 && (!(omega > 0.0) || !std::isfinite(omega) || sgs_sweeps < 1 || !(sgs_omega > 0.0) ||
+                     !std::isfinite(sgs_omega)))) {
+    set_error("amgc_set_smoother: invalid argument");
+    return AMGC_EINVAL;
+  }
+  if (kind != 0 && (h->n_inst > 1 || h->opts.precision != 64)) {
+    set_error("amgc_set_smoother: the block smoothers need a single FP64 hierarchy");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
+  const int prev = h->smoother_kind;
+  h->smoother_kind = kind;
+  h->block_omega = omega;
+  h->sgs_sweeps = sgs_sweeps;
+  h->sgs_omega = sgs_omega;
+  if (kind != 0) {
+    const int st = block_smoother_setup(h, false);
+    if (st != AMGC_OK) {
+      h->smoother_kind = prev;
+      return st;
+    }
+  }
+  drop_cycle_graphs(h);
+  return AMGC_OK;
+}
+
+int amgc_set_preconditioner(struct amgc_hierarchy* h, int32_t kind, int32_t outer_sweeps, double omega, void* stream) {
+  if (!h || (kind != 0 && kind != 1) || (kind == 1 && (outer_sweeps < 1 || !(omega > 0.0) || !std::isfinite(omega)))) {
+    set_error("amgc_set_preconditioner: invalid argument");
+    return AMGC_EINVAL;
+  }
+  if (kind == 1 && (h->n_inst > 1 || h->opts.precision != 64)) {
+    set_error("amgc_set_preconditioner: nested multigrid needs a single FP64 hierarchy");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
+  if (kind == 1) {
+    h->nest_sweeps = outer_sweeps;
+    h->nest_omega = omega;
+    if (h->nest.empty()) AMGC_TRY(nested_setup(h));
+  }
+  h->prec_kind = kind;
+  return AMGC_OK;
+}
+
 int amgc_set_wait_limit(struct amgc_hierarchy* h, int64_t polls) {
   if (!h || polls > 0xffffffffLL) {
     set_error("amgc_set_wait_limit: invalid argument");
@@ -439,6 +490,10 @@ static int enter_transposed(amgc_hierarchy* h, void* stream, const char* where) 
   }
   if (h->opts.coarse_solver != 0) {
     set_error(std::string(where) + ": the transposed cycle needs coarse_solver 0 (the coarsest inverse)");
+    return AMGC_EINVAL;
+  }
+  if (h->prec_kind != 0 || h->smoother_kind != 0) {
+    set_error(std::string(where) + ": the transposed cycle is that of the coupled V-cycle with CheapSIMPLE smoothing");
     return AMGC_EINVAL;
   }
   h->stream = (cudaStream_t)stream;
@@ -550,6 +605,7 @@ int64_t amgc_export(const struct amgc_hierarchy* h, int32_t level, int32_t what,
     case AMGC_EXPORT_OMEGA: src = scal; nb = 16; break;
     case AMGC_EXPORT_COARSE_INV: src = L.Ainv.p; nb = L.Ainv.p ? (int64_t)L.Ainv.n * 8 : 0; break;
     case AMGC_EXPORT_SCHUR_RHO: src = L.schur_rho.data(); nb = (int64_t)L.schur_rho.size() * 8; break;
+    case AMGC_EXPORT_COLOR: src = L.color.p; nb = L.color.p ? (int64_t)L.nn * 4 : 0; break;
     default: set_error("amgc_export: unknown array"); return AMGC_EINVAL;
   }
   if (!dst || nb == 0) return nb;

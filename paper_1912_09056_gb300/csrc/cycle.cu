@@ -792,8 +792,13 @@ static int fork_join(amgc_hierarchy* h, FMain&& main_fn, FSide&& side_fn) {
   return AMGC_OK;
 }
 
+static int block_smooth(amgc_hierarchy* h, int l, const double* b, double* x, bool zero_guess);
+
 template <class T>
 static int smooth(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, T* x, bool zero_guess) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->smoother_kind != 0) return block_smooth(h, l, b, x, zero_guess);
+  }
   cudaStream_t s = h->stream;
   const int nu = L.nu();
   const T* f = b;
@@ -843,6 +848,211 @@ static int smooth(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, T* x
                                                        L.atinv, (T)h->opts.simple_alpha, u));
     AMGC_CUDA_TRY(cudaGetLastError());
   }
+  return AMGC_OK;
+}
+
+// ------------------------------------------------------------------ block smoothers (Sec. 5.1, 5.2)
+// Uzawa (Algorithm 2), Braess-Sarazin (Algorithm 3) and SIMPLE (Algorithm 4) in the cheap forms:
+// K solves by damped symmetric block Gauss-Seidel in colour order, Schur solves by the block ILU(0)
+// factors of the assembled approximation (set up in blocksmooth.cu).  FP64, one sweep per call.
+
+// x_i += omega K_ii^-1 (b_i - sum_j K_ij x_j) for the nodes of one colour (one warp per node; the
+// nodes of a colour do not couple, so they update x in place together)
+template <int BU>
+__global__ void __launch_bounds__(128)
+k_cbsgs(int cnt, const int* __restrict__ nodes, const int* __restrict__ rp, const int* __restrict__ col,
+        const double* __restrict__ val, const double* __restrict__ kdinv, const double* __restrict__ b,
+        double* __restrict__ x, double omega) {
+  const int lane = threadIdx.x & 31;
+  const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (t >= cnt) return;
+  const int i = nodes[t];
+  double acc[BU];
+#pragma unroll
+  for (int r = 0; r < BU; ++r) acc[r] = 0.0;
+  lane_blocks<BU, BU, double>(rp[i], rp[i + 1], col, val, x, lane, acc);
+#pragma unroll
+  for (int r = 0; r < BU; ++r) acc[r] = warp_sum(acc[r]);
+  if (lane != 0) return;
+  double res[BU];
+#pragma unroll
+  for (int r = 0; r < BU; ++r) res[r] = b[(int64_t)i * BU + r] - acc[r];
+  const double* D = kdinv + (int64_t)i * BU * BU;
+#pragma unroll
+  for (int r = 0; r < BU; ++r) {
+    double d = 0.0;
+#pragma unroll
+    for (int c = 0; c < BU; ++c) d = fma(D[r * BU + c], res[c], d);
+    x[(int64_t)i * BU + r] += omega * d;
+  }
+}
+
+// x = U^-1 L^-1 r with the block ILU(0) factors, by levels in one CTA: forward y_i = r_i - sum_{j<i}
+// L_ij y_j, then backward x_i = U_ii^-1 (y_i - sum_{j>i} U_ij x_j), in place in x; one warp per row
+// of a level, a CTA barrier between levels (rows of a level read only rows of earlier levels)
+constexpr int kIluThreads = 1024;
+__global__ void __launch_bounds__(kIluThreads)
+k_ilu_solve(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+            const int* __restrict__ diag, const double* __restrict__ uinv, int nlev_l, const int* __restrict__ lptr,
+            const int* __restrict__ lrows, int nlev_u, const int* __restrict__ uptr, const int* __restrict__ urows,
+            const double* __restrict__ r, double* x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int v = 0; v < nlev_l; ++v) {
+    for (int t = lptr[v] + wid; t < lptr[v + 1]; t += nw) {
+      const int i = lrows[t];
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+      for (int e = rp[i] + lane; e < diag[i]; e += 32) {
+        const double* m = val + (int64_t)e * 9;
+        const double* y = x + 3 * (int64_t)col[e];
+        a0 += m[0] * y[0] + m[1] * y[1] + m[2] * y[2];
+        a1 += m[3] * y[0] + m[4] * y[1] + m[5] * y[2];
+        a2 += m[6] * y[0] + m[7] * y[1] + m[8] * y[2];
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      if (lane == 0) {
+        x[3 * (int64_t)i] = r[3 * (int64_t)i] - a0;
+        x[3 * (int64_t)i + 1] = r[3 * (int64_t)i + 1] - a1;
+        x[3 * (int64_t)i + 2] = r[3 * (int64_t)i + 2] - a2;
+      }
+    }
+    __syncthreads();
+  }
+  for (int v = 0; v < nlev_u; ++v) {
+    for (int t = uptr[v] + wid; t < uptr[v + 1]; t += nw) {
+      const int i = urows[t];
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+      for (int e = diag[i] + 1 + lane; e < rp[i + 1]; e += 32) {
+        const double* m = val + (int64_t)e * 9;
+        const double* y = x + 3 * (int64_t)col[e];
+        a0 += m[0] * y[0] + m[1] * y[1] + m[2] * y[2];
+        a1 += m[3] * y[0] + m[4] * y[1] + m[5] * y[2];
+        a2 += m[6] * y[0] + m[7] * y[1] + m[8] * y[2];
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      if (lane == 0) {
+        const double t0 = x[3 * (int64_t)i] - a0, t1 = x[3 * (int64_t)i + 1] - a1, t2 = x[3 * (int64_t)i + 2] - a2;
+        const double* U = uinv + (int64_t)i * 9;
+        x[3 * (int64_t)i] = U[0] * t0 + U[1] * t1 + U[2] * t2;
+        x[3 * (int64_t)i + 1] = U[3] * t0 + U[4] * t1 + U[5] * t2;
+        x[3 * (int64_t)i + 2] = U[6] * t0 + U[7] * t1 + U[8] * t2;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_add_vec(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a[i] + b[i];
+}
+__global__ void k_axpy2(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+
+// `sweeps` damped symmetric block Gauss-Seidel sweeps on K x = b from the x given, colours
+// ascending then descending
+static int colored_sgs(amgc_hierarchy* h, const Level& L, const LevelV<double>& V, const double* b, double* x) {
+  cudaStream_t s = h->stream;
+  for (int sw = 0; sw < h->sgs_sweeps; ++sw)
+    for (int k = 0; k < 2 * L.ncolor; ++k) {
+      const int c = k < L.ncolor ? k : 2 * L.ncolor - 1 - k;
+      const int cnt = L.h_col_ptr[c + 1] - L.h_col_ptr[c];
+      if (cnt == 0) continue;
+      const int* nodes = L.col_nodes.p + L.h_col_ptr[c];
+      if (L.bu == 3)
+        AMGC_LAUNCH(k_cbsgs<3><<<div_up((int64_t)cnt * 32, 128), 128, 0, s>>>(cnt, nodes, V.K.rp, V.K.col, V.K.val,
+                                                                             L.kdblk_inv.p, b, x, h->sgs_omega));
+      else
+        AMGC_LAUNCH(k_cbsgs<6><<<div_up((int64_t)cnt * 32, 128), 128, 0, s>>>(cnt, nodes, V.K.rp, V.K.col, V.K.val,
+                                                                             L.kdblk_inv.p, b, x, h->sgs_omega));
+    }
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+static int ilu_apply(amgc_hierarchy* h, const Level& L, const double* r, double* x) {
+  AMGC_LAUNCH(k_ilu_solve<<<1, kIluThreads, 0, h->stream>>>(L.S.rowptr.p, L.S.col.p, L.S.val.p, L.s_diag.p,
+                                                          L.s_uinv.p, L.s_nlev_l, L.s_lptr.p, L.s_lrows.p,
+                                                          L.s_nlev_u, L.s_uptr.p, L.s_urows.p, r, x));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+// u = uh - alpha A~^-1 B1 dlam over all displacement rows
+static int b1_correct(amgc_hierarchy* h, const LevelV<double>& V, const double* uh, const double* dlam, double alpha,
+                      double* u) {
+  const int nu = V.nu();
+  const int nc = div_up(nu, 128);
+  const int gb = div_up((int64_t)V.n_b1_rows * 32, 128);
+  if (V.bu == 3)
+    AMGC_LAUNCH(k_copy_b1<3, double><<<nc + gb, 128, 0, h->stream>>>(nu, nc, uh, V.n_b1_rows, V.b1_rows, V.B1.rp,
+                                                                    V.B1.col, V.B1.val, dlam, V.atinv, alpha, u));
+  else
+    AMGC_LAUNCH(k_copy_b1<6, double><<<nc + gb, 128, 0, h->stream>>>(nu, nc, uh, V.n_b1_rows, V.b1_rows, V.B1.rp,
+                                                                    V.B1.col, V.B1.val, dlam, V.atinv, alpha, u));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+// one sweep of the level's block smoother on [u; lam] (zero_guess: from u = 0, lam = 0)
+static int block_smooth(amgc_hierarchy* h, int l, const double* b, double* x, bool zero_guess) {
+  const LevelV<double>& V = h->v64[l];
+  const Level& L = h->L[l];
+  cudaStream_t s = h->stream;
+  const int th = 256;
+  const int nu = V.nu(), nl3 = 3 * V.nl;
+  const double* f = b;
+  const double* g = b + nu;
+  double* u = x;
+  double* lam = x + nu;
+  double* w = L.bs_w.p;
+  double* d = L.bs_d.p;
+  double* rl = L.bs_l.p;
+  double* sm = L.bs_m.p;
+  const double om = h->block_omega;
+  const BsrV<double>* B1 = V.nl ? &V.B1 : nullptr;
+  if (zero_guess) AMGC_LAUNCH(k_zero<double><<<div_up(V.rows(), th), th, 0, s>>>(V.rows(), x));
+  if (h->smoother_kind == 1) {                      // Uzawa
+    AMGC_TRY((mapped_apply<2, double>(V.K, V.Ks, V.kmap, B1, u, lam, f, nullptr, nullptr, 0.0, w, s)));
+    AMGC_LAUNCH(k_zero<double><<<div_up(nu, th), th, 0, s>>>(nu, d));
+    AMGC_TRY(colored_sgs(h, L, V, w, d));                                       // du ~ K^-1 (f - K u - B1 lam)
+    if (V.nl > 0) {
+      AMGC_LAUNCH(k_add_vec<<<div_up(nu, th), th, 0, s>>>(nu, u, d, w));        // u + du
+      AMGC_TRY((lm_op<0, double>(V, w, g, lam, 0.0, rl, s)));                   // g - B2 (u + du) + Z lam
+      AMGC_TRY(ilu_apply(h, L, rl, sm));                                         // dlam = -sm
+      AMGC_LAUNCH(k_axpy2<<<div_up(nl3, th), th, 0, s>>>(nl3, -om, sm, lam));
+    }
+    AMGC_LAUNCH(k_axpy2<<<div_up(nu, th), th, 0, s>>>(nu, om, d, u));
+  } else if (h->smoother_kind == 2) {               // Braess-Sarazin
+    AMGC_TRY((mapped_apply<3, double>(V.K, V.Ks, V.kmap, B1, u, lam, f, u, V.atinv, 1.0 / om, w, s)));   // u_h
+    if (V.nl > 0) {
+      AMGC_TRY((lm_op<0, double>(V, w, g, lam, 0.0, rl, s)));                   // g + Z lam - B2 u_h
+      AMGC_TRY(ilu_apply(h, L, rl, sm));                                         // dlam = -sm
+      AMGC_LAUNCH(k_axpy2<<<div_up(nl3, th), th, 0, s>>>(nl3, -1.0, sm, lam));
+      AMGC_TRY(b1_correct(h, V, w, sm, -1.0 / om, u));                           // u = u_h - A~^-1 B1 dlam / omega
+    } else {
+      AMGC_LAUNCH(k_copy<double><<<div_up(nu, th), th, 0, s>>>(nu, w, u));
+    }
+  } else {                                          // SIMPLE with the SGS predictor
+    if (V.nl > 0) AMGC_TRY((rowop<2, double>(V.B1, lam, nullptr, nullptr, f, nullptr, nullptr, 0.0, w, s)));   // f - B1 lam
+    else AMGC_LAUNCH(k_copy<double><<<div_up(nu, th), th, 0, s>>>(nu, f, w));
+    AMGC_LAUNCH(k_copy<double><<<div_up(nu, th), th, 0, s>>>(nu, u, d));
+    AMGC_TRY(colored_sgs(h, L, V, w, d));                                       // u_h ~ K^-1 (f - B1 lam) from u
+    if (V.nl > 0) {
+      AMGC_TRY((lm_op<0, double>(V, d, g, lam, 0.0, rl, s)));                   // g + Z lam - B2 u_h
+      AMGC_TRY(ilu_apply(h, L, rl, sm));                                         // dlam = -sm
+      AMGC_LAUNCH(k_axpy2<<<div_up(nl3, th), th, 0, s>>>(nl3, -om, sm, lam));
+      AMGC_TRY(b1_correct(h, V, d, sm, -om, u));                                 // u = u_h - omega A~^-1 B1 dlam
+    } else {
+      AMGC_LAUNCH(k_copy<double><<<div_up(nu, th), th, 0, s>>>(nu, d, u));
+    }
+  }
+  AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
 
@@ -1090,10 +1300,205 @@ static int replay_cycle(amgc_hierarchy* h, int idx) {
   return AMGC_OK;
 }
 
+// ------------------------------------------------------------------ nested multigrid (Sec. 3.2)
+// The comparison preconditioner of Sec. 3.2 (Fig. mgmphmodelsA): the displacement-multiplier
+// coupling is treated on the finest level only, by outer SIMPLE sweeps (Algorithm 4) whose
+// predictor is one single-field AMG V-cycle on K:
+//     u_h = u + V_K (f - K u - B1 lam)
+//     dlam = -S_hat^-1 (g + Z lam - B2 u_h),   S_hat = Z + B2 A~^-1 B1 (exact, dense)
+//     lam += omega dlam,   u = u_h - omega A~^-1 B1 dlam
+// The K hierarchy is the displacement part of the coupled one: the same aggregates, transfers,
+// Galerkin K_c, lambda_max and omega_J D^-1; V_K smooths with damped Jacobi (smoother_sweeps pre and
+// post) and solves the coarsest K_c with its dense inverse.  FP64.
+
+// dense S_hat rows of multiplier node l (one thread per node, which owns its three rows)
+__global__ void k_dense_schur(int nl, const int* __restrict__ rp2, const int* __restrict__ c2,
+                              const double* __restrict__ v2, const int* __restrict__ rp1, const int* __restrict__ c1,
+                              const double* __restrict__ v1, const double* __restrict__ atinv,
+                              const double* __restrict__ Z, double* __restrict__ A) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nl) return;
+  const int64_t n = 3 * (int64_t)nl;
+  for (int e = rp2[l]; e < rp2[l + 1]; ++e) {
+    const int i = c2[e];
+    const double* b2 = v2 + (int64_t)e * 9;
+    double ba[9];
+    for (int r = 0; r < 3; ++r)
+      for (int k = 0; k < 3; ++k) ba[r * 3 + k] = b2[r * 3 + k] * atinv[3 * (int64_t)i + k];
+    for (int q = rp1[i]; q < rp1[i + 1]; ++q) {
+      const int m = c1[q];
+      const double* b1 = v1 + (int64_t)q * 9;
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+          double acc = A[(3 * (int64_t)l + r) * n + 3 * (int64_t)m + c];
+          for (int k = 0; k < 3; ++k) acc = fma(ba[r * 3 + k], b1[k * 3 + c], acc);
+          A[(3 * (int64_t)l + r) * n + 3 * (int64_t)m + c] = acc;
+        }
+    }
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) A[(3 * (int64_t)l + r) * n + 3 * (int64_t)l + c] += Z[(int64_t)l * 9 + r * 3 + c];
+}
+// dense copy of a BR x BR block matrix (one warp per block row)
+template <int BR>
+__global__ void k_dense_blocks(int nbr, const int* __restrict__ rp, const int* __restrict__ col,
+                               const double* __restrict__ val, double* __restrict__ A) {
+  constexpr int NQ = BR * BR;
+  const int lane = threadIdx.x & 31;
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (i >= nbr) return;
+  const int64_t n = (int64_t)nbr * BR;
+  const int e0 = rp[i], nq = (rp[i + 1] - e0) * NQ;
+  for (int q = lane; q < nq; q += 32) {
+    const int eb = q / NQ, w = q - eb * NQ;
+    const int r = w / BR, c = w - r * BR;
+    A[(int64_t)(i * BR + r) * n + (int64_t)col[e0 + eb] * BR + c] = val[(int64_t)e0 * NQ + q];
+  }
+}
+__global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+
+int nested_setup(amgc_hierarchy* h) {
+  cudaStream_t s = h->stream;
+  const int nlev = (int)h->L.size();
+  const Level& Lc = h->L[nlev - 1];
+  const Level& L0 = h->L[0];
+  const int nk = Lc.nu();
+  const int nsch = 3 * L0.nl;
+  constexpr int kMaxDense = 16384;
+  if (nk > kMaxDense || nsch > kMaxDense) {
+    set_error("nested multigrid: the coarsest K (" + std::to_string(nk) + " rows) or S_hat (" + std::to_string(nsch) +
+              " rows) exceeds the dense limit of " + std::to_string(kMaxDense));
+    return AMGC_EINVAL;
+  }
+  for (int l = 0; l + 1 < nlev; ++l)
+    if (!h->L[l].jdinv.p) {
+      set_error("nested multigrid: level without Jacobi data");
+      return AMGC_EINVAL;
+    }
+  AMGC_TRY(h->nest_Kinv.alloc((size_t)nk * nk));
+  AMGC_CUDA_TRY(cudaMemsetAsync(h->nest_Kinv.p, 0, (size_t)nk * nk * sizeof(double), s));
+  if (Lc.bu == 3)
+    AMGC_LAUNCH(k_dense_blocks<3><<<div_up((int64_t)Lc.nn * 32, 128), 128, 0, s>>>(Lc.nn, Lc.K.rowptr.p, Lc.K.col.p,
+                                                                                 Lc.K.val.p, h->nest_Kinv.p));
+  else
+    AMGC_LAUNCH(k_dense_blocks<6><<<div_up((int64_t)Lc.nn * 32, 128), 128, 0, s>>>(Lc.nn, Lc.K.rowptr.p, Lc.K.col.p,
+                                                                                 Lc.K.val.p, h->nest_Kinv.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(dense_inverse(h, h->nest_Kinv.p, nk));
+  AMGC_TRY(h->nest_Sinv.alloc((size_t)std::max(nsch, 1) * std::max(nsch, 1)));
+  if (nsch > 0) {
+    AMGC_CUDA_TRY(cudaMemsetAsync(h->nest_Sinv.p, 0, (size_t)nsch * nsch * sizeof(double), s));
+    AMGC_LAUNCH(k_dense_schur<<<div_up(L0.nl, 128), 128, 0, s>>>(L0.nl, L0.B2.rowptr.p, L0.B2.col.p, L0.B2.val.p,
+                                                                L0.B1.rowptr.p, L0.B1.col.p, L0.B1.val.p, L0.atinv.p,
+                                                                L0.Z.p, h->nest_Sinv.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    AMGC_TRY(dense_inverse(h, h->nest_Sinv.p, nsch));
+  }
+  AMGC_TRY(check_status(h, "nested multigrid: dense inverses"));
+  h->nest.clear();
+  h->nest.resize(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    const size_t n = (size_t)std::max(h->L[l].nu(), 1);
+    amgc_hierarchy::NestBufs& B = h->nest[l];
+    AMGC_TRY(B.x.alloc(n));
+    AMGC_TRY(B.b.alloc(n));
+    AMGC_TRY(B.r.alloc(n));
+    AMGC_TRY(B.t.alloc(n));
+  }
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMGC_OK;
+}
+
+// x = V_K(b) on level l of the K hierarchy (zero initial guess)
+static int kcycle(amgc_hierarchy* h, int l, const double* b, double* x) {
+  const std::vector<LevelV<double>>& V = h->v64;
+  const LevelV<double>& L = V[l];
+  cudaStream_t s = h->stream;
+  const int th = 256;
+  const int nu = L.nu();
+  if (l == (int)V.size() - 1) {
+    AMGC_LAUNCH(k_gemv<double><<<div_up((int64_t)nu * 32, th), th, 0, s>>>(nu, h->nest_Kinv.p, b, x));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    return AMGC_OK;
+  }
+  amgc_hierarchy::NestBufs& B = h->nest[l];
+  amgc_hierarchy::NestBufs& C = h->nest[l + 1];
+  const int J = h->opts.smoother_sweeps;
+  // J damped Jacobi sweeps, each out of place (it gathers its input at the neighbours): they
+  // alternate between x and B.t.  From a zero guess the first sweep needs no product and its
+  // buffer is chosen so that the last one ends in x; from the iterate in x the first goes to B.t
+  // and a copy brings an odd count's result back.
+  auto sweeps = [&](bool zero_guess) -> int {
+    double* cur = x;
+    for (int j = 0; j < J; ++j) {
+      double* dst = zero_guess ? (((J - 1 - j) % 2 == 0) ? x : B.t.p) : (cur == x ? B.t.p : x);
+      if (zero_guess && j == 0) {
+        AMGC_LAUNCH(k_jacobi_zero<double><<<div_up(nu, th), th, 0, s>>>(nu, 0, b, L.dinv, 1.0, dst, nullptr));
+        AMGC_CUDA_TRY(cudaGetLastError());
+      } else {
+        AMGC_TRY((mapped_apply<3, double>(L.K, L.Ks, L.kmap, nullptr, cur, nullptr, b, cur, L.dinv, L.omega_j, dst, s)));
+      }
+      cur = dst;
+    }
+    if (cur != x) AMGC_LAUNCH(k_copy<double><<<div_up(nu, th), th, 0, s>>>(nu, cur, x));
+    return AMGC_OK;
+  };
+  if (J == 0) AMGC_LAUNCH(k_zero<double><<<div_up(nu, th), th, 0, s>>>(nu, x));
+  else AMGC_TRY(sweeps(true));
+  AMGC_TRY((mapped_apply<2, double>(L.K, L.Ks, L.kmap, nullptr, x, nullptr, b, nullptr, nullptr, 0.0, B.r.p, s)));
+  AMGC_TRY((mapped_apply<0, double>(L.R, L.Rs, L.rmap, nullptr, B.r.p, nullptr, nullptr, nullptr, nullptr, 0.0, C.b.p, s)));
+  AMGC_TRY(kcycle(h, l + 1, C.b.p, C.x.p));
+  AMGC_TRY((mapped_apply<1, double>(L.P, L.Ps, L.pmap, nullptr, C.x.p, nullptr, nullptr, nullptr, nullptr, 0.0, x, s)));
+  if (J > 0) AMGC_TRY(sweeps(false));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
+// z = the nested preconditioner applied to r (FP64, device vectors of the finest saddle rows)
+static int nested_apply(amgc_hierarchy* h, const double* r, double* z) {
+  const LevelV<double>& L = h->v64[0];
+  cudaStream_t s = h->stream;
+  const int th = 256;
+  const int nu = L.nu();
+  const int nl3 = 3 * L.nl;
+  const double* f = r;
+  const double* g = r + nu;
+  double* u = z;
+  double* lam = z + nu;
+  amgc_hierarchy::NestBufs& B = h->nest[0];
+  double* rl = L.r + nu;          // the multiplier residual (the coupled cycle's scratch)
+  double* w = L.dlam;             // S_hat^-1 r_lambda
+  const double om = h->nest_omega;
+  for (int k = 0; k < h->nest_sweeps; ++k) {
+    if (k == 0) {
+      AMGC_TRY(kcycle(h, 0, f, u));                                            // u_h = V_K f
+      AMGC_LAUNCH(k_zero<double><<<div_up(std::max(nl3, 1), th), th, 0, s>>>(nl3, lam));
+    } else {
+      AMGC_TRY((mapped_apply<2, double>(L.K, L.Ks, L.kmap, L.nl ? &L.B1 : nullptr, u, lam, f, nullptr, nullptr, 0.0,
+                                        B.b.p, s)));                          // f - K u - B1 lam
+      AMGC_TRY(kcycle(h, 0, B.b.p, B.x.p));
+      AMGC_LAUNCH(k_axpy<<<div_up(nu, th), th, 0, s>>>(nu, 1.0, B.x.p, u));     // u_h = u + V_K(...)
+    }
+    if (L.nl == 0) continue;
+    AMGC_TRY((lm_op<0, double>(L, u, g, lam, 0.0, rl, s)));                   // g - B2 u_h + Z lam
+    AMGC_LAUNCH(k_gemv<double><<<div_up((int64_t)nl3 * 32, th), th, 0, s>>>(nl3, h->nest_Sinv.p, rl, w));
+    AMGC_LAUNCH(k_axpy<<<div_up(nl3, th), th, 0, s>>>(nl3, -om, w, lam));     // lam += omega dlam, dlam = -w
+    if (L.n_b1_rows > 0)                                                       // u = u_h + omega A~^-1 B1 w
+      AMGC_LAUNCH(k_b1_update<3, double><<<div_up((int64_t)L.n_b1_rows * 32, 128), 128, 0, s>>>(
+          L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, w, L.atinv, -om, u));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  return AMGC_OK;
+}
+
 // One V-cycle with FP64 input and output; the FP32 cycle converts at entry and exit.  Outside
 // kernel timing the cycle core runs as a captured CUDA graph.
 int precond_apply(amgc_hierarchy* h, const double* r, double* z) {
   if (h->transposed) return vcycle_transposed(h, 0, r, z);
+  if (h->prec_kind == 1) return nested_apply(h, r, z);
   const bool graph = h->prof == 0;
   const int64_t n = h->L[0].rows();
   const int th = 256;

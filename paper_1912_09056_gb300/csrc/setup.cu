@@ -104,7 +104,7 @@ __global__ void k_copy_int(int n, const int* __restrict__ a, int* __restrict__ b
   if (i < n) b[i] = a[i];
 }
 
-static int bucket_lists(int n, const int* bucket, int nb, DBuf<int>& ptr, DBuf<int>& idx, cudaStream_t s) {
+int bucket_lists(int n, const int* bucket, int nb, DBuf<int>& ptr, DBuf<int>& idx, cudaStream_t s) {
   AMGC_TRY(ptr.alloc(nb + 1));
   DBuf<int> cur;
   AMGC_TRY(cur.alloc(nb + 1));
@@ -375,27 +375,28 @@ int build_fine_level(amgc_hierarchy* h, const amgc_bsr* K, const double* D, cons
                                               dT.p, L.B2.col.p, L.B2.val.p, L.Z.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   AMGC_TRY(check_status(h, "interface assembly"));
+  // --- interface data kept for active-set updates
+  L.if_D = std::move(dD);
+  L.if_Mv = std::move(dMv);
+  L.if_T = std::move(dT);
+  L.if_Mrp = std::move(dMrp);
+  L.if_Mcol = std::move(dMcol);
+  L.if_Sl = std::move(dSl);
+  L.if_Ms = std::move(dMs);
+  L.if_act = std::move(dAct);
   // --- multiplier data
   AMGC_TRY(L.Bl.alloc(std::max(ns, 1)));
   AMGC_LAUNCH(k_fill_dbl<<<div_up(std::max(ns, 1), 256), 256, 0, s>>>(ns, 1.0, L.Bl.p));
   AMGC_TRY(L.lm_dnode.alloc(std::max(ns, 1)));
-  if (ns > 0) AMGC_LAUNCH(k_copy_int<<<div_up(ns, 256), 256, 0, s>>>(ns, dSl.p, L.lm_dnode.p));
+  if (ns > 0) AMGC_LAUNCH(k_copy_int<<<div_up(ns, 256), 256, 0, s>>>(ns, L.if_Sl.p, L.lm_dnode.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   AMGC_CUDA_TRY(cudaStreamSynchronize(s));
   return AMGC_OK;
 }
 
 // ======================================================================== MIS-2 aggregation
-// Priority of node i: fmix32(i ^ seed) * 2^32 + i (MurmurHash3 finaliser, A. Appleby); the
-// stored value is priority + 1 for an undecided node and 0 otherwise.
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-  h ^= h >> 16;
-  h *= 0x85ebca6bu;
-  h ^= h >> 13;
-  h *= 0xc2b2ae35u;
-  h ^= h >> 16;
-  return h;
-}
+// Priority of node i: fmix32(i ^ seed) * 2^32 + i (fmix32 in amgc_internal.cuh); the stored
+// value is priority + 1 for an undecided node and 0 otherwise.
 enum : int8_t { UND = 0, ROOT = 1, OUT = 2 };
 
 // key_base (batched hierarchies): first node of the node's instance, so that the hash uses the
@@ -1169,7 +1170,7 @@ static int spgemm_numeric(const DBsr& A, const DBsr& B, DBsr& C, int cmax, SpUni
 }
 
 // sym: C = A B is known to be block-symmetric (a Galerkin product P^T K P): square blocks only
-static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C, bool sym = false) {
+int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C, bool sym) {
   cudaStream_t s = h->stream;
   if (A.bc != B.br || A.nbc != B.nbr) {
     set_error("spgemm: shape mismatch");
@@ -1265,6 +1266,7 @@ static int spgemm(amgc_hierarchy* h, const DBsr& A, const DBsr& B, DBsr& C, bool
   AMGC_GEMM_CASE(6, 6, 6)
   AMGC_GEMM_CASE(6, 6, 3)
   AMGC_GEMM_CASE(3, 6, 6)
+  AMGC_GEMM_CASE(3, 6, 3)
 #undef AMGC_GEMM_CASE
   set_error("spgemm: unsupported block shape");
   return AMGC_EINVAL;
@@ -1810,6 +1812,8 @@ int coarsen_level(amgc_hierarchy* h, int l) {
     AMGC_TRY(C.Z.alloc((size_t)n_lagg * 9));
     AMGC_LAUNCH(k_zc<<<div_up(n_lagg, 128), 128, 0, s>>>(n_lagg, L.rl_ptr.p, L.rl_idx.p, L.pl_w.p, L.Z.p, C.Z.p));
     AMGC_CUDA_TRY(cudaGetLastError());
+    L.Pl = std::move(Pl);
+    L.Rl = std::move(Rl);
   } else {
     C.B1.nbr = n_agg; C.B1.nbc = 0; C.B1.br = 6; C.B1.bc = 3;
     AMGC_TRY(C.B1.rowptr.alloc(n_agg + 1));
@@ -1831,6 +1835,90 @@ int coarsen_level(amgc_hierarchy* h, int l) {
   Level& Cn = h->L[l + 1];
   AMGC_LAUNCH(k_gather_body<<<div_up(n_agg, 256), 256, 0, s>>>(n_agg, roots.p, Lf.body.p, Cn.body.p));
   AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMGC_OK;
+}
+
+// ======================================================================== active-set update
+// The constraint blocks B2 and Z are the only parts of the system that depend on the active set
+// (inactive slave nodes: zero B2 row and -Z = I; active ones: the weighted-gap row and the
+// tangential rows).  Aggregation, the transfers, lambda_max and the coarse K depend on K (and the
+// interface pattern) alone, so an active-set change reuses them and forms anew: B2 and Z on the
+// finest level, B2_c = R^lambda B2 P and Z_c on the coarser ones (B1_c does not change), the
+// inverted Schur blocks (and their damping), the coarsest inverse (or the coarsest smoother data)
+// and the FP32 mirrors.
+int update_active_set(amgc_hierarchy* h, const uint8_t* active) {
+  cudaStream_t s = h->stream;
+  const int nlev = (int)h->L.size();
+  Level& L0 = h->L[0];
+  const int ns = L0.nl;
+  DBuf<uint8_t> dAct;
+  AMGC_TRY(dAct.alloc(std::max(ns, 1)));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(dAct.p, active, ns, cudaMemcpyDefault, s));
+  // finest level: B2 (pattern and values) and Z
+  DBsr B2;
+  B2.nbr = ns; B2.nbc = L0.nn; B2.br = 3; B2.bc = 3;
+  AMGC_TRY(B2.rowptr.alloc(ns + 1));
+  AMGC_CUDA_TRY(cudaMemsetAsync(B2.rowptr.p, 0, (ns + 1) * sizeof(int), s));
+  AMGC_LAUNCH(k_b2_count<<<div_up(ns, 256), 256, 0, s>>>(ns, dAct.p, L0.if_Mrp.p, B2.rowptr.p));
+  int b2n = 0;
+  AMGC_TRY(exclusive_scan(B2.rowptr.p, B2.rowptr.p, ns + 1, s, &b2n));
+  B2.nnzb = b2n;
+  AMGC_TRY(B2.col.alloc(std::max(b2n, 1)));
+  AMGC_TRY(B2.val.alloc((size_t)std::max(b2n, 1) * 9));
+  AMGC_LAUNCH(k_b2_fill<<<div_up(ns, 256), 256, 0, s>>>(ns, dAct.p, B2.rowptr.p, L0.if_Sl.p, L0.if_Ms.p, L0.if_D.p,
+                                                       L0.if_Mrp.p, L0.if_Mcol.p, L0.if_Mv.p, L0.if_T.p, B2.col.p,
+                                                       B2.val.p, L0.Z.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  L0.B2 = std::move(B2);
+  L0.if_act = std::move(dAct);
+  // coarser levels: B2_c = R^lambda (B2 P), Z_c = sum w^2 Z
+  for (int l = 0; l + 1 < nlev; ++l) {
+    Level& L = h->L[l];
+    Level& C = h->L[l + 1];
+    if (L.nl == 0) continue;
+    DBsr B2P;
+    AMGC_TRY(spgemm(h, L.B2, L.P, B2P));
+    AMGC_TRY(spgemm(h, L.Rl, B2P, C.B2));
+    AMGC_LAUNCH(k_zc<<<div_up(C.nl, 128), 128, 0, s>>>(C.nl, L.rl_ptr.p, L.rl_idx.p, L.pl_w.p, L.Z.p, C.Z.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  AMGC_TRY(check_status(h, "active-set update: constraint blocks"));
+  // Schur blocks (and their damping) on every smoothed level, then the coarsest level
+  const bool coarse_smooth = h->opts.coarse_solver == 1 && nlev > 1;
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = h->L[l];
+    const bool smoothed = l + 1 < nlev || coarse_smooth;
+    if (!smoothed || L.nl == 0) continue;
+    if (L.bu == 3)
+      AMGC_LAUNCH(k_schur<3><<<div_up((int64_t)L.nl * 32, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p,
+                                                   L.B1.rowptr.p, L.B1.col.p, L.B1.val.p, L.atinv.p, L.Z.p, L.Sinv.p,
+                                                   h->status.p));
+    else
+      AMGC_LAUNCH(k_schur<6><<<div_up((int64_t)L.nl * 32, 128), 128, 0, s>>>(L.nl, L.B2.rowptr.p, L.B2.col.p, L.B2.val.p,
+                                                   L.B1.rowptr.p, L.B1.col.p, L.B1.val.p, L.atinv.p, L.Z.p, L.Sinv.p,
+                                                   h->status.p));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    AMGC_TRY(check_status(h, "active-set update: Schur blocks"));
+    if (h->opts.schur_damping) AMGC_TRY(schur_damping_setup(h, L));
+  }
+  if (!coarse_smooth) AMGC_TRY(coarse_setup(h, nlev - 1));
+  // transposed data is formed again on the next transposed call
+  for (auto& L : h->L) {
+    L.has_transposed = false;
+    L.B1T = DBsr();
+    L.B2T = DBsr();
+  }
+  // statistics of the changed blocks
+  amgc_stats_t& st = h->stats;
+  double nnz0 = 0.0, nnz_all = 0.0;
+  for (int l = 0; l < nlev; ++l) {
+    const Level& L = h->L[l];
+    st.nnz[l] = L.K.nnzb * L.bu * L.bu + L.B1.nnzb * L.bu * 3 + L.B2.nnzb * 3 * L.bu + (int64_t)L.nl * 9;
+    if (l == 0) nnz0 = (double)st.nnz[l];
+    nnz_all += (double)st.nnz[l];
+  }
+  st.operator_complexity = nnz0 > 0 ? nnz_all / nnz0 : 0.0;
   AMGC_CUDA_TRY(cudaStreamSynchronize(s));
   return AMGC_OK;
 }
@@ -2454,6 +2542,61 @@ static int coarse_setup_batched(amgc_hierarchy* h, int l) {
   return AMGC_OK;
 }
 
+// In-place inverse of the dense row-major n x n matrix A by Gauss-Jordan elimination with partial
+// pivoting (one cooperative launch where the device allows it, else a pivot and an update launch
+// per column); a zero pivot sets ST_SINGULAR, which the caller's status check reports.
+int dense_inverse(amgc_hierarchy* h, double* A, int n) {
+  cudaStream_t s = h->stream;
+  DBuf<int> piv;
+  AMGC_TRY(piv.alloc(n));
+  // one cooperative launch when the device supports it and two rows fit in shared memory,
+  // else one pivot launch and one update launch per column
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  AMGC_CUDA_TRY(cudaGetDevice(&dev));
+  AMGC_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  AMGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // kGjB pivots per barrier while the panel tables fit in shared memory, else one per barrier
+  const bool blocked = n <= kGjBlockedMax;
+  const int gjb = 8;
+  const void* kern = !blocked ? (const void*)k_gj_coop : (const void*)k_gj_blocked<8>;
+  const size_t smem = blocked ? (size_t)n * (2 * gjb * sizeof(double) + 2 * sizeof(int))
+                              : 2 * (size_t)n * sizeof(double);
+  if (coop && smem <= 200 * 1024) {
+    // (raised whatever the size: the kernel's static shared memory counts against 48 KB too)
+    AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AMGC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGjcThreads, smem));
+  }
+  if (per_sm > 0) {
+    // the blocked kernel repeats the panel elimination in every CTA: one CTA per SM
+    const int grid = std::min(n, blocked ? sms : sms * std::min(per_sm, 2));
+    DBuf<double> tmp;
+    AMGC_TRY(tmp.alloc((size_t)n * n));
+    int nn = n;
+    double* a = A;
+    double* b = tmp.p;
+    int* pv = piv.p;
+    int* st = h->status.p;
+    void* args[] = {&nn, &a, &b, &pv, &st};
+    AMGC_CUDA_TRY(AMGC_LAUNCH(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kGjcThreads), args, smem, s)));
+    // the buffers alternate once per barrier; the permuted result is in the other one
+    const int passes = blocked ? (n + gjb - 1) / gjb : n;
+    if (passes % 2 == 0)
+      AMGC_CUDA_TRY(cudaMemcpyAsync(A, tmp.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  } else {
+    DBuf<double> f;
+    AMGC_TRY(f.alloc(n));
+    const int64_t nn2 = (int64_t)n * n;
+    for (int k = 0; k < n; ++k) {
+      AMGC_LAUNCH(k_gj_pivot<<<1, 1024, 0, s>>>(n, k, A, piv.p, f.p, h->status.p));
+      AMGC_LAUNCH(k_gj_update<<<div_up(nn2, 256), 256, 0, s>>>(n, k, A, f.p));
+    }
+    AMGC_LAUNCH(k_gj_unscramble<<<div_up(n, 128), 128, 0, s>>>(n, piv.p, A));
+    AMGC_CUDA_TRY(cudaGetLastError());
+  }
+  return AMGC_OK;
+}
+
 int coarse_setup(amgc_hierarchy* h, int l) {
   if (h->n_inst > 1) return coarse_setup_batched(h, l);
   cudaStream_t s = h->stream;
@@ -2481,53 +2624,7 @@ int coarse_setup(amgc_hierarchy* h, int l) {
   }
   if (L.nl > 0) AMGC_LAUNCH(k_dense_z<<<div_up(L.nl, 128), 128, 0, s>>>(L.nl, L.Z.p, nu, n, L.Ainv.p));
   AMGC_CUDA_TRY(cudaGetLastError());
-  DBuf<int> piv;
-  AMGC_TRY(piv.alloc(n));
-  // one cooperative launch when the device supports it and two rows fit in shared memory,
-  // else one pivot launch and one update launch per column
-  int dev = 0, coop = 0, sms = 0, per_sm = 0;
-  AMGC_CUDA_TRY(cudaGetDevice(&dev));
-  AMGC_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  AMGC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // kGjB pivots per barrier while the panel tables fit in shared memory, else one per barrier
-  const bool blocked = n <= kGjBlockedMax;
-  const int gjb = 8;
-  const void* kern = !blocked ? (const void*)k_gj_coop : (const void*)k_gj_blocked<8>;
-  const size_t smem = blocked ? (size_t)n * (2 * gjb * sizeof(double) + 2 * sizeof(int))
-                              : 2 * (size_t)n * sizeof(double);
-  if (coop && smem <= 200 * 1024) {
-    // (raised whatever the size: the kernel's static shared memory counts against 48 KB too)
-    AMGC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    AMGC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGjcThreads, smem));
-  }
-  if (per_sm > 0) {
-    // the blocked kernel repeats the panel elimination in every CTA: one CTA per SM
-    const int grid = std::min(n, blocked ? sms : sms * std::min(per_sm, 2));
-    DBuf<double> tmp;
-    AMGC_TRY(tmp.alloc((size_t)n * n));
-    int nn = n;
-    double* a = L.Ainv.p;
-    double* b = tmp.p;
-    int* pv = piv.p;
-    int* st = h->status.p;
-    void* args[] = {&nn, &a, &b, &pv, &st};
-    AMGC_CUDA_TRY(AMGC_LAUNCH(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kGjcThreads), args, smem, s)));
-    // the buffers alternate once per barrier; the permuted result is in the other one
-    const int passes = blocked ? (n + gjb - 1) / gjb : n;
-    if (passes % 2 == 0)
-      AMGC_CUDA_TRY(cudaMemcpyAsync(L.Ainv.p, tmp.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    AMGC_CUDA_TRY(cudaStreamSynchronize(s));
-  } else {
-    DBuf<double> f;
-    AMGC_TRY(f.alloc(n));
-    const int64_t nn2 = (int64_t)n * n;
-    for (int k = 0; k < n; ++k) {
-      AMGC_LAUNCH(k_gj_pivot<<<1, 1024, 0, s>>>(n, k, L.Ainv.p, piv.p, f.p, h->status.p));
-      AMGC_LAUNCH(k_gj_update<<<div_up(nn2, 256), 256, 0, s>>>(n, k, L.Ainv.p, f.p));
-    }
-    AMGC_LAUNCH(k_gj_unscramble<<<div_up(n, 128), 128, 0, s>>>(n, piv.p, L.Ainv.p));
-    AMGC_CUDA_TRY(cudaGetLastError());
-  }
+  AMGC_TRY(dense_inverse(h, L.Ainv.p, n));
   AMGC_TRY(check_status(h, "coarsest factorisation"));
   AMGC_TRY(alloc_work(L));
   return AMGC_OK;
