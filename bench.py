@@ -3,7 +3,7 @@
 
 A step is one pass of the whole path on the large two-block contact workload (110x110x55 master
 + 97x97x49 slave hex8 bricks, E 1 / 100, nu 0.3 / 0.45, all interface nodes active, 3.47 M rows,
-4 smoothed-aggregation levels): amgc_setup on device-resident inputs (aggregation, transfers,
+4 smoothed-aggregation levels, three CheapSIMPLE sweeps): amgc_setup on device-resident inputs (aggregation, transfers,
 Galerkin products, smoother data, coarsest inverse) followed by amgc_solve with FGMRES + one FP64
 V-cycle per iteration to a 1e-8 relative residual.  The same step with the FP32 V-cycle, the
 V-cycle times against the HBM roofline, the adjoint workload and the batched set are reported
@@ -32,7 +32,9 @@ if ROOT not in sys.path:
 
 METRIC = "FGMRES+AMG solve ms to 1e-8 rel res (FP32-cycle vs FP64); V-cycle %HBM; adjoint ms"
 WORKLOAD = 2
-OPTS = dict(levels_max=4, coarse_max_rows=0, transfer=1)   # 4 levels, SA (4/3)/lambda_max for u, PA for lambda
+# 4 levels, SA (4/3)/lambda_max for u, PA for lambda, three CheapSIMPLE(0.8) sweeps pre and post (the
+# smoothing of the paper's weak-scaling study on the same brick family, Sec. 6.2)
+OPTS = dict(levels_max=4, coarse_max_rows=0, transfer=1, smoother_sweeps=3)
 
 
 def parse():
@@ -44,6 +46,7 @@ def parse():
     ap.add_argument("--oracle-worker", default="", help=argparse.SUPPRESS)
     ap.add_argument("--workload", type=int, default=WORKLOAD,
                     help="workload of --profile-run (0 tiny, 1 medium, 2 large)")
+    ap.add_argument("--precisions", default="64,32", help="V-cycle precisions of --profile-run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -63,15 +66,20 @@ def max_over_ranks(x: float, world: int, device="cpu") -> float:
     return float(t.item())
 
 
-def vcycle_bytes(h, s: int) -> float:
-    """Algorithmic bytes of one V-cycle with storage size s (8: FP64 cycle, 4: FP32): every matrix
-    value and index streamed once per use and every vector once per kernel that touches it.
-    Per level: two K applies (residual, Jacobi predictor) with the B1 rows, three multiplier-row
-    passes (two Schur corrections and the residual), two B1 corrections, the zero-guess predictor,
-    restriction and prolongation; the coarsest level reads its dense FP64 inverse once."""
+def vcycle_bytes(h, s: int, sweeps: int = OPTS["smoother_sweeps"]) -> float:
+    """Algorithmic bytes of one V-cycle with storage size s (8: FP64 cycle, 4: FP32) and `sweeps`
+    CheapSIMPLE sweeps pre and post (one Jacobi sweep each): every matrix value and index streamed
+    once per use and every vector once per kernel that touches it.  Per level: the first
+    pre-sweep's Jacobi step from zero (f, D^-1 read, u written, lambda zeroed); 2 sweeps - 1 Jacobi
+    K applies with the B1 rows (x, lambda, f, D^-1 read, the new iterate written); one residual K
+    apply (x, lambda, f read, r written); 2 sweeps + 1 multiplier-row passes (B2 rows, Z, FP64
+    Schur-block inverses, g, lambda; lambda and the correction written); 2 sweeps B1 corrections
+    (B1 rows, the correction, A~^-1; the out-of-place ones also copy the iterate); restriction and
+    prolongation (P read once each, vectors once).  The coarsest level reads its FP64 inverse once."""
     st = h.stats()
     total = 0.0
     nlev = st["n_levels"]
+    S = max(int(sweeps), 1)
     for l in range(nlev):
         bu, nn, nl, n = st["dofs_per_node"][l], st["disp_nodes"][l], st["lm_nodes"][l], st["rows"][l]
         nu = bu * nn
@@ -82,12 +90,13 @@ def vcycle_bytes(h, s: int) -> float:
         b1 = h.export_size(l, "b1_col")
         b2 = h.export_size(l, "b2_col")
         pb = h.export_size(l, "p_col")
-        k_apply = kb * (bu * bu * s + 4) + b1 * (3 * bu * s + 4) + 8.0 * (nn + 1)
-        total += 2 * k_apply + (3 * nu + 3 * nl) * s + (5 * nu + 3 * nl) * s
-        total += 3 * (b2 * (3 * bu * s + 4) + nl * (9 * s + 72) + 4 * 3 * nl * s)
-        total += 2 * (b1 * (3 * bu * s + 4) + 2 * 3 * nl * s)
-        total += 3 * nu * s
-        total += 2 * (pb * (bu * 6 * s + 4)) + 3 * nu * s
+        k_mat = kb * (bu * bu * s + 4) + b1 * (3 * bu * s + 4) + 8.0 * (nn + 1)
+        total += (3 * nu + 3 * nl) * s                                   # Jacobi step from zero
+        total += (2 * S - 1) * (k_mat + (5 * nu + 3 * nl) * s)           # Jacobi K applies
+        total += k_mat + (4 * nu + 3 * nl) * s                           # residual K apply
+        total += (2 * S + 1) * (b2 * (3 * bu * s + 4) + nl * (9 * s + 72) + 4 * 3 * nl * s)
+        total += 2 * S * (b1 * (3 * bu * s + 4) + 2 * 3 * nl * s) + (2 * S - 1) * 2 * nu * s
+        total += 2 * (pb * (bu * 6 * s + 4)) + 3 * nu * s                # restriction, prolongation
     return total
 
 
@@ -524,7 +533,7 @@ def main_gpu(args):
             "config": {"workload": workload_name(), "step": "amgc_setup + amgc_solve (FP64 V-cycle) to 1e-8",
                        "rows": st["rows"][0], "levels": st["n_levels"], "level_rows": st["rows"],
                        "operator_complexity": round(st["operator_complexity"], 4),
-                       "transfer": "SA (4/3)/lambda_max for u, PA for lambda", "smoother": "CheapSIMPLE(0.8) x1",
+                       "transfer": "SA (4/3)/lambda_max for u, PA for lambda", "smoother": "CheapSIMPLE(0.8) x3 pre and post, 1 Jacobi sweep each",
                        "l2": "inputs larger than L2 (fine K blocks %.0f MB)" % (prob.K_val.nbytes / 1e6),
                        "parallelism": f"replicas x{world}"},
             "iters": iters[-1], "relres": relres[-1], "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
@@ -573,8 +582,8 @@ def main_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def profile_run(cfg: int):
-    """One FP64-cycle and one FP32-cycle setup + solve, nothing timed: the command ncu captures."""
+def profile_run(cfg: int, precisions=(64, 32)):
+    """One setup + solve per V-cycle precision (FP64, FP32), nothing timed: the command ncu captures."""
     import torch
 
     from paper_1912_09056_gb300 import amgc
@@ -582,7 +591,7 @@ def profile_run(cfg: int):
     prob = workload(cfg)
     opts = OPTS if cfg == WORKLOAD else dict(levels_max=10, coarse_max_rows=5000, transfer=1)
     b = torch.from_numpy(prob.rhs).cuda()
-    for precision in (64, 32):
+    for precision in precisions:
         h = amgc.setup(prob, amgc.default_options(precision=precision, **opts))
         x = torch.zeros_like(b)
         it, rr, _ = h.solve(b, x)
@@ -594,7 +603,7 @@ def profile_run(cfg: int):
 if __name__ == "__main__":
     a = parse()
     if a.profile_run:
-        profile_run(a.workload)
+        profile_run(a.workload, tuple(int(p) for p in a.precisions.split(",")))
     elif a.oracle_worker:
         print(json.dumps(oracle_worker(a.oracle_worker)))
     elif a.impl == "reference":

@@ -794,10 +794,20 @@ static int fork_join(amgc_hierarchy* h, FMain&& main_fn, FSide&& side_fn) {
 
 static int block_smooth(amgc_hierarchy* h, int l, const double* b, double* x, bool zero_guess);
 
+// `sweeps` CheapSIMPLE sweeps on [u; lambda] = x (Algorithm 4 in its cheap form), each: J damped
+// Jacobi steps on the displacements, the multiplier corrector dlam = -S_bd^-1 (g - B2 u_h + Z lam),
+// lam += alpha dlam, and u = u_h - alpha A~^-1 B1 dlam.  A Jacobi step reads its iterate at the
+// neighbours, so it writes the other of the two displacement buffers (u and the level's t); the
+// corrector and the B1 update then work in place on the buffer that holds the iterate.  From a zero
+// guess the first step needs no product and its buffer is chosen so that the last step ends in u;
+// from the iterate in u the steps alternate t, u, ..., and an odd count ends with one copy into u.
 template <class T>
-static int smooth(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, T* x, bool zero_guess) {
+static int smooth_sweeps(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, T* x, int sweeps, bool zero_guess) {
   if constexpr (sizeof(T) == 8) {
-    if (h->smoother_kind != 0) return block_smooth(h, l, b, x, zero_guess);
+    if (h->smoother_kind != 0) {
+      for (int k = 0; k < sweeps; ++k) AMGC_TRY(block_smooth(h, l, b, x, zero_guess && k == 0));
+      return AMGC_OK;
+    }
   }
   cudaStream_t s = h->stream;
   const int nu = L.nu();
@@ -808,44 +818,39 @@ static int smooth(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* b, T* x
   T* t = L.t;
   const int th = 256;
   const int J = h->opts.jacobi_sweeps;
-  // sweep j reads the iterate of sweep j-1 and writes the other buffer; from a zero guess the
-  // first sweep reads no iterate, and its buffer is chosen so that the last sweep ends in u
+  const int steps = sweeps * J;
+  const int gb = div_up((int64_t)L.n_b1_rows * 32, 128);
   T* cur = u;
-  for (int j = 0; j < J; ++j) {
-    if (zero_guess && j == 0) {
-      T* dst = (J % 2 == 1) ? u : t;
-      const int64_t nlam = 3 * (int64_t)L.nl;
-      AMGC_LAUNCH(k_jacobi_zero<T><<<div_up(std::max<int64_t>(nu, nlam), th), th, 0, s>>>(nu, nlam, f, L.dinv,
-                                                                                      (T)L.omega_j, dst, lam));
+  int step = 0;
+  for (int k = 0; k < sweeps; ++k) {
+    for (int j = 0; j < J; ++j, ++step) {
+      if (zero_guess && step == 0) {
+        T* dst = ((steps - 1) % 2 == 0) ? u : t;
+        const int64_t nlam = 3 * (int64_t)L.nl;
+        AMGC_LAUNCH(k_jacobi_zero<T><<<div_up(std::max<int64_t>(nu, nlam), th), th, 0, s>>>(nu, nlam, f, L.dinv,
+                                                                                        (T)L.omega_j, dst, lam));
+        AMGC_CUDA_TRY(cudaGetLastError());
+        cur = dst;
+      } else {
+        T* dst = cur == u ? t : u;
+        AMGC_TRY((k_apply<3, T>(h, L, l, cur, lam, f, cur, dst)));
+        cur = dst;
+      }
+    }
+    // corrector on the multipliers and the B1 update of the displacements, in place on cur
+    AMGC_TRY((lm_op<1, T>(L, cur, g, lam, h->opts.simple_alpha, L.dlam, s)));
+    if (L.n_b1_rows > 0) {
+      if (L.bu == 3)
+        AMGC_LAUNCH(k_b1_update<3, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
+                                                         L.atinv, (T)h->opts.simple_alpha, cur));
+      else
+        AMGC_LAUNCH(k_b1_update<6, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
+                                                         L.atinv, (T)h->opts.simple_alpha, cur));
       AMGC_CUDA_TRY(cudaGetLastError());
-      cur = dst;
-    } else {
-      T* dst = cur == u ? t : u;
-      AMGC_TRY((k_apply<3, T>(h, L, l, cur, lam, f, cur, dst)));
-      cur = dst;
     }
   }
-  T* uh = cur;   // u_half
-  // corrector on the multipliers: dlam = -S^-1 (g - B2 uh + Z lam), lam += alpha dlam
-  AMGC_TRY((lm_op<1, T>(L, uh, g, lam, h->opts.simple_alpha, L.dlam, s)));
-  // u = uh - alpha A~^-1 B1 dlam
-  const int gb = div_up((int64_t)L.n_b1_rows * 32, 128);
-  if (uh != u) {
-    const int nc = div_up(nu, 128);
-    if (L.bu == 3)
-      AMGC_LAUNCH(k_copy_b1<3, T><<<nc + gb, 128, 0, s>>>(nu, nc, uh, L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col,
-                                                          L.B1.val, L.dlam, L.atinv, (T)h->opts.simple_alpha, u));
-    else
-      AMGC_LAUNCH(k_copy_b1<6, T><<<nc + gb, 128, 0, s>>>(nu, nc, uh, L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col,
-                                                          L.B1.val, L.dlam, L.atinv, (T)h->opts.simple_alpha, u));
-    AMGC_CUDA_TRY(cudaGetLastError());
-  } else if (L.n_b1_rows > 0) {
-    if (L.bu == 3)
-      AMGC_LAUNCH(k_b1_update<3, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
-                                                       L.atinv, (T)h->opts.simple_alpha, u));
-    else
-      AMGC_LAUNCH(k_b1_update<6, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
-                                                       L.atinv, (T)h->opts.simple_alpha, u));
+  if (cur != u) {
+    AMGC_LAUNCH(k_copy<T><<<div_up(nu, th), th, 0, s>>>(nu, cur, u));
     AMGC_CUDA_TRY(cudaGetLastError());
   }
   return AMGC_OK;
@@ -1076,7 +1081,7 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
       AMGC_LAUNCH(k_zero<T><<<div_up(L.rows(), th), th, 0, s>>>(L.rows(), x));
       AMGC_CUDA_TRY(cudaGetLastError());
     }
-    for (int k = 0; k < sweeps; ++k) AMGC_TRY(smooth<T>(h, L, l, b, x, k == 0));
+    AMGC_TRY(smooth_sweeps<T>(h, L, l, b, x, sweeps, true));
     return AMGC_OK;
   }
   if (l == (int)V.size() - 1) {
@@ -1096,7 +1101,7 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
     AMGC_LAUNCH(k_zero<T><<<div_up(L.rows(), th), th, 0, s>>>(L.rows(), x));
     AMGC_CUDA_TRY(cudaGetLastError());
   }
-  for (int k = 0; k < sweeps; ++k) AMGC_TRY(smooth<T>(h, L, l, b, x, k == 0));
+  AMGC_TRY(smooth_sweeps<T>(h, L, l, b, x, sweeps, true));
   AMGC_TRY(residual<T>(h, L, l, b, x, L.r));
   // restrict: C.b = [R r_u ; R^lambda r_lambda] (the multiplier part beside the displacement part)
   AMGC_TRY(fork_join(
@@ -1120,7 +1125,7 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
         }
         return AMGC_OK;
       }));
-  for (int k = 0; k < sweeps; ++k) AMGC_TRY(smooth<T>(h, L, l, b, x, false));
+  AMGC_TRY(smooth_sweeps<T>(h, L, l, b, x, sweeps, false));
   return AMGC_OK;
 }
 

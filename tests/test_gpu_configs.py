@@ -49,7 +49,7 @@ def _check_aggregates(h, prob):
 
 def test_large_fp32_and_fp64_cycles_reach_the_tolerance_and_agree(large_problem):
     prob = large_problem
-    opts = dict(levels_max=4, coarse_max_rows=0, transfer=1)
+    opts = dict(levels_max=4, coarse_max_rows=0, transfer=1, smoother_sweeps=3)
     b = _cuda(prob.rhs)
     xs, its = {}, {}
     for precision in (64, 32):

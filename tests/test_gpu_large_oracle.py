@@ -1,4 +1,5 @@
-"""The large workload (3.47 M rows, 4 smoothed-aggregation levels) against the FP64 oracle:
+"""The large workload (3.47 M rows, 4 smoothed-aggregation levels, three CheapSIMPLE sweeps: the
+bench's configuration) against the FP64 oracle:
 aggregates, multiplier aggregates and every sparsity pattern bit for bit on all levels, transfers,
 coarse operators and smoother data within 1e-10, one FP64 V-cycle within 1e-10, and the solutions
 of the FP64-cycle and FP32-cycle solves against the oracle's FGMRES solution (all three meet the
@@ -15,7 +16,7 @@ from oracle.krylov import fgmres  # noqa: E402
 from paper_1912_09056_gb300 import amgc  # noqa: E402
 from test_gpu_parity import RTOL, compare_hierarchy, vcycle_and_apply  # noqa: E402
 
-OPTS = dict(levels_max=4, coarse_max_rows=0, transfer=1)
+OPTS = dict(levels_max=4, coarse_max_rows=0, transfer=1, smoother_sweeps=3)   # the bench configuration
 
 
 def test_large_workload_matches_the_oracle(large_problem):
