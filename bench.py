@@ -264,16 +264,20 @@ def _peaks() -> dict:
         return {}
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu capture of the
-# medium workload scaled to this workload by its block count (the kernel streams every block
-# once), keyed by the hash of the kernel source they were measured on: null once it has changed.
+# DRAM bytes (read + write) per launch of the dominant kernel, from an ncu capture of the medium
+# workload's FP64 residual launches scaled to this workload by its block count (the kernel streams
+# every block once), keyed by the hash of the kernel's source section (the SELL-32 apply of
+# cycle.cu) it was measured on: null once that source has changed.
 NCU_TRAFFIC = {"source_sha16": None, "bytes_per_block": None}
 
 
 def _kernel_source_sha16() -> str:
     import hashlib
-    with open(os.path.join(ROOT, "paper_1912_09056_gb300", "csrc", "cycle.cu"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    with open(os.path.join(ROOT, "paper_1912_09056_gb300", "csrc", "cycle.cu")) as fh:
+        src = fh.read()
+    a = src.index("// ------------------------------------------------------------------ SELL-32 row apply")
+    b = src.index("// ---------------------------------------------------------------- TMA-staged FP32 fine-level apply")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def main_gpu(args):

@@ -10,7 +10,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "lib", "libamgc.so")
-SOURCES = ["api.cu", "scan.cu", "cycle.cu", "setup.cu", "krylov.cu", "grad.cu", "batch.cu", "noalloc.cu", "contact.cu", "blocksmooth.cu"]
+SOURCES = ["api.cu", "scan.cu", "cycle.cu", "setup.cu", "krylov.cu", "grad.cu", "batch.cu", "noalloc.cu", "contact.cu", "blocksmooth.cu", "batch_cycle.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -12,6 +12,9 @@
 
 namespace amgc {
 
+struct McState;                 // work buffers of the multi-column cycle (batch_cycle.cu)
+constexpr int kMcCols = 4;      // right-hand sides per multi-column cycle
+
 // ------------------------------------------------------------------ error handling
 void set_error(const std::string& msg);
 // Source location of the first launch in this thread that left a launch error, if any since the
@@ -70,6 +73,8 @@ struct StreamScope {
 };
 int pool_alloc(void** p, size_t bytes);
 void pool_free(void* p);
+// true when buffers freed now are ordered on stream s (s is the stream of the entry point in progress)
+bool allocations_ordered_on(cudaStream_t s);
 
 // Owning device buffer; the hierarchy keeps these alive.
 template <class T>
@@ -314,6 +319,7 @@ struct amgc_hierarchy {
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   amgc::DBuf<double> cyc_in, cyc_out;      // fixed FP64 input/output of the captured FP64 cycle
   // batched FGMRES workspace
+  amgc::McState* mc = nullptr;     // multi-column cycle buffers (created on first use)
   amgc::DBuf<int> b_chunk_row0, b_chunk_row1, b_chunk_ptr, b_row_inst;
   int b_nchunk = 0;
   double* h_pinned = nullptr;      // pinned host scalars
@@ -452,6 +458,10 @@ int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y);
 int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol, int* iters, double* relres);
 // batched problems (batch.cu)
 int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, int* iters, double* relres);
+// kMcCols columns at once (column stride rows[0], FP64 in and out): V-cycle, saddle apply (batch_cycle.cu)
+int precond_apply_cols(amgc_hierarchy* h, const double* r, double* z);
+int saddle_apply_cols(amgc_hierarchy* h, const double* x, double* y);
+void mc_state_free(McState* st);
 // gradients (grad.cu)
 int grad_scatter(amgc_hierarchy* h, const double* adj, const double* x, double* gK, double* gB1, double* gB2);
 // the element-gradient kernels with caller-provided scratch `lift` (3 ne doubles, used when gt != 0),

@@ -64,6 +64,7 @@ int pool_alloc(void** p, size_t bytes) {
 }
 
 void pool_free(void* p) { cudaFreeAsync(p, g_alloc_stream); }
+bool allocations_ordered_on(cudaStream_t s) { return s == g_alloc_stream; }
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 static thread_local std::string g_launch_site;
@@ -667,6 +668,7 @@ void amgc_destroy(struct amgc_hierarchy* h) {
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->join_ev) cudaEventDestroy(h->join_ev);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  mc_state_free(h->mc);
   delete h;
 }
 

@@ -246,8 +246,15 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
     AMGC_CUDA_TRY(cudaGetLastError());
     return AMGC_OK;
   };
+  // groups of kMcCols right-hand sides go through the multi-column cycle and operator apply (each
+  // matrix block read once per group), the rest one column at a time
   auto apply_cols = [&](bool precond, const double* in, double* out) -> int {
-    for (int r = 0; r < nrhs; ++r) {
+    int r = 0;
+    for (; r + kMcCols <= nrhs; r += kMcCols) {
+      if (precond) AMGC_TRY(precond_apply_cols(h, in + r * n, out + r * n));
+      else AMGC_TRY(saddle_apply_cols(h, in + r * n, out + r * n));
+    }
+    for (; r < nrhs; ++r) {
       if (precond) AMGC_TRY(precond_apply(h, in + r * n, out + r * n));
       else AMGC_TRY(saddle_apply(h, 0, in + r * n, out + r * n));
     }

@@ -74,26 +74,37 @@ int scan_rec(const int* in, int* out, int n, cudaStream_t s) {
   AMGC_TRY(scan_rec(sums.p, offs.p, tiles, s));
   AMGC_LAUNCH(add_tile_offsets<<<tiles, kScanThreads, 0, s>>>(out, offs.p, n));
   AMGC_CUDA_TRY(cudaGetLastError());
-  AMGC_CUDA_TRY(cudaStreamSynchronize(s));   // sums/offs are freed on return
+  // sums / offs go back to the pool on return, ordered on the allocation stream: wait only if the
+  // scan ran on another stream
+  if (!allocations_ordered_on(s)) AMGC_CUDA_TRY(cudaStreamSynchronize(s));
   return AMGC_OK;
+}
+
+__global__ void k_scan_total(const int* __restrict__ last_out, int* __restrict__ t) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) t[1] = last_out[0] + t[0];
 }
 
 }  // namespace
 
 // out[i] = sum_{k<i} in[k]; *total_host (optional) = sum of all inputs.  in may equal out.
+// The total is formed on the device (the last input is saved before the scan, since in may equal
+// out) and read back with one synchronisation.
 int exclusive_scan(const int* in, int* out, int n, cudaStream_t s, int* total_host) {
-  int last_in = 0;
-  if (total_host && n > 0) AMGC_CUDA_TRY(cudaMemcpyAsync(&last_in, in + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  if (total_host && n > 0) AMGC_CUDA_TRY(cudaStreamSynchronize(s));
-  AMGC_TRY(scan_rec(in, out, n, s));
-  if (total_host) {
-    int last_out = 0;
-    if (n > 0) {
-      AMGC_CUDA_TRY(cudaMemcpyAsync(&last_out, out + n - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-      AMGC_CUDA_TRY(cudaStreamSynchronize(s));
-    }
-    *total_host = n > 0 ? last_out + last_in : 0;
+  if (!total_host) return scan_rec(in, out, n, s);
+  if (n <= 0) {
+    *total_host = 0;
+    return AMGC_OK;
   }
+  DBuf<int> t;
+  AMGC_TRY(t.alloc(2));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(t.p, in + n - 1, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  AMGC_TRY(scan_rec(in, out, n, s));
+  AMGC_LAUNCH(k_scan_total<<<1, 32, 0, s>>>(out + n - 1, t.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  int tot = 0;
+  AMGC_CUDA_TRY(cudaMemcpyAsync(&tot, t.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  *total_host = tot;
   return AMGC_OK;
 }
 
