@@ -285,13 +285,17 @@ int amgc_pdass(struct amgc_hierarchy* h, const double* f, const double* g0, doub
 
 /* Adjoint calls (transposed system).  The first one builds, once, the transposed data of every
  * level (B1^T, B2^T, blockwise transposes of Z and of the Schur-block inverses, the transposed
- * coarsest inverse).  They need jacobi_sweeps == 1 (AMGC_EINVAL otherwise) and run in FP64.
+ * coarsest inverse).  They run in FP64, with the coupled V-cycle and CheapSIMPLE smoothing
+ * (AMGC_EINVAL after amgc_set_smoother or amgc_set_preconditioner chose another kind, for a
+ * batched hierarchy, or with coarse_solver 1).
  *
  * amgc_apply_transposed:  y = A^T x.
  * amgc_vcycle_transposed: z = M^T r, M the V-cycle of amgc_vcycle.  Since K is symmetric, M^T
  *   is the V-cycle on A^T with each CheapSIMPLE sweep transposed (multiplier update
- *   w = -alpha S^-T (e_lambda - B1^T A~^-1 e_u) first, then u += omega D^-1 (e_u - B2^T w)),
- *   unchanged transfers and the transposed coarsest inverse, so <M x, y> = <x, M^T y>.
+ *   w = -alpha S^-T (e_lambda - B1^T A~^-1 e_u) first, then u += J^T (e_u - B2^T w) with J the
+ *   predictor's jacobi_sweeps damped Jacobi steps in residual form,
+ *   J^T = sum_{i<jacobi_sweeps} omega D^-1 (I - omega K D^-1)^i), unchanged transfers and the
+ *   transposed coarsest inverse, so <M x, y> = <x, M^T y>.
  * amgc_solve_transposed:  FGMRES on A^T x = rhs preconditioned by M^T, stopped at
  *   ||r_k|| / ||r_0|| < tol (tol <= 0: the setup tolerance).  Device vectors, as amgc_solve. */
 int amgc_apply_transposed(struct amgc_hierarchy* h, const double* x, double* y, void* stream);

@@ -195,6 +195,7 @@ struct LevelV {
   T* r = nullptr;
   T* t = nullptr;
   T* dlam = nullptr;
+  T* tsw = nullptr;     // transposed sweep with several Jacobi steps: two work vectors of nu
 };
 
 // One level of the hierarchy.
@@ -258,6 +259,7 @@ struct Level {
   DBuf<double> ZT, SinvT, AinvT;
   DBuf<int> b2t_rows;
   int n_b2t_rows = 0;
+  DBuf<double> tsw;          // 2 nu: work vectors of the transposed multi-step Jacobi predictor
   bool has_transposed = false;
 
   // interface data of the finest level, kept for active-set updates: D, M (CSR over slave rows),

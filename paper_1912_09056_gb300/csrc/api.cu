@@ -481,10 +481,6 @@ static int enter_transposed(amgc_hierarchy* h, void* stream, const char* where) 
     set_error(std::string(where) + ": invalid argument");
     return AMGC_EINVAL;
   }
-  if (h->opts.jacobi_sweeps != 1) {
-    set_error(std::string(where) + ": the transposed cycle needs jacobi_sweeps == 1");
-    return AMGC_EINVAL;
-  }
   if (h->n_inst > 1) {
     set_error(std::string(where) + ": not available for batched hierarchies");
     return AMGC_EINVAL;

@@ -1133,10 +1133,12 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
 // The cycle operator is M = (I - Q A) [Q + P M_c R (I - A Q)] + Q for one sweep each side, Q the
 // CheapSIMPLE sweep operator; its transpose is the same V-cycle on A^T with the sweep Q^T, the
 // transfers R = P^T and P unchanged, and the transposed coarsest inverse.  From the residual
-// e = y - A^T x of a transposed sweep (one Jacobi predictor sweep):
+// e = y - A^T x of a transposed sweep:
 //   w   = -alpha S^-T (e_lambda - B1^T A~^-1 e_u),  lambda += w
-//   u  += omega D^-1 (e_u - B2^T w)
-// (the order of the multiplier and displacement updates is reversed with respect to Q).
+//   u  += J_k^T (e_u - B2^T w)
+// with J_k = sum_{i<k} (I - omega D^-1 K)^i omega D^-1 the k-step Jacobi predictor in residual form
+// (J_1 = omega D^-1); the order of the multiplier and displacement updates is reversed with
+// respect to Q.
 
 // w_l = -alpha S^-T_l (e_l - sum_i B1T[l,i] (atinv_i e_u,i)); lam_l += w_l; out_l = w_l
 template <int BU>
@@ -1179,6 +1181,16 @@ __global__ void k_axpy_dinv(int64_t n, const double* __restrict__ e, const doubl
   if (i < n) u[i] += omega * dinv[i] * e[i];
 }
 
+// s = omega D^-1 v (the folded Jacobi diagonal), u += s
+__global__ void k_tjacobi_step(int64_t n, const double* __restrict__ v, const double* __restrict__ jdinv,
+                               double* __restrict__ sv, double* __restrict__ u) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double si = jdinv[i] * v[i];
+  sv[i] = si;
+  u[i] += si;
+}
+
 template <class T>
 static int tsmooth(amgc_hierarchy* h, const LevelV<double>& L, int l, const double* y, double* x, bool zero_guess) {
   cudaStream_t s = h->stream;
@@ -1200,6 +1212,25 @@ static int tsmooth(amgc_hierarchy* h, const LevelV<double>& L, int l, const doub
     else
       AMGC_LAUNCH(k_lm_tsweep<6><<<gl, 128, 0, s>>>(L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
                                                     h->opts.simple_alpha, x + nu, L.dlam));
+  }
+  const int J = h->opts.jacobi_sweeps;
+  if (J > 1) {
+    // u += J_k^T (e_u - B2^T w), J_k^T = sum_{i<k} omega D^-1 (I - omega K D^-1)^i (K symmetric):
+    // v = e_u - B2^T w; then k times: s = omega D^-1 v, u += s, v <- v - K s (the last skipped)
+    double* v = L.t;
+    double* sv = L.tsw;
+    double* vn = L.tsw + nu;
+    if (L.nl > 0) AMGC_TRY((rowop<2, double>(L.B2T, L.dlam, nullptr, nullptr, e, nullptr, nullptr, 0.0, v, s)));
+    else AMGC_LAUNCH(k_copy<double><<<div_up(nu, th), th, 0, s>>>(nu, e, v));
+    for (int i = 0; i < J; ++i) {
+      AMGC_LAUNCH(k_tjacobi_step<<<div_up(nu, th), th, 0, s>>>(nu, v, L.dinv, sv, x));
+      if (i + 1 < J) {
+        AMGC_TRY((mapped_apply<2, double>(L.K, L.Ks, L.kmap, nullptr, sv, nullptr, v, nullptr, nullptr, 0.0, vn, s)));
+        std::swap(v, vn);
+      }
+    }
+    AMGC_CUDA_TRY(cudaGetLastError());
+    return AMGC_OK;
   }
   AMGC_LAUNCH(k_axpy_dinv<<<div_up(nu, th), th, 0, s>>>(nu, e, L.dinv, L.omega_j, x));
   if (L.n_b2t_rows > 0) {
@@ -1584,7 +1615,7 @@ int make_views(amgc_hierarchy* h) {
     v.Rs = sview<double>(L.Rs, L.Rs.val.p);
     v.kmap = L.kmap[0]; v.pmap = L.pmap[0]; v.rmap = L.rmap[0];
     v.Z = L.Z.p; v.dinv = L.jdinv.p; v.atinv = L.atinv.p; v.pl_w = L.pl_w.p;
-    v.x = L.x.p; v.b = L.b.p; v.r = L.r.p; v.t = L.t.p; v.dlam = L.dlam.p;
+    v.x = L.x.p; v.b = L.b.p; v.r = L.r.p; v.t = L.t.p; v.dlam = L.dlam.p; v.tsw = L.tsw.p;
     if (L.has_transposed) {
       v.B1T = bview<double>(L.B1T, L.B1T.val.p);
       v.B2T = bview<double>(L.B2T, L.B2T.val.p);

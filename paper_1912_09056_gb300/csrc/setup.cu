@@ -1957,6 +1957,7 @@ int transposed_setup(amgc_hierarchy* h) {
       int cnt = 0;
       AMGC_TRY(exclusive_scan(flag.p, flag.p, L.nn, s, &cnt));
       L.n_b2t_rows = cnt;
+      if (h->opts.jacobi_sweeps > 1) AMGC_TRY(L.tsw.alloc((size_t)2 * std::max(L.nu(), 1)));
       AMGC_TRY(L.b2t_rows.alloc(std::max(cnt, 1)));
       AMGC_LAUNCH(k_compact<<<div_up(L.nn, 256), 256, 0, s>>>(L.nn, L.B2T.rowptr.p, flag.p, L.b2t_rows.p));
     } else {

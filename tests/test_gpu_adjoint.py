@@ -24,7 +24,10 @@ def _cuda(a):
 
 @pytest.mark.parametrize("opts", [dict(levels_max=3, coarse_max_rows=0, transfer=0),
                                   dict(levels_max=3, coarse_max_rows=0, transfer=1, smoother_sweeps=2),
-                                  dict(levels_max=4, coarse_max_rows=200, transfer=1)])
+                                  dict(levels_max=4, coarse_max_rows=200, transfer=1),
+                                  dict(levels_max=3, coarse_max_rows=0, transfer=1, jacobi_sweeps=2),
+                                  dict(levels_max=3, coarse_max_rows=0, transfer=0, smoother_sweeps=2,
+                                       jacobi_sweeps=3)])
 def test_transposed_cycle_and_apply(opts):
     prob = two_block_problem(**SMALL)
     h = amgc.setup(prob, **opts)
@@ -161,12 +164,15 @@ def test_autograd_function_matches_finite_differences():
     assert abs(fdb - anb) <= 1e-6 * abs(anb), (fdb, anb)
 
 
-def test_transposed_cycle_rejects_multiple_jacobi_sweeps():
+def test_transposed_cycle_refuses_other_smoothers_and_preconditioners():
     prob = workload(0)
-    h = amgc.setup(prob, levels_max=3, coarse_max_rows=0, jacobi_sweeps=2)
+    h = amgc.setup(prob, levels_max=3, coarse_max_rows=0)
     r = _cuda(np.ones(prob.n))
     z = torch.empty_like(r)
+    h.set_smoother("uzawa")
     with pytest.raises(amgc.AmgcError) as e:
         h.vcycle_transposed(r, z)
     assert e.value.code == amgc.AMGC_EINVAL
+    h.set_smoother("cheap_simple")
+    h.vcycle_transposed(r, z)
     h.close()
