@@ -322,7 +322,7 @@ struct amgc_hierarchy {
   amgc::DBuf<double> cyc_in, cyc_out;      // fixed FP64 input/output of the captured FP64 cycle
   // batched FGMRES workspace
   amgc::McState* mc = nullptr;     // multi-column cycle buffers (created on first use)
-  amgc::DBuf<int> b_chunk_row0, b_chunk_row1, b_chunk_ptr, b_row_inst;
+  amgc::DBuf<int> b_chunk_row0, b_chunk_row1, b_chunk_ptr, b_chunk_inst, b_row_inst;
   int b_nchunk = 0;
   double* h_pinned = nullptr;      // pinned host scalars
   // level smoother: 0 CheapSIMPLE, 1 Uzawa, 2 Braess-Sarazin, 3 SIMPLE with an SGS predictor
@@ -460,9 +460,10 @@ int saddle_apply(amgc_hierarchy* h, int l, const double* x, double* y);
 int fgmres(amgc_hierarchy* h, const double* rhs, double* x, double tol, int* iters, double* relres);
 // batched problems (batch.cu)
 int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, int* iters, double* relres);
-// kMcCols columns at once (column stride rows[0], FP64 in and out): V-cycle, saddle apply (batch_cycle.cu)
-int precond_apply_cols(amgc_hierarchy* h, const double* r, double* z);
-int saddle_apply_cols(amgc_hierarchy* h, const double* x, double* y);
+// kMcCols columns at once (column stride rows[0], FP64 in and out): V-cycle, saddle apply
+// (batch_cycle.cu); rows of instances q with live[q] == 0 are skipped when live (device) is given
+int precond_apply_cols(amgc_hierarchy* h, const double* r, double* z, const int* live);
+int saddle_apply_cols(amgc_hierarchy* h, const double* x, double* y, const int* live);
 void mc_state_free(McState* st);
 // gradients (grad.cu)
 int grad_scatter(amgc_hierarchy* h, const double* adj, const double* x, double* gK, double* gB1, double* gB2);

@@ -17,8 +17,10 @@ constexpr int kBThreads = 256;
 // part[(k * nrhs + r) * nchunk + c] = sum over chunk c of V[k][r][i] * w[r][i]
 __global__ void __launch_bounds__(kBThreads)
 k_bmultidot(int nchunk, const int* __restrict__ row0, const int* __restrict__ row1, int nrhs, int64_t n, int nk,
-            const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ part) {
+            const double* __restrict__ V, const double* __restrict__ w, double* __restrict__ part,
+            const int* __restrict__ chunk_inst, const int* __restrict__ live) {
   const int c = blockIdx.x, r = blockIdx.y;
+  if (live && !live[chunk_inst[c]]) return;   // a finished instance: its sums are not read
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t b0 = row0[c], b1 = row1[c];
   const double* wr = w + (int64_t)r * n;
@@ -51,11 +53,13 @@ __global__ void k_bmultidot_final(int nk, int ni, int nrhs, int nchunk, const in
 }
 // w[r][i] -= sum_k V[k][r][i] hk[sys][k], sys = (instance of row i, r)
 __global__ void k_bbasis_update(int64_t n, int nrhs, int nk, const double* __restrict__ V, const double* __restrict__ hk,
-                                int ldh, const int* __restrict__ row_inst, double* __restrict__ w) {
+                                int ldh, const int* __restrict__ row_inst, double* __restrict__ w,
+                                const int* __restrict__ live) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * nrhs) return;
   const int r = (int)(t / n);
   const int64_t i = t - (int64_t)r * n;
+  if (live && !live[row_inst[i]]) return;
   const int sys = row_inst[i] * nrhs + r;
   const double* h = hk + (int64_t)sys * ldh;
   double s = w[t];
@@ -71,11 +75,12 @@ __global__ void k_brsqrt(int nsys, const double* __restrict__ nrm2, double* __re
 }
 // v = w / sqrt(nrm2[sys]) with inv = k_brsqrt(nrm2) (0 on breakdown)
 __global__ void k_bnormalize(int64_t n, int nrhs, const int* __restrict__ row_inst, const double* __restrict__ inv,
-                             const double* __restrict__ w, double* __restrict__ v) {
+                             const double* __restrict__ w, double* __restrict__ v, const int* __restrict__ live) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * nrhs) return;
   const int r = (int)(t / n);
   const int64_t i = t - (int64_t)r * n;
+  if (live && !live[row_inst[i]]) return;
   v[t] = w[t] * inv[row_inst[i] * nrhs + r];
 }
 // H[sys][j+1][j] = sqrt(nrm2[sys])
@@ -134,17 +139,20 @@ __global__ void k_bbacksolve(int nsys, int m, const double* __restrict__ H, cons
     ys[i] = s / Hs[i * m + i];
   }
 }
-// x[r][i] += sum_{k < nk} Zs[k][r][i] y[sys][k]
+// x[r][i] += sum_{k < jd[sys]} Zs[k][r][i] y[sys][k]: only the columns the system's own Krylov space
+// holds (the later columns of a finished instance were never written)
 __global__ void k_bsolution_update(int64_t n, int nrhs, int nk, const double* __restrict__ Zs,
                                    const double* __restrict__ y, int ldy, const int* __restrict__ row_inst,
-                                   double* __restrict__ x) {
+                                   const int* __restrict__ jd, double* __restrict__ x) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * nrhs) return;
   const int r = (int)(t / n);
   const int64_t i = t - (int64_t)r * n;
-  const double* ys = y + (int64_t)(row_inst[i] * nrhs + r) * ldy;
+  const int sys = row_inst[i] * nrhs + r;
+  const double* ys = y + (int64_t)sys * ldy;
+  const int kk = min(nk, jd[sys]);
   double s = x[t];
-  for (int k = 0; k < nk; ++k) s = fma(Zs[((int64_t)k * nrhs + r) * n + i], ys[k], s);
+  for (int k = 0; k < kk; ++k) s = fma(Zs[((int64_t)k * nrhs + r) * n + i], ys[k], s);
   x[t] = s;
 }
 // start of a cycle for the live systems: v0 = r / beta with inv = k_brsqrt(beta^2)
@@ -162,6 +170,14 @@ __global__ void k_bgvec(int nsys, int m, const double* __restrict__ nrm2, double
   g[(int64_t)sys * (m + 1)] = sqrt(nrm2[sys]);
   for (int k = 1; k <= m; ++k) g[(int64_t)sys * (m + 1) + k] = 0.0;
   jd[sys] = 0;
+}
+// live[q] = some system of instance q is still iterating
+__global__ void k_binst_live(int ni, int nrhs, const int* __restrict__ done, int* __restrict__ live) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ni) return;
+  int a = 0;
+  for (int r = 0; r < nrhs; ++r) a |= done[q * nrhs + r] == 0;
+  live[q] = a;
 }
 __global__ void k_bsub(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -192,12 +208,17 @@ static int batch_tables(amgc_hierarchy* h) {
   AMGC_TRY(h->b_chunk_row0.alloc(nc));
   AMGC_TRY(h->b_chunk_row1.alloc(nc));
   AMGC_TRY(h->b_chunk_ptr.alloc(ni + 1));
+  AMGC_TRY(h->b_chunk_inst.alloc(nc));
   AMGC_TRY(h->b_row_inst.alloc(n));
+  std::vector<int> cinst(nc, 0);
+  for (int q = 0; q < ni; ++q)
+    for (int c = cptr[q]; c < cptr[q + 1]; ++c) cinst[c] = q;
   cudaStream_t s = h->stream;
   AMGC_CUDA_TRY(cudaMemcpyAsync(h->b_chunk_row0.p, r0.data(), nc * sizeof(int), cudaMemcpyHostToDevice, s));
   AMGC_CUDA_TRY(cudaMemcpyAsync(h->b_chunk_row1.p, r1.data(), nc * sizeof(int), cudaMemcpyHostToDevice, s));
   AMGC_CUDA_TRY(cudaMemcpyAsync(h->b_chunk_ptr.p, cptr.data(), (ni + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   AMGC_CUDA_TRY(cudaMemcpyAsync(h->b_row_inst.p, inst.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_CUDA_TRY(cudaMemcpyAsync(h->b_chunk_inst.p, cinst.data(), nc * sizeof(int), cudaMemcpyHostToDevice, s));
   AMGC_CUDA_TRY(cudaStreamSynchronize(s));
   h->b_nchunk = nc;
   return AMGC_OK;
@@ -218,7 +239,7 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
   const int gv = div_up(nv, th);
   const int gs = div_up(nsys, 128);
   DBuf<double> V, Zs, H, cs, sn, g, y, hk, part, nrm2, beta0, rv, rinv;
-  DBuf<int> done, jd, it, cnt;
+  DBuf<int> done, jd, it, cnt, ilive;
   AMGC_TRY(V.alloc((size_t)(m + 1) * nv));
   AMGC_TRY(Zs.alloc((size_t)m * nv));
   AMGC_TRY(H.alloc((size_t)nsys * (m + 1) * m));
@@ -236,11 +257,13 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
   AMGC_TRY(jd.alloc(nsys));
   AMGC_TRY(it.alloc(nsys));
   AMGC_TRY(cnt.alloc(2));
+  AMGC_TRY(ilive.alloc(ni));
   const int* ri = h->b_row_inst.p;
   // segmented squared norms of the nrhs columns of a -> out[sys]
-  auto segnorm2 = [&](const double* a, double* out) -> int {
+  // lv: the instance flags (rows of finished instances skipped), or null for every row
+  auto segnorm2 = [&](const double* a, double* out, const int* lv) -> int {
     AMGC_LAUNCH(k_bmultidot<<<dim3(nc, nrhs), kBThreads, 0, s>>>(nc, h->b_chunk_row0.p, h->b_chunk_row1.p, nrhs, n, 1,
-                                                                 a, a, part.p));
+                                                                 a, a, part.p, h->b_chunk_inst.p, lv));
     AMGC_LAUNCH(k_bmultidot_final<<<div_up((int64_t)nsys * 32, 128), 128, 0, s>>>(
         1, ni, nrhs, nc, h->b_chunk_ptr.p, part.p, out, 1, 0, 0, nullptr, 0));
     AMGC_CUDA_TRY(cudaGetLastError());
@@ -248,11 +271,11 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
   };
   // groups of kMcCols right-hand sides go through the multi-column cycle and operator apply (each
   // matrix block read once per group), the rest one column at a time
-  auto apply_cols = [&](bool precond, const double* in, double* out) -> int {
+  auto apply_cols = [&](bool precond, const double* in, double* out, const int* lv) -> int {
     int r = 0;
     for (; r + kMcCols <= nrhs; r += kMcCols) {
-      if (precond) AMGC_TRY(precond_apply_cols(h, in + r * n, out + r * n));
-      else AMGC_TRY(saddle_apply_cols(h, in + r * n, out + r * n));
+      if (precond) AMGC_TRY(precond_apply_cols(h, in + r * n, out + r * n, lv));
+      else AMGC_TRY(saddle_apply_cols(h, in + r * n, out + r * n, lv));
     }
     for (; r < nrhs; ++r) {
       if (precond) AMGC_TRY(precond_apply(h, in + r * n, out + r * n));
@@ -262,7 +285,7 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
   };
   AMGC_CUDA_TRY(cudaMemsetAsync(x, 0, nv * sizeof(double), s));
   AMGC_CUDA_TRY(cudaMemsetAsync(it.p, 0, nsys * sizeof(int), s));
-  AMGC_TRY(segnorm2(rhs, nrm2.p));
+  AMGC_TRY(segnorm2(rhs, nrm2.p, nullptr));
   std::vector<double> hb(nsys);
   AMGC_CUDA_TRY(cudaMemcpyAsync(hb.data(), nrm2.p, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));
   AMGC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -277,12 +300,13 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
   }
   AMGC_CUDA_TRY(cudaMemcpyAsync(beta0.p, hb.data(), nsys * sizeof(double), cudaMemcpyHostToDevice, s));
   AMGC_CUDA_TRY(cudaMemcpyAsync(done.p, hdone.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, s));
+  AMGC_LAUNCH(k_binst_live<<<div_up(ni, 128), 128, 0, s>>>(ni, nrhs, done.p, ilive.p));
   AMGC_CUDA_TRY(cudaMemcpyAsync(rv.p, rhs, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
   int total = 0, live = 0;
   for (int q = 0; q < nsys; ++q) live += hdone[q] == 0;
   while (total < maxit && live > 0) {
     // cycle start on the current residual rv
-    AMGC_TRY(segnorm2(rv.p, nrm2.p));
+    AMGC_TRY(segnorm2(rv.p, nrm2.p, nullptr));
     AMGC_LAUNCH(k_brsqrt<<<gs, 128, 0, s>>>(nsys, nrm2.p, rinv.p));
     AMGC_LAUNCH(k_bcycle_start<<<gv, th, 0, s>>>(n, nrhs, ri, rinv.p, rv.p, V.p));
     AMGC_LAUNCH(k_bgvec<<<gs, 128, 0, s>>>(nsys, m, nrm2.p, g.p, jd.p));
@@ -292,23 +316,24 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
       double* vj = V.p + (int64_t)j * nv;
       double* zj = Zs.p + (int64_t)j * nv;
       double* w = V.p + (int64_t)(j + 1) * nv;
-      AMGC_TRY(apply_cols(true, vj, zj));
-      AMGC_TRY(apply_cols(false, zj, w));
+      AMGC_TRY(apply_cols(true, vj, zj, ilive.p));
+      AMGC_TRY(apply_cols(false, zj, w, ilive.p));
       for (int pass = 0; pass < 2; ++pass) {
         AMGC_LAUNCH(k_bmultidot<<<dim3(nc, nrhs), kBThreads, 0, s>>>(nc, h->b_chunk_row0.p, h->b_chunk_row1.p, nrhs, n,
-                                                                     j + 1, V.p, w, part.p));
+                                                                     j + 1, V.p, w, part.p, h->b_chunk_inst.p, ilive.p));
         AMGC_LAUNCH(k_bmultidot_final<<<div_up((int64_t)(j + 1) * nsys * 32, 128), 128, 0, s>>>(
             j + 1, ni, nrhs, nc, h->b_chunk_ptr.p, part.p, H.p + j, (int64_t)(m + 1) * m, m, pass, hk.p, m + 1));
-        AMGC_LAUNCH(k_bbasis_update<<<gv, th, 0, s>>>(n, nrhs, j + 1, V.p, hk.p, m + 1, ri, w));
+        AMGC_LAUNCH(k_bbasis_update<<<gv, th, 0, s>>>(n, nrhs, j + 1, V.p, hk.p, m + 1, ri, w, ilive.p));
       }
-      AMGC_TRY(segnorm2(w, nrm2.p));
+      AMGC_TRY(segnorm2(w, nrm2.p, ilive.p));
       AMGC_LAUNCH(k_bsubdiag<<<gs, 128, 0, s>>>(nsys, j, m, nrm2.p, H.p));
       AMGC_LAUNCH(k_brsqrt<<<gs, 128, 0, s>>>(nsys, nrm2.p, rinv.p));
-      AMGC_LAUNCH(k_bnormalize<<<gv, th, 0, s>>>(n, nrhs, ri, rinv.p, w, w));
+      AMGC_LAUNCH(k_bnormalize<<<gv, th, 0, s>>>(n, nrhs, ri, rinv.p, w, w, ilive.p));
       ++total;
       AMGC_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int), s));
       AMGC_LAUNCH(k_bgivens<<<gs, 128, 0, s>>>(nsys, j, m, H.p, cs.p, sn.p, g.p, beta0.p, done.p, jd.p, it.p, total,
                                                tol, cnt.p, cnt.p + 1));
+      AMGC_LAUNCH(k_binst_live<<<div_up(ni, 128), 128, 0, s>>>(ni, nrhs, done.p, ilive.p));
       AMGC_CUDA_TRY(cudaGetLastError());
       int hc[2] = {0, 0};
       AMGC_CUDA_TRY(cudaMemcpyAsync(hc, cnt.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -322,13 +347,13 @@ int fgmres_batched(amgc_hierarchy* h, int nrhs, const double* rhs, double* x, in
       if (live == 0) break;
     }
     AMGC_LAUNCH(k_bbacksolve<<<gs, 128, 0, s>>>(nsys, m, H.p, g.p, jd.p, y.p));
-    AMGC_LAUNCH(k_bsolution_update<<<gv, th, 0, s>>>(n, nrhs, jmax, Zs.p, y.p, m + 1, ri, x));
-    AMGC_TRY(apply_cols(false, x, rv.p));
+    AMGC_LAUNCH(k_bsolution_update<<<gv, th, 0, s>>>(n, nrhs, jmax, Zs.p, y.p, m + 1, ri, jd.p, x));
+    AMGC_TRY(apply_cols(false, x, rv.p, nullptr));   // every system's true residual
     AMGC_LAUNCH(k_bsub<<<gv, th, 0, s>>>(nv, rhs, rv.p));
     AMGC_CUDA_TRY(cudaGetLastError());
   }
   // true relative residuals per system
-  AMGC_TRY(segnorm2(rv.p, nrm2.p));
+  AMGC_TRY(segnorm2(rv.p, nrm2.p, nullptr));
   std::vector<double> hr(nsys);
   std::vector<int> hi(nsys), hd(nsys);
   AMGC_CUDA_TRY(cudaMemcpyAsync(hr.data(), nrm2.p, nsys * sizeof(double), cudaMemcpyDeviceToHost, s));

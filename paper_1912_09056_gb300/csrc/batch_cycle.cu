@@ -36,10 +36,11 @@ __global__ void __launch_bounds__(128)
 k_mc_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, const int* __restrict__ scol,
           const T* __restrict__ sval, const T* __restrict__ x, int64_t ldx, const int* __restrict__ rp2,
           const int* __restrict__ c2, const T* __restrict__ v2, const T* __restrict__ x2, const T* __restrict__ b,
-          const T* __restrict__ x0, const T* __restrict__ dinv, T omega, T* __restrict__ y, int64_t ldy) {
+          const T* __restrict__ x0, const T* __restrict__ dinv, T omega, T* __restrict__ y, int64_t ldy,
+          const int* __restrict__ rinst, const int* __restrict__ live) {
   constexpr int BS = BR * BC;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nbr) return;
+  if (row >= nbr || (live && !live[rinst[row]])) return;
   const int sl = row >> 5, ls = row & 31;
   const int64_t o = soff[sl];
   const int L = slen[sl];
@@ -96,11 +97,12 @@ __global__ void __launch_bounds__(256)
 k_mc_rows(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const T* __restrict__ v1,
           const T* __restrict__ x1, int64_t ldx, const int* __restrict__ rp2, const int* __restrict__ c2,
           const T* __restrict__ v2, const T* __restrict__ x2, const T* __restrict__ b, const T* __restrict__ x0,
-          const T* __restrict__ dinv, T omega, T* __restrict__ y, int64_t ldy) {
+          const T* __restrict__ dinv, T omega, T* __restrict__ y, int64_t ldy, const int* __restrict__ rinst,
+          const int* __restrict__ live) {
   __shared__ T part[W > 1 ? W : 1][NC * BR];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int row = W > 1 ? (int)blockIdx.x : (int)blockIdx.x * (blockDim.x >> 5) + wid;
-  if (row >= nbr) return;
+  if (row >= nbr || (live && !live[rinst[row]])) return;   // uniform over the row's warps
   const int w = W > 1 ? wid : 0;
   T acc[NC][BR];
 #pragma unroll
@@ -177,10 +179,11 @@ template <int BU, int MODE, class T>
 __global__ void __launch_bounds__(128)
 k_mc_lm(int nl, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
         const T* __restrict__ u, const T* __restrict__ Z, const T* __restrict__ g, T* __restrict__ lam,
-        const double* __restrict__ Sinv, double alpha, T* __restrict__ out, int64_t ld) {
+        const double* __restrict__ Sinv, double alpha, T* __restrict__ out, int64_t ld, const int* __restrict__ linst,
+        const int* __restrict__ live) {
   const int lane = threadIdx.x & 31;
   const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (l >= nl) return;
+  if (l >= nl || (live && !live[linst[l]])) return;
   const int64_t co = blockIdx.y * ld;
   u += co;
   lam += co;
@@ -234,7 +237,7 @@ template <int BU, class T>
 __global__ void __launch_bounds__(128)
 k_mc_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp, const int* __restrict__ col,
                const T* __restrict__ val, const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha,
-               T* __restrict__ u, int64_t ld) {
+               T* __restrict__ u, int64_t ld, const int* __restrict__ ninst, const int* __restrict__ live) {
   const int lane = threadIdx.x & 31;
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (t >= nrows) return;
@@ -242,6 +245,7 @@ k_mc_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ 
   dlam += co;
   u += co;
   const int i = rows[t];
+  if (live && !live[ninst[i]]) return;
   T acc[BU];
 #pragma unroll
   for (int r = 0; r < BU; ++r) acc[r] = T(0);
@@ -261,18 +265,21 @@ k_mc_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ 
   if (lane < BU) u[(int64_t)i * BU + lane] -= alpha * atinv[(int64_t)i * BU + lane] * out;
 }
 
+// (masked: the DOFs of node i / bu and the multiplier entries of node i / 3 of finished instances)
 template <class T>
 __global__ void k_mc_jacobi_zero(int64_t n, int64_t nlam, const T* __restrict__ f, const T* __restrict__ dinv, T omega,
-                                 T* __restrict__ y, T* __restrict__ lam, int64_t ld) {
+                                 T* __restrict__ y, T* __restrict__ lam, int64_t ld, int bu, const int* __restrict__ ninst,
+                                 const int* __restrict__ linst, const int* __restrict__ live) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t co = blockIdx.y * ld;
-  if (i < n) y[co + i] = omega * dinv[i] * f[co + i];
-  if (i < nlam) lam[co + i] = T(0);
+  if (i < n && (!live || live[ninst[i / bu]])) y[co + i] = omega * dinv[i] * f[co + i];
+  if (i < nlam && (!live || live[linst[i / 3]])) lam[co + i] = T(0);
 }
 template <class T>
-__global__ void k_mc_copy(int64_t n, const T* __restrict__ a, int64_t lda, T* __restrict__ y, int64_t ldy) {
+__global__ void k_mc_copy(int64_t n, const T* __restrict__ a, int64_t lda, T* __restrict__ y, int64_t ldy, int bu,
+                          const int* __restrict__ ninst, const int* __restrict__ live) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) y[blockIdx.y * ldy + i] = a[blockIdx.y * lda + i];
+  if (i < n && (!live || live[ninst[i / bu]])) y[blockIdx.y * ldy + i] = a[blockIdx.y * lda + i];
 }
 template <class T>
 __global__ void k_mc_zero(int64_t n, T* __restrict__ y, int64_t ld) {
@@ -288,10 +295,10 @@ __global__ void k_mc_convert(int64_t n, const Ta* __restrict__ a, int64_t lda, T
 template <class T>
 __global__ void k_mc_restrict_lm(int nlc, const int* __restrict__ ptr, const int* __restrict__ idx,
                                  const T* __restrict__ w, const T* __restrict__ r, int64_t ldr, T* __restrict__ out,
-                                 int64_t ldo) {
+                                 int64_t ldo, const int* __restrict__ linst_c, const int* __restrict__ live) {
   const int lane = threadIdx.x & 31;
   const int L = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  if (L >= nlc) return;
+  if (L >= nlc || (live && !live[linst_c[L]])) return;
   r += blockIdx.y * ldr;
   out += blockIdx.y * ldo;
   T s0 = 0, s1 = 0, s2 = 0;
@@ -313,9 +320,10 @@ __global__ void k_mc_restrict_lm(int nlc, const int* __restrict__ ptr, const int
 }
 template <class T>
 __global__ void k_mc_prolong_lm(int nl, const int* __restrict__ lagg, const T* __restrict__ w, const T* __restrict__ c,
-                                int64_t ldc, T* __restrict__ lam, int64_t ldl) {
+                                int64_t ldc, T* __restrict__ lam, int64_t ldl, const int* __restrict__ linst,
+                                const int* __restrict__ live) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= nl) return;
+  if (l >= nl || (live && !live[linst[l]])) return;
   c += blockIdx.y * ldc;
   lam += blockIdx.y * ldl;
   const int L = lagg[l];
@@ -329,11 +337,12 @@ template <class T, int NC>
 __global__ void k_mc_gemv_batched(int n, const int* __restrict__ inst, const int* __restrict__ loc,
                                   const int* __restrict__ glob, const int* __restrict__ goff,
                                   const int64_t* __restrict__ doff, const double* __restrict__ A,
-                                  const T* __restrict__ x, T* __restrict__ y, int64_t ld) {
+                                  const T* __restrict__ x, T* __restrict__ y, int64_t ld, const int* __restrict__ live) {
   const int lane = threadIdx.x & 31;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row >= n) return;
   const int q = inst[row];
+  if (live && !live[q]) return;
   const int g0 = goff[q], nq = goff[q + 1] - g0;
   const double* a = A + doff[q] + (int64_t)loc[row] * nq;
   double s[NC];
@@ -359,10 +368,12 @@ struct McBufs {
 };
 
 // y (ldy) = op(A x (ldx) [+ A2 x2]) for NC columns; SELL when the matrix has a 3-row SELL copy,
-// else W warps per row by the mean row length (as the single-column kernels choose)
+// else W warps per row by the mean row length (as the single-column kernels choose).  Rows whose
+// instance is finished (live[rinst[row]] == 0) are skipped when live is given.
 template <int MODE, class T, int NC>
 int mc_apply(const BsrV<T>& A, const SellV<T>& S, const BsrV<T>* A2, const T* x, const T* x2, int64_t ldx,
-             const T* b, const T* x0, const T* dinv, double omega, T* y, int64_t ldy, cudaStream_t s) {
+             const T* b, const T* x0, const T* dinv, double omega, T* y, int64_t ldy, const int* rinst,
+             const int* live, cudaStream_t s) {
   if (A.nbr == 0) return AMGC_OK;
   const int* r2 = A2 ? A2->rp : nullptr;
   const int* k2 = A2 ? A2->col : nullptr;
@@ -371,10 +382,10 @@ int mc_apply(const BsrV<T>& A, const SellV<T>& S, const BsrV<T>* A2, const T* x,
     const int g = div_up(A.nbr, 128);
     if (S.bc == 3)
       AMGC_LAUNCH(k_mc_sell<3, 3, MODE, T, NC><<<g, 128, 0, s>>>(A.nbr, S.off, S.len, S.col, S.val, x, ldx, r2, k2,
-                                                                w2, x2, b, x0, dinv, (T)omega, y, ldy));
+                                                                w2, x2, b, x0, dinv, (T)omega, y, ldy, rinst, live));
     else if (S.bc == 6)
       AMGC_LAUNCH(k_mc_sell<3, 6, MODE, T, NC><<<g, 128, 0, s>>>(A.nbr, S.off, S.len, S.col, S.val, x, ldx, r2, k2,
-                                                                w2, x2, b, x0, dinv, (T)omega, y, ldy));
+                                                                w2, x2, b, x0, dinv, (T)omega, y, ldy, rinst, live));
     else {
       set_error("multi-column apply: unsupported SELL block shape");
       return AMGC_EINVAL;
@@ -387,16 +398,14 @@ int mc_apply(const BsrV<T>& A, const SellV<T>& S, const BsrV<T>* A2, const T* x,
 #define AMGC_MC_ROWS(BR_, BC1_)                                                                                 \
   if (A.br == BR_ && A.bc == BC1_ && bc2 == 3) {                                                                \
     if (mean > 96)                                                                                              \
-      AMGC_LAUNCH(k_mc_rows<BR_, BC1_, 3, MODE, T, NC, 8><<<A.nbr, 256, 0, s>>>(A.nbr, A.rp, A.col, A.val, x, ldx, \
-                                                                               r2, k2, w2, x2, b, x0, dinv,     \
-                                                                               (T)omega, y, ldy));              \
+      AMGC_LAUNCH(k_mc_rows<BR_, BC1_, 3, MODE, T, NC, 8><<<A.nbr, 256, 0, s>>>(                                  \
+          A.nbr, A.rp, A.col, A.val, x, ldx, r2, k2, w2, x2, b, x0, dinv, (T)omega, y, ldy, rinst, live));        \
     else if (mean > 24)                                                                                         \
-      AMGC_LAUNCH(k_mc_rows<BR_, BC1_, 3, MODE, T, NC, 2><<<A.nbr, 64, 0, s>>>(A.nbr, A.rp, A.col, A.val, x, ldx,  \
-                                                                              r2, k2, w2, x2, b, x0, dinv,      \
-                                                                              (T)omega, y, ldy));               \
+      AMGC_LAUNCH(k_mc_rows<BR_, BC1_, 3, MODE, T, NC, 2><<<A.nbr, 64, 0, s>>>(                                   \
+          A.nbr, A.rp, A.col, A.val, x, ldx, r2, k2, w2, x2, b, x0, dinv, (T)omega, y, ldy, rinst, live));        \
     else                                                                                                        \
       AMGC_LAUNCH(k_mc_rows<BR_, BC1_, 3, MODE, T, NC, 1><<<div_up(A.nbr, 8), 256, 0, s>>>(                     \
-          A.nbr, A.rp, A.col, A.val, x, ldx, r2, k2, w2, x2, b, x0, dinv, (T)omega, y, ldy));                     \
+          A.nbr, A.rp, A.col, A.val, x, ldx, r2, k2, w2, x2, b, x0, dinv, (T)omega, y, ldy, rinst, live));        \
     AMGC_CUDA_TRY(cudaGetLastError());                                                                          \
     return AMGC_OK;                                                                                             \
   }
@@ -409,20 +418,31 @@ int mc_apply(const BsrV<T>& A, const SellV<T>& S, const BsrV<T>* A2, const T* x,
   return AMGC_EINVAL;
 }
 
+// instance of every displacement node and multiplier node of every level (masks)
+struct McMaps {
+  std::vector<DBuf<int>> node, lm;
+};
+
 template <class T, int NC>
 struct McCycle {
   amgc_hierarchy* h;
   std::vector<LevelV<T>>& V;
   std::vector<McBufs<T>>& B;
+  const McMaps& maps;
+  const int* live;      // instance flags (null: every instance)
   cudaStream_t s;
   static constexpr int th = 256;
 
-  int lm(const LevelV<T>& L, int mode, const T* u, const T* g, T* lam, double alpha, T* out, int64_t ld) {
+  const int* ni(int l) const { return maps.node[l].p; }
+  const int* li(int l) const { return maps.lm[l].p; }
+
+  int lm(int l, int mode, const T* u, const T* g, T* lam, double alpha, T* out, int64_t ld) {
+    const LevelV<T>& L = V[l];
     if (L.nl == 0) return AMGC_OK;
     const dim3 grid(div_up((int64_t)L.nl * 32, 128), NC);
 #define AMGC_MC_LM(BU_, M_)                                                                                       \
   AMGC_LAUNCH(k_mc_lm<BU_, M_, T><<<grid, 128, 0, s>>>(L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam, L.Sinv, \
-                                                        alpha, out, ld))
+                                                        alpha, out, ld, li(l), live))
     if (L.bu == 3) {
       if (mode == 0) AMGC_MC_LM(3, 0);
       else if (mode == 1) AMGC_MC_LM(3, 1);
@@ -438,7 +458,8 @@ struct McCycle {
   }
 
   // `sweeps` CheapSIMPLE sweeps (as cycle.cu's smooth_sweeps), every column at once
-  int smooth(const LevelV<T>& L, McBufs<T>& W, const T* b, T* x, int sweeps, bool zero_guess) {
+  int smooth(int l, McBufs<T>& W, const T* b, T* x, int sweeps, bool zero_guess) {
+    const LevelV<T>& L = V[l];
     const int nu = L.nu();
     const int64_t ld = L.rows();
     const T* f = b;
@@ -457,29 +478,31 @@ struct McCycle {
           T* dst = ((steps - 1) % 2 == 0) ? u : t;
           const int64_t nlam = 3 * (int64_t)L.nl;
           AMGC_LAUNCH(k_mc_jacobi_zero<T><<<dim3(div_up(std::max<int64_t>(nu, nlam), th), NC), th, 0, s>>>(
-              nu, nlam, f, L.dinv, (T)L.omega_j, dst, lam, ld));
+              nu, nlam, f, L.dinv, (T)L.omega_j, dst, lam, ld, L.bu, ni(l), li(l), live));
           AMGC_CUDA_TRY(cudaGetLastError());
           cur = dst;
         } else {
           T* dst = cur == u ? t : u;
-          AMGC_TRY((mc_apply<3, T, NC>(L.K, L.Ks, B1, cur, lam, ld, f, cur, L.dinv, L.omega_j, dst, ld, s)));
+          AMGC_TRY((mc_apply<3, T, NC>(L.K, L.Ks, B1, cur, lam, ld, f, cur, L.dinv, L.omega_j, dst, ld, ni(l), live, s)));
           cur = dst;
         }
       }
-      AMGC_TRY(lm(L, 1, cur, g, lam, h->opts.simple_alpha, W.dl.p, ld));
+      AMGC_TRY(lm(l, 1, cur, g, lam, h->opts.simple_alpha, W.dl.p, ld));
       if (L.n_b1_rows > 0) {
         const dim3 gb(div_up((int64_t)L.n_b1_rows * 32, 128), NC);
         if (L.bu == 3)
           AMGC_LAUNCH(k_mc_b1_update<3, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val,
-                                                              W.dl.p, L.atinv, (T)h->opts.simple_alpha, cur, ld));
+                                                              W.dl.p, L.atinv, (T)h->opts.simple_alpha, cur, ld, ni(l),
+                                                              live));
         else
           AMGC_LAUNCH(k_mc_b1_update<6, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val,
-                                                              W.dl.p, L.atinv, (T)h->opts.simple_alpha, cur, ld));
+                                                              W.dl.p, L.atinv, (T)h->opts.simple_alpha, cur, ld, ni(l),
+                                                              live));
         AMGC_CUDA_TRY(cudaGetLastError());
       }
     }
     if (cur != u) {
-      AMGC_LAUNCH(k_mc_copy<T><<<dim3(div_up(nu, th), NC), th, 0, s>>>(nu, cur, ld, u, ld));
+      AMGC_LAUNCH(k_mc_copy<T><<<dim3(div_up(nu, th), NC), th, 0, s>>>(nu, cur, ld, u, ld, L.bu, ni(l), live));
       AMGC_CUDA_TRY(cudaGetLastError());
     }
     return AMGC_OK;
@@ -492,7 +515,7 @@ struct McCycle {
     if (l == (int)V.size() - 1) {
       const int n = L.rows();
       AMGC_LAUNCH(k_mc_gemv_batched<T, NC><<<div_up((int64_t)n * 32, th), th, 0, s>>>(
-          n, L.c_inst, L.c_loc, L.c_glob, L.c_goff, L.c_doff, L.Ainv, b, x, ld));
+          n, L.c_inst, L.c_loc, L.c_glob, L.c_goff, L.c_doff, L.Ainv, b, x, ld, live));
       AMGC_CUDA_TRY(cudaGetLastError());
       return AMGC_OK;
     }
@@ -502,26 +525,28 @@ struct McCycle {
     const int64_t ldc = C.rows();
     const int sweeps = h->opts.smoother_sweeps;
     if (sweeps == 0) AMGC_LAUNCH(k_mc_zero<T><<<dim3(div_up(L.rows(), th), NC), th, 0, s>>>(L.rows(), x, ld));
-    AMGC_TRY(smooth(L, W, b, x, sweeps, true));
-    // residual, restriction
+    AMGC_TRY(smooth(l, W, b, x, sweeps, true));
+    // residual, restriction (the rows of R are the coarse level's nodes)
     const BsrV<T>* B1 = L.nl ? &L.B1 : nullptr;
-    AMGC_TRY((mc_apply<2, T, NC>(L.K, L.Ks, B1, x, x + nu, ld, b, nullptr, nullptr, 0.0, W.r.p, ld, s)));
-    AMGC_TRY(lm(L, 0, x, b + nu, x + nu, 0.0, W.r.p + nu, ld));
-    AMGC_TRY((mc_apply<0, T, NC>(L.R, L.Rs, nullptr, W.r.p, nullptr, ld, nullptr, nullptr, nullptr, 0.0, CW.b.p, ldc, s)));
+    AMGC_TRY((mc_apply<2, T, NC>(L.K, L.Ks, B1, x, x + nu, ld, b, nullptr, nullptr, 0.0, W.r.p, ld, ni(l), live, s)));
+    AMGC_TRY(lm(l, 0, x, b + nu, x + nu, 0.0, W.r.p + nu, ld));
+    AMGC_TRY((mc_apply<0, T, NC>(L.R, L.Rs, nullptr, W.r.p, nullptr, ld, nullptr, nullptr, nullptr, 0.0, CW.b.p, ldc,
+                                 ni(l + 1), live, s)));
     if (C.nl > 0) {
       AMGC_LAUNCH(k_mc_restrict_lm<T><<<dim3(div_up((int64_t)C.nl * 32, 128), NC), 128, 0, s>>>(
-          C.nl, L.rl_ptr, L.rl_idx, L.pl_w, W.r.p + nu, ld, CW.b.p + C.nu(), ldc));
+          C.nl, L.rl_ptr, L.rl_idx, L.pl_w, W.r.p + nu, ld, CW.b.p + C.nu(), ldc, li(l + 1), live));
       AMGC_CUDA_TRY(cudaGetLastError());
     }
     AMGC_TRY(cycle(l + 1, CW.b.p, CW.x.p));
     // prolongation
-    AMGC_TRY((mc_apply<1, T, NC>(L.P, L.Ps, nullptr, CW.x.p, nullptr, ldc, nullptr, nullptr, nullptr, 0.0, x, ld, s)));
+    AMGC_TRY((mc_apply<1, T, NC>(L.P, L.Ps, nullptr, CW.x.p, nullptr, ldc, nullptr, nullptr, nullptr, 0.0, x, ld, ni(l),
+                                 live, s)));
     if (L.nl > 0) {
       AMGC_LAUNCH(k_mc_prolong_lm<T><<<dim3(div_up(L.nl, 128), NC), 128, 0, s>>>(L.nl, L.lagg, L.pl_w, CW.x.p + C.nu(),
-                                                                                 ldc, x + nu, ld));
+                                                                                 ldc, x + nu, ld, li(l), live));
       AMGC_CUDA_TRY(cudaGetLastError());
     }
-    AMGC_TRY(smooth(L, W, b, x, sweeps, false));
+    AMGC_TRY(smooth(l, W, b, x, sweeps, false));
     return AMGC_OK;
   }
 };
@@ -543,23 +568,52 @@ int alloc_mc(amgc_hierarchy* h, std::vector<McBufs<T>>& B, int nc) {
   return AMGC_OK;
 }
 
+// node -> instance and multiplier node -> instance of every level, from the instance ranges
+int build_maps(amgc_hierarchy* h, McMaps& M) {
+  const int nlev = (int)h->L.size();
+  if ((int)M.node.size() == nlev) return AMGC_OK;
+  M.node.clear();
+  M.lm.clear();
+  M.node.resize(nlev);
+  M.lm.resize(nlev);
+  cudaStream_t s = h->stream;
+  for (int l = 0; l < nlev; ++l) {
+    const Level& L = h->L[l];
+    std::vector<int> a(std::max(L.nn, 1), 0), b(std::max(L.nl, 1), 0);
+    if (h->n_inst > 1 && (int)L.nptr.size() == h->n_inst + 1 && (int)L.lptr.size() == h->n_inst + 1) {
+      for (int q = 0; q < h->n_inst; ++q) {
+        for (int i = L.nptr[q]; i < L.nptr[q + 1]; ++i) a[i] = q;
+        for (int i = L.lptr[q]; i < L.lptr[q + 1]; ++i) b[i] = q;
+      }
+    }
+    AMGC_TRY(M.node[l].alloc(a.size()));
+    AMGC_TRY(M.lm[l].alloc(b.size()));
+    AMGC_CUDA_TRY(cudaMemcpyAsync(M.node[l].p, a.data(), a.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    AMGC_CUDA_TRY(cudaMemcpyAsync(M.lm[l].p, b.data(), b.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  AMGC_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMGC_OK;
+}
+
 }  // namespace
 
-// Work buffers of the multi-column cycle, kept by the hierarchy between calls.
+// Work buffers and instance maps of the multi-column cycle, kept by the hierarchy between calls.
 struct McState {
   std::vector<McBufs<double>> b64;
   std::vector<McBufs<float>> b32;
   DBuf<float> in32, out32;
+  McMaps maps;
 };
 
 void mc_state_free(McState* st) { delete st; }
 
-// z = V-cycle(r) for kMcCols columns at once (column stride rows[0], FP64 in and out); the FP32
-// cycle converts at entry and exit
-int precond_apply_cols(amgc_hierarchy* h, const double* r, double* z) {
+// z = V-cycle(r) for kMcCols columns at once (column stride rows[0], FP64 in and out), skipping the
+// rows of instances with live[q] == 0 when live is given; the FP32 cycle converts at entry and exit
+int precond_apply_cols(amgc_hierarchy* h, const double* r, double* z, const int* live) {
   constexpr int NC = kMcCols;
   if (!h->mc) h->mc = new McState();
   McState& M = *h->mc;
+  AMGC_TRY(build_maps(h, M.maps));
   const int64_t n = h->L[0].rows();
   cudaStream_t s = h->stream;
   if (h->opts.precision == 32) {
@@ -569,29 +623,35 @@ int precond_apply_cols(amgc_hierarchy* h, const double* r, double* z) {
       AMGC_TRY(M.out32.alloc((size_t)NC * n));
     }
     AMGC_LAUNCH((k_mc_convert<double, float><<<dim3(div_up(n, 256), NC), 256, 0, s>>>(n, r, n, M.in32.p, n)));
-    McCycle<float, NC> c{h, h->v32, M.b32, s};
+    McCycle<float, NC> c{h, h->v32, M.b32, M.maps, live, s};
     AMGC_TRY(c.cycle(0, M.in32.p, M.out32.p));
     AMGC_LAUNCH((k_mc_convert<float, double><<<dim3(div_up(n, 256), NC), 256, 0, s>>>(n, M.out32.p, n, z, n)));
     AMGC_CUDA_TRY(cudaGetLastError());
     return AMGC_OK;
   }
   AMGC_TRY(alloc_mc<double>(h, M.b64, NC));
-  McCycle<double, NC> c{h, h->v64, M.b64, s};
+  McCycle<double, NC> c{h, h->v64, M.b64, M.maps, live, s};
   return c.cycle(0, r, z);
 }
 
-// y = A x for kMcCols columns (FP64, column stride rows[0]): the fine K (with B1) read once
-int saddle_apply_cols(amgc_hierarchy* h, const double* x, double* y) {
+// y = A x for kMcCols columns (FP64, column stride rows[0]): the fine K (with B1) read once; rows of
+// instances with live[q] == 0 skipped when live is given
+int saddle_apply_cols(amgc_hierarchy* h, const double* x, double* y, const int* live) {
   constexpr int NC = kMcCols;
+  if (!h->mc) h->mc = new McState();
+  AMGC_TRY(build_maps(h, h->mc->maps));
+  const McMaps& maps = h->mc->maps;
   const LevelV<double>& L = h->v64[0];
   const int nu = L.nu();
   const int64_t ld = L.rows();
   cudaStream_t s = h->stream;
   const BsrV<double>* B1 = L.nl ? &L.B1 : nullptr;
-  AMGC_TRY((mc_apply<0, double, NC>(L.K, L.Ks, B1, x, x + nu, ld, nullptr, nullptr, nullptr, 0.0, y, ld, s)));
+  AMGC_TRY((mc_apply<0, double, NC>(L.K, L.Ks, B1, x, x + nu, ld, nullptr, nullptr, nullptr, 0.0, y, ld,
+                                    maps.node[0].p, live, s)));
   if (L.nl > 0) {
     AMGC_LAUNCH(k_mc_lm<3, 2, double><<<dim3(div_up((int64_t)L.nl * 32, 128), NC), 128, 0, s>>>(
-        L.nl, L.B2.rp, L.B2.col, L.B2.val, x, L.Z, nullptr, const_cast<double*>(x + nu), L.Sinv, 0.0, y + nu, ld));
+        L.nl, L.B2.rp, L.B2.col, L.B2.val, x, L.Z, nullptr, const_cast<double*>(x + nu), L.Sinv, 0.0, y + nu, ld,
+        maps.lm[0].p, live));
     AMGC_CUDA_TRY(cudaGetLastError());
   }
   return AMGC_OK;
