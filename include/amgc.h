@@ -94,7 +94,9 @@ typedef struct {
   double tol;                /* relative residual tolerance ||r_k|| / ||r_0||                  */
   int32_t autotune;          /* 1: time the row mappings of every level's K, P and R apply at
                                 setup and keep the fastest (warp per row, SELL with one or two
-                                threads per row), separately for the FP64 and FP32 cycle     */
+                                threads per row), and the smoother fusion of every level (the
+                                sweep's corrector and B1 update as two launches or one fused
+                                single-CTA launch), separately for the FP64 and FP32 cycle  */
   int32_t schur_damping;     /* 0: the multiplier correction is damped by simple_alpha alone
                                 (Sec. 5.2).  1: per level (per instance when batched) it is
                                 damped by min(simple_alpha, (4/3) / rho), rho = spectral radius
@@ -396,9 +398,12 @@ int amgc_profile(struct amgc_hierarchy* h, int32_t enable);
 int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launches, double* bytes,
                       double* flops);
 
-/* Overrides the row mapping of one sparse apply of the cycle (the choice the setup-time autotuner
- * makes when opts.autotune = 1).  level: 0 .. n_levels-1; matrix: 0 = the level's K (with its B1
- * coupling), 1 = its prolongator P, 2 = its restriction R (P and R: not on the coarsest level);
+/* Overrides the row mapping of one sparse apply of the cycle, or the smoother fusion of a level (the
+ * choices the setup-time autotuner makes when opts.autotune = 1).  level: 0 .. n_levels-1; matrix:
+ * 0 = the level's K (with its B1 coupling), 1 = its prolongator P, 2 = its restriction R (P and R:
+ * not on the coarsest level), 3 = the CheapSIMPLE sweep's multiplier corrector and B1 update
+ * (mapping 0 or -1: two launches, the default; 1: one fused launch of one thread block, which the
+ * autotuner picks on levels with few multiplier rows; the same arithmetic either way);
  * precision: 64 = the FP64 views (the Krylov operator apply and the FP64 cycle), 32 = the FP32
  * cycle (hierarchies set up with precision 32 only); mapping: -1 = the default, 0 = one warp per
  * block row, 1 / 2 = SELL-32 with one / two threads per block row, 3 = the shared-memory staged

@@ -266,11 +266,12 @@ class Hierarchy:
                "amgc_profile_read")
         return ms.value, n.value, b.value, f.value
 
-    ROW_MATRIX = dict(K=0, P=1, R=2)
+    ROW_MATRIX = dict(K=0, P=1, R=2, fuse=3)
 
     def set_row_mapping(self, level: int, matrix: str, precision: int, mapping: int):
         """amgc_set_row_mapping: matrix 'K', 'P' or 'R'; mapping -1 default, 0 warp per row,
-        1 / 2 SELL threads per row, 3 staged FP32 kernel (level-0 K, precision 32)."""
+        1 / 2 SELL threads per row, 3 staged FP32 kernel (level-0 K, precision 32).  matrix 'fuse':
+        the level's smoother fusion, mapping 1 fused, 0 two launches."""
         _check(self._lib.amgc_set_row_mapping(self._h, int(level), self.ROW_MATRIX[matrix], int(precision),
                                               int(mapping)), "amgc_set_row_mapping")
 

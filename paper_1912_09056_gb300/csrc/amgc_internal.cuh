@@ -166,6 +166,7 @@ struct LevelV {
   BsrV<T> K, B1, B2, P, R;
   SellV<T> Ks, Ps, Rs;
   int kmap = -1, pmap = -1, rmap = -1;   // row mappings (see Level)
+  int fuse = 0;                          // 1: fused single-CTA corrector + B1 update (see Level)
   const T* Z = nullptr;
   const double* Sinv = nullptr;    // FP64 in both precisions
   const T* dinv = nullptr;
@@ -211,6 +212,9 @@ struct Level {
   // row mapping of the K, P, R applies per precision (0: FP64, 1: FP32):
   // 0 = warp per row, 1 = SELL one thread per row, 2 = SELL two threads per row, -1 = default
   int kmap[2] = {-1, -1}, pmap[2] = {-1, -1}, rmap[2] = {-1, -1};
+  // smoother fusion per precision: 1 = the sweep's corrector and B1 update in one single-CTA
+  // launch, 0 = two launches (the autotuner's choice; 0 by default)
+  int fuse[2] = {0, 0};
   DBuf<double> Z;          // nl*9
   DBuf<int> body;          // nn
   DBuf<double> B;          // nullspace nu*6

@@ -535,14 +535,12 @@ static int mapped_apply(const BsrV<T>& A, const SellV<T>& S, int map, const BsrV
 // MODE 0: out_l = g_l - (B2 u)_l + Z_l lam_l                       (residual)
 // MODE 1: d = -Sinv_l (g_l - (B2 u)_l + Z_l lam_l); lam_l += alpha d; out_l = d  (corrector)
 // MODE 2: out_l = (B2 u)_l - Z_l lam_l                             (saddle apply)
+// one multiplier node l (one warp)
 template <int BU, int MODE, class T>
-__global__ void __launch_bounds__(128)
-k_lm(int nl, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
-     const T* __restrict__ u, const T* __restrict__ Z, const T* __restrict__ g, T* __restrict__ lam,
-     const double* __restrict__ Sinv, double alpha, T* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (l >= nl) return;
+__device__ __forceinline__ void lm_node(int l, int lane, const int* __restrict__ rp, const int* __restrict__ col,
+                                        const T* __restrict__ val, const T* __restrict__ u, const T* __restrict__ Z,
+                                        const T* __restrict__ g, T* __restrict__ lam, const double* __restrict__ Sinv,
+                                        double alpha, T* __restrict__ out) {
   T acc[3] = {T(0), T(0), T(0)};
   lane_blocks<3, BU, T>(rp[l], rp[l + 1], col, val, u, lane, acc);
   const T bu0 = warp_sum(acc[0]), bu1 = warp_sum(acc[1]), bu2 = warp_sum(acc[2]);
@@ -575,6 +573,17 @@ k_lm(int nl, const int* __restrict__ rp, const int* __restrict__ col, const T* _
   out[3 * l] = (T)d0;
   out[3 * l + 1] = (T)d1;
   out[3 * l + 2] = (T)d2;
+}
+
+template <int BU, int MODE, class T>
+__global__ void __launch_bounds__(128)
+k_lm(int nl, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+     const T* __restrict__ u, const T* __restrict__ Z, const T* __restrict__ g, T* __restrict__ lam,
+     const double* __restrict__ Sinv, double alpha, T* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (l >= nl) return;
+  lm_node<BU, MODE, T>(l, lane, rp, col, val, u, Z, g, lam, Sinv, alpha, out);
 }
 
 template <int MODE, class T>
@@ -623,16 +632,11 @@ __global__ void k_jacobi_zero(int64_t n, int64_t nlam, const T* __restrict__ f, 
   if (i < n) y[i] = omega * dinv[i] * f[i];
   if (i < nlam) lam[i] = T(0);
 }
-// u_i -= alpha atinv_i (B1 dlam)_i over the rows of B1 with entries, one warp per row
+// u_i -= alpha atinv_i (B1 dlam)_i for row i of B1 (one warp)
 template <int BU, class T>
-__global__ void __launch_bounds__(128)
-k_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp, const int* __restrict__ col,
-            const T* __restrict__ val, const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha,
-            T* __restrict__ u) {
-  const int lane = threadIdx.x & 31;
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (t >= nrows) return;
-  const int i = rows[t];
+__device__ __forceinline__ void b1_row(int i, int lane, const int* __restrict__ rp, const int* __restrict__ col,
+                                       const T* __restrict__ val, const T* __restrict__ dlam,
+                                       const T* __restrict__ atinv, T alpha, T* __restrict__ u) {
   T acc[BU];
 #pragma unroll
   for (int r = 0; r < BU; ++r) acc[r] = T(0);
@@ -645,6 +649,49 @@ k_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp,
   }
   if (lane < BU) u[(int64_t)i * BU + lane] -= alpha * atinv[(int64_t)i * BU + lane] * out;
 }
+// the same over the rows of B1 with entries, one warp per row
+template <int BU, class T>
+__global__ void __launch_bounds__(128)
+k_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp, const int* __restrict__ col,
+            const T* __restrict__ val, const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha,
+            T* __restrict__ u) {
+  const int lane = threadIdx.x & 31;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (t >= nrows) return;
+  b1_row<BU, T>(rows[t], lane, rp, col, val, dlam, atinv, alpha, u);
+}
+// Fused corrector and B1 update of a CheapSIMPLE sweep in one CTA: the multiplier corrector on
+// every node (as k_lm MODE 1), a block barrier, then the B1 update of every row of B1 with entries
+// (as k_b1_update); the same arithmetic as the two launches, in one launch.  One CTA, so it pays
+// only where a level's multiplier rows are few (the autotuner decides per level).
+constexpr int kFuseThreads = 1024;
+template <int BU, class T>
+__global__ void __launch_bounds__(kFuseThreads)
+k_corrector_b1_fused(int nl, const int* __restrict__ rp2, const int* __restrict__ c2, const T* __restrict__ v2,
+                     const T* u_in, const T* __restrict__ Z, const T* __restrict__ g,
+                     T* __restrict__ lam, const double* __restrict__ Sinv, double alpha, T* __restrict__ dlam,
+                     int nrows, const int* __restrict__ rows, const int* __restrict__ rp1, const int* __restrict__ c1,
+                     const T* __restrict__ v1, const T* __restrict__ atinv, T* u) {
+  // u_in and u are the same iterate: read by the corrector, updated after the barrier
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = wid; l < nl; l += nw) lm_node<BU, 1, T>(l, lane, rp2, c2, v2, u_in, Z, g, lam, Sinv, alpha, dlam);
+  __syncthreads();
+  for (int t = wid; t < nrows; t += nw) b1_row<BU, T>(rows[t], lane, rp1, c1, v1, dlam, atinv, (T)alpha, u);
+}
+template <class T>
+static int corrector_b1_fused(const LevelV<T>& L, T* u, const T* g, T* lam, double alpha, cudaStream_t s) {
+  if (L.bu == 3)
+    AMGC_LAUNCH(k_corrector_b1_fused<3, T><<<1, kFuseThreads, 0, s>>>(L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam,
+                                                                     L.Sinv, alpha, L.dlam, L.n_b1_rows, L.b1_rows,
+                                                                     L.B1.rp, L.B1.col, L.B1.val, L.atinv, u));
+  else
+    AMGC_LAUNCH(k_corrector_b1_fused<6, T><<<1, kFuseThreads, 0, s>>>(L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam,
+                                                                     L.Sinv, alpha, L.dlam, L.n_b1_rows, L.b1_rows,
+                                                                     L.B1.rp, L.B1.col, L.B1.val, L.atinv, u));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+
 // u = uh - alpha atinv (B1 dlam) in one launch: blocks below ncopy copy uh into u on the rows
 // without B1 entries (one thread per DOF), the others update the rows of B1 as k_b1_update does,
 // reading uh
@@ -837,7 +884,12 @@ static int smooth_sweeps(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* 
         cur = dst;
       }
     }
-    // corrector on the multipliers and the B1 update of the displacements, in place on cur
+    // corrector on the multipliers and the B1 update of the displacements, in place on cur: one
+    // fused single-CTA launch where the autotuner found it faster, else two launches
+    if (L.fuse && L.nl > 0) {
+      AMGC_TRY(corrector_b1_fused<T>(L, cur, g, lam, h->opts.simple_alpha, s));
+      continue;
+    }
     AMGC_TRY((lm_op<1, T>(L, cur, g, lam, h->opts.simple_alpha, L.dlam, s)));
     if (L.n_b1_rows > 0) {
       if (L.bu == 3)
@@ -1613,7 +1665,7 @@ int make_views(amgc_hierarchy* h) {
     v.Ks = sview<double>(L.Ks, L.Ks.val.p);
     v.Ps = sview<double>(L.Ps, L.Ps.val.p);
     v.Rs = sview<double>(L.Rs, L.Rs.val.p);
-    v.kmap = L.kmap[0]; v.pmap = L.pmap[0]; v.rmap = L.rmap[0];
+    v.kmap = L.kmap[0]; v.pmap = L.pmap[0]; v.rmap = L.rmap[0]; v.fuse = L.fuse[0];
     v.Z = L.Z.p; v.dinv = L.jdinv.p; v.atinv = L.atinv.p; v.pl_w = L.pl_w.p;
     v.x = L.x.p; v.b = L.b.p; v.r = L.r.p; v.t = L.t.p; v.dlam = L.dlam.p; v.tsw = L.tsw.p;
     if (L.has_transposed) {
@@ -1667,7 +1719,7 @@ int make_views(amgc_hierarchy* h) {
     }
     v.Ps = sview<float>(L.Ps, F.Ps.p);
     v.Rs = sview<float>(L.Rs, F.Rs.p);
-    v.kmap = L.kmap[1]; v.pmap = L.pmap[1]; v.rmap = L.rmap[1];
+    v.kmap = L.kmap[1]; v.pmap = L.pmap[1]; v.rmap = L.rmap[1]; v.fuse = L.fuse[1];
     v.Z = F.Z.p; v.dinv = F.jdinv.p; v.atinv = F.atinv.p; v.pl_w = F.pl_w.p;
     v.x = F.x.p; v.b = F.b.p; v.r = F.r.p; v.t = F.t.p; v.dlam = F.dlam.p;
     h->v32.push_back(v);
@@ -1693,10 +1745,22 @@ void drop_cycle_graphs(amgc_hierarchy* h) {
 // row), 1 / 2 (SELL, one / two threads per row), 3 (the staged FP32 kernel: level-0 K only)
 int set_row_mapping(amgc_hierarchy* h, int level, int matrix, int precision, int mapping) {
   const int nlev = (int)h->L.size();
-  if (level < 0 || level >= nlev || matrix < 0 || matrix > 2 || (precision != 64 && precision != 32) ||
-      mapping < -1 || mapping > 3 || (matrix > 0 && level == nlev - 1)) {
+  if (level < 0 || level >= nlev || matrix < 0 || matrix > 3 || (precision != 64 && precision != 32) ||
+      mapping < -1 || mapping > 3 || (matrix > 0 && level == nlev - 1) || (matrix == 3 && mapping > 1)) {
     set_error("amgc_set_row_mapping: invalid level, matrix, precision or mapping");
     return AMGC_EINVAL;
+  }
+  if (matrix == 3) {   // the smoother fusion of the level: 0 (or -1) two launches, 1 fused
+    if (precision == 32 && h->opts.precision != 32) {
+      set_error("amgc_set_row_mapping: the hierarchy has no FP32 cycle (precision 64)");
+      return AMGC_EINVAL;
+    }
+    const int f = mapping == 1 ? 1 : 0;
+    h->L[level].fuse[precision == 32 ? 1 : 0] = f;
+    if (precision == 64) h->v64[level].fuse = f;
+    else h->v32[level].fuse = f;
+    drop_cycle_graphs(h);
+    return AMGC_OK;
   }
   if (precision == 32 && h->opts.precision != 32) {
     set_error("amgc_set_row_mapping: the hierarchy has no FP32 cycle (precision 64)");
@@ -1774,6 +1838,57 @@ static int tune_one(amgc_hierarchy* h, const BsrV<T>& A, const SellV<T>& S, cons
   return AMGC_OK;
 }
 
+// Times a sweep's corrector + B1 update as two launches and as the fused single-CTA launch
+// (1 warm-up, 3 timed, CUDA events on the hierarchy's stream) and keeps the faster; the work
+// vectors hold finite values, the results are not used.
+template <class T>
+static int tune_fuse(amgc_hierarchy* h, const LevelV<T>& L, int* fuse) {
+  *fuse = 0;
+  if (L.nl == 0) return AMGC_OK;
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1, e2, e3;
+  AMGC_CUDA_TRY(cudaEventCreate(&e0));
+  AMGC_CUDA_TRY(cudaEventCreate(&e1));
+  AMGC_CUDA_TRY(cudaEventCreate(&e2));
+  AMGC_CUDA_TRY(cudaEventCreate(&e3));
+  T* u = L.x;
+  T* lam = L.x + L.nu();
+  const T* g = L.b + L.nu();
+  const int gb = div_up((int64_t)L.n_b1_rows * 32, 128);
+  auto separate = [&]() -> int {
+    AMGC_TRY((lm_op<1, T>(L, u, g, lam, h->opts.simple_alpha, L.dlam, s)));
+    if (L.n_b1_rows > 0) {
+      if (L.bu == 3)
+        AMGC_LAUNCH(k_b1_update<3, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
+                                                         L.atinv, (T)h->opts.simple_alpha, u));
+      else
+        AMGC_LAUNCH(k_b1_update<6, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
+                                                         L.atinv, (T)h->opts.simple_alpha, u));
+    }
+    AMGC_CUDA_TRY(cudaGetLastError());
+    return AMGC_OK;
+  };
+  AMGC_TRY(separate());
+  AMGC_CUDA_TRY(cudaEventRecord(e0, s));
+  for (int rep = 0; rep < 3; ++rep) AMGC_TRY(separate());
+  AMGC_CUDA_TRY(cudaEventRecord(e1, s));
+  for (int rep = 0; rep < 4; ++rep) {
+    if (rep == 1) AMGC_CUDA_TRY(cudaEventRecord(e2, s));
+    AMGC_TRY(corrector_b1_fused<T>(L, u, g, lam, h->opts.simple_alpha, s));
+  }
+  AMGC_CUDA_TRY(cudaEventRecord(e3, s));
+  AMGC_CUDA_TRY(cudaEventSynchronize(e3));
+  float t_sep = 0.f, t_fused = 0.f;
+  AMGC_CUDA_TRY(cudaEventElapsedTime(&t_sep, e0, e1));
+  AMGC_CUDA_TRY(cudaEventElapsedTime(&t_fused, e2, e3));
+  *fuse = t_fused < t_sep ? 1 : 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  cudaEventDestroy(e3);
+  return AMGC_OK;
+}
+
 // fine_k_only: only the finest K (the Krylov operator apply) is tuned; the other maps keep
 // their defaults (the FP64 views of a hierarchy whose cycle runs in FP32)
 template <class T>
@@ -1788,6 +1903,10 @@ static int tune_views(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int pidx, bo
     if (!fine_k_only) {
       AMGC_TRY((tune_one<1, T>(h, L.P, L.Ps, nullptr, C.x, nullptr, nullptr, nullptr, L.t, &pm)));
       AMGC_TRY((tune_one<0, T>(h, L.R, L.Rs, nullptr, L.r, nullptr, nullptr, nullptr, C.b, &rm)));
+      int fz = 0;
+      AMGC_TRY(tune_fuse<T>(h, L, &fz));
+      L.fuse = fz;
+      LL.fuse[pidx] = fz;
     }
     L.kmap = km; L.pmap = pm; L.rmap = rm;
     LL.kmap[pidx] = km; LL.pmap[pidx] = pm; LL.rmap[pidx] = rm;

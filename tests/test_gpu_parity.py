@@ -250,3 +250,30 @@ def test_fp32_autotuned_mappings_give_the_same_cycle():
     assert (torch.linalg.norm(z0 - z1) / torch.linalg.norm(z0)).item() <= 1e-5
     h0.close()
     h1.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_smoother_fusion_gives_the_same_cycle(precision):
+    """The fused single-CTA corrector + B1 update (the autotuner's smoother-fusion choice) runs the
+    same arithmetic as the two launches: the same bits, and the oracle's cycle."""
+    prob = two_block_problem(master_n=(13, 12, 11), slave_n=(10, 11, 9), E_slave=10.0, tilt_deg=5.0, seed=11,
+                             active_fraction=0.6)
+    opts = dict(levels_max=4, coarse_max_rows=200, transfer=1, smoother_sweeps=2)
+    h = amgc.setup(prob, precision=precision, **opts)
+    r = torch.from_numpy(np.random.default_rng(9).standard_normal(prob.n)).cuda()
+    z0, z1 = torch.empty_like(r), torch.empty_like(r)
+    h.vcycle(r, z0)
+    nlev = h.stats()["n_levels"]
+    for l in range(nlev - 1):
+        h.set_row_mapping(l, "fuse", precision, 1)
+    h.vcycle(r, z1)
+    assert torch.equal(z0, z1)
+    ref = oracle_setup(prob, Options(**opts))
+    zr = ref.vcycle(r.cpu().numpy())
+    assert rel(z1.cpu().numpy(), zr) <= (RTOL if precision == 64 else 1e-4)
+    h.close()
+    # the autotuned hierarchy (row mappings and fusion chosen by timing) gives the oracle's cycle too
+    ht = amgc.setup(prob, precision=precision, autotune=1, **opts)
+    ht.vcycle(r, z1)
+    assert rel(z1.cpu().numpy(), zr) <= (1e-12 if precision == 64 else 1e-4)
+    ht.close()
