@@ -203,6 +203,13 @@ int amgc_apply(struct amgc_hierarchy* h, const double* x, double* y, void* strea
 int amgc_solve(struct amgc_hierarchy* h, const double* rhs, double* x, int32_t* iters,
                double* relres, void* stream);
 
+/* amgc_solve with the solution split into its two fields: u (3n displacements) and lam (3 n_s
+ * Cartesian multipliers, three per slave node), the form (u, lambda) of the problem statement
+ * (Sec. 2.3).  rhs: device vector of rows[0]; u, lam: host or device arrays (unified addressing
+ * decides), not overlapping rhs.  Synchronises `stream`.  Results and errors as amgc_solve. */
+int amgc_solve_split(struct amgc_hierarchy* h, const double* rhs, double* u, double* lam, int32_t* iters,
+                     double* relres, void* stream);
+
 /* Same as amgc_solve but rhs and x are HOST arrays: the call copies rhs to the device,
  * solves, and copies x back (synchronous with respect to the host). */
 int amgc_solve_host(struct amgc_hierarchy* h, const double* rhs_host, double* x_host,

@@ -86,6 +86,8 @@ def load():
         getattr(lib, name).restype = C.c_int
     lib.amgc_solve.argtypes = [vp, vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
     lib.amgc_solve.restype = C.c_int
+    lib.amgc_solve_split.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
+    lib.amgc_solve_split.restype = C.c_int
     lib.amgc_solve_host.argtypes = [vp, vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
     lib.amgc_solve_host.restype = C.c_int
     lib.amgc_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -294,6 +296,16 @@ class Hierarchy:
         code = self._lib.amgc_solve(self._h, _ptr(rhs), _ptr(x), C.byref(it), C.byref(rr), _stream_ptr(stream))
         if check:
             _check(code, "amgc_solve")
+        return it.value, rr.value, code
+
+    def solve_split(self, rhs, u, lam, stream=None, check: bool = True):
+        """amgc_solve_split: the solution's displacements into u and multipliers into lam."""
+        it = C.c_int32(0)
+        rr = C.c_double(0.0)
+        code = self._lib.amgc_solve_split(self._h, _ptr(rhs), _ptr(u), _ptr(lam), C.byref(it), C.byref(rr),
+                                          _stream_ptr(stream))
+        if check:
+            _check(code, "amgc_solve_split")
         return it.value, rr.value, code
 
     def apply_transposed(self, x, y, stream=None):

@@ -452,6 +452,31 @@ int amgc_solve(struct amgc_hierarchy* h, const double* rhs, double* x, int32_t* 
   return st;
 }
 
+int amgc_solve_split(struct amgc_hierarchy* h, const double* rhs, double* u, double* lam, int32_t* iters,
+                     double* relres, void* stream) {
+  if (!h || !rhs || !u || (!lam && h->L[0].nl > 0) || u == rhs || lam == rhs) {
+    set_error("amgc_solve_split: invalid argument");
+    return AMGC_EINVAL;
+  }
+  h->stream = (cudaStream_t)stream;
+  StreamScope scope_(h->stream);
+  const size_t n = (size_t)h->L[0].rows();
+  const size_t nu = (size_t)h->L[0].nu();
+  DBuf<double> x;
+  AMGC_TRY(x.alloc(n));
+  int it = 0;
+  double rr = 0.0;
+  const int st = fgmres(h, rhs, x.p, 0.0, &it, &rr);
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  if (st == AMGC_OK || st == AMGC_NOT_CONVERGED) {
+    AMGC_CUDA_TRY(cudaMemcpyAsync(u, x.p, nu * sizeof(double), cudaMemcpyDefault, h->stream));
+    if (n > nu) AMGC_CUDA_TRY(cudaMemcpyAsync(lam, x.p + nu, (n - nu) * sizeof(double), cudaMemcpyDefault, h->stream));
+  }
+  AMGC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return st;
+}
+
 int amgc_solve_host(struct amgc_hierarchy* h, const double* rhs_host, double* x_host, int32_t* iters, double* relres,
                     void* stream) {
   if (!h || !rhs_host || !x_host) {

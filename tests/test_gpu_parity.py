@@ -137,6 +137,11 @@ def test_hierarchy_vcycle_and_solve_match_oracle(case):
     # host-buffer entry point gives the same solution
     xh, it_h, rr_h, _ = h.solve_host(prob.rhs)
     assert it_h == it and np.array_equal(xh, xg)
+    # and so does the split form (u on the device, lambda on the host)
+    u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
+    lam = np.empty(prob.n - prob.n_u)
+    it_s, _, _ = h.solve_split(b, u, lam)
+    assert it_s == it and np.array_equal(u.cpu().numpy(), xg[:prob.n_u]) and np.array_equal(lam, xg[prob.n_u:])
     h.close()
 
 
