@@ -408,9 +408,14 @@ int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launc
 /* Overrides the row mapping of one sparse apply of the cycle, or the smoother fusion of a level (the
  * choices the setup-time autotuner makes when opts.autotune = 1).  level: 0 .. n_levels-1; matrix:
  * 0 = the level's K (with its B1 coupling), 1 = its prolongator P, 2 = its restriction R (P and R:
- * not on the coarsest level), 3 = the CheapSIMPLE sweep's multiplier corrector and B1 update
- * (mapping 0 or -1: two launches, the default; 1: one fused launch of one thread block, which the
- * autotuner picks on levels with few multiplier rows; the same arithmetic either way);
+ * not on the coarsest level), 3 = the form of the CheapSIMPLE sweep's multiplier corrector and B1
+ * update (mapping 0: two launches after the sweep's Jacobi step; 1: one fused launch of one thread
+ * block, which the autotuner picks on levels with few multiplier rows, with the arithmetic of
+ * form 0; 2: split, the interface rows (B1's rows and B2's columns) take the last Jacobi step of
+ * the sweep, the corrector and the B1 update on a second stream beside the Jacobi step of the
+ * other rows, equal to form 0 up to the summation order of the interface rows' K products; -1:
+ * the default: in the FP32 cycle form 2 where the interface rows are at most an eighth of the
+ * level's nodes, else 0);
  * precision: 64 = the FP64 views (the Krylov operator apply and the FP64 cycle), 32 = the FP32
  * cycle (hierarchies set up with precision 32 only); mapping: -1 = the default, 0 = one warp per
  * block row, 1 / 2 = SELL-32 with one / two threads per block row, 3 = the shared-memory staged

@@ -273,7 +273,7 @@ class Hierarchy:
     def set_row_mapping(self, level: int, matrix: str, precision: int, mapping: int):
         """amgc_set_row_mapping: matrix 'K', 'P' or 'R'; mapping -1 default, 0 warp per row,
         1 / 2 SELL threads per row, 3 staged FP32 kernel (level-0 K, precision 32).  matrix 'fuse':
-        the level's smoother fusion, mapping 1 fused, 0 two launches."""
+        the level's smoother form, mapping 0 two launches, 1 fused, 2 split, -1 default."""
         _check(self._lib.amgc_set_row_mapping(self._h, int(level), self.ROW_MATRIX[matrix], int(precision),
                                               int(mapping)), "amgc_set_row_mapping")
 
@@ -375,9 +375,14 @@ class Hierarchy:
             _check(code, "amgc_pdass")
         return act, steps.value, its.value, code
 
-    def solve_host(self, rhs: np.ndarray, stream=None, check: bool = True):
+    def solve_host(self, rhs: np.ndarray, stream=None, check: bool = True, x: np.ndarray = None):
+        """amgc_solve_host; x, when given, is the host output array (float64, contiguous, the size
+        of rhs; page-locked memory makes the device-to-host copy direct), else a new array."""
         rhs = np.ascontiguousarray(rhs, dtype=np.float64)
-        x = np.empty_like(rhs)
+        if x is None:
+            x = np.empty_like(rhs)
+        elif x.dtype != np.float64 or not x.flags.c_contiguous or x.size != rhs.size:
+            raise ValueError("solve_host: x must be a contiguous float64 array of the size of rhs")
         it = C.c_int32(0)
         rr = C.c_double(0.0)
         code = self._lib.amgc_solve_host(self._h, rhs.ctypes.data, x.ctypes.data, C.byref(it), C.byref(rr),

@@ -134,7 +134,7 @@ struct Sell {
 // FP32 mirrors of the cycle data of one level (values only; index arrays are shared).
 struct LevelF32 {
   DBuf<float> K, B1, B2, P, R, Z, Ks, Ps, Rs, jdinv, atinv, pl_w;
-  DBuf<float> x, b, r, t, dlam;
+  DBuf<float> x, b, r, t, dlam, ir_u;
 };
 
 // Non-owning views of one level's cycle data in storage type T.
@@ -166,7 +166,11 @@ struct LevelV {
   BsrV<T> K, B1, B2, P, R;
   SellV<T> Ks, Ps, Rs;
   int kmap = -1, pmap = -1, rmap = -1;   // row mappings (see Level)
-  int fuse = 0;                          // 1: fused single-CTA corrector + B1 update (see Level)
+  int fuse = 0;                          // smoother form, resolved: 0, 1 or 2 (see Level)
+  const int* ir_rows = nullptr;          // interface rows and B2's columns among them (see Level)
+  const int* ir_b2c = nullptr;
+  int n_ir = 0;
+  T* ir_u = nullptr;
   const T* Z = nullptr;
   const double* Sinv = nullptr;    // FP64 in both precisions
   const T* dinv = nullptr;
@@ -212,9 +216,16 @@ struct Level {
   // row mapping of the K, P, R applies per precision (0: FP64, 1: FP32):
   // 0 = warp per row, 1 = SELL one thread per row, 2 = SELL two threads per row, -1 = default
   int kmap[2] = {-1, -1}, pmap[2] = {-1, -1}, rmap[2] = {-1, -1};
-  // smoother fusion per precision: 1 = the sweep's corrector and B1 update in one single-CTA
-  // launch, 0 = two launches (the autotuner's choice; 0 by default)
-  int fuse[2] = {0, 0};
+  // smoother form per precision: 0 = the sweep's corrector and B1 update as two launches after the
+  // Jacobi step, 1 = both in one single-CTA launch, 2 = split (the interface rows' Jacobi step,
+  // the corrector and the B1 update beside the Jacobi step of the other rows), -1 = default (2
+  // where the interface rows are few against the level's rows, else 0)
+  int fuse[2] = {-1, -1};
+  // interface rows: the displacement nodes with B1 entries or B2 columns, ascending; B2's block
+  // columns as positions in that list; the split sweep's interface iterate (FP64 cycle)
+  DBuf<int> ir_rows, ir_b2c;
+  int n_ir = 0;
+  DBuf<double> ir_u;
   DBuf<double> Z;          // nl*9
   DBuf<int> body;          // nn
   DBuf<double> B;          // nullspace nu*6

@@ -535,44 +535,76 @@ static int mapped_apply(const BsrV<T>& A, const SellV<T>& S, int map, const BsrV
 // MODE 0: out_l = g_l - (B2 u)_l + Z_l lam_l                       (residual)
 // MODE 1: d = -Sinv_l (g_l - (B2 u)_l + Z_l lam_l); lam_l += alpha d; out_l = d  (corrector)
 // MODE 2: out_l = (B2 u)_l - Z_l lam_l                             (saddle apply)
-// one multiplier node l (one warp)
-template <int BU, int MODE, class T>
-__device__ __forceinline__ void lm_node(int l, int lane, const int* __restrict__ rp, const int* __restrict__ col,
-                                        const T* __restrict__ val, const T* __restrict__ u, const T* __restrict__ Z,
-                                        const T* __restrict__ g, T* __restrict__ lam, const double* __restrict__ Sinv,
-                                        double alpha, T* __restrict__ out) {
+// Lanes per multiplier node (and per B1 row) of the multiplier-row kernels: a group of G lanes
+// shares a row's blocks (lane-per-block in strides of G), the group sum is an xor butterfly (every
+// lane of the group ends with the same bits: IEEE addition commutes), and the per-component
+// epilogue runs on lanes 0 .. 2 (0 .. BU-1) of the group, so that a warp serves 32 / G rows and
+// the FP64 epilogue costs one warp instruction per step for all of them.
+template <int BU>
+struct RowGroup {
+  static constexpr int G = BU <= 4 ? 4 : 8;
+};
+template <int G, class T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+template <int BR, int BC, int G, class T>
+__device__ __forceinline__ void group_blocks(int64_t b0, int64_t b1, const int* __restrict__ col,
+                                             const T* __restrict__ val, const T* __restrict__ x, int gl,
+                                             T (&acc)[BR]) {
+  for (int64_t b = b0 + gl; b < b1; b += G) {
+    const T* xc = x + (int64_t)__ldg(col + b) * BC;
+    T xv[BC];
+#pragma unroll
+    for (int c = 0; c < BC; ++c) xv[c] = ldg(xc + c);
+    const T* v = val + b * (BR * BC);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int c = 0; c < BC; ++c) acc[r] = fma(ldg(v + r * BC + c), xv[c], acc[r]);
+  }
+}
+// one multiplier node l per group of G lanes (gl: lane in the group); every lane of the warp calls
+// it (the group sums and the exchange of the residual components are warp shuffles), `valid`
+// false for the groups past the last node
+template <int G, int BU, int MODE, class T>
+__device__ __forceinline__ void lm_node(int l, bool valid, int gl, const int* __restrict__ rp,
+                                        const int* __restrict__ col, const T* __restrict__ val,
+                                        const T* __restrict__ u, const T* __restrict__ Z, const T* __restrict__ g,
+                                        T* __restrict__ lam, const double* __restrict__ Sinv, double alpha,
+                                        T* __restrict__ out) {
   T acc[3] = {T(0), T(0), T(0)};
-  lane_blocks<3, BU, T>(rp[l], rp[l + 1], col, val, u, lane, acc);
-  const T bu0 = warp_sum(acc[0]), bu1 = warp_sum(acc[1]), bu2 = warp_sum(acc[2]);
-  if (lane != 0) return;
-  const T* z = Z + (int64_t)l * 9;
-  const T l0 = lam[3 * l], l1 = lam[3 * l + 1], l2 = lam[3 * l + 2];
-  const T zl0 = z[0] * l0 + z[1] * l1 + z[2] * l2;
-  const T zl1 = z[3] * l0 + z[4] * l1 + z[5] * l2;
-  const T zl2 = z[6] * l0 + z[7] * l1 + z[8] * l2;
+  if (valid) group_blocks<3, BU, G, T>(rp[l], rp[l + 1], col, val, u, gl, acc);
+  const T bu0 = group_sum<G>(acc[0]), bu1 = group_sum<G>(acc[1]), bu2 = group_sum<G>(acc[2]);
+  const int c = gl < 3 ? gl : 0;   // lanes 3 .. G-1 of a group mirror component 0 and store nothing
+  const bool st = valid && gl < 3;
+  T lc = T(0), rc = T(0), zl = T(0);
+  const T buc = c == 0 ? bu0 : (c == 1 ? bu1 : bu2);
+  if (valid) {
+    const T* z = Z + (int64_t)l * 9 + 3 * c;
+    const T l0 = lam[3 * (int64_t)l], l1 = lam[3 * (int64_t)l + 1], l2 = lam[3 * (int64_t)l + 2];
+    zl = z[0] * l0 + z[1] * l1 + z[2] * l2;
+    lc = c == 0 ? l0 : (c == 1 ? l1 : l2);
+    rc = g[3 * (int64_t)l + c] - buc + zl;
+  }
   if (MODE == 2) {
-    out[3 * l] = bu0 - zl0;
-    out[3 * l + 1] = bu1 - zl1;
-    out[3 * l + 2] = bu2 - zl2;
+    if (st) out[3 * (int64_t)l + c] = buc - zl;
     return;
   }
-  const T r0 = g[3 * l] - bu0 + zl0, r1 = g[3 * l + 1] - bu1 + zl1, r2 = g[3 * l + 2] - bu2 + zl2;
   if (MODE == 0) {
-    out[3 * l] = r0;
-    out[3 * l + 1] = r1;
-    out[3 * l + 2] = r2;
+    if (st) out[3 * (int64_t)l + c] = rc;
     return;
   }
-  const double* S = Sinv + (int64_t)l * 9;   // FP64 Schur-block inverse
-  const double d0 = -(S[0] * r0 + S[1] * r1 + S[2] * r2);
-  const double d1 = -(S[3] * r0 + S[4] * r1 + S[5] * r2);
-  const double d2 = -(S[6] * r0 + S[7] * r1 + S[8] * r2);
-  lam[3 * l] = (T)(l0 + alpha * d0);
-  lam[3 * l + 1] = (T)(l1 + alpha * d1);
-  lam[3 * l + 2] = (T)(l2 + alpha * d2);
-  out[3 * l] = (T)d0;
-  out[3 * l + 1] = (T)d1;
-  out[3 * l + 2] = (T)d2;
+  const int g0 = (threadIdx.x & 31) & ~(G - 1);   // first lane of the group
+  const T r0 = __shfl_sync(0xffffffffu, rc, g0), r1 = __shfl_sync(0xffffffffu, rc, g0 + 1),
+          r2 = __shfl_sync(0xffffffffu, rc, g0 + 2);
+  if (!st) return;
+  const double* S = Sinv + (int64_t)l * 9 + 3 * c;   // FP64 Schur-block inverse, row c
+  const double d = -(S[0] * r0 + S[1] * r1 + S[2] * r2);
+  lam[3 * (int64_t)l + c] = (T)(lc + alpha * d);
+  out[3 * (int64_t)l + c] = (T)d;
 }
 
 template <int BU, int MODE, class T>
@@ -580,10 +612,18 @@ __global__ void __launch_bounds__(128)
 k_lm(int nl, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
      const T* __restrict__ u, const T* __restrict__ Z, const T* __restrict__ g, T* __restrict__ lam,
      const double* __restrict__ Sinv, double alpha, T* __restrict__ out) {
+  constexpr int G = RowGroup<BU>::G;
   const int lane = threadIdx.x & 31;
-  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (l >= nl) return;
-  lm_node<BU, MODE, T>(l, lane, rp, col, val, u, Z, g, lam, Sinv, alpha, out);
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int first = (int)((gt >> 5) * (32 / G));   // the warp's first node
+  if (first >= nl) return;                         // whole warps only: the groups shuffle
+  const int l = first + lane / G;
+  lm_node<G, BU, MODE, T>(l, l < nl, lane & (G - 1), rp, col, val, u, Z, g, lam, Sinv, alpha, out);
+}
+// grid of the group-per-row kernels: 32 / G rows per warp, 128-thread blocks
+template <int BU>
+static int group_grid(int64_t rows) {
+  return (int)div_up(rows * RowGroup<BU>::G, 128);
 }
 
 template <int MODE, class T>
@@ -591,13 +631,14 @@ static int lm_op(const LevelV<T>& L, const T* u, const T* g, T* lam, double alph
                  bool transposed = false) {
   if (L.nl == 0) return AMGC_OK;
   const int th = 128;
-  const int gl = div_up((int64_t)L.nl * 32, th);
   const BsrV<T>& B = transposed ? L.B1T : L.B2;   // multiplier rows of A: B2; of A^T: B1^T
   const T* Z = transposed ? L.ZT : L.Z;
   if (L.bu == 3)
-    AMGC_LAUNCH(k_lm<3, MODE, T><<<gl, th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g, lam, L.Sinv, alpha, out));
+    AMGC_LAUNCH(k_lm<3, MODE, T><<<group_grid<3>(L.nl), th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g, lam, L.Sinv,
+                                                                    alpha, out));
   else
-    AMGC_LAUNCH(k_lm<6, MODE, T><<<gl, th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g, lam, L.Sinv, alpha, out));
+    AMGC_LAUNCH(k_lm<6, MODE, T><<<group_grid<6>(L.nl), th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g, lam, L.Sinv,
+                                                                    alpha, out));
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
@@ -632,39 +673,126 @@ __global__ void k_jacobi_zero(int64_t n, int64_t nlam, const T* __restrict__ f, 
   if (i < n) y[i] = omega * dinv[i] * f[i];
   if (i < nlam) lam[i] = T(0);
 }
-// u_i -= alpha atinv_i (B1 dlam)_i for row i of B1 (one warp)
-template <int BU, class T>
-__device__ __forceinline__ void b1_row(int i, int lane, const int* __restrict__ rp, const int* __restrict__ col,
-                                       const T* __restrict__ val, const T* __restrict__ dlam,
-                                       const T* __restrict__ atinv, T alpha, T* __restrict__ u) {
+// u_i = uin_i - alpha atinv_i (B1 dlam)_i for row i of B1 (one group of G lanes, see lm_node),
+// with uin = u for the update in place
+template <int G, int BU, class T>
+__device__ __forceinline__ void b1_row(int i, bool valid, int gl, const int* __restrict__ rp,
+                                       const int* __restrict__ col, const T* __restrict__ val,
+                                       const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha,
+                                       const T* uin, T* u) {
   T acc[BU];
 #pragma unroll
   for (int r = 0; r < BU; ++r) acc[r] = T(0);
-  lane_blocks<BU, 3, T>(rp[i], rp[i + 1], col, val, dlam, lane, acc);
+  if (valid) group_blocks<BU, 3, G, T>(rp[i], rp[i + 1], col, val, dlam, gl, acc);
+  T out = T(0);
+#pragma unroll
+  for (int r = 0; r < BU; ++r) {
+    const T v = group_sum<G>(acc[r]);
+    if (gl == r) out = v;
+  }
+  if (valid && gl < BU) {
+    T ui = uin[(int64_t)i * BU + gl];
+    ui -= alpha * atinv[(int64_t)i * BU + gl] * out;
+    u[(int64_t)i * BU + gl] = ui;
+  }
+}
+// the same over the rows of B1 with entries, in place, 32 / G rows per warp
+template <int BU, class T>
+__global__ void __launch_bounds__(128)
+k_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp, const int* __restrict__ col,
+            const T* __restrict__ val, const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha, T* u) {
+  constexpr int G = RowGroup<BU>::G;
+  const int lane = threadIdx.x & 31;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int first = (int)((gt >> 5) * (32 / G));
+  if (first >= nrows) return;
+  const int t = first + lane / G;
+  const bool valid = t < nrows;
+  b1_row<G, BU, T>(valid ? rows[t] : 0, valid, lane & (G - 1), rp, col, val, dlam, atinv, alpha, u, u);
+}
+template <class T>
+static int b1_update(int bu, int nrows, const int* rows, const BsrV<T>& B, const T* dlam, const T* atinv, T alpha, T* u,
+                     cudaStream_t s) {
+  if (nrows == 0) return AMGC_OK;
+  if (bu == 3)
+    AMGC_LAUNCH(k_b1_update<3, T><<<group_grid<3>(nrows), 128, 0, s>>>(nrows, rows, B.rp, B.col, B.val, dlam, atinv,
+                                                                       alpha, u));
+  else
+    AMGC_LAUNCH(k_b1_update<6, T><<<group_grid<6>(nrows), 128, 0, s>>>(nrows, rows, B.rp, B.col, B.val, dlam, atinv,
+                                                                       alpha, u));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  return AMGC_OK;
+}
+// Split sweep (smoother form 2).  The corrector reads the Jacobi iterate only on the interface rows
+// (B2's columns) and the B1 update writes only there (B1's rows), so those rows take their Jacobi
+// step into a compact vector uI on a second stream, where the corrector follows at once, while
+// the Jacobi step of all rows runs on the main stream; after the join the B1 update writes the
+// interface rows' final values over the main step's output.  The arithmetic per row is that of
+// the sequential sweep, the K row's sum in lane-per-block order.
+// uI_t = x_i + omega dinv_i (f_i - K_i x - B1_i lam) for interface row i = rows[t] (one warp)
+template <int BU, class T>
+__global__ void __launch_bounds__(128)
+k_ir_jacobi(int n, const int* __restrict__ rows, const int* __restrict__ krp, const int* __restrict__ kcol,
+            const T* __restrict__ kval, const T* __restrict__ x, const int* __restrict__ brp,
+            const int* __restrict__ bcol, const T* __restrict__ bval, const T* __restrict__ lam,
+            const T* __restrict__ f, const T* __restrict__ dinv, T omega, T* __restrict__ uI) {
+  const int lane = threadIdx.x & 31;
+  const int t = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (t >= n) return;
+  const int i = rows[t];
+  T acc[BU];
+#pragma unroll
+  for (int r = 0; r < BU; ++r) acc[r] = T(0);
+  lane_blocks<BU, BU, T>(krp[i], krp[i + 1], kcol, kval, x, lane, acc);
+  lane_blocks<BU, 3, T>(brp[i], brp[i + 1], bcol, bval, lam, lane, acc);
   T out = T(0);
 #pragma unroll
   for (int r = 0; r < BU; ++r) {
     const T v = warp_sum(acc[r]);
     if (lane == r) out = v;
   }
-  if (lane < BU) u[(int64_t)i * BU + lane] -= alpha * atinv[(int64_t)i * BU + lane] * out;
+  if (lane < BU) {
+    const int64_t o = (int64_t)i * BU + lane;
+    uI[(int64_t)t * BU + lane] = x[o] + omega * dinv[o] * (f[o] - out);
+  }
 }
-// the same over the rows of B1 with entries, one warp per row
+// u_i = uI_t - alpha atinv_i (B1 dlam)_i for interface row i = rows[t] (groups of G lanes, as
+// k_b1_update)
 template <int BU, class T>
 __global__ void __launch_bounds__(128)
-k_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp, const int* __restrict__ col,
-            const T* __restrict__ val, const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha,
-            T* __restrict__ u) {
-  const int lane = threadIdx.x & 31;
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (t >= nrows) return;
-  b1_row<BU, T>(rows[t], lane, rp, col, val, dlam, atinv, alpha, u);
+k_ir_b1(int n, const int* __restrict__ rows, const int* __restrict__ rp, const int* __restrict__ col,
+        const T* __restrict__ val, const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha,
+        const T* __restrict__ uI, T* __restrict__ u) {
+  constexpr int G = RowGroup<BU>::G;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int first = (int)((gt >> 5) * (32 / G));
+  if (first >= n) return;
+  const int t = first + lane / G;
+  const bool valid = t < n;
+  const int i = valid ? rows[t] : 0;
+  T acc[BU];
+#pragma unroll
+  for (int r = 0; r < BU; ++r) acc[r] = T(0);
+  if (valid) group_blocks<BU, 3, G, T>(rp[i], rp[i + 1], col, val, dlam, gl, acc);
+  T out = T(0);
+#pragma unroll
+  for (int r = 0; r < BU; ++r) {
+    const T v = group_sum<G>(acc[r]);
+    if (gl == r) out = v;
+  }
+  if (valid && gl < BU) {
+    T ui = uI[(int64_t)t * BU + gl];
+    ui -= alpha * atinv[(int64_t)i * BU + gl] * out;
+    u[(int64_t)i * BU + gl] = ui;
+  }
 }
 // Fused corrector and B1 update of a CheapSIMPLE sweep in one CTA: the multiplier corrector on
 // every node (as k_lm MODE 1), a block barrier, then the B1 update of every row of B1 with entries
 // (as k_b1_update); the same arithmetic as the two launches, in one launch.  One CTA, so it pays
 // only where a level's multiplier rows are few (the autotuner decides per level).
 constexpr int kFuseThreads = 1024;
+constexpr int kFuseMaxNodes = 2048;   // largest level the autotuner tries the single-CTA form on
 template <int BU, class T>
 __global__ void __launch_bounds__(kFuseThreads)
 k_corrector_b1_fused(int nl, const int* __restrict__ rp2, const int* __restrict__ c2, const T* __restrict__ v2,
@@ -673,10 +801,19 @@ k_corrector_b1_fused(int nl, const int* __restrict__ rp2, const int* __restrict_
                      int nrows, const int* __restrict__ rows, const int* __restrict__ rp1, const int* __restrict__ c1,
                      const T* __restrict__ v1, const T* __restrict__ atinv, T* u) {
   // u_in and u are the same iterate: read by the corrector, updated after the barrier
+  constexpr int G = RowGroup<BU>::G, RW = 32 / G;   // rows per warp
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int l = wid; l < nl; l += nw) lm_node<BU, 1, T>(l, lane, rp2, c2, v2, u_in, Z, g, lam, Sinv, alpha, dlam);
+  const int gl = lane & (G - 1), gi = lane / G;
+  for (int f = wid * RW; f < nl; f += nw * RW) {   // warp-uniform bounds: the groups shuffle
+    const int l = f + gi;
+    lm_node<G, BU, 1, T>(l, l < nl, gl, rp2, c2, v2, u_in, Z, g, lam, Sinv, alpha, dlam);
+  }
   __syncthreads();
-  for (int t = wid; t < nrows; t += nw) b1_row<BU, T>(rows[t], lane, rp1, c1, v1, dlam, atinv, (T)alpha, u);
+  for (int f = wid * RW; f < nrows; f += nw * RW) {
+    const int t = f + gi;
+    const bool valid = t < nrows;
+    b1_row<G, BU, T>(valid ? rows[t] : 0, valid, gl, rp1, c1, v1, dlam, atinv, (T)alpha, u, u);
+  }
 }
 template <class T>
 static int corrector_b1_fused(const LevelV<T>& L, T* u, const T* g, T* lam, double alpha, cudaStream_t s) {
@@ -803,15 +940,17 @@ static double k_apply_bytes(const LevelV<T>& L, int extra_vecs) {
 }
 
 // K apply of level l (MODE of k_rowop), timed when the level is the finest one.
+// Without `with_b1` the multiplier coupling is left out (the split sweep, whose interface rows,
+// the only rows of B1, are recomputed beside it).
 template <int MODE, class T>
 static int k_apply(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* x1, const T* lam, const T* b, const T* x0,
-                   T* y, bool transposed = false) {
+                   T* y, bool transposed = false, bool with_b1 = true) {
   const bool t = l == 0;
   const int kind = sizeof(T) == 8 ? 1 : 2;
   if (t) AMGC_TRY(prof_begin(h, kind));
   // K is symmetric on every level (elasticity and Galerkin products), so A^T shares it;
   // the multiplier coupling of the u rows is B1 for A and B2^T for A^T.
-  const BsrV<T>* B1 = L.nl ? (transposed ? &L.B2T : &L.B1) : nullptr;
+  const BsrV<T>* B1 = (L.nl && with_b1) ? (transposed ? &L.B2T : &L.B1) : nullptr;
   AMGC_TRY((mapped_apply<MODE, T>(L.K, L.Ks, L.kmap, B1, x1, lam, b, x0, L.dinv, L.omega_j, y, h->stream)));
   if (t)
     AMGC_TRY(prof_end(h, kind, k_apply_bytes(L, MODE == 3 ? 3 : (MODE == 2 ? 1 : 0)),
@@ -826,7 +965,11 @@ static int k_apply(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* x1, co
 template <class FMain, class FSide>
 static int fork_join(amgc_hierarchy* h, FMain&& main_fn, FSide&& side_fn) {
   if (!h->side_stream) {
-    AMGC_CUDA_TRY(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+    // the side stream's short kernels get the highest priority, so that their blocks start as soon
+    // as blocks of the long kernel beside them retire
+    int least = 0, greatest = 0;
+    AMGC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    AMGC_CUDA_TRY(cudaStreamCreateWithPriority(&h->side_stream, cudaStreamNonBlocking, greatest));
     AMGC_CUDA_TRY(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
     AMGC_CUDA_TRY(cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
   }
@@ -866,12 +1009,44 @@ static int smooth_sweeps(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* 
   const int th = 256;
   const int J = h->opts.jacobi_sweeps;
   const int steps = sweeps * J;
-  const int gb = div_up((int64_t)L.n_b1_rows * 32, 128);
   T* cur = u;
   int step = 0;
+  const bool split = L.fuse == 2 && L.nl > 0 && L.n_ir > 0;
   for (int k = 0; k < sweeps; ++k) {
+    bool corrected = false;
     for (int j = 0; j < J; ++j, ++step) {
-      if (zero_guess && step == 0) {
+      if (split && j == J - 1 && !(zero_guess && step == 0)) {
+        // the last Jacobi step of the sweep with the corrector and B1 update split off (form 2)
+        T* dst = cur == u ? t : u;
+        const T* src = cur;
+        const T alpha = (T)h->opts.simple_alpha;
+        AMGC_TRY(fork_join(
+            h, [&]() { return k_apply<3, T>(h, L, l, src, lam, f, src, dst, false, false); },
+            [&](cudaStream_t ss) -> int {
+              const int gi = div_up((int64_t)L.n_ir * 32, 128);
+              if (L.bu == 3)
+                AMGC_LAUNCH(k_ir_jacobi<3, T><<<gi, 128, 0, ss>>>(L.n_ir, L.ir_rows, L.K.rp, L.K.col, L.K.val, src,
+                                                                  L.B1.rp, L.B1.col, L.B1.val, lam, f, L.dinv,
+                                                                  (T)L.omega_j, L.ir_u));
+              else
+                AMGC_LAUNCH(k_ir_jacobi<6, T><<<gi, 128, 0, ss>>>(L.n_ir, L.ir_rows, L.K.rp, L.K.col, L.K.val, src,
+                                                                  L.B1.rp, L.B1.col, L.B1.val, lam, f, L.dinv,
+                                                                  (T)L.omega_j, L.ir_u));
+              AMGC_CUDA_TRY(cudaGetLastError());
+              LevelV<T> Li = L;   // B2 with its columns numbered among the interface rows
+              Li.B2.col = L.ir_b2c;
+              return lm_op<1, T>(Li, L.ir_u, g, lam, h->opts.simple_alpha, L.dlam, ss);
+            }));
+        if (L.bu == 3)
+          AMGC_LAUNCH(k_ir_b1<3, T><<<group_grid<3>(L.n_ir), 128, 0, s>>>(L.n_ir, L.ir_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
+                                                       L.atinv, alpha, L.ir_u, dst));
+        else
+          AMGC_LAUNCH(k_ir_b1<6, T><<<group_grid<6>(L.n_ir), 128, 0, s>>>(L.n_ir, L.ir_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
+                                                       L.atinv, alpha, L.ir_u, dst));
+        AMGC_CUDA_TRY(cudaGetLastError());
+        cur = dst;
+        corrected = true;
+      } else if (zero_guess && step == 0) {
         T* dst = ((steps - 1) % 2 == 0) ? u : t;
         const int64_t nlam = 3 * (int64_t)L.nl;
         AMGC_LAUNCH(k_jacobi_zero<T><<<div_up(std::max<int64_t>(nu, nlam), th), th, 0, s>>>(nu, nlam, f, L.dinv,
@@ -884,22 +1059,15 @@ static int smooth_sweeps(amgc_hierarchy* h, const LevelV<T>& L, int l, const T* 
         cur = dst;
       }
     }
+    if (corrected) continue;
     // corrector on the multipliers and the B1 update of the displacements, in place on cur: one
     // fused single-CTA launch where the autotuner found it faster, else two launches
-    if (L.fuse && L.nl > 0) {
+    if (L.fuse == 1 && L.nl > 0) {
       AMGC_TRY(corrector_b1_fused<T>(L, cur, g, lam, h->opts.simple_alpha, s));
       continue;
     }
     AMGC_TRY((lm_op<1, T>(L, cur, g, lam, h->opts.simple_alpha, L.dlam, s)));
-    if (L.n_b1_rows > 0) {
-      if (L.bu == 3)
-        AMGC_LAUNCH(k_b1_update<3, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
-                                                         L.atinv, (T)h->opts.simple_alpha, cur));
-      else
-        AMGC_LAUNCH(k_b1_update<6, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
-                                                         L.atinv, (T)h->opts.simple_alpha, cur));
-      AMGC_CUDA_TRY(cudaGetLastError());
-    }
+    AMGC_TRY(b1_update<T>(L.bu, L.n_b1_rows, L.b1_rows, L.B1, L.dlam, L.atinv, (T)h->opts.simple_alpha, cur, s));
   }
   if (cur != u) {
     AMGC_LAUNCH(k_copy<T><<<div_up(nu, th), th, 0, s>>>(nu, cur, u));
@@ -1285,17 +1453,8 @@ static int tsmooth(amgc_hierarchy* h, const LevelV<double>& L, int l, const doub
     return AMGC_OK;
   }
   AMGC_LAUNCH(k_axpy_dinv<<<div_up(nu, th), th, 0, s>>>(nu, e, L.dinv, L.omega_j, x));
-  if (L.n_b2t_rows > 0) {
-    const int gb = div_up((int64_t)L.n_b2t_rows * 32, 128);
-    if (L.bu == 3)
-      AMGC_LAUNCH(k_b1_update<3, double><<<gb, 128, 0, s>>>(L.n_b2t_rows, L.b2t_rows, L.B2T.rp, L.B2T.col, L.B2T.val,
-                                                            L.dlam, L.dinv, L.omega_j, x));
-    else
-      AMGC_LAUNCH(k_b1_update<6, double><<<gb, 128, 0, s>>>(L.n_b2t_rows, L.b2t_rows, L.B2T.rp, L.B2T.col, L.B2T.val,
-                                                            L.dlam, L.dinv, L.omega_j, x));
-  }
   AMGC_CUDA_TRY(cudaGetLastError());
-  return AMGC_OK;
+  return b1_update<double>(L.bu, L.n_b2t_rows, L.b2t_rows, L.B2T, L.dlam, L.dinv, L.omega_j, x, s);
 }
 
 static int vcycle_transposed(amgc_hierarchy* h, int l, const double* y, double* x) {
@@ -1574,10 +1733,8 @@ static int nested_apply(amgc_hierarchy* h, const double* r, double* z) {
     AMGC_TRY((lm_op<0, double>(L, u, g, lam, 0.0, rl, s)));                   // g - B2 u_h + Z lam
     AMGC_LAUNCH(k_gemv<double><<<div_up((int64_t)nl3 * 32, th), th, 0, s>>>(nl3, h->nest_Sinv.p, rl, w));
     AMGC_LAUNCH(k_axpy<<<div_up(nl3, th), th, 0, s>>>(nl3, -om, w, lam));     // lam += omega dlam, dlam = -w
-    if (L.n_b1_rows > 0)                                                       // u = u_h + omega A~^-1 B1 w
-      AMGC_LAUNCH(k_b1_update<3, double><<<div_up((int64_t)L.n_b1_rows * 32, 128), 128, 0, s>>>(
-          L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, w, L.atinv, -om, u));
-    AMGC_CUDA_TRY(cudaGetLastError());
+    AMGC_CUDA_TRY(cudaGetLastError());                                         // u = u_h + omega A~^-1 B1 w
+    AMGC_TRY(b1_update<double>(3, L.n_b1_rows, L.b1_rows, L.B1, w, L.atinv, -om, u, s));
   }
   return AMGC_OK;
 }
@@ -1646,16 +1803,70 @@ static LevelV<T> common_view(const Level& L) {
   v.nn = L.nn; v.bu = L.bu; v.nl = L.nl; v.omega_j = 1.0;
   v.Sinv = L.Sinv.p; v.lagg = L.lagg.p; v.rl_ptr = L.rl_ptr.p; v.rl_idx = L.rl_idx.p;
   v.b1_rows = L.b1_rows.p; v.n_b1_rows = L.n_b1_rows; v.Ainv = L.Ainv.p;
+  v.ir_rows = L.ir_rows.p; v.ir_b2c = L.ir_b2c.p; v.n_ir = L.n_ir;
   v.c_inst = L.c_inst.p; v.c_loc = L.c_loc.p; v.c_glob = L.c_glob.p; v.c_goff = L.c_goff.p; v.c_doff = L.c_doff.p;
   return v;
 }
 
+// Interface rows of a level (see Level::ir_rows): flags on B1's rows with entries and on B2's
+// block columns, an exclusive scan for the positions, the ascending list and B2's columns mapped
+// to positions.
+__global__ void k_ir_mark_rows(int nn, const int* __restrict__ rp, int* __restrict__ mark) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nn) mark[i] = rp[i + 1] > rp[i] ? 1 : 0;
+}
+__global__ void k_ir_mark_cols(int64_t nnzb, const int* __restrict__ col, int* __restrict__ mark) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nnzb) mark[col[e]] = 1;
+}
+__global__ void k_ir_list(int nn, const int* __restrict__ mark, const int* __restrict__ pos, int* __restrict__ rows) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nn && mark[i]) rows[pos[i]] = i;
+}
+__global__ void k_ir_remap(int64_t nnzb, const int* __restrict__ col, const int* __restrict__ pos, int* __restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nnzb) out[e] = pos[col[e]];
+}
+static int ir_setup(amgc_hierarchy* h, Level& L) {
+  cudaStream_t s = h->stream;
+  L.n_ir = 0;
+  if (L.nl == 0 || L.nn == 0) return AMGC_OK;
+  DBuf<int> mark, pos;
+  AMGC_TRY(mark.alloc(L.nn));
+  AMGC_TRY(pos.alloc(L.nn));
+  AMGC_LAUNCH(k_ir_mark_rows<<<div_up(L.nn, 256), 256, 0, s>>>(L.nn, L.B1.rowptr.p, mark.p));
+  if (L.B2.nnzb > 0)
+    AMGC_LAUNCH(k_ir_mark_cols<<<div_up(L.B2.nnzb, 256), 256, 0, s>>>(L.B2.nnzb, L.B2.col.p, mark.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  int n = 0;
+  AMGC_TRY(exclusive_scan(mark.p, pos.p, L.nn, s, &n));
+  AMGC_TRY(L.ir_rows.alloc(std::max(n, 1)));
+  AMGC_TRY(L.ir_b2c.alloc(std::max<int64_t>(L.B2.nnzb, 1)));
+  AMGC_LAUNCH(k_ir_list<<<div_up(L.nn, 256), 256, 0, s>>>(L.nn, mark.p, pos.p, L.ir_rows.p));
+  if (L.B2.nnzb > 0)
+    AMGC_LAUNCH(k_ir_remap<<<div_up(L.B2.nnzb, 256), 256, 0, s>>>(L.B2.nnzb, L.B2.col.p, pos.p, L.ir_b2c.p));
+  AMGC_CUDA_TRY(cudaGetLastError());
+  AMGC_TRY(L.ir_u.alloc((size_t)std::max(n, 1) * L.bu));
+  L.n_ir = n;
+  return AMGC_OK;
+}
+// The smoother form a view runs: the level's setting, or by default, in the FP32 cycle, the split
+// sweep where the interface rows are at most an eighth of the level's rows (the memory-bound step
+// beside them is long enough to hide the corrector), else two launches.  The FP64 step is bound by
+// the FP64 FMA rate, which the interface rows' step beside it only shares: two launches.
+static int resolve_form(const Level& L, int f, bool fp32) {
+  if (f >= 0) return f;
+  return (fp32 && L.n_ir > 0 && (int64_t)L.nn >= 8 * (int64_t)L.n_ir) ? 2 : 0;
+}
+
 int make_views(amgc_hierarchy* h) {
+  drop_cycle_graphs(h);   // captured cycles hold the pointers of the views rebuilt here
   h->v64.clear();
   h->v32.clear();
   const int nlev = (int)h->L.size();
   for (int l = 0; l < nlev; ++l) {
     Level& L = h->L[l];
+    AMGC_TRY(ir_setup(h, L));
     LevelV<double> v = common_view<double>(L);
     v.K = bview<double>(L.K, L.K.val.p);
     v.B1 = bview<double>(L.B1, L.B1.val.p);
@@ -1665,7 +1876,8 @@ int make_views(amgc_hierarchy* h) {
     v.Ks = sview<double>(L.Ks, L.Ks.val.p);
     v.Ps = sview<double>(L.Ps, L.Ps.val.p);
     v.Rs = sview<double>(L.Rs, L.Rs.val.p);
-    v.kmap = L.kmap[0]; v.pmap = L.pmap[0]; v.rmap = L.rmap[0]; v.fuse = L.fuse[0];
+    v.kmap = L.kmap[0]; v.pmap = L.pmap[0]; v.rmap = L.rmap[0]; v.fuse = resolve_form(L, L.fuse[0], false);
+    v.ir_u = L.ir_u.p;
     v.Z = L.Z.p; v.dinv = L.jdinv.p; v.atinv = L.atinv.p; v.pl_w = L.pl_w.p;
     v.x = L.x.p; v.b = L.b.p; v.r = L.r.p; v.t = L.t.p; v.dlam = L.dlam.p; v.tsw = L.tsw.p;
     if (L.has_transposed) {
@@ -1704,6 +1916,7 @@ int make_views(amgc_hierarchy* h) {
     AMGC_TRY(F.r.alloc(n));
     AMGC_TRY(F.t.alloc(n));
     AMGC_TRY(F.dlam.alloc(std::max(3 * L.nl, 1)));
+    AMGC_TRY(F.ir_u.alloc((size_t)std::max(L.n_ir, 1) * L.bu));
     LevelV<float> v = common_view<float>(L);
     v.K = bview<float>(L.K, F.K.p);
     v.B1 = bview<float>(L.B1, F.B1.p);
@@ -1719,7 +1932,8 @@ int make_views(amgc_hierarchy* h) {
     }
     v.Ps = sview<float>(L.Ps, F.Ps.p);
     v.Rs = sview<float>(L.Rs, F.Rs.p);
-    v.kmap = L.kmap[1]; v.pmap = L.pmap[1]; v.rmap = L.rmap[1]; v.fuse = L.fuse[1];
+    v.kmap = L.kmap[1]; v.pmap = L.pmap[1]; v.rmap = L.rmap[1]; v.fuse = resolve_form(L, L.fuse[1], true);
+    v.ir_u = F.ir_u.p;
     v.Z = F.Z.p; v.dinv = F.jdinv.p; v.atinv = F.atinv.p; v.pl_w = F.pl_w.p;
     v.x = F.x.p; v.b = F.b.p; v.r = F.r.p; v.t = F.t.p; v.dlam = F.dlam.p;
     h->v32.push_back(v);
@@ -1746,17 +1960,18 @@ void drop_cycle_graphs(amgc_hierarchy* h) {
 int set_row_mapping(amgc_hierarchy* h, int level, int matrix, int precision, int mapping) {
   const int nlev = (int)h->L.size();
   if (level < 0 || level >= nlev || matrix < 0 || matrix > 3 || (precision != 64 && precision != 32) ||
-      mapping < -1 || mapping > 3 || (matrix > 0 && level == nlev - 1) || (matrix == 3 && mapping > 1)) {
+      mapping < -1 || mapping > 3 || (matrix > 0 && matrix < 3 && level == nlev - 1) || (matrix == 3 && mapping > 2)) {
     set_error("amgc_set_row_mapping: invalid level, matrix, precision or mapping");
     return AMGC_EINVAL;
   }
-  if (matrix == 3) {   // the smoother fusion of the level: 0 (or -1) two launches, 1 fused
+  if (matrix == 3) {   // the smoother form of the level: -1 default, 0 two launches, 1 fused, 2 split
     if (precision == 32 && h->opts.precision != 32) {
       set_error("amgc_set_row_mapping: the hierarchy has no FP32 cycle (precision 64)");
       return AMGC_EINVAL;
     }
-    const int f = mapping == 1 ? 1 : 0;
-    h->L[level].fuse[precision == 32 ? 1 : 0] = f;
+    Level& L = h->L[level];
+    L.fuse[precision == 32 ? 1 : 0] = mapping;
+    const int f = resolve_form(L, mapping, precision == 32);
     if (precision == 64) h->v64[level].fuse = f;
     else h->v32[level].fuse = f;
     drop_cycle_graphs(h);
@@ -1844,7 +2059,9 @@ static int tune_one(amgc_hierarchy* h, const BsrV<T>& A, const SellV<T>& S, cons
 template <class T>
 static int tune_fuse(amgc_hierarchy* h, const LevelV<T>& L, int* fuse) {
   *fuse = 0;
-  if (L.nl == 0) return AMGC_OK;
+  // one CTA walks every multiplier node and B1 row: beyond a few thousand of them the grid-wide
+  // two-launch form always wins, and timing the single-CTA form would only lengthen the setup
+  if (L.nl == 0 || L.nl > kFuseMaxNodes || L.n_b1_rows > 4 * kFuseMaxNodes) return AMGC_OK;
   cudaStream_t s = h->stream;
   cudaEvent_t e0, e1, e2, e3;
   AMGC_CUDA_TRY(cudaEventCreate(&e0));
@@ -1854,19 +2071,9 @@ static int tune_fuse(amgc_hierarchy* h, const LevelV<T>& L, int* fuse) {
   T* u = L.x;
   T* lam = L.x + L.nu();
   const T* g = L.b + L.nu();
-  const int gb = div_up((int64_t)L.n_b1_rows * 32, 128);
   auto separate = [&]() -> int {
     AMGC_TRY((lm_op<1, T>(L, u, g, lam, h->opts.simple_alpha, L.dlam, s)));
-    if (L.n_b1_rows > 0) {
-      if (L.bu == 3)
-        AMGC_LAUNCH(k_b1_update<3, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
-                                                         L.atinv, (T)h->opts.simple_alpha, u));
-      else
-        AMGC_LAUNCH(k_b1_update<6, T><<<gb, 128, 0, s>>>(L.n_b1_rows, L.b1_rows, L.B1.rp, L.B1.col, L.B1.val, L.dlam,
-                                                         L.atinv, (T)h->opts.simple_alpha, u));
-    }
-    AMGC_CUDA_TRY(cudaGetLastError());
-    return AMGC_OK;
+    return b1_update<T>(L.bu, L.n_b1_rows, L.b1_rows, L.B1, L.dlam, L.atinv, (T)h->opts.simple_alpha, u, s);
   };
   AMGC_TRY(separate());
   AMGC_CUDA_TRY(cudaEventRecord(e0, s));
@@ -1905,8 +2112,8 @@ static int tune_views(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int pidx, bo
       AMGC_TRY((tune_one<0, T>(h, L.R, L.Rs, nullptr, L.r, nullptr, nullptr, nullptr, C.b, &rm)));
       int fz = 0;
       AMGC_TRY(tune_fuse<T>(h, L, &fz));
-      L.fuse = fz;
-      LL.fuse[pidx] = fz;
+      LL.fuse[pidx] = fz ? 1 : -1;   // the fused form where it won, else the default form
+      L.fuse = resolve_form(LL, LL.fuse[pidx], pidx == 1);
     }
     L.kmap = km; L.pmap = pm; L.rmap = rm;
     LL.kmap[pidx] = km; LL.pmap[pidx] = pm; LL.rmap[pidx] = rm;

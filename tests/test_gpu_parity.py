@@ -137,6 +137,9 @@ def test_hierarchy_vcycle_and_solve_match_oracle(case):
     # host-buffer entry point gives the same solution
     xh, it_h, rr_h, _ = h.solve_host(prob.rhs)
     assert it_h == it and np.array_equal(xh, xg)
+    xp = torch.empty(prob.n, dtype=torch.float64).pin_memory()   # caller-owned page-locked output
+    _, it_p, _, _ = h.solve_host(prob.rhs, x=xp.numpy())
+    assert it_p == it and np.array_equal(xp.numpy(), xg)
     # and so does the split form (u on the device, lambda on the host)
     u = torch.empty(prob.n_u, dtype=torch.float64, device="cuda")
     lam = np.empty(prob.n - prob.n_u)
@@ -258,27 +261,36 @@ def test_fp32_autotuned_mappings_give_the_same_cycle():
 
 
 @pytest.mark.parametrize("precision", [64, 32])
-def test_smoother_fusion_gives_the_same_cycle(precision):
-    """The fused single-CTA corrector + B1 update (the autotuner's smoother-fusion choice) runs the
-    same arithmetic as the two launches: the same bits, and the oracle's cycle."""
+def test_smoother_forms_give_the_same_cycle(precision):
+    """The sweep's corrector + B1 update as two launches (form 0), fused into one single-CTA launch
+    (form 1, the same arithmetic: the same bits) and split onto a second stream beside the Jacobi
+    step (form 2, the interface rows' K products summed in another order): the oracle's cycle in
+    every form, and with the default and the autotuned forms."""
     prob = two_block_problem(master_n=(13, 12, 11), slave_n=(10, 11, 9), E_slave=10.0, tilt_deg=5.0, seed=11,
                              active_fraction=0.6)
     opts = dict(levels_max=4, coarse_max_rows=200, transfer=1, smoother_sweeps=2)
     h = amgc.setup(prob, precision=precision, **opts)
     r = torch.from_numpy(np.random.default_rng(9).standard_normal(prob.n)).cuda()
-    z0, z1 = torch.empty_like(r), torch.empty_like(r)
-    h.vcycle(r, z0)
     nlev = h.stats()["n_levels"]
-    for l in range(nlev - 1):
-        h.set_row_mapping(l, "fuse", precision, 1)
-    h.vcycle(r, z1)
-    assert torch.equal(z0, z1)
+    z = {}
+    for form in (-1, 0, 1, 2):
+        for l in range(nlev - 1):
+            h.set_row_mapping(l, "fuse", precision, form)
+        z[form] = torch.empty_like(r)
+        h.vcycle(r, z[form])
+    assert torch.equal(z[0], z[1])
+    tight = 1e-13 if precision == 64 else 1e-5
+    for form in (2, -1):
+        assert (torch.linalg.norm(z[form] - z[0]) / torch.linalg.norm(z[0])).item() <= tight, form
+    assert not torch.equal(z[2], z[0]), "the split sweep ran (level 0 sums its interface rows in another order)"
     ref = oracle_setup(prob, Options(**opts))
     zr = ref.vcycle(r.cpu().numpy())
-    assert rel(z1.cpu().numpy(), zr) <= (RTOL if precision == 64 else 1e-4)
+    for form in (0, 2, -1):
+        assert rel(z[form].cpu().numpy(), zr) <= (RTOL if precision == 64 else 1e-4), form
     h.close()
-    # the autotuned hierarchy (row mappings and fusion chosen by timing) gives the oracle's cycle too
+    # the autotuned hierarchy (row mappings and forms chosen by timing) gives the oracle's cycle too
     ht = amgc.setup(prob, precision=precision, autotune=1, **opts)
+    z1 = torch.empty_like(r)
     ht.vcycle(r, z1)
     assert rel(z1.cpu().numpy(), zr) <= (1e-12 if precision == 64 else 1e-4)
     ht.close()
