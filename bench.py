@@ -594,7 +594,7 @@ def profile_run(cfg: int, precisions=(64, 32)):
     from paper_1912_09056_gb300 import amgc
     from paper_1912_09056_gb300.problem import workload
     prob = workload(cfg)
-    opts = OPTS if cfg == WORKLOAD else dict(levels_max=10, coarse_max_rows=5000, transfer=1)
+    opts = OPTS   # the bench's hierarchy options on every workload
     b = torch.from_numpy(prob.rhs).cuda()
     for precision in precisions:
         h = amgc.setup(prob, amgc.default_options(precision=precision, **opts))

@@ -414,8 +414,7 @@ int amgc_profile_read(struct amgc_hierarchy* h, double* total_ms, int64_t* launc
  * form 0; 2: split, the interface rows (B1's rows and B2's columns) take the last Jacobi step of
  * the sweep, the corrector and the B1 update on a second stream beside the Jacobi step of the
  * other rows, equal to form 0 up to the summation order of the interface rows' K products; -1:
- * the default: in the FP32 cycle form 2 where the interface rows are at most an eighth of the
- * level's nodes, else 0);
+ * the default, form 0; the autotuner times the forms a level has and keeps the fastest);
  * precision: 64 = the FP64 views (the Krylov operator apply and the FP64 cycle), 32 = the FP32
  * cycle (hierarchies set up with precision 32 only); mapping: -1 = the default, 0 = one warp per
  * block row, 1 / 2 = SELL-32 with one / two threads per block row, 3 = the shared-memory staged

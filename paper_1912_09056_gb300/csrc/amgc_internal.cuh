@@ -218,8 +218,8 @@ struct Level {
   int kmap[2] = {-1, -1}, pmap[2] = {-1, -1}, rmap[2] = {-1, -1};
   // smoother form per precision: 0 = the sweep's corrector and B1 update as two launches after the
   // Jacobi step, 1 = both in one single-CTA launch, 2 = split (the interface rows' Jacobi step,
-  // the corrector and the B1 update beside the Jacobi step of the other rows), -1 = default (2
-  // where the interface rows are few against the level's rows, else 0)
+  // the corrector and the B1 update beside the Jacobi step of the other rows), -1 = default (0);
+  // the autotuner's choice where it ran
   int fuse[2] = {-1, -1};
   // interface rows: the displacement nodes with B1 entries or B2 columns, ascending; B2's block
   // columns as positions in that list; the split sweep's interface iterate (FP64 cycle)

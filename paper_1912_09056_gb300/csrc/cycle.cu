@@ -554,6 +554,7 @@ template <int BR, int BC, int G, class T>
 __device__ __forceinline__ void group_blocks(int64_t b0, int64_t b1, const int* __restrict__ col,
                                              const T* __restrict__ val, const T* __restrict__ x, int gl,
                                              T (&acc)[BR]) {
+#pragma unroll 2
   for (int64_t b = b0 + gl; b < b1; b += G) {
     const T* xc = x + (int64_t)__ldg(col + b) * BC;
     T xv[BC];
@@ -575,24 +576,41 @@ __device__ __forceinline__ void lm_node(int l, bool valid, int gl, const int* __
                                         const T* __restrict__ u, const T* __restrict__ Z, const T* __restrict__ g,
                                         T* __restrict__ lam, const double* __restrict__ Sinv, double alpha,
                                         T* __restrict__ out) {
-  T acc[3] = {T(0), T(0), T(0)};
-  if (valid) group_blocks<3, BU, G, T>(rp[l], rp[l + 1], col, val, u, gl, acc);
-  const T bu0 = group_sum<G>(acc[0]), bu1 = group_sum<G>(acc[1]), bu2 = group_sum<G>(acc[2]);
+  // the loads that do not depend on the row's blocks go first, so that their latencies overlap
   const int c = gl < 3 ? gl : 0;   // lanes 3 .. G-1 of a group mirror component 0 and store nothing
   const bool st = valid && gl < 3;
-  T lc = T(0), rc = T(0), zl = T(0);
-  const T buc = c == 0 ? bu0 : (c == 1 ? bu1 : bu2);
+  int b0 = 0, b1 = 0;
+  T z0 = T(0), z1 = T(0), z2 = T(0), l0 = T(0), l1 = T(0), l2 = T(0), gc = T(0);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   if (valid) {
+    b0 = rp[l];
+    b1 = rp[l + 1];
     const T* z = Z + (int64_t)l * 9 + 3 * c;
-    const T l0 = lam[3 * (int64_t)l], l1 = lam[3 * (int64_t)l + 1], l2 = lam[3 * (int64_t)l + 2];
-    zl = z[0] * l0 + z[1] * l1 + z[2] * l2;
-    lc = c == 0 ? l0 : (c == 1 ? l1 : l2);
-    rc = g[3 * (int64_t)l + c] - buc + zl;
+    z0 = z[0];
+    z1 = z[1];
+    z2 = z[2];
+    l0 = lam[3 * (int64_t)l];
+    l1 = lam[3 * (int64_t)l + 1];
+    l2 = lam[3 * (int64_t)l + 2];
+    if (MODE != 2) gc = g[3 * (int64_t)l + c];
+    if (MODE == 1) {
+      const double* S = Sinv + (int64_t)l * 9 + 3 * c;   // FP64 Schur-block inverse, row c
+      s0 = S[0];
+      s1 = S[1];
+      s2 = S[2];
+    }
   }
+  T acc[3] = {T(0), T(0), T(0)};
+  if (valid) group_blocks<3, BU, G, T>(b0, b1, col, val, u, gl, acc);
+  const T bu0 = group_sum<G>(acc[0]), bu1 = group_sum<G>(acc[1]), bu2 = group_sum<G>(acc[2]);
+  const T buc = c == 0 ? bu0 : (c == 1 ? bu1 : bu2);
+  const T zl = z0 * l0 + z1 * l1 + z2 * l2;
+  const T lc = c == 0 ? l0 : (c == 1 ? l1 : l2);
   if (MODE == 2) {
     if (st) out[3 * (int64_t)l + c] = buc - zl;
     return;
   }
+  const T rc = gc - buc + zl;
   if (MODE == 0) {
     if (st) out[3 * (int64_t)l + c] = rc;
     return;
@@ -601,8 +619,7 @@ __device__ __forceinline__ void lm_node(int l, bool valid, int gl, const int* __
   const T r0 = __shfl_sync(0xffffffffu, rc, g0), r1 = __shfl_sync(0xffffffffu, rc, g0 + 1),
           r2 = __shfl_sync(0xffffffffu, rc, g0 + 2);
   if (!st) return;
-  const double* S = Sinv + (int64_t)l * 9 + 3 * c;   // FP64 Schur-block inverse, row c
-  const double d = -(S[0] * r0 + S[1] * r1 + S[2] * r2);
+  const double d = -(s0 * r0 + s1 * r1 + s2 * r2);
   lam[3 * (int64_t)l + c] = (T)(lc + alpha * d);
   out[3 * (int64_t)l + c] = (T)d;
 }
@@ -680,19 +697,29 @@ __device__ __forceinline__ void b1_row(int i, bool valid, int gl, const int* __r
                                        const int* __restrict__ col, const T* __restrict__ val,
                                        const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha,
                                        const T* uin, T* u) {
+  const bool st = valid && gl < BU;
+  int b0 = 0, b1 = 0;
+  T ui = T(0), ai = T(0);
+  if (valid) {
+    b0 = rp[i];
+    b1 = rp[i + 1];
+  }
+  if (st) {   // independent of the row's blocks: issued before them
+    ui = uin[(int64_t)i * BU + gl];
+    ai = atinv[(int64_t)i * BU + gl];
+  }
   T acc[BU];
 #pragma unroll
   for (int r = 0; r < BU; ++r) acc[r] = T(0);
-  if (valid) group_blocks<BU, 3, G, T>(rp[i], rp[i + 1], col, val, dlam, gl, acc);
+  if (valid) group_blocks<BU, 3, G, T>(b0, b1, col, val, dlam, gl, acc);
   T out = T(0);
 #pragma unroll
   for (int r = 0; r < BU; ++r) {
     const T v = group_sum<G>(acc[r]);
     if (gl == r) out = v;
   }
-  if (valid && gl < BU) {
-    T ui = uin[(int64_t)i * BU + gl];
-    ui -= alpha * atinv[(int64_t)i * BU + gl] * out;
+  if (st) {
+    ui -= alpha * ai * out;
     u[(int64_t)i * BU + gl] = ui;
   }
 }
@@ -1850,14 +1877,12 @@ static int ir_setup(amgc_hierarchy* h, Level& L) {
   L.n_ir = n;
   return AMGC_OK;
 }
-// The smoother form a view runs: the level's setting, or by default, in the FP32 cycle, the split
-// sweep where the interface rows are at most an eighth of the level's rows (the memory-bound step
-// beside them is long enough to hide the corrector), else two launches.  The FP64 step is bound by
-// the FP64 FMA rate, which the interface rows' step beside it only shares: two launches.
-static int resolve_form(const Level& L, int f, bool fp32) {
-  if (f >= 0) return f;
-  return (fp32 && L.n_ir > 0 && (int64_t)L.nn >= 8 * (int64_t)L.n_ir) ? 2 : 0;
-}
+// The smoother form a view runs: the level's setting, by default two launches.  (With the
+// multiplier-row kernels on lane groups the corrector and B1 update are short enough that the
+// split sweep does not pay by default on the large two-block workload: the FP64 step beside it
+// shares the FP64 FMA rate, and the FP32 step gains less than the fork and join cost; the
+// autotuner times the forms per level.)
+static int resolve_form(int f) { return f >= 0 ? f : 0; }
 
 int make_views(amgc_hierarchy* h) {
   drop_cycle_graphs(h);   // captured cycles hold the pointers of the views rebuilt here
@@ -1876,7 +1901,7 @@ int make_views(amgc_hierarchy* h) {
     v.Ks = sview<double>(L.Ks, L.Ks.val.p);
     v.Ps = sview<double>(L.Ps, L.Ps.val.p);
     v.Rs = sview<double>(L.Rs, L.Rs.val.p);
-    v.kmap = L.kmap[0]; v.pmap = L.pmap[0]; v.rmap = L.rmap[0]; v.fuse = resolve_form(L, L.fuse[0], false);
+    v.kmap = L.kmap[0]; v.pmap = L.pmap[0]; v.rmap = L.rmap[0]; v.fuse = resolve_form(L.fuse[0]);
     v.ir_u = L.ir_u.p;
     v.Z = L.Z.p; v.dinv = L.jdinv.p; v.atinv = L.atinv.p; v.pl_w = L.pl_w.p;
     v.x = L.x.p; v.b = L.b.p; v.r = L.r.p; v.t = L.t.p; v.dlam = L.dlam.p; v.tsw = L.tsw.p;
@@ -1932,7 +1957,7 @@ int make_views(amgc_hierarchy* h) {
     }
     v.Ps = sview<float>(L.Ps, F.Ps.p);
     v.Rs = sview<float>(L.Rs, F.Rs.p);
-    v.kmap = L.kmap[1]; v.pmap = L.pmap[1]; v.rmap = L.rmap[1]; v.fuse = resolve_form(L, L.fuse[1], true);
+    v.kmap = L.kmap[1]; v.pmap = L.pmap[1]; v.rmap = L.rmap[1]; v.fuse = resolve_form(L.fuse[1]);
     v.ir_u = F.ir_u.p;
     v.Z = F.Z.p; v.dinv = F.jdinv.p; v.atinv = F.atinv.p; v.pl_w = F.pl_w.p;
     v.x = F.x.p; v.b = F.b.p; v.r = F.r.p; v.t = F.t.p; v.dlam = F.dlam.p;
@@ -1971,7 +1996,7 @@ int set_row_mapping(amgc_hierarchy* h, int level, int matrix, int precision, int
     }
     Level& L = h->L[level];
     L.fuse[precision == 32 ? 1 : 0] = mapping;
-    const int f = resolve_form(L, mapping, precision == 32);
+    const int f = resolve_form(mapping);
     if (precision == 64) h->v64[level].fuse = f;
     else h->v32[level].fuse = f;
     drop_cycle_graphs(h);
@@ -2053,46 +2078,42 @@ static int tune_one(amgc_hierarchy* h, const BsrV<T>& A, const SellV<T>& S, cons
   return AMGC_OK;
 }
 
-// Times a sweep's corrector + B1 update as two launches and as the fused single-CTA launch
-// (1 warm-up, 3 timed, CUDA events on the hierarchy's stream) and keeps the faster; the work
-// vectors hold finite values, the results are not used.
+// Times one CheapSIMPLE sweep of the level in each smoother form it has (0: two launches after
+// the Jacobi step; 1: the fused single-CTA launch, tried on levels with few multiplier rows; 2:
+// the split sweep, where the level has interface rows) with 1 warm-up and 3 timed sweeps (CUDA
+// events on the hierarchy's stream) and keeps the fastest.  The work vectors hold finite values;
+// the results are not used.
 template <class T>
-static int tune_fuse(amgc_hierarchy* h, const LevelV<T>& L, int* fuse) {
-  *fuse = 0;
+static int tune_form(amgc_hierarchy* h, const LevelV<T>& L, int l, int* form) {
+  *form = 0;
+  if (L.nl == 0 || h->smoother_kind != 0) return AMGC_OK;
   // one CTA walks every multiplier node and B1 row: beyond a few thousand of them the grid-wide
-  // two-launch form always wins, and timing the single-CTA form would only lengthen the setup
-  if (L.nl == 0 || L.nl > kFuseMaxNodes || L.n_b1_rows > 4 * kFuseMaxNodes) return AMGC_OK;
+  // forms always win, and timing the single-CTA form would only lengthen the setup
+  const bool small = L.nl <= kFuseMaxNodes && L.n_b1_rows <= 4 * kFuseMaxNodes;
   cudaStream_t s = h->stream;
-  cudaEvent_t e0, e1, e2, e3;
+  cudaEvent_t e0, e1;
   AMGC_CUDA_TRY(cudaEventCreate(&e0));
   AMGC_CUDA_TRY(cudaEventCreate(&e1));
-  AMGC_CUDA_TRY(cudaEventCreate(&e2));
-  AMGC_CUDA_TRY(cudaEventCreate(&e3));
-  T* u = L.x;
-  T* lam = L.x + L.nu();
-  const T* g = L.b + L.nu();
-  auto separate = [&]() -> int {
-    AMGC_TRY((lm_op<1, T>(L, u, g, lam, h->opts.simple_alpha, L.dlam, s)));
-    return b1_update<T>(L.bu, L.n_b1_rows, L.b1_rows, L.B1, L.dlam, L.atinv, (T)h->opts.simple_alpha, u, s);
-  };
-  AMGC_TRY(separate());
-  AMGC_CUDA_TRY(cudaEventRecord(e0, s));
-  for (int rep = 0; rep < 3; ++rep) AMGC_TRY(separate());
-  AMGC_CUDA_TRY(cudaEventRecord(e1, s));
-  for (int rep = 0; rep < 4; ++rep) {
-    if (rep == 1) AMGC_CUDA_TRY(cudaEventRecord(e2, s));
-    AMGC_TRY(corrector_b1_fused<T>(L, u, g, lam, h->opts.simple_alpha, s));
+  float best = 1e30f;
+  for (int cand = 0; cand < 3; ++cand) {
+    if ((cand == 1 && !small) || (cand == 2 && L.n_ir == 0)) continue;
+    LevelV<T> Lc = L;
+    Lc.fuse = cand;
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) AMGC_CUDA_TRY(cudaEventRecord(e0, s));
+      AMGC_TRY(smooth_sweeps<T>(h, Lc, l, L.b, L.x, 1, false));
+    }
+    AMGC_CUDA_TRY(cudaEventRecord(e1, s));
+    AMGC_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMGC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      *form = cand;
+    }
   }
-  AMGC_CUDA_TRY(cudaEventRecord(e3, s));
-  AMGC_CUDA_TRY(cudaEventSynchronize(e3));
-  float t_sep = 0.f, t_fused = 0.f;
-  AMGC_CUDA_TRY(cudaEventElapsedTime(&t_sep, e0, e1));
-  AMGC_CUDA_TRY(cudaEventElapsedTime(&t_fused, e2, e3));
-  *fuse = t_fused < t_sep ? 1 : 0;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaEventDestroy(e2);
-  cudaEventDestroy(e3);
   return AMGC_OK;
 }
 
@@ -2110,12 +2131,14 @@ static int tune_views(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int pidx, bo
     if (!fine_k_only) {
       AMGC_TRY((tune_one<1, T>(h, L.P, L.Ps, nullptr, C.x, nullptr, nullptr, nullptr, L.t, &pm)));
       AMGC_TRY((tune_one<0, T>(h, L.R, L.Rs, nullptr, L.r, nullptr, nullptr, nullptr, C.b, &rm)));
-      int fz = 0;
-      AMGC_TRY(tune_fuse<T>(h, L, &fz));
-      LL.fuse[pidx] = fz ? 1 : -1;   // the fused form where it won, else the default form
-      L.fuse = resolve_form(LL, LL.fuse[pidx], pidx == 1);
     }
     L.kmap = km; L.pmap = pm; L.rmap = rm;
+    if (!fine_k_only) {   // the sweep's form, timed with the K mapping just chosen
+      int form = 0;
+      AMGC_TRY(tune_form<T>(h, L, l, &form));
+      LL.fuse[pidx] = form;
+      L.fuse = form;
+    }
     LL.kmap[pidx] = km; LL.pmap[pidx] = pm; LL.rmap[pidx] = rm;
     if (fine_k_only) break;
   }
