@@ -86,18 +86,44 @@ k_rowop(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const 
 // every fifth block of the row starting at slot s, so the six lanes of a slot read one block's
 // 6 x BC values contiguously and share the x gather; lanes 30 and 31 idle.  The five partial
 // sums of each block row are then added across slots (lanes r, r+6, ..., r+24).
-template <int BC, class T>
+// acc += sum_c v[c] x[c] over one block row (c in order); VEC (BC = 6): the six values of v and of x
+// in three two-element loads each (both 8 * sizeof(T)-aligned: checked by the launcher), half the
+// load instructions of the scalar form and the same arithmetic
+template <class T>
+struct Pair;
+template <>
+struct Pair<double> { using type = double2; };
+template <>
+struct Pair<float> { using type = float2; };
+template <int BC, bool VEC, class T>
+__device__ __forceinline__ T block_row_dot(const T* __restrict__ v, const T* __restrict__ x, T acc) {
+  if constexpr (VEC && BC == 6) {
+    using P2 = typename Pair<T>::type;
+    const P2* vp = reinterpret_cast<const P2*>(v);
+    const P2* xp = reinterpret_cast<const P2*>(x);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const P2 a = __ldg(vp + k), y = __ldg(xp + k);
+      acc = fma(a.x, y.x, acc);
+      acc = fma(a.y, y.y, acc);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < BC; ++c) acc = fma(ldg(v + c), ldg(x + c), acc);
+  }
+  return acc;
+}
+template <int BC, bool VEC, class T>
 __device__ __forceinline__ void slot_blocks6(int b0, int b1, const int* __restrict__ col, const T* __restrict__ val,
                                              const T* __restrict__ x, int s, int r, T& acc) {
   if (s >= 5) return;
   for (int b = b0 + s; b < b1; b += 5) {
     const T* xc = x + (int64_t)__ldg(col + b) * BC;
     const T* v = val + (int64_t)b * (6 * BC) + r * BC;
-#pragma unroll
-    for (int c = 0; c < BC; ++c) acc = fma(ldg(v + c), ldg(xc + c), acc);
+    acc = block_row_dot<BC, VEC, T>(v, xc, acc);
   }
 }
-template <int BC1, int BC2, int MODE, class T>
+template <int BC1, int BC2, int MODE, class T, bool VEC>
 __global__ void __launch_bounds__(kRowWarps * 32)
 k_rowop6(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const T* __restrict__ v1,
          const T* __restrict__ x1, const int* __restrict__ rp2, const int* __restrict__ c2, const T* __restrict__ v2,
@@ -108,8 +134,8 @@ k_rowop6(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const
   if (row >= nbr) return;
   const int s = lane / 6, r = lane - 6 * (lane / 6);
   T acc = T(0);
-  slot_blocks6<BC1, T>(rp1[row], rp1[row + 1], c1, v1, x1, s, r, acc);
-  if (rp2 != nullptr) slot_blocks6<BC2, T>(rp2[row], rp2[row + 1], c2, v2, x2, s, r, acc);
+  slot_blocks6<BC1, VEC, T>(rp1[row], rp1[row + 1], c1, v1, x1, s, r, acc);
+  if (rp2 != nullptr) slot_blocks6<BC2, false, T>(rp2[row], rp2[row + 1], c2, v2, x2, s, r, acc);
   const T a1 = acc + __shfl_down_sync(0xffffffffu, acc, 6);
   const T a2 = a1 + __shfl_down_sync(0xffffffffu, a1, 12);
   const T out = a2 + __shfl_down_sync(0xffffffffu, acc, 24);
@@ -121,7 +147,7 @@ k_rowop6(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const
 // coarse K, about 40 blocks per row, with W = 2).  Warp w takes slots 5w .. 5w+4 of every
 // group of 5 W consecutive blocks with the lane mapping of k_rowop6; the warps' row sums are
 // added in warp order (deterministic).
-template <int W, int BC1, int BC2, int MODE, class T>
+template <int W, int BC1, int BC2, int MODE, class T, bool VEC>
 __global__ void __launch_bounds__(W * 32)
 k_rowop6_long(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const T* __restrict__ v1,
               const T* __restrict__ x1, const int* __restrict__ rp2, const int* __restrict__ c2,
@@ -139,8 +165,7 @@ k_rowop6_long(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, 
     for (int blk = rp1[row] + 5 * wid + s; blk < rp1[row + 1]; blk += stride) {
       const T* xc = x1 + (int64_t)__ldg(c1 + blk) * BC1;
       const T* v = v1 + (int64_t)blk * (6 * BC1) + r * BC1;
-#pragma unroll
-      for (int c = 0; c < BC1; ++c) acc = fma(ldg(v + c), ldg(xc + c), acc);
+      acc = block_row_dot<BC1, VEC, T>(v, xc, acc);
     }
     if (rp2 != nullptr) {
       for (int blk = rp2[row] + 5 * wid + s; blk < rp2[row + 1]; blk += stride) {
@@ -168,25 +193,43 @@ template <int BR, int BC1, int BC2, int MODE, class T>
 static int launch_rowop(const BsrV<T>& A1, const T* x1, const BsrV<T>* A2, const T* x2, const T* b, const T* x0,
                         const T* dinv, double omega, T* y, cudaStream_t s) {
   if (A1.nbr == 0) return AMGC_OK;
+  // six-column blocks: the paired loads need both operands aligned to two elements
+  const size_t pair = 2 * sizeof(T);
+  const bool vec = BC1 == 6 && reinterpret_cast<uintptr_t>(A1.val) % pair == 0 &&
+                   reinterpret_cast<uintptr_t>(x1) % pair == 0;
   // long rows of 6-row blocks: a CTA of 8 (more than 96 blocks per row) or 2 (more than 24)
   // warps per row, so that the SMs hold enough warps
   if (BR == 6 && A1.nbr < (1 << 16) && A1.nnzb > 24 * (int64_t)A1.nbr) {
     const int* r2 = A2 ? A2->rp : nullptr;
     const int* k2 = A2 ? A2->col : nullptr;
     const T* w2 = A2 ? A2->val : nullptr;
-    if (A1.nnzb > 96 * (int64_t)A1.nbr)
-      AMGC_LAUNCH(k_rowop6_long<8, BC1, BC2, MODE, T><<<A1.nbr, 8 * 32, 0, s>>>(
-          A1.nbr, A1.rp, A1.col, A1.val, x1, r2, k2, w2, x2, b, x0, dinv, (T)omega, y));
-    else
-      AMGC_LAUNCH(k_rowop6_long<2, BC1, BC2, MODE, T><<<A1.nbr, 2 * 32, 0, s>>>(
-          A1.nbr, A1.rp, A1.col, A1.val, x1, r2, k2, w2, x2, b, x0, dinv, (T)omega, y));
+    if (A1.nnzb > 96 * (int64_t)A1.nbr) {
+      if (vec)
+        AMGC_LAUNCH(k_rowop6_long<8, BC1, BC2, MODE, T, true><<<A1.nbr, 8 * 32, 0, s>>>(
+            A1.nbr, A1.rp, A1.col, A1.val, x1, r2, k2, w2, x2, b, x0, dinv, (T)omega, y));
+      else
+        AMGC_LAUNCH(k_rowop6_long<8, BC1, BC2, MODE, T, false><<<A1.nbr, 8 * 32, 0, s>>>(
+            A1.nbr, A1.rp, A1.col, A1.val, x1, r2, k2, w2, x2, b, x0, dinv, (T)omega, y));
+    } else {
+      if (vec)
+        AMGC_LAUNCH(k_rowop6_long<2, BC1, BC2, MODE, T, true><<<A1.nbr, 2 * 32, 0, s>>>(
+            A1.nbr, A1.rp, A1.col, A1.val, x1, r2, k2, w2, x2, b, x0, dinv, (T)omega, y));
+      else
+        AMGC_LAUNCH(k_rowop6_long<2, BC1, BC2, MODE, T, false><<<A1.nbr, 2 * 32, 0, s>>>(
+            A1.nbr, A1.rp, A1.col, A1.val, x1, r2, k2, w2, x2, b, x0, dinv, (T)omega, y));
+    }
     AMGC_CUDA_TRY(cudaGetLastError());
     return AMGC_OK;
   }
   if (BR == 6 && BC1 == 6) {
-    AMGC_LAUNCH(k_rowop6<BC1, BC2, MODE, T><<<div_up(A1.nbr, kRowWarps), kRowWarps * 32, 0, s>>>(
-        A1.nbr, A1.rp, A1.col, A1.val, x1, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr, A2 ? A2->val : nullptr, x2,
-        b, x0, dinv, (T)omega, y));
+    if (vec)
+      AMGC_LAUNCH(k_rowop6<BC1, BC2, MODE, T, true><<<div_up(A1.nbr, kRowWarps), kRowWarps * 32, 0, s>>>(
+          A1.nbr, A1.rp, A1.col, A1.val, x1, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr, A2 ? A2->val : nullptr,
+          x2, b, x0, dinv, (T)omega, y));
+    else
+      AMGC_LAUNCH(k_rowop6<BC1, BC2, MODE, T, false><<<div_up(A1.nbr, kRowWarps), kRowWarps * 32, 0, s>>>(
+          A1.nbr, A1.rp, A1.col, A1.val, x1, A2 ? A2->rp : nullptr, A2 ? A2->col : nullptr, A2 ? A2->val : nullptr,
+          x2, b, x0, dinv, (T)omega, y));
     AMGC_CUDA_TRY(cudaGetLastError());
     return AMGC_OK;
   }
@@ -1877,11 +1920,11 @@ static int ir_setup(amgc_hierarchy* h, Level& L) {
   L.n_ir = n;
   return AMGC_OK;
 }
-// The smoother form a view runs: the level's setting, by default two launches.  (With the
-// multiplier-row kernels on lane groups the corrector and B1 update are short enough that the
-// split sweep does not pay by default on the large two-block workload: the FP64 step beside it
-// shares the FP64 FMA rate, and the FP32 step gains less than the fork and join cost; the
-// autotuner times the forms per level.)
+// The smoother form a view runs: the level's setting, by default two launches.  (On the large
+// two-block workload the split sweep does not pay by default once the multiplier-row kernels run on
+// lane groups: the FP64 step beside it shares the FP64 FMA rate, and the FP32 step gains less than
+// the fork and join cost; nor does the fused form on the coarse levels.  The autotuner times the
+// forms per level.)
 static int resolve_form(int f) { return f >= 0 ? f : 0; }
 
 int make_views(amgc_hierarchy* h) {
