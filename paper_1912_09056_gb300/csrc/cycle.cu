@@ -1436,34 +1436,48 @@ __global__ void __launch_bounds__(128)
 k_lm_tsweep(int nl, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
             const double* __restrict__ eu, const double* __restrict__ atinv, const double* __restrict__ el,
             const double* __restrict__ SinvT, double alpha, double* __restrict__ lam, double* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (l >= nl) return;
+  // one node per group of G lanes, as k_lm
+  constexpr int G = RowGroup<BU>::G;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int first = (int)((gt >> 5) * (32 / G));
+  if (first >= nl) return;
+  const int l = first + lane / G;
+  const bool valid = l < nl;
+  const int c = gl < 3 ? gl : 0;
+  const bool st = valid && gl < 3;
+  int b0 = 0, b1 = 0;
+  double elc = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  if (valid) {
+    b0 = rp[l];
+    b1 = rp[l + 1];
+    elc = el[3 * (int64_t)l + c];
+    const double* S = SinvT + (int64_t)l * 9 + 3 * c;
+    s0 = S[0];
+    s1 = S[1];
+    s2 = S[2];
+  }
   double acc[3] = {0.0, 0.0, 0.0};
-  for (int64_t b = rp[l] + lane; b < rp[l + 1]; b += 32) {
+  for (int64_t b = b0 + gl; b < b1; b += G) {
     const int64_t c0 = (int64_t)col[b] * BU;
     const double* v = val + b * (3 * BU);
 #pragma unroll
-    for (int c = 0; c < BU; ++c) {
-      const double xv = atinv[c0 + c] * eu[c0 + c];
-      acc[0] = fma(v[c], xv, acc[0]);
-      acc[1] = fma(v[BU + c], xv, acc[1]);
-      acc[2] = fma(v[2 * BU + c], xv, acc[2]);
+    for (int cc = 0; cc < BU; ++cc) {
+      const double xv = atinv[c0 + cc] * eu[c0 + cc];
+      acc[0] = fma(v[cc], xv, acc[0]);
+      acc[1] = fma(v[BU + cc], xv, acc[1]);
+      acc[2] = fma(v[2 * BU + cc], xv, acc[2]);
     }
   }
-  const double s0 = warp_sum(acc[0]), s1 = warp_sum(acc[1]), s2 = warp_sum(acc[2]);
-  if (lane != 0) return;
-  const double r0 = el[3 * l] - s0, r1 = el[3 * l + 1] - s1, r2 = el[3 * l + 2] - s2;
-  const double* S = SinvT + (int64_t)l * 9;
-  const double w0 = -alpha * (S[0] * r0 + S[1] * r1 + S[2] * r2);
-  const double w1 = -alpha * (S[3] * r0 + S[4] * r1 + S[5] * r2);
-  const double w2 = -alpha * (S[6] * r0 + S[7] * r1 + S[8] * r2);
-  lam[3 * l] += w0;
-  lam[3 * l + 1] += w1;
-  lam[3 * l + 2] += w2;
-  out[3 * l] = w0;
-  out[3 * l + 1] = w1;
-  out[3 * l + 2] = w2;
+  const double a0 = group_sum<G>(acc[0]), a1 = group_sum<G>(acc[1]), a2 = group_sum<G>(acc[2]);
+  const double rc = elc - (c == 0 ? a0 : (c == 1 ? a1 : a2));
+  const int g0 = lane & ~(G - 1);
+  const double r0 = __shfl_sync(0xffffffffu, rc, g0), r1 = __shfl_sync(0xffffffffu, rc, g0 + 1),
+               r2 = __shfl_sync(0xffffffffu, rc, g0 + 2);
+  if (!st) return;
+  const double w = -alpha * (s0 * r0 + s1 * r1 + s2 * r2);
+  lam[3 * (int64_t)l + c] += w;
+  out[3 * (int64_t)l + c] = w;
 }
 __global__ void k_axpy_dinv(int64_t n, const double* __restrict__ e, const double* __restrict__ dinv, double omega,
                             double* __restrict__ u) {
@@ -1495,12 +1509,11 @@ static int tsmooth(amgc_hierarchy* h, const LevelV<double>& L, int l, const doub
     AMGC_TRY((lm_op<0, double>(L, x, y + nu, x + nu, 0.0, e + nu, s, true)));
   }
   if (L.nl > 0) {
-    const int gl = div_up((int64_t)L.nl * 32, 128);
     if (L.bu == 3)
-      AMGC_LAUNCH(k_lm_tsweep<3><<<gl, 128, 0, s>>>(L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
+      AMGC_LAUNCH(k_lm_tsweep<3><<<group_grid<3>(L.nl), 128, 0, s>>>(L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
                                                     h->opts.simple_alpha, x + nu, L.dlam));
     else
-      AMGC_LAUNCH(k_lm_tsweep<6><<<gl, 128, 0, s>>>(L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
+      AMGC_LAUNCH(k_lm_tsweep<6><<<group_grid<6>(L.nl), 128, 0, s>>>(L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
                                                     h->opts.simple_alpha, x + nu, L.dlam));
   }
   const int J = h->opts.jacobi_sweeps;
