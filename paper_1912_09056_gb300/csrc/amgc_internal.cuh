@@ -129,6 +129,7 @@ struct Sell {
   int64_t slots = 0;
   DBuf<int> off, len, col;
   DBuf<double> val;
+  DBuf<int> perm;   // SELL position -> block row (rows sorted by length within windows); empty: identity
 };
 
 // FP32 mirrors of the cycle data of one level (values only; index arrays are shared).
@@ -153,6 +154,7 @@ struct SellV {
   const int* len = nullptr;
   const int* col = nullptr;
   const T* val = nullptr;
+  const int* perm = nullptr;  // SELL position -> block row, null for the identity
   unsigned* ctr = nullptr;   // slice counter of the staged FP32 kernel (fine level), else null
   int* st = nullptr;         // status word for its bounded waits
   long long polls = -1;      // poll limit of those waits (< 0: the kernel's default)

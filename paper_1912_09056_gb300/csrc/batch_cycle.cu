@@ -37,11 +37,13 @@ k_mc_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, c
           const T* __restrict__ sval, const T* __restrict__ x, int64_t ldx, const int* __restrict__ rp2,
           const int* __restrict__ c2, const T* __restrict__ v2, const T* __restrict__ x2, const T* __restrict__ b,
           const T* __restrict__ x0, const T* __restrict__ dinv, T omega, T* __restrict__ y, int64_t ldy,
-          const int* __restrict__ rinst, const int* __restrict__ live) {
+          const int* __restrict__ rinst, const int* __restrict__ live, const int* __restrict__ perm) {
   constexpr int BS = BR * BC;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nbr || (live && !live[rinst[row]])) return;
-  const int sl = row >> 5, ls = row & 31;
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;   // SELL position
+  if (pos >= nbr) return;
+  const int row = perm ? perm[pos] : pos;                  // its block row
+  if (live && !live[rinst[row]]) return;
+  const int sl = pos >> 5, ls = pos & 31;
   const int64_t o = soff[sl];
   const int L = slen[sl];
   const int* cp = scol + o * 32 + ls;
@@ -382,10 +384,10 @@ int mc_apply(const BsrV<T>& A, const SellV<T>& S, const BsrV<T>* A2, const T* x,
     const int g = div_up(A.nbr, 128);
     if (S.bc == 3)
       AMGC_LAUNCH(k_mc_sell<3, 3, MODE, T, NC><<<g, 128, 0, s>>>(A.nbr, S.off, S.len, S.col, S.val, x, ldx, r2, k2,
-                                                                w2, x2, b, x0, dinv, (T)omega, y, ldy, rinst, live));
+                                                                w2, x2, b, x0, dinv, (T)omega, y, ldy, rinst, live, S.perm));
     else if (S.bc == 6)
       AMGC_LAUNCH(k_mc_sell<3, 6, MODE, T, NC><<<g, 128, 0, s>>>(A.nbr, S.off, S.len, S.col, S.val, x, ldx, r2, k2,
-                                                                w2, x2, b, x0, dinv, (T)omega, y, ldy, rinst, live));
+                                                                w2, x2, b, x0, dinv, (T)omega, y, ldy, rinst, live, S.perm));
     else {
       set_error("multi-column apply: unsupported SELL block shape");
       return AMGC_EINVAL;

@@ -117,6 +117,7 @@ template <int BC, bool VEC, class T>
 __device__ __forceinline__ void slot_blocks6(int b0, int b1, const int* __restrict__ col, const T* __restrict__ val,
                                              const T* __restrict__ x, int s, int r, T& acc) {
   if (s >= 5) return;
+#pragma unroll 2
   for (int b = b0 + s; b < b1; b += 5) {
     const T* xc = x + (int64_t)__ldg(col + b) * BC;
     const T* v = val + (int64_t)b * (6 * BC) + r * BC;
@@ -162,6 +163,7 @@ k_rowop6_long(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, 
   T acc = T(0);
   if (s < 5) {
     const int stride = 5 * kLongWarps;
+#pragma unroll 2
     for (int blk = rp1[row] + 5 * wid + s; blk < rp1[row + 1]; blk += stride) {
       const T* xc = x1 + (int64_t)__ldg(c1 + blk) * BC1;
       const T* v = v1 + (int64_t)blk * (6 * BC1) + r * BC1;
@@ -284,16 +286,17 @@ __global__ void __launch_bounds__(kSellThreads)
 k_sell(int nbr, const int* __restrict__ soff, const int* __restrict__ slen, const int* __restrict__ scol,
        const T* __restrict__ sval, const T* __restrict__ x, const int* __restrict__ rp2, const int* __restrict__ c2,
        const T* __restrict__ v2, const T* __restrict__ x2, const T* __restrict__ b, const T* __restrict__ x0,
-       const T* __restrict__ dinv, T omega, T* __restrict__ y) {
+       const T* __restrict__ dinv, T omega, T* __restrict__ y, const int* __restrict__ perm) {
   constexpr int BS = BR * BC;
   constexpr int RPW = 32 / TPR;                                // rows per warp
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int part = lane / RPW;                                 // slot residue handled by this lane
-  const int row = (gt >> 5) * RPW + (lane % RPW);
-  const bool live = row < nbr;
-  const int r = live ? row : nbr - 1;                          // dead lanes mirror a valid row
+  const int pos = (gt >> 5) * RPW + (lane % RPW);              // SELL position
+  const bool live = pos < nbr;
+  const int r = live ? pos : nbr - 1;                          // dead lanes mirror a valid position
   const int sl = r >> 5, ls = r & 31;
+  const int row = perm ? __ldg(perm + r) : r;                  // the block row at that position
   const int64_t o = soff[sl];
   const int L = slen[sl];
   const int* cp = scol + o * 32 + ls;
@@ -339,7 +342,7 @@ static void launch_sell(const SellV<T>& S, int nbr, const int* rp2, const int* c
   const int threads = sizeof(T) == 8 ? kSellThreads / 2 : kSellThreads;
   const int g = div_up((int64_t)nbr * TPR, threads);
   AMGC_LAUNCH(k_sell<BR, BC, MODE, T, TPR><<<g, threads, 0, s>>>(nbr, S.off, S.len, S.col, S.val, x, rp2, c2, v2, x2,
-                                                                 b, x0, dinv, (T)omega, y));
+                                                                 b, x0, dinv, (T)omega, y, S.perm));
 }
 
 // ---------------------------------------------------------------- TMA-staged FP32 fine-level apply
@@ -565,7 +568,7 @@ static int mapped_apply(const BsrV<T>& A, const SellV<T>& S, int map, const BsrV
                         const T* b, const T* x0, const T* dinv, double omega, T* y, cudaStream_t s) {
   // map 3: the staged kernel for the FP32 fine-level 3x3 K (an autotuner candidate)
   if constexpr (sizeof(T) == 4 && MODE != 1 && MODE != 4) {
-    if (map == 3 && S.ctr != nullptr && S.nslice > 0 && S.br == 3 && S.bc == 3)
+    if (map == 3 && S.ctr != nullptr && S.nslice > 0 && S.br == 3 && S.bc == 3 && S.perm == nullptr)
       return launch_sell_tma<MODE>(S, A.nbr, A2, x, x2, b, x0, dinv, omega, y, s);
   }
   if (map == 3) map = -1;
@@ -1875,7 +1878,7 @@ template <class T>
 static SellV<T> sview(const Sell& S, const T* val) {
   SellV<T> v;
   v.br = S.br; v.bc = S.bc; v.nslice = S.nslice;
-  v.off = S.off.p; v.len = S.len.p; v.col = S.col.p; v.val = val;
+  v.off = S.off.p; v.len = S.len.p; v.col = S.col.p; v.val = val; v.perm = S.perm.p;
   return v;
 }
 

@@ -1586,24 +1586,67 @@ static int smoother_rest(amgc_hierarchy* h, Level& L) {
   return AMGC_OK;
 }
 
-// ======================================================================== SELL-32 copy of K
-__global__ void k_sell_len(int nbr, int nslice, const int* __restrict__ rp, int* __restrict__ len) {
+// ======================================================================== SELL-32 copies
+// Slice sl holds the block rows at SELL positions 32 sl .. 32 sl + 31, padded to the longest of
+// them.  Where row lengths vary (the prolongators, the coarse K), the rows are first sorted by
+// length within windows of kSellWindow rows (perm: position -> row, longest first, ties by row),
+// so that a slice holds rows of nearly equal length and little padding; the applies write each
+// row at its own index, and a row's sum runs over its blocks in the same order either way.
+constexpr int kSellWindow = 1024;
+__global__ void __launch_bounds__(kSellWindow)
+k_sell_sort(int nbr, const int* __restrict__ rp, int* __restrict__ perm) {
+  __shared__ unsigned key[kSellWindow];
+  const int w0 = blockIdx.x * kSellWindow;
+  const int t = threadIdx.x;
+  const int row = w0 + t;
+  // key: (2^20 - 1 - length) above the local index, so ascending keys put long rows first and
+  // equal lengths in row order; positions past the last row sort to the end
+  if (row < nbr) {
+    const int len = min(rp[row + 1] - rp[row], (1 << 20) - 1);
+    key[t] = ((unsigned)((1 << 20) - 1 - len) << 11) | (unsigned)t;
+  } else {
+    key[t] = 0xffffffffu;
+  }
+  __syncthreads();
+  // bitonic sort of the window's keys, ascending
+  for (int k = 2; k <= kSellWindow; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int q = t ^ j;
+      if (q > t) {
+        const unsigned a = key[t], b = key[q];
+        const bool up = (t & k) == 0;
+        if ((a > b) == up) {
+          key[t] = b;
+          key[q] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (row < nbr) perm[row] = w0 + (int)(key[t] & 2047u);
+}
+__global__ void k_sell_len(int nbr, int nslice, const int* __restrict__ rp, const int* __restrict__ perm,
+                           int* __restrict__ len) {
   int sl = blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= nslice) return;
   int m = 0;
-  for (int r = sl * 32; r < sl * 32 + 32 && r < nbr; ++r) m = max(m, rp[r + 1] - rp[r]);
+  for (int p = sl * 32; p < sl * 32 + 32 && p < nbr; ++p) {
+    const int r = perm ? perm[p] : p;
+    m = max(m, rp[r + 1] - rp[r]);
+  }
   len[sl] = m;
 }
 __global__ void k_sell_fill(int nbr, int nslice, int bs, const int* __restrict__ rp, const int* __restrict__ col,
                             const double* __restrict__ val, const int* __restrict__ off, const int* __restrict__ len,
-                            int* __restrict__ scol, double* __restrict__ sval) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nslice * 32) return;
-  const int lane = row & 31, sl = row >> 5;
+                            const int* __restrict__ perm, int* __restrict__ scol, double* __restrict__ sval) {
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= nslice * 32) return;
+  const int lane = pos & 31, sl = pos >> 5;
   const int64_t o = off[sl];
   const int L = len[sl];
-  const int b0 = row < nbr ? rp[row] : 0;
-  const int nb = row < nbr ? rp[row + 1] - b0 : 0;
+  const int row = pos < nbr ? (perm ? perm[pos] : pos) : -1;
+  const int b0 = row >= 0 ? rp[row] : 0;
+  const int nb = row >= 0 ? rp[row + 1] - b0 : 0;
   for (int t = 0; t < L; ++t) {
     const int64_t ci = (o + t) * 32 + lane;
     const int64_t vi = (o + t) * bs * 32 + lane;
@@ -1618,15 +1661,23 @@ __global__ void k_sell_fill(int nbr, int nslice, int bs, const int* __restrict__
   }
 }
 
+// The fine level's 3x3 K (rows of nearly equal length, and the staged FP32 kernel reads its slices
+// as rows) keeps the identity order; every other matrix is sorted by length within windows.
 int build_sell_of(amgc_hierarchy* h, const DBsr& A, Sell& S) {
   cudaStream_t s = h->stream;
   const int ns = div_up(A.nbr, 32);
   const int bs = A.br * A.bc;
   S.br = A.br;
   S.bc = A.bc;
+  const bool sorted = !(A.br == 3 && A.bc == 3) && A.nbr > 32;
+  S.perm.release();
+  if (sorted) {
+    AMGC_TRY(S.perm.alloc(A.nbr));
+    AMGC_LAUNCH(k_sell_sort<<<div_up(A.nbr, kSellWindow), kSellWindow, 0, s>>>(A.nbr, A.rowptr.p, S.perm.p));
+  }
   AMGC_TRY(S.len.alloc(ns));
   AMGC_TRY(S.off.alloc(ns + 1));
-  AMGC_LAUNCH(k_sell_len<<<div_up(ns, 128), 128, 0, s>>>(A.nbr, ns, A.rowptr.p, S.len.p));
+  AMGC_LAUNCH(k_sell_len<<<div_up(ns, 128), 128, 0, s>>>(A.nbr, ns, A.rowptr.p, S.perm.p, S.len.p));
   AMGC_CUDA_TRY(cudaMemsetAsync(S.off.p, 0, (ns + 1) * sizeof(int), s));
   AMGC_LAUNCH(k_copy_int<<<div_up(ns, 256), 256, 0, s>>>(ns, S.len.p, S.off.p));
   int slots = 0;
@@ -1635,7 +1686,7 @@ int build_sell_of(amgc_hierarchy* h, const DBsr& A, Sell& S) {
   AMGC_TRY(S.col.alloc((size_t)std::max(slots, 1) * 32));
   AMGC_TRY(S.val.alloc((size_t)std::max(slots, 1) * bs * 32));
   AMGC_LAUNCH(k_sell_fill<<<div_up((int64_t)ns * 32, 256), 256, 0, s>>>(A.nbr, ns, bs, A.rowptr.p, A.col.p, A.val.p,
-                                                                      S.off.p, S.len.p, S.col.p, S.val.p));
+                                                                      S.off.p, S.len.p, S.perm.p, S.col.p, S.val.p));
   AMGC_CUDA_TRY(cudaGetLastError());
   S.nslice = ns;
   return AMGC_OK;
