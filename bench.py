@@ -268,7 +268,7 @@ def _peaks() -> dict:
 # workload's FP64 residual launches scaled to this workload by its block count (the kernel streams
 # every block once), keyed by the hash of the kernel's source section (the SELL-32 apply of
 # cycle.cu) it was measured on: null once that source has changed.
-NCU_TRAFFIC = {"source_sha16": "c96d998d7bd34fd3", "bytes_per_block": 80.163}   # profiles/k_sell_fp64_residual_medium_48x41.md
+NCU_TRAFFIC = {"source_sha16": "bd8917331a15088a", "bytes_per_block": 80.152}   # profiles/k_sell_fp64_residual_medium_48x41.md
 
 
 def _kernel_source_sha16() -> str:

@@ -191,12 +191,98 @@ k_rowop6_long(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, 
   }
 }
 
+// The restriction from a 3-DOF level (6 x 3 blocks, about 190 per row on the finest level): one
+// block per lane, its 18 values in nine paired loads and its three x values, six running sums
+// per lane (a third of the load instructions of the lane-per-block-row mapping and all 32 lanes
+// busy); the six sums are reduced over the warp by a reduce-scatter butterfly (nine shuffles:
+// after the rounds on lane bits 4, 3 and 2 lane L holds the partial of row 4 b4 + 2 b3 + b2 of
+// its eight-lane set, rounds on bits 1 and 0 finish it), then over the CTA's warps in order.
+template <int W, int MODE, class T>
+__global__ void __launch_bounds__(W * 32)
+k_rowop63_long(int nbr, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
+               const T* __restrict__ x, const T* __restrict__ b, const T* __restrict__ x0,
+               const T* __restrict__ dinv, T omega, T* __restrict__ y) {
+  using P2 = typename Pair<T>::type;
+  __shared__ T part[W][6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row = blockIdx.x;
+  if (row >= nbr) return;
+  T a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = T(0);
+  const int e1 = rp[row + 1];
+#pragma unroll 2
+  for (int blk = rp[row] + wid * 32 + lane; blk < e1; blk += W * 32) {
+    const T* xc = x + (int64_t)__ldg(col + blk) * 3;
+    const T xa = ldg(xc), xb = ldg(xc + 1), xd = ldg(xc + 2);
+    const P2* vp = reinterpret_cast<const P2*>(val + (int64_t)blk * 18);
+    T v[18];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const P2 q = __ldg(vp + k);
+      v[2 * k] = q.x;
+      v[2 * k + 1] = q.y;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      a[r] = fma(v[3 * r], xa, a[r]);
+      a[r] = fma(v[3 * r + 1], xb, a[r]);
+      a[r] = fma(v[3 * r + 2], xd, a[r]);
+    }
+  }
+  {   // lane bit 4: keep rows 0..3 (bit clear) or 4..7 (set)
+    const bool hi = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const T send = hi ? a[k] : a[k + 4], keep = hi ? a[k + 4] : a[k];
+      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  {   // lane bit 3: of those four, keep two
+    const bool hi = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const T send = hi ? a[k] : a[k + 2], keep = hi ? a[k + 2] : a[k];
+      a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  {   // lane bit 2: keep one
+    const bool hi = lane & 4;
+    const T send = hi ? a[0] : a[1], keep = hi ? a[1] : a[0];
+    a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
+  a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+  const int r = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  if ((lane & 3) == 0 && r < 6) part[wid][r] = a[0];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    T out = T(0);
+#pragma unroll
+    for (int q = 0; q < W; ++q) out += part[q][threadIdx.x];
+    store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * 6 + threadIdx.x, out);
+  }
+}
+
 template <int BR, int BC1, int BC2, int MODE, class T>
 static int launch_rowop(const BsrV<T>& A1, const T* x1, const BsrV<T>* A2, const T* x2, const T* b, const T* x0,
                         const T* dinv, double omega, T* y, cudaStream_t s) {
   if (A1.nbr == 0) return AMGC_OK;
   // six-column blocks: the paired loads need both operands aligned to two elements
   const size_t pair = 2 * sizeof(T);
+  if (BR == 6 && BC1 == 3 && A2 == nullptr && A1.nbr < (1 << 16) && A1.nnzb > 24 * (int64_t)A1.nbr &&
+      reinterpret_cast<uintptr_t>(A1.val) % pair == 0) {
+    // FP32 (memory-bound): eight warps per row keep more loads in flight; FP64 (bound by the FMA
+    // rate): two, so that the row's blocks fill the lanes over several passes
+    if (sizeof(T) == 4 && A1.nnzb > 96 * (int64_t)A1.nbr)
+      AMGC_LAUNCH(k_rowop63_long<8, MODE, T><<<A1.nbr, 8 * 32, 0, s>>>(A1.nbr, A1.rp, A1.col, A1.val, x1, b, x0, dinv,
+                                                                      (T)omega, y));
+    else
+      AMGC_LAUNCH(k_rowop63_long<2, MODE, T><<<A1.nbr, 2 * 32, 0, s>>>(A1.nbr, A1.rp, A1.col, A1.val, x1, b, x0, dinv,
+                                                                      (T)omega, y));
+    AMGC_CUDA_TRY(cudaGetLastError());
+    return AMGC_OK;
+  }
   const bool vec = BC1 == 6 && reinterpret_cast<uintptr_t>(A1.val) % pair == 0 &&
                    reinterpret_cast<uintptr_t>(x1) % pair == 0;
   // long rows of 6-row blocks: a CTA of 8 (more than 96 blocks per row) or 2 (more than 24)
