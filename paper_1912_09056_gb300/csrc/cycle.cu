@@ -756,12 +756,11 @@ __device__ __forceinline__ void lm_node(int l, bool valid, int gl, const int* __
   out[3 * (int64_t)l + c] = (T)d;
 }
 
-template <int BU, int MODE, class T>
+template <int BU, int MODE, class T, int G>
 __global__ void __launch_bounds__(128)
 k_lm(int nl, const int* __restrict__ rp, const int* __restrict__ col, const T* __restrict__ val,
      const T* __restrict__ u, const T* __restrict__ Z, const T* __restrict__ g, T* __restrict__ lam,
      const double* __restrict__ Sinv, double alpha, T* __restrict__ out) {
-  constexpr int G = RowGroup<BU>::G;
   const int lane = threadIdx.x & 31;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int first = (int)((gt >> 5) * (32 / G));   // the warp's first node
@@ -774,6 +773,41 @@ template <int BU>
 static int group_grid(int64_t rows) {
   return (int)div_up(rows * RowGroup<BU>::G, 128);
 }
+// Lanes per row of the corrector, multiplier-residual and B1-update launches.  Few rows (under
+// kGroupRowsFP64 in FP64, any count in FP32) leave these launches bound by the chain of dependent
+// loads of a row: the smallest of 8, 16, 32 lanes that covers the rows' mean length, so that a
+// row takes one pass of its group.  Many FP64 rows make the FP64 pipe the limit, where every
+// group-sum round costs a warp instruction whatever the group's width: 4 lanes per row (8 for
+// six-DOF B1 rows, which need six), a few passes per row and two rounds per sum.
+constexpr int64_t kGroupRowsFP64 = 4096;
+static int pick_group(int64_t nnzb, int64_t rows, bool fp64, int bu) {
+  if (fp64 && rows >= kGroupRowsFP64) return bu <= 4 ? 4 : 8;
+  const double mean = rows > 0 ? (double)nnzb / (double)rows : 0.0;
+  return mean <= 8.0 ? 8 : (mean <= 16.0 ? 16 : 32);
+}
+// the same with 4 lanes allowed (three-DOF rows)
+#define AMGC_GROUP_DISPATCH3(gsel, LAUNCH) \
+  do {                                     \
+    if ((gsel) == 4) {                     \
+      constexpr int G_ = 4;                \
+      LAUNCH;                              \
+    } else {                               \
+      AMGC_GROUP_DISPATCH(gsel, LAUNCH);   \
+    }                                      \
+  } while (0)
+#define AMGC_GROUP_DISPATCH(gsel, LAUNCH) \
+  do {                                    \
+    if ((gsel) == 8) {                    \
+      constexpr int G_ = 8;               \
+      LAUNCH;                             \
+    } else if ((gsel) == 16) {            \
+      constexpr int G_ = 16;              \
+      LAUNCH;                             \
+    } else {                              \
+      constexpr int G_ = 32;              \
+      LAUNCH;                             \
+    }                                     \
+  } while (0)
 
 template <int MODE, class T>
 static int lm_op(const LevelV<T>& L, const T* u, const T* g, T* lam, double alpha, T* out, cudaStream_t s,
@@ -782,12 +816,14 @@ static int lm_op(const LevelV<T>& L, const T* u, const T* g, T* lam, double alph
   const int th = 128;
   const BsrV<T>& B = transposed ? L.B1T : L.B2;   // multiplier rows of A: B2; of A^T: B1^T
   const T* Z = transposed ? L.ZT : L.Z;
+  const int gs = pick_group(B.nnzb, L.nl, sizeof(T) == 8, L.bu);
+  const int grid = (int)div_up((int64_t)L.nl * gs, th);
   if (L.bu == 3)
-    AMGC_LAUNCH(k_lm<3, MODE, T><<<group_grid<3>(L.nl), th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g, lam, L.Sinv,
-                                                                    alpha, out));
+    AMGC_GROUP_DISPATCH3(gs, AMGC_LAUNCH((k_lm<3, MODE, T, G_><<<grid, th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g,
+                                                                                 lam, L.Sinv, alpha, out))));
   else
-    AMGC_LAUNCH(k_lm<6, MODE, T><<<group_grid<6>(L.nl), th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g, lam, L.Sinv,
-                                                                    alpha, out));
+    AMGC_GROUP_DISPATCH(gs, AMGC_LAUNCH((k_lm<6, MODE, T, G_><<<grid, th, 0, s>>>(L.nl, B.rp, B.col, B.val, u, Z, g,
+                                                                                 lam, L.Sinv, alpha, out))));
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
@@ -856,11 +892,11 @@ __device__ __forceinline__ void b1_row(int i, bool valid, int gl, const int* __r
   }
 }
 // the same over the rows of B1 with entries, in place, 32 / G rows per warp
-template <int BU, class T>
+template <int BU, class T, int G>
 __global__ void __launch_bounds__(128)
 k_b1_update(int nrows, const int* __restrict__ rows, const int* __restrict__ rp, const int* __restrict__ col,
             const T* __restrict__ val, const T* __restrict__ dlam, const T* __restrict__ atinv, T alpha, T* u) {
-  constexpr int G = RowGroup<BU>::G;
+  static_assert(G >= BU, "a B1 row's update needs BU lanes of its group");
   const int lane = threadIdx.x & 31;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int first = (int)((gt >> 5) * (32 / G));
@@ -873,12 +909,14 @@ template <class T>
 static int b1_update(int bu, int nrows, const int* rows, const BsrV<T>& B, const T* dlam, const T* atinv, T alpha, T* u,
                      cudaStream_t s) {
   if (nrows == 0) return AMGC_OK;
+  const int gs = pick_group(B.nnzb, nrows, sizeof(T) == 8, bu);   // the rows listed hold all of B's blocks
+  const int grid = (int)div_up((int64_t)nrows * gs, 128);
   if (bu == 3)
-    AMGC_LAUNCH(k_b1_update<3, T><<<group_grid<3>(nrows), 128, 0, s>>>(nrows, rows, B.rp, B.col, B.val, dlam, atinv,
-                                                                       alpha, u));
+    AMGC_GROUP_DISPATCH3(gs, AMGC_LAUNCH((k_b1_update<3, T, G_><<<grid, 128, 0, s>>>(nrows, rows, B.rp, B.col, B.val,
+                                                                                   dlam, atinv, alpha, u))));
   else
-    AMGC_LAUNCH(k_b1_update<6, T><<<group_grid<6>(nrows), 128, 0, s>>>(nrows, rows, B.rp, B.col, B.val, dlam, atinv,
-                                                                       alpha, u));
+    AMGC_GROUP_DISPATCH(gs, AMGC_LAUNCH((k_b1_update<6, T, G_><<<grid, 128, 0, s>>>(nrows, rows, B.rp, B.col, B.val,
+                                                                                   dlam, atinv, alpha, u))));
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
@@ -952,38 +990,47 @@ k_ir_b1(int n, const int* __restrict__ rows, const int* __restrict__ rp, const i
 // only where a level's multiplier rows are few (the autotuner decides per level).
 constexpr int kFuseThreads = 1024;
 constexpr int kFuseMaxNodes = 2048;   // largest level the autotuner tries the single-CTA form on
-template <int BU, class T>
+template <int BU, class T, int GL, int GB>
 __global__ void __launch_bounds__(kFuseThreads)
 k_corrector_b1_fused(int nl, const int* __restrict__ rp2, const int* __restrict__ c2, const T* __restrict__ v2,
                      const T* u_in, const T* __restrict__ Z, const T* __restrict__ g,
                      T* __restrict__ lam, const double* __restrict__ Sinv, double alpha, T* __restrict__ dlam,
                      int nrows, const int* __restrict__ rows, const int* __restrict__ rp1, const int* __restrict__ c1,
                      const T* __restrict__ v1, const T* __restrict__ atinv, T* u) {
-  // u_in and u are the same iterate: read by the corrector, updated after the barrier
-  constexpr int G = RowGroup<BU>::G, RW = 32 / G;   // rows per warp
+  // u_in and u are the same iterate: read by the corrector, updated after the barrier; GL and GB
+  // lanes per row, as the two launches choose them (the same arithmetic, the same bits)
+  constexpr int RL = 32 / GL, RB = 32 / GB;   // rows per warp
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int gl = lane & (G - 1), gi = lane / G;
-  for (int f = wid * RW; f < nl; f += nw * RW) {   // warp-uniform bounds: the groups shuffle
-    const int l = f + gi;
-    lm_node<G, BU, 1, T>(l, l < nl, gl, rp2, c2, v2, u_in, Z, g, lam, Sinv, alpha, dlam);
+  for (int f = wid * RL; f < nl; f += nw * RL) {   // warp-uniform bounds: the groups shuffle
+    const int l = f + lane / GL;
+    lm_node<GL, BU, 1, T>(l, l < nl, lane & (GL - 1), rp2, c2, v2, u_in, Z, g, lam, Sinv, alpha, dlam);
   }
   __syncthreads();
-  for (int f = wid * RW; f < nrows; f += nw * RW) {
-    const int t = f + gi;
+  for (int f = wid * RB; f < nrows; f += nw * RB) {
+    const int t = f + lane / GB;
     const bool valid = t < nrows;
-    b1_row<G, BU, T>(valid ? rows[t] : 0, valid, gl, rp1, c1, v1, dlam, atinv, (T)alpha, u, u);
+    b1_row<GB, BU, T>(valid ? rows[t] : 0, valid, lane & (GB - 1), rp1, c1, v1, dlam, atinv, (T)alpha, u, u);
   }
+}
+template <int BU, class T, int GL>
+static void launch_fused(const LevelV<T>& L, int gb, T* u, const T* g, T* lam, double alpha, cudaStream_t s) {
+#define AMGC_FUSED_LAUNCH                                                                            \
+  AMGC_LAUNCH((k_corrector_b1_fused<BU, T, GL, G_><<<1, kFuseThreads, 0, s>>>(                       \
+      L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam, L.Sinv, alpha, L.dlam, L.n_b1_rows, L.b1_rows, \
+      L.B1.rp, L.B1.col, L.B1.val, L.atinv, u)))
+  if constexpr (BU == 3) AMGC_GROUP_DISPATCH3(gb, AMGC_FUSED_LAUNCH);
+  else AMGC_GROUP_DISPATCH(gb, AMGC_FUSED_LAUNCH);
+#undef AMGC_FUSED_LAUNCH
 }
 template <class T>
 static int corrector_b1_fused(const LevelV<T>& L, T* u, const T* g, T* lam, double alpha, cudaStream_t s) {
+  // the lane groups of the two launches (lm_op, b1_update), so that the bits are theirs
+  const bool fp64 = sizeof(T) == 8;
+  const int gl = pick_group(L.B2.nnzb, L.nl, fp64, L.bu), gb = pick_group(L.B1.nnzb, L.n_b1_rows, fp64, L.bu);
   if (L.bu == 3)
-    AMGC_LAUNCH(k_corrector_b1_fused<3, T><<<1, kFuseThreads, 0, s>>>(L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam,
-                                                                     L.Sinv, alpha, L.dlam, L.n_b1_rows, L.b1_rows,
-                                                                     L.B1.rp, L.B1.col, L.B1.val, L.atinv, u));
+    AMGC_GROUP_DISPATCH3(gl, (launch_fused<3, T, G_>(L, gb, u, g, lam, alpha, s)));
   else
-    AMGC_LAUNCH(k_corrector_b1_fused<6, T><<<1, kFuseThreads, 0, s>>>(L.nl, L.B2.rp, L.B2.col, L.B2.val, u, L.Z, g, lam,
-                                                                     L.Sinv, alpha, L.dlam, L.n_b1_rows, L.b1_rows,
-                                                                     L.B1.rp, L.B1.col, L.B1.val, L.atinv, u));
+    AMGC_GROUP_DISPATCH(gl, (launch_fused<6, T, G_>(L, gb, u, g, lam, alpha, s)));
   AMGC_CUDA_TRY(cudaGetLastError());
   return AMGC_OK;
 }
@@ -1520,13 +1567,12 @@ static int vcycle_t(amgc_hierarchy* h, std::vector<LevelV<T>>& V, int l, const T
 // respect to Q.
 
 // w_l = -alpha S^-T_l (e_l - sum_i B1T[l,i] (atinv_i e_u,i)); lam_l += w_l; out_l = w_l
-template <int BU>
+template <int BU, int G>
 __global__ void __launch_bounds__(128)
 k_lm_tsweep(int nl, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
             const double* __restrict__ eu, const double* __restrict__ atinv, const double* __restrict__ el,
             const double* __restrict__ SinvT, double alpha, double* __restrict__ lam, double* __restrict__ out) {
   // one node per group of G lanes, as k_lm
-  constexpr int G = RowGroup<BU>::G;
   const int lane = threadIdx.x & 31, gl = lane & (G - 1);
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int first = (int)((gt >> 5) * (32 / G));
@@ -1598,12 +1644,16 @@ static int tsmooth(amgc_hierarchy* h, const LevelV<double>& L, int l, const doub
     AMGC_TRY((lm_op<0, double>(L, x, y + nu, x + nu, 0.0, e + nu, s, true)));
   }
   if (L.nl > 0) {
+    const int gs = pick_group(L.B1T.nnzb, L.nl, true, L.bu);
+    const int grid = (int)div_up((int64_t)L.nl * gs, 128);
     if (L.bu == 3)
-      AMGC_LAUNCH(k_lm_tsweep<3><<<group_grid<3>(L.nl), 128, 0, s>>>(L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
-                                                    h->opts.simple_alpha, x + nu, L.dlam));
+      AMGC_GROUP_DISPATCH3(gs, AMGC_LAUNCH((k_lm_tsweep<3, G_><<<grid, 128, 0, s>>>(
+                                  L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
+                                  h->opts.simple_alpha, x + nu, L.dlam))));
     else
-      AMGC_LAUNCH(k_lm_tsweep<6><<<group_grid<6>(L.nl), 128, 0, s>>>(L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
-                                                    h->opts.simple_alpha, x + nu, L.dlam));
+      AMGC_GROUP_DISPATCH(gs, AMGC_LAUNCH((k_lm_tsweep<6, G_><<<grid, 128, 0, s>>>(
+                                  L.nl, L.B1T.rp, L.B1T.col, L.B1T.val, e, L.atinv, e + nu, L.SinvT,
+                                  h->opts.simple_alpha, x + nu, L.dlam))));
   }
   const int J = h->opts.jacobi_sweeps;
   if (J > 1) {
