@@ -143,9 +143,10 @@ k_rowop6(int nbr, const int* __restrict__ rp1, const int* __restrict__ c1, const
   if (lane < 6) store_row<MODE, T>(y, b, x0, dinv, omega, (int64_t)row * 6 + lane, out);
 }
 
-// CTA of W warps per block row for long rows of 6-row blocks (the restrictions, about 180
-// blocks per row from the finest level and several hundred to the coarsest, with W = 8; the
-// coarse K, about 40 blocks per row, with W = 2).  Warp w takes slots 5w .. 5w+4 of every
+// CTA of W warps per block row for long rows of 6-row blocks (the restrictions between coarse
+// levels, several hundred blocks per row, with W = 8; the coarse K, about 40 blocks per row, with
+// W = 2; the restriction from a 3-DOF level has its own kernel, k_rowop63_long, unless its values
+// are not aligned for paired loads).  Warp w takes slots 5w .. 5w+4 of every
 // group of 5 W consecutive blocks with the lane mapping of k_rowop6; the warps' row sums are
 // added in warp order (deterministic).
 template <int W, int BC1, int BC2, int MODE, class T, bool VEC>
